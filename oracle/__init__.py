@@ -1,0 +1,274 @@
+"""FP64 CPU oracle for the DOE scalar-diffraction path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  The product library never does, and this package imports nothing
+from it: the two share no code.  The arithmetic lives in ``doe_oracle.c`` (plain C, FP64,
+its own radix-2 FFT); this module only compiles it and marshals numpy arrays.
+
+Every function follows Wei et al., "Large-Area Fabrication-Aware Computational Diffractive
+Optics" (TOG 2025), Sec. 3.1:
+  * Eq. 1  phase  Phi = 2 pi (n - 1) h / lambda
+  * Eq. 2  field  E_doe = E_in exp(+i Phi)
+  * Eq. 3  angular-spectrum propagation with the band-limited transfer function H
+  * I = |E_dest|^2 (PSF), and the gradient of Eq. 4's objective with an L2 penalty.
+Parity is pinned in ``tests/test_oracle_pins.py`` against closed forms, invariants, brute
+force and a Rayleigh-Sommerfeld direct sum; no pin compares the oracle with itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "doe_oracle.c"
+_LIB_PATH = _HERE / "liboracle.so"
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile doe_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".so.tmp{os.getpid()}")
+        subprocess.run(
+            ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(tmp), str(_SRC), "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(str(build()))
+    P = ctypes.c_void_p
+    L = ctypes.c_long
+    D = ctypes.c_double
+    Ii = ctypes.c_int
+    sig = {
+        "orc_num_threads": ([], Ii),
+        "orc_fft1d": ([P, L, Ii], None),
+        "orc_fft2d": ([P, L, L, Ii], Ii),
+        "orc_dft1d": ([P, P, L, Ii], None),
+        "orc_kmax": ([D, D, L, D, Ii], L),
+        "orc_mev": ([D, D, L], ctypes.c_int64),
+        "orc_transfer": ([P, L, D, D, D, Ii], None),
+        "orc_band_mask": ([P, L, D, D, D, Ii], None),
+        "orc_propagate": ([L, L, D, D, D, D, Ii, P, P, P], Ii),
+        "orc_psf": ([L, L, D, D, D, D, Ii, P, P, P], Ii),
+        "orc_psf_rows": ([L, L, D, D, D, D, Ii, P, P, L, P, P], Ii),
+        "orc_grad": ([L, L, D, D, L, P, P, Ii, P, P, P, Ii, P, P], Ii),
+        "orc_loss_l2": ([L, L, D, D, L, P, P, Ii, P, P, P, P], Ii),
+        "orc_fd_exact": ([L, L, D, D, L, P, P, Ii, P, P, P, L, P, P, D, P], Ii),
+        "orc_render": ([L, L, L, P, L, L, P, P], Ii),
+        "orc_wiener": ([L, L, L, P, L, L, P, D, P], Ii),
+        "orc_rs_direct": ([L, L, D, D, D, P, P], Ii),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _c128(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# ---------------------------------------------------------------- FFT
+def fft(x, inverse: bool = False) -> np.ndarray:
+    """Unnormalised 1-D DFT (sign -1 forward, +1 inverse) with the oracle's radix-2 FFT."""
+    a = np.array(x, dtype=np.complex128, copy=True)
+    _load().orc_fft1d(_ptr(a), a.shape[0], +1 if inverse else -1)
+    return a
+
+
+def fft2(x, inverse: bool = False) -> np.ndarray:
+    a = np.array(x, dtype=np.complex128, copy=True)
+    _check(_load().orc_fft2d(_ptr(a), a.shape[0], a.shape[1], +1 if inverse else -1), "fft2")
+    return a
+
+
+def dft(x, inverse: bool = False) -> np.ndarray:
+    """Plain O(n^2) DFT (brute force)."""
+    a = _c128(x)
+    out = np.empty_like(a)
+    _load().orc_dft1d(_ptr(a), _ptr(out), a.shape[0], +1 if inverse else -1)
+    return out
+
+
+# ---------------------------------------------------------------- band limit / H
+def kmax(lam: float, dx: float, P: int, z: float, bandlimit: bool = True) -> int:
+    return int(_load().orc_kmax(lam, dx, P, z, int(bandlimit)))
+
+
+def m_ev(lam: float, dx: float, P: int) -> int:
+    return int(_load().orc_mev(lam, dx, P))
+
+
+def transfer(P: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
+    H = np.empty((P, P), np.complex128)
+    _load().orc_transfer(_ptr(H), P, dx, z, lam, int(bandlimit))
+    return H
+
+
+def band_mask(P: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
+    m = np.empty((P, P), np.uint8)
+    _load().orc_band_mask(_ptr(m), P, dx, z, lam, int(bandlimit))
+    return m
+
+
+# ---------------------------------------------------------------- forward path
+def propagate(h, dx, z, lam, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """E_dest on the P x P grid for one wavelength (Eq. 1-3)."""
+    h = _f32(h)
+    N = h.shape[0]
+    P = pad * N
+    out = np.empty((P, P), np.complex128)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_propagate(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), _ptr(out)),
+        "propagate",
+    )
+    return out
+
+
+def psf(h, dx, z, lams, n_index=None, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """FP64 PSFs [L][P][P] = |E_dest|^2 per wavelength."""
+    h = _f32(h)
+    lams = np.atleast_1d(np.asarray(lams, np.float64))
+    nidx = np.full(lams.shape, 1.46) if n_index is None else np.broadcast_to(np.asarray(n_index, np.float64), lams.shape)
+    N = h.shape[0]
+    P = pad * N
+    out = np.empty((lams.size, P, P), np.float64)
+    e_in = _c128(e_in)
+    for j, lam in enumerate(lams):
+        _check(
+            _load().orc_psf(N, pad, dx, z, float(lam), float(nidx[j]), int(bandlimit), _ptr(h), _ptr(e_in), _ptr(out[j])),
+            "psf",
+        )
+    return out
+
+
+def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """Exact FP64 PSF rows ``rows`` of one wavelength without holding the P x P field."""
+    h = _f32(h)
+    N = h.shape[0]
+    P = pad * N
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.size, P), np.float64)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_psf_rows(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows), _ptr(out)),
+        "psf_rows",
+    )
+    return out
+
+
+def grad(h, dx, z, lams, t_or_g, n_index=None, pad=2, e_in=None, mode="l2", bandlimit=True):
+    """(dL/dh [N][N] FP64, loss) for L = sum_j sum (I_j - T_j)^2 (mode 'l2') or the VJP
+    with dL/dI = t_or_g (mode 'vjp'; loss is then 0)."""
+    h = _f32(h)
+    lams = np.atleast_1d(np.asarray(lams, np.float64))
+    nidx = np.full(lams.shape, 1.46) if n_index is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lams.shape))
+    N = h.shape[0]
+    P = pad * N
+    t = _f32(t_or_g).reshape(lams.size, P, P)
+    g = np.empty((N, N), np.float64)
+    loss = ctypes.c_double(0.0)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_grad(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h), _ptr(e_in),
+                         _ptr(t), 0 if mode == "l2" else 1, _ptr(g), ctypes.byref(loss)),
+        "grad",
+    )
+    return g, float(loss.value)
+
+
+def loss_l2(h64, dx, z, lams, target, n_index=None, pad=2, e_in=None, bandlimit=True) -> float:
+    h64 = np.ascontiguousarray(h64, np.float64)
+    lams = np.atleast_1d(np.asarray(lams, np.float64))
+    nidx = np.full(lams.shape, 1.46) if n_index is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lams.shape))
+    N = h64.shape[0]
+    P = pad * N
+    t = _f32(target).reshape(lams.size, P, P)
+    out = ctypes.c_double(0.0)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_loss_l2(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h64), _ptr(e_in), _ptr(t), ctypes.byref(out)),
+        "loss",
+    )
+    return float(out.value)
+
+
+def fd_exact(h, dx, z, lams, target, pix_y, pix_x, eps, n_index=None, pad=2, e_in=None, bandlimit=True):
+    """Central finite differences of the L2 loss at the given DOE pixels, evaluated by exact
+    FP64 differences (no cancellation)."""
+    h = _f32(h)
+    lams = np.atleast_1d(np.asarray(lams, np.float64))
+    nidx = np.full(lams.shape, 1.46) if n_index is None else np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lams.shape))
+    N = h.shape[0]
+    P = pad * N
+    t = _f32(target).reshape(lams.size, P, P)
+    py = np.ascontiguousarray(pix_y, np.int64)
+    px = np.ascontiguousarray(pix_x, np.int64)
+    out = np.empty(py.size, np.float64)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_fd_exact(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h), _ptr(e_in),
+                             _ptr(t), py.size, _ptr(py), _ptr(px), eps, _ptr(out)),
+        "fd_exact",
+    )
+    return out
+
+
+# ---------------------------------------------------------------- render / wiener / RS
+def render(psf_arr, img) -> np.ndarray:
+    psf_arr = _f32(psf_arr)
+    img = _f32(img)
+    C, H, W = img.shape
+    Py, Px = psf_arr.shape[-2:]
+    out = np.empty((C, H, W), np.float64)
+    _check(_load().orc_render(C, H, W, _ptr(psf_arr), Py, Px, _ptr(img), _ptr(out)), "render")
+    return out
+
+
+def wiener(psf_arr, y, gamma) -> np.ndarray:
+    psf_arr = _f32(psf_arr)
+    y = _f32(y)
+    C, H, W = y.shape
+    Py, Px = psf_arr.shape[-2:]
+    out = np.empty((C, H, W), np.float64)
+    _check(_load().orc_wiener(C, H, W, _ptr(psf_arr), Py, Px, _ptr(y), gamma, _ptr(out)), "wiener")
+    return out
+
+
+def rs_direct(e_doe, P, dx, z, lam) -> np.ndarray:
+    e_doe = _c128(e_doe)
+    N = e_doe.shape[0]
+    out = np.empty((P, P), np.complex128)
+    _check(_load().orc_rs_direct(N, P, dx, z, lam, _ptr(e_doe), _ptr(out)), "rs_direct")
+    return out

@@ -1,0 +1,156 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no step of the diffraction method (no phase, no transform, no
+propagation): it only draws and shapes random inputs.  The tests feed the very same
+arrays to the CUDA library and to the FP64 oracle; the benchmark uses them as its
+synthetic workload.  Nothing here depends on the CUDA library or on the oracle.
+
+Recipes (seeds: heights 1000 + c, images and targets 2000 + c, request stream 3000):
+  heights  raw ~ U[0, 1) float32 (PCG64, numpy default_rng(seed)); separable Gaussian
+           smoothing, sigma = 2 px, radius 8 (weights normalised), periodic boundary,
+           evaluated in FP64; rounded to float32; affine rescale of that float32 field so
+           that its minimum is 0 and its maximum is hmax = 1.2 um exactly; float32 metres.
+           (Sec. 3.2's contrast-curve footnote ties ~1.2 um of resist to a 2 pi phase at
+           550 nm, which is why the heights span [0, 1.2] um.)
+  image    C x H x W float32: iid U[0, 1), then 64 filled disks painted over it, each with
+           radius U[8, 128] px, a uniform random centre, and one U[0, 1) value per channel.
+  target   8 x 8 lattice of Gaussian spots per wavelength (the beam-splitter task of
+           Sec. 5.2): pitch P/32, sigma 8 px, each centre jittered by U[-P/256, P/256] in
+           both axes, lattice centred at (P/2, P/2), scaled so that each wavelength's
+           target sums to N^2 (the energy of a unit-amplitude N x N aperture).
+  requests Poisson arrivals at a given rate; side N uniform in {1024, ..., 16384};
+           1..31 wavelengths uniform in [400, 700] nm; z uniform in [10, 100] mm;
+           pitch 1 um; per-request heights seed 100000 + request id.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HMAX = 1.2e-6
+
+
+def _gauss_weights(sigma: float, radius: int) -> np.ndarray:
+    t = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-0.5 * (t / sigma) ** 2)
+    return w / w.sum()
+
+
+def _smooth_rows_periodic(block: np.ndarray, w: np.ndarray) -> np.ndarray:
+    from scipy.ndimage import correlate1d
+
+    return correlate1d(block, w, axis=1, mode="wrap")
+
+
+def heights(N: int, seed: int, hmax: float = HMAX, sigma: float = 2.0, radius: int = 8) -> np.ndarray:
+    """Smoothed random DOE height map, float32 metres, [N][N]."""
+    rng = np.random.default_rng(seed)
+    raw = rng.random((N, N), dtype=np.float32)
+    w = _gauss_weights(sigma, radius)
+    out = np.empty((N, N), np.float32)
+    B = min(N, 256)
+    for r0 in range(0, N, B):
+        idx = np.arange(r0 - radius, r0 + B + radius) % N
+        blk = _smooth_rows_periodic(raw[idx].astype(np.float64), w)
+        from scipy.ndimage import correlate1d
+
+        acc = correlate1d(blk, w, axis=0, mode="constant")[radius:radius + B]
+        out[r0:r0 + B] = acc.astype(np.float32)
+    mn = float(out.min())
+    mx = float(out.max())
+    scale = hmax / (mx - mn)
+    for r0 in range(0, N, B):
+        out[r0:r0 + B] = ((out[r0:r0 + B].astype(np.float64) - mn) * scale).astype(np.float32)
+    return out
+
+
+def image(C: int, H: int, W: int, seed: int, n_disks: int = 64) -> np.ndarray:
+    """C x H x W float32 test scene: iid uniform noise with filled disks painted on top."""
+    rng = np.random.default_rng(seed)
+    img = rng.random((C, H, W), dtype=np.float32)
+    yy = np.arange(H)[:, None]
+    xx = np.arange(W)[None, :]
+    for _ in range(n_disks):
+        r = rng.uniform(8, 128)
+        cy = rng.uniform(0, H)
+        cx = rng.uniform(0, W)
+        vals = rng.random(C).astype(np.float32)
+        y0, y1 = max(0, int(cy - r) - 1), min(H, int(cy + r) + 2)
+        x0, x1 = max(0, int(cx - r) - 1), min(W, int(cx + r) + 2)
+        m = (yy[y0:y1] - cy) ** 2 + (xx[:, x0:x1] - cx) ** 2 <= r * r
+        for c in range(C):
+            img[c, y0:y1, x0:x1][m] = vals[c]
+    return img
+
+
+def spot_target(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: float = 8.0) -> np.ndarray:
+    """[L][P][P] float32 Gaussian spot-array targets, each summing to N^2."""
+    rng = np.random.default_rng(seed)
+    T = np.zeros((n_lambda, P, P), np.float32)
+    pitch = P / 32.0
+    jit = P / 256.0
+    rad = int(np.ceil(5 * sigma))
+    offs = (np.arange(grid) - (grid - 1) / 2.0) * pitch + P / 2.0
+    for j in range(n_lambda):
+        spots = []
+        for cy0 in offs:
+            for cx0 in offs:
+                cy = cy0 + rng.uniform(-jit, jit)
+                cx = cx0 + rng.uniform(-jit, jit)
+                spots.append((cy, cx))
+        total = 0.0
+        tiles = []
+        for cy, cx in spots:
+            y0, y1 = max(0, int(cy) - rad), min(P, int(cy) + rad + 1)
+            x0, x1 = max(0, int(cx) - rad), min(P, int(cx) + rad + 1)
+            ys = np.arange(y0, y1)[:, None]
+            xs = np.arange(x0, x1)[None, :]
+            g = np.exp(-((ys - cy) ** 2 + (xs - cx) ** 2) / (2 * sigma * sigma))
+            tiles.append((y0, y1, x0, x1, g))
+            total += g.sum()
+        scale = float(N) * float(N) / total
+        for y0, y1, x0, x1, g in tiles:
+            T[j, y0:y1, x0:x1] += (g * scale).astype(np.float32)
+    return T
+
+
+def gaussian_beam(N: int, dx: float, w0: float) -> np.ndarray:
+    """Unit-peak Gaussian amplitude exp(-r^2 / w0^2) sampled on the N x N DOE grid, with
+    the beam axis at DOE sample (N/2, N/2) (the optical axis of a 2x padded grid)."""
+    c = (np.arange(N) - N // 2) * dx
+    r2 = c[:, None] ** 2 + c[None, :] ** 2
+    return np.exp(-r2 / (w0 * w0)).astype(np.complex128)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    N: int
+    lambdas: np.ndarray
+    z: float
+    dx: float = 1e-6
+    seed: int = 0
+    n_index: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def P(self) -> int:
+        return 2 * self.N
+
+
+def request_stream(n: int, rate_hz: float, seed: int = 3000,
+                   sides=(1024, 2048, 4096, 8192, 16384), max_lambda: int = 31) -> list[Request]:
+    """Seeded Poisson request trace for the serving workload."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        N = int(rng.choice(sides))
+        L = int(rng.integers(1, max_lambda + 1))
+        lams = rng.uniform(400e-9, 700e-9, size=L)
+        z = float(rng.uniform(10e-3, 100e-3))
+        out.append(Request(rid=rid, arrival_s=t, N=N, lambdas=lams, z=z, dx=1e-6,
+                           seed=100000 + rid, n_index=np.full(L, 1.46)))
+    return out

@@ -1,0 +1,278 @@
+"""Pins for the FP64 oracle against things other than itself: brute force, closed forms,
+invariants, an independent physical model, and the paper's printed grid sizes."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_22313_b300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(7)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+# ------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft_matches_brute_force_dft(n, inverse):
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    # brute force written here: sum_j x_j exp(-+2 pi i j k / n)
+    s = 1.0 if inverse else -1.0
+    jk = np.outer(np.arange(n), np.arange(n))
+    ref = (x[None, :] * np.exp(s * 2j * np.pi * jk / n)).sum(axis=1)
+    got = oracle.fft(x, inverse=inverse)
+    assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    assert np.abs(oracle.dft(x, inverse=inverse) - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n", [128, 1024, 4096])
+def test_fft_matches_numpy(n):
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    assert rel_l2(oracle.fft(x), np.fft.fft(x)) < 1e-12
+    assert rel_l2(oracle.fft(x, inverse=True), np.fft.ifft(x) * n) < 1e-12
+
+
+def test_fft2_non_square_brute_force():
+    ny, nx = 8, 32
+    a = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    y = np.arange(ny)
+    x = np.arange(nx)
+    Wy = np.exp(-2j * np.pi * np.outer(y, y) / ny)
+    Wx = np.exp(-2j * np.pi * np.outer(x, x) / nx)
+    ref = np.zeros_like(a)
+    for l in range(ny):
+        for k in range(nx):
+            ref[l, k] = (a * Wy[l][:, None] * Wx[k][None, :]).sum()
+    assert rel_l2(oracle.fft2(a), ref) < 1e-13
+
+
+def test_fft_roundtrip_identity():
+    n = 2048
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    back = oracle.fft(oracle.fft(x), inverse=True) / n
+    assert rel_l2(back, x) < 1e-14
+
+
+# ------------------------------------------------------------------ band limit
+def _local_freq(u, lam, z):
+    """Local frequency (cycles per unit u) of the ASM phase 2 pi z sqrt(1/lam^2 - u^2) along u,
+    by a centred FP64 difference of the phase -- independent of the closed form f_lim."""
+    phase = lambda v: z * np.sqrt(1.0 / lam**2 - v * v)  # phase / (2 pi)
+    d = 1e-6 * max(abs(u), 1.0)
+    return abs(phase(u + d) - phase(u - d)) / (2 * d)
+
+
+@pytest.mark.parametrize(
+    "N,dx,z,lam",
+    [(256, 2e-6, 20e-3, 550e-9), (4096, 1e-6, 50e-3, 450e-9), (4096, 1e-6, 50e-3, 650e-9),
+     (8192, 1e-6, 50e-3, 550e-9), (512, 1e-6, 5e-3, 700e-9), (1024, 0.5e-6, 10e-3, 520.6e-9)],
+)
+def test_kmax_is_the_nyquist_limit_of_the_transfer_phase(N, dx, z, lam):
+    P = 2 * N
+    du = 1.0 / (P * dx)
+    k = oracle.kmax(lam, dx, P, z)
+    nyq = 1.0 / (2 * du)
+    if k < P // 2:
+        # the last kept index is sampled at or under Nyquist, the first dropped one above
+        assert _local_freq(k * du, lam, z) <= nyq * (1 + 1e-9)
+        assert _local_freq((k + 1) * du, lam, z) > nyq * (1 - 1e-9)
+    else:
+        assert _local_freq((P // 2) * du, lam, z) <= nyq * (1 + 1e-9)
+
+
+def test_kmax_config_values():
+    # values of the band limit for the stated workloads (C1, C2, C3)
+    assert oracle.kmax(550e-9, 2e-6, 512, 20e-3) == 47
+    assert [oracle.kmax(l, 1e-6, 8192, 50e-3) for l in (450e-9, 550e-9, 650e-9)] == [1486, 1216, 1028]
+    assert [oracle.kmax(l, 1e-6, 16384, 50e-3) for l in (450e-9, 550e-9, 650e-9)] == [5886, 4816, 4075]
+    assert oracle.kmax(550e-9, 1e-6, 65536, 100e-3) == 32768  # inactive at the large-area grid
+
+
+def test_band_mask_integer_rules():
+    P, dx, z, lam = 64, 0.25e-6, 5e-6, 700e-9  # fine pitch: the evanescent cut is active
+    m = oracle.band_mask(P, dx, z, lam)
+    k = oracle.kmax(lam, dx, P, z)
+    du = 1.0 / (P * dx)
+    kt = np.where(np.arange(P) < P // 2, np.arange(P), np.arange(P) - P)
+    prop = (lam**2) * ((kt[None, :] * du) ** 2 + (kt[:, None] * du) ** 2) < 1.0
+    inband = (np.abs(kt[None, :]) <= k) & (np.abs(kt[:, None]) <= k)
+    assert np.array_equal(m.astype(bool), prop & inband)
+    assert (~prop).any()  # the case really exercises the evanescent cut
+
+
+# ------------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("P,z,lam", [(16, 20e-3, 550e-9), (64, 0.1, 550e-9), (256, 50e-3, 450e-9), (1024, 0.1, 650e-9)])
+def test_flat_plate(P, z, lam):
+    # h = c everywhere, pad = 1: the spectrum is a DC delta, so E_out = exp(i(k' c + 2 pi z / lam))
+    c = 0.37e-6
+    h = np.full((P, P), c, np.float32)
+    e = oracle.propagate(h, 1e-6, z, lam, n_index=1.46, pad=1)
+    phase = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z / lam
+    ref = np.exp(1j * np.fmod(phase, 2 * np.pi))
+    assert np.abs(e - ref).max() < 1e-8
+
+
+def test_gaussian_beam_paraxial():
+    # E_in = exp(-r^2/w0^2), h = 0; paraxial closed form of a Gaussian beam after z
+    N, P, dx, lam, z, w0 = 2048, 4096, 1e-6, 550e-9, 50e-3, 100e-6
+    e_in = inputs.gaussian_beam(N, dx, w0)
+    e = oracle.propagate(np.zeros((N, N), np.float32), dx, z, lam, pad=2, e_in=e_in)
+    k = 2 * np.pi / lam
+    zr = np.pi * w0**2 / lam
+    w = w0 * np.sqrt(1 + (z / zr) ** 2)
+    R = z * (1 + (zr / z) ** 2)
+    psi = np.arctan(z / zr)
+    c = (np.arange(P) - P // 2) * dx
+    r2 = c[:, None] ** 2 + c[None, :] ** 2
+    ref = (w0 / w) * np.exp(-r2 / w**2) * np.exp(1j * (np.fmod(k * z, 2 * np.pi) + k * r2 / (2 * R) - psi))
+    assert rel_l2(e, ref) < 5e-6  # measured 8.2e-7; non-paraxial terms ~1e-6
+
+
+def test_parseval_over_band():
+    N, dx, z, lam = 128, 1e-6, 5e-3, 550e-9
+    P = 2 * N
+    h = inputs.heights(N, 11)
+    e = oracle.propagate(h, dx, z, lam)
+    # independent route: numpy FFT of the padded field, band from the stated integer rules
+    epad = np.zeros((P, P), np.complex128)
+    epad[N // 2:N // 2 + N, N // 2:N // 2 + N] = np.exp(1j * 2 * np.pi * 0.46 * h.astype(np.float64) / lam)
+    U = np.fft.fft2(epad)
+    du = 1.0 / (P * dx)
+    kt = np.fft.fftfreq(P, 1.0 / P)
+    flim = 1.0 / (lam * np.sqrt((2 * du * z) ** 2 + 1))
+    inband = (np.abs(kt)[None, :] * du < flim) & (np.abs(kt)[:, None] * du < flim)
+    lhs = (np.abs(e) ** 2).sum()
+    rhs = (np.abs(U[inband]) ** 2).sum() / P**2
+    assert abs(lhs - rhs) / rhs < 1e-12
+    assert lhs <= N * N * (1 + 1e-12)
+
+
+def test_rayleigh_sommerfeld_direct_sum():
+    # smooth apodised field whose spectrum lies inside the band: ASM ~ RS-I direct sum
+    N, P, dx, lam, z = 32, 64, 0.5e-6, 550e-9, 50e-6
+    yy, xx = np.mgrid[0:N, 0:N]
+    r2 = (yy - N / 2) ** 2 + (xx - N / 2) ** 2
+    amp = np.exp(-r2 / 36.0)
+    h = (0.3e-6 * np.exp(-r2 / 200.0)).astype(np.float32)
+    e_doe = amp * np.exp(1j * 2 * np.pi * 0.46 * h.astype(np.float64) / lam)
+    e_asm = oracle.propagate(h, dx, z, lam, pad=2, e_in=amp)
+    e_rs = oracle.rs_direct(e_doe, P, dx, z, lam)
+    err = rel_l2(e_asm, e_rs)
+    assert err < 1e-3, err  # measured 2.1e-4
+    # a flipped sign convention or a missing transfer function fails by orders of magnitude
+    e_conj = oracle.propagate(h, dx, -z, lam, pad=2, e_in=amp)
+    assert rel_l2(e_conj, e_rs) > 0.1
+
+
+# ------------------------------------------------------------------ gradient
+def test_gradient_matches_fp64_central_differences():
+    N, dx, z = 8, 2e-6, 1e-3
+    lams = np.array([450e-9, 650e-9])
+    P = 2 * N
+    h = inputs.heights(N, 21)
+    T = rng.random((2, P, P)).astype(np.float32) * 0.5
+    g, loss = oracle.grad(h, dx, z, lams, T)
+    h64 = h.astype(np.float64)
+    assert abs(oracle.loss_l2(h64, dx, z, lams, T) - loss) <= 1e-12 * loss
+    eps = 1e-11
+    fd = np.zeros((N, N))
+    for i in range(N):
+        for j in range(N):
+            hp = h64.copy(); hp[i, j] += eps
+            hm = h64.copy(); hm[i, j] -= eps
+            fd[i, j] = (oracle.loss_l2(hp, dx, z, lams, T) - oracle.loss_l2(hm, dx, z, lams, T)) / (2 * eps)
+    assert rel_l2(g, fd) < 1e-5
+
+
+def test_gradient_vjp_mode_equals_l2_mode():
+    N, dx, z, lam = 16, 1e-6, 2e-3, 550e-9
+    P = 2 * N
+    h = inputs.heights(N, 22)
+    T = rng.random((1, P, P)).astype(np.float32)
+    g_l2, _ = oracle.grad(h, dx, z, [lam], T)
+    I = oracle.psf(h, dx, z, [lam])
+    G = (2.0 * (I - T.astype(np.float64))).astype(np.float32)
+    g_vjp, _ = oracle.grad(h, dx, z, [lam], G, mode="vjp")
+    assert rel_l2(g_vjp, g_l2) < 1e-6  # G is rounded to float32
+
+
+def test_exact_difference_fd_matches_plain_fd():
+    N, dx, z = 16, 1e-6, 2e-3
+    lams = np.array([500e-9])
+    P = 2 * N
+    h = inputs.heights(N, 23)
+    T = rng.random((1, P, P)).astype(np.float32)
+    py = np.array([0, 3, 7, 15]); px = np.array([5, 8, 0, 15])
+    eps = 1e-10
+    fd = oracle.fd_exact(h, dx, z, lams, T, py, px, eps)
+    h64 = h.astype(np.float64)
+    for q in range(py.size):
+        hp = h64.copy(); hp[py[q], px[q]] += eps
+        hm = h64.copy(); hm[py[q], px[q]] -= eps
+        ref = (oracle.loss_l2(hp, dx, z, lams, T) - oracle.loss_l2(hm, dx, z, lams, T)) / (2 * eps)
+        assert abs(fd[q] - ref) <= 1e-6 * abs(ref) + 1e-9
+
+
+# ------------------------------------------------------------------ render / Wiener
+def test_render_matches_direct_sum():
+    C, H, W, Pp = 2, 8, 16, 32
+    psf = rng.random((C, Pp, Pp)).astype(np.float32)
+    img = rng.random((C, H, W)).astype(np.float32)
+    out = oracle.render(psf, img)
+    for c in range(C):
+        k = psf[c, Pp // 2 - H // 2:Pp // 2 - H // 2 + H, Pp // 2 - W // 2:Pp // 2 - W // 2 + W].astype(np.float64)
+        k = k / k.sum()
+        ref = np.zeros((H, W))
+        for y in range(H):
+            for x in range(W):
+                s = 0.0
+                for u in range(H):
+                    for v in range(W):
+                        yy, xx = y + H // 2 - u, x + W // 2 - v
+                        if 0 <= yy < H and 0 <= xx < W:
+                            s += img[c, yy, xx] * k[u, v]
+                ref[y, x] = s
+        assert rel_l2(out[c], ref) < 1e-13
+
+
+def test_wiener_inverts_a_circular_blur():
+    C, H, W, Pp = 1, 16, 16, 32
+    k = np.zeros((Pp, Pp), np.float32)
+    k[Pp // 2, Pp // 2] = 4.0
+    k[Pp // 2 + 1, Pp // 2] = 1.0
+    k[Pp // 2, Pp // 2 - 1] = 0.5
+    psf = k[None]
+    x = rng.random((C, H, W))
+    kc = psf[0, Pp // 2 - H // 2:Pp // 2 + H // 2, Pp // 2 - W // 2:Pp // 2 + W // 2].astype(np.float64)
+    kc /= kc.sum()
+    y = np.zeros((C, H, W))
+    for yy in range(H):  # circular blur by brute force, kernel centre at (H/2, W/2)
+        for xx in range(W):
+            for u in range(H):
+                for v in range(W):
+                    y[0, yy, xx] += kc[u, v] * x[0, (yy - (u - H // 2)) % H, (xx - (v - W // 2)) % W]
+    xh = oracle.wiener(psf, y.astype(np.float32), 1e-12)
+    assert rel_l2(xh, x) < 1e-5  # limited by the float32 rounding of y
+
+
+# ------------------------------------------------------------------ consistency + paper grids
+def test_psf_rows_equal_full_psf():
+    N, dx, z, lam = 32, 1e-6, 3e-3, 600e-9
+    h = inputs.heights(N, 24)
+    full = oracle.psf(h, dx, z, [lam])[0]
+    rows = np.array([0, 5, 31, 32, 63])
+    part = oracle.psf_rows(h, dx, z, lam, rows)
+    assert np.abs(part - full[rows]).max() <= 1e-12 * full.max()
+
+
+def test_table2_grids_are_twice_the_design_sample_count():
+    rows = np.loadtxt(os.path.join(GOLD, "table2_grids.txt"))
+    for ay, ax, pitch, gy, gx in rows:
+        ny = round(ay * 1e3 / pitch)
+        nx = round(ax * 1e3 / pitch)
+        assert (2 * ny, 2 * nx) == (int(gy), int(gx))
