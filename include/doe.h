@@ -1,0 +1,157 @@
+/*
+ * doe.h -- C ABI of libdoe: scalar-diffraction simulation of a diffractive optical element
+ * (DOE) on one NVIDIA B300 (sm_103a), after Wei et al., "Large-Area Fabrication-Aware
+ * Computational Diffractive Optics", ACM TOG 44(6), 2025, Sec. 3.1.
+ *
+ * The path: height map h -> phase Phi = 2 pi (n - 1) h / lambda (Eq. 1) -> transmittance
+ * E_doe = E_in exp(+i Phi) (Eq. 2) -> zero padding -> FFT -> product with the band-limited
+ * angular-spectrum transfer function H_lambda -> inverse FFT (Eq. 3) -> intensity
+ * I = |E_dest|^2 (the PSF) per wavelength; the gradient of sum_lambda L(I_lambda) with
+ * respect to h (Eq. 4) by a hand-written adjoint; and the convolution of an image with the
+ * PSFs (the image-formation model behind the imaging application's Eq. 9).
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are row-major [row = y][col = x].  "complex" arrays are interleaved (re, im)
+ *    float pairs (8 bytes per sample, the layout of CUDA float2 / torch.complex64).
+ *  - Every data pointer is DEVICE memory owned by the caller, except the geometry's
+ *    lambda / n_index arrays, which are HOST memory read during the call.
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *    work is enqueued on it asynchronously; no call synchronises the device.  Device-side
+ *    faults therefore surface at the caller's next synchronisation.
+ *  - The library allocates no device memory on these paths: the caller passes a workspace
+ *    (`ws`, `ws_bytes`, 256-byte aligned) sized with the matching *_workspace_bytes call.
+ *    Read-only FFT twiddle tables live in static device memory (about 1.1 MB per device,
+ *    held until the process exits) and are uploaded on the first call on each device, or by
+ *    doe_init(); make that first call before capturing a stream into a CUDA graph.
+ *  - Return value: DOE_OK (0) or a negative DOE_E* code; nothing is launched when a call
+ *    fails validation.  No C++ exception crosses this interface.
+ *  - Grid: N x N DOE samples (N a power of two, 16 <= N), padded to P = pad * N per axis with
+ *    the DOE at offset (P - N) / 2; output sample (y, x) lies at the same physical position
+ *    as padded input sample (y, x) (the optical axis is at (P/2, P/2)).  This build supports
+ *    P <= 16384.
+ */
+#ifndef DOE_H
+#define DOE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DOE_OK 0
+#define DOE_EINVAL (-1)       /* an argument is out of range or a required pointer is NULL */
+#define DOE_EUNSUPPORTED (-2) /* a size or shape this build does not implement */
+#define DOE_ENOWS (-3)        /* workspace missing, too small or not 256-byte aligned */
+#define DOE_ECUDA (-4)        /* a CUDA runtime call or kernel launch failed */
+#define DOE_ETIMEDOUT (-5)    /* a bounded host-side wait expired (serving layer) */
+
+/* ---- geometry flags ---- */
+#define DOE_BANDLIMIT 0x1u /* apply the band limit of the transfer function (default on) */
+
+/* ---- operations, for doe_workspace_bytes ---- */
+#define DOE_OP_PROPAGATE 1
+#define DOE_OP_PSF 2
+#define DOE_OP_GRAD 3
+
+/* ---- gradient modes ---- */
+#define DOE_GRAD_L2_TARGET 0 /* L = sum_lambda sum_xy (I - T)^2 with target T */
+#define DOE_GRAD_VJP 1       /* vector-Jacobian product with a given dL/dI */
+
+/* Geometry of one DOE evaluation (Sec. 3.1 notation). */
+typedef struct doe_geom {
+    int32_t nx, ny;        /* DOE samples per axis; powers of two, >= 16; nx == ny in this build */
+    int32_t pad;           /* 1 or 2: padded grid P = pad * n per axis (the paper's grids are 2x) */
+    double dx;             /* sampling pitch [m], square pixels, > 0 */
+    double z;              /* propagation distance [m], > 0 */
+    int32_t n_lambda;      /* number of wavelengths, 1..64 */
+    const double* lambda;  /* HOST [n_lambda] wavelengths [m], > 0 */
+    const double* n_index; /* HOST [n_lambda] refractive index n_lambda of the DOE material, >= 1 */
+    uint32_t flags;        /* DOE_BANDLIMIT */
+} doe_geom;
+
+/* Per-device set-up (uploads the twiddle tables).  Optional: the first call of any entry
+ * point on a device does it.  Uses the current CUDA device.  Returns DOE_OK or DOE_ECUDA. */
+int doe_init(void);
+
+/* Bytes of workspace the given operation needs for geometry g (0 on invalid geometry).
+ * op is DOE_OP_PROPAGATE, DOE_OP_PSF or DOE_OP_GRAD. */
+size_t doe_workspace_bytes(const doe_geom* g, int op);
+
+/* Destination field E_dest (Eq. 3) for every wavelength.
+ *   h      device float [ny][nx]          heights in metres (Eq. 1)
+ *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
+ *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
+ * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (P > 16384 or
+ * nx != ny), DOE_ENOWS (workspace), DOE_ECUDA. */
+int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
+                  size_t ws_bytes, void* stream);
+
+/* PSF I = |E_dest|^2 (Sec. 3.1, after Eq. 4) for every wavelength.
+ *   psf    device float [n_lambda][P][P] written; raw intensity of a unit-amplitude field,
+ *          not normalised.
+ * Other arguments and errors as doe_propagate. */
+int doe_psf(const doe_geom* g, const float* h, const float* e_in, float* psf, void* ws,
+            size_t ws_bytes, void* stream);
+
+/* PSFs of several independent DOEs in one set of launches (the serving path batches
+ * requests this way).  All geometries must share nx, ny and pad (hence P); dx, z, the
+ * wavelengths and the heights may differ.  h[r], e_in[r] (NULL entries allowed) and psf[r]
+ * are device pointers held in HOST arrays of length n_req; psf[r] receives
+ * [geoms[r].n_lambda][P][P].  The total number of wavelengths must be <= 64.  Workspace:
+ * doe_workspace_bytes_many(..., DOE_OP_PSF).  Errors as doe_psf. */
+int doe_psf_many(int n_req, const doe_geom* geoms, const float* const* h, const float* const* e_in,
+                 float* const* psf, void* ws, size_t ws_bytes, void* stream);
+size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op);
+
+/* Gradient of Eq. 4's objective with respect to the heights, by the adjoint of the chain:
+ *   g_out = 2 (I - T) E_dest (DOE_GRAD_L2_TARGET) or (dL/dI) E_dest (DOE_GRAD_VJP);
+ *   g_pad = IFFT2( conj(H) FFT2(g_out) ); g_doe = g_pad on the DOE window;
+ *   dL/dh = sum_lambda -2 k'_lambda Im(conj(g_doe) E_doe), k' = 2 pi (n - 1) / lambda.
+ *   t_or_dldi  device float [n_lambda][P][P]: the target T or dL/dI
+ *   grad_h     device float [ny][nx], overwritten (per metre of height)
+ *   loss_dev   device double[1] or NULL: receives sum (I - T)^2 in DOE_GRAD_L2_TARGET mode
+ *              (summed in FP64 from FP32 per-row partials), 0 in DOE_GRAD_VJP mode
+ *   recompute  1: the forward field is recomputed inside the call (no stored field);
+ *              0: ws still holds the fields left by a doe_psf call with the same
+ *              geometry, heights and e_in on the same workspace (a DOE_OP_GRAD-sized ws);
+ *              the forward passes are then skipped.
+ * Errors as doe_propagate; DOE_EINVAL for a bad mode. */
+int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* t_or_dldi, int mode,
+             float* grad_h, double* loss_dev, int recompute, void* ws, size_t ws_bytes, void* stream);
+
+/* Image formation by PSF convolution, channel c with PSF c:
+ *   k_c = psf_c cropped to H x W around the optical axis (rows Py/2 - H/2 .., cols Px/2 - W/2 ..),
+ *         normalised to sum 1;
+ *   out_c[y][x] = sum_{u,v} img_c[y + H/2 - u][x + W/2 - v] k_c[u][v], zero outside the image
+ *   (linear convolution, "same" window), computed with 2H x 2W transforms.
+ *   psf  device float [C][Py][Px];  img, out  device float [C][H][W]
+ * H and W are powers of two with 16 <= H <= Py, 16 <= W <= Px and 2H, 2W <= 16384.
+ * Workspace: doe_render_workspace_bytes(C, H, W).  Errors: DOE_EINVAL, DOE_EUNSUPPORTED,
+ * DOE_ENOWS, DOE_ECUDA. */
+int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out,
+               void* ws, size_t ws_bytes, void* stream);
+size_t doe_render_workspace_bytes(int C, int H, int W);
+
+/* Integer band logic of the transfer function, computed on the host exactly as the kernels
+ * use it (for bit-exact checks).  For wavelength j: kmax[j] = the largest signed frequency
+ * index kept per axis (ceil(f_lim / du) - 1 capped at P/2, with
+ * f_lim = 1 / (lambda sqrt((2 du z)^2 + 1)), du = 1 / (P dx), Matsushima & Shimobaba 2009
+ * as cited next to Eq. 3), and m_ev[j] = ceil(1 / (lambda du)^2): a sample (kt, lt) with
+ * |kt|, |lt| <= kmax propagates iff kt^2 + lt^2 < m_ev.  Host arrays of n_lambda entries. */
+int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev);
+
+/* Debug: writes the band mask the kernels apply for wavelength j (1 = H != 0) as device
+ * uint8 [P][P] in FFT order, read back from the transfer table the kernels use. */
+int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Human-readable text for a status code. */
+const char* doe_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOE_H */

@@ -1,0 +1,93 @@
+"""ctypes view of libdoe.so (include/doe.h).  Argument marshalling only.
+
+The library is required: if libdoe.so is missing or fails to load, every call raises.
+There is no CPU or PyTorch fallback for any step of the path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libdoe.so"
+
+DOE_OK = 0
+DOE_EINVAL = -1
+DOE_EUNSUPPORTED = -2
+DOE_ENOWS = -3
+DOE_ECUDA = -4
+DOE_ETIMEDOUT = -5
+DOE_BANDLIMIT = 0x1
+DOE_OP_PROPAGATE, DOE_OP_PSF, DOE_OP_GRAD = 1, 2, 3
+DOE_GRAD_L2_TARGET, DOE_GRAD_VJP = 0, 1
+
+# every entry point declared in include/doe.h
+EXPORTS = (
+    "doe_init", "doe_workspace_bytes", "doe_propagate", "doe_psf", "doe_psf_many",
+    "doe_workspace_bytes_many", "doe_grad", "doe_render", "doe_render_workspace_bytes",
+    "doe_band_limits", "doe_debug_band_mask", "doe_strerror",
+)
+
+
+class DoeError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = load().doe_strerror(code).decode() if code != 0 else "ok"
+        super().__init__(f"{what}: {msg} (code {code})")
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("dx", ctypes.c_double),
+        ("z", ctypes.c_double),
+        ("n_lambda", ctypes.c_int32),
+        ("lambda_", ctypes.POINTER(ctypes.c_double)),
+        ("n_index", ctypes.POINTER(ctypes.c_double)),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def load(path: Path | None = None) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"libdoe.so not built ({p}); run `python -m paper_2505_22313_b300.build`")
+    lib = ctypes.CDLL(str(p))
+    V = ctypes.c_void_p
+    I = ctypes.c_int
+    S = ctypes.c_size_t
+    G = ctypes.POINTER(Geom)
+    F = ctypes.c_void_p  # device float* / complex* / double*
+    sig = {
+        "doe_init": ([], I),
+        "doe_workspace_bytes": ([G, I], S),
+        "doe_workspace_bytes_many": ([I, G, I], S),
+        "doe_propagate": ([G, F, F, F, V, S, V], I),
+        "doe_psf": ([G, F, F, F, V, S, V], I),
+        "doe_psf_many": ([I, G, ctypes.POINTER(V), ctypes.POINTER(V), ctypes.POINTER(V), V, S, V], I),
+        "doe_grad": ([G, F, F, F, I, F, F, I, V, S, V], I),
+        "doe_render": ([I, I, I, F, I, I, F, F, V, S, V], I),
+        "doe_render_workspace_bytes": ([I, I, I], S),
+        "doe_band_limits": ([G, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], I),
+        "doe_debug_band_mask": ([G, I, F, V, S, V], I),
+        "doe_strerror": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def check(code: int, what: str) -> None:
+    if code != DOE_OK:
+        raise DoeError(code, what)

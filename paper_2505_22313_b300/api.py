@@ -1,0 +1,227 @@
+"""PyTorch-facing API over libdoe.  Tensors supply device memory and the current CUDA
+stream; every step of the computation runs in the library's CUDA kernels.
+
+Notation (Wei et al. 2025, Sec. 3.1): h = DOE height map (metres), lambda = wavelength,
+n = refractive index, z = propagation distance, dx = pitch, pad = zero-padding factor.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+@dataclass
+class Geometry:
+    """One DOE evaluation: N x N samples at pitch dx, padded to P = pad * N, at distance z,
+    for the wavelengths `lambdas` with refractive indices `n_index`."""
+
+    N: int
+    dx: float
+    z: float
+    lambdas: np.ndarray
+    n_index: np.ndarray
+    pad: int = 2
+    bandlimit: bool = True
+
+    @staticmethod
+    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True) -> "Geometry":
+        lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, np.float64)))
+        nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
+        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit))
+
+    @property
+    def P(self) -> int:
+        return self.pad * self.N
+
+    @property
+    def L(self) -> int:
+        return int(self.lambdas.size)
+
+    def c(self) -> L.Geom:
+        g = L.Geom()
+        g.nx = g.ny = self.N
+        g.pad = self.pad
+        g.dx = self.dx
+        g.z = self.z
+        g.n_lambda = self.L
+        g.lambda_ = self.lambdas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        g.n_index = self.n_index.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        g.flags = L.DOE_BANDLIMIT if self.bandlimit else 0
+        return g
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor | None, dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def workspace_bytes(geom: Geometry, op: int = L.DOE_OP_PSF) -> int:
+    g = geom.c()
+    return int(L.load().doe_workspace_bytes(ctypes.byref(g), op))
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device buffer usable as a libdoe workspace (the caching allocator aligns to 512 B)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def _ws_args(ws: torch.Tensor | None, need: int, device):
+    if ws is None:
+        ws = workspace(need, device)
+    if ws.numel() < need:
+        raise ValueError(f"workspace too small: {ws.numel()} < {need} bytes")
+    return ws, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())
+
+
+def init() -> None:
+    L.check(L.load().doe_init(), "doe_init")
+
+
+def psf(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: torch.Tensor | None = None,
+        ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """PSFs I_lambda = |E_dest|^2 on the padded grid: float32 [L, P, P]."""
+    N, P = geom.N, geom.P
+    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
+    if out is None:
+        out = torch.empty((geom.L, P, P), dtype=torch.float32, device=h.device)
+    op = _dev_ptr(out, torch.float32, (geom.L, P, P), "out")
+    g = geom.c()
+    need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PSF))
+    ws, wp, wb = _ws_args(ws, need, h.device)
+    L.check(L.load().doe_psf(ctypes.byref(g), hp, ep, op, wp, wb, _stream(stream)), "doe_psf")
+    return out
+
+
+def propagate(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Destination fields E_dest (Eq. 3): complex64 [L, P, P]."""
+    N, P = geom.N, geom.P
+    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
+    if out is None:
+        out = torch.empty((geom.L, P, P), dtype=torch.complex64, device=h.device)
+    op = _dev_ptr(out, torch.complex64, (geom.L, P, P), "out")
+    g = geom.c()
+    need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PROPAGATE))
+    ws, wp, wb = _ws_args(ws, need, h.device)
+    L.check(L.load().doe_propagate(ctypes.byref(g), hp, ep, op, wp, wb, _stream(stream)), "doe_propagate")
+    return out
+
+
+def psf_many(hs, geoms, e_ins=None, outs=None, ws: torch.Tensor | None = None, stream=None):
+    """PSFs of several DOEs (same N and pad) in one set of launches."""
+    n = len(geoms)
+    gs = (L.Geom * n)(*[g.c() for g in geoms])
+    if outs is None:
+        outs = [torch.empty((g.L, g.P, g.P), dtype=torch.float32, device=hs[0].device) for g in geoms]
+    hp = (ctypes.c_void_p * n)(*[_dev_ptr(h, torch.float32, (g.N, g.N), "h").value for h, g in zip(hs, geoms)])
+    ep = (ctypes.c_void_p * n)(*[(e.data_ptr() if e is not None else None) for e in (e_ins or [None] * n)])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o, torch.float32, (g.L, g.P, g.P), "out").value for o, g in zip(outs, geoms)])
+    need = int(L.load().doe_workspace_bytes_many(n, gs, L.DOE_OP_PSF))
+    ws, wp, wb = _ws_args(ws, need, hs[0].device)
+    L.check(L.load().doe_psf_many(n, gs, hp, ep, op, wp, wb, _stream(stream)), "doe_psf_many")
+    return outs
+
+
+def grad(h: torch.Tensor, geom: Geometry, t_or_dldi: torch.Tensor, mode: str = "l2",
+         e_in: torch.Tensor | None = None, recompute: bool = True, out: torch.Tensor | None = None,
+         loss: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """(dL/dh float32 [N, N], loss float64 [1]) for L = sum (I - T)^2 (mode 'l2') or the
+    vector-Jacobian product with dL/dI (mode 'vjp'; loss is then 0)."""
+    N, P = geom.N, geom.P
+    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
+    tp = _dev_ptr(t_or_dldi, torch.float32, (geom.L, P, P), "t_or_dldi")
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.float32, device=h.device)
+    gp = _dev_ptr(out, torch.float32, (N, N), "grad")
+    if loss is None:
+        loss = torch.empty((1,), dtype=torch.float64, device=h.device)
+    lp = _dev_ptr(loss, torch.float64, (1,), "loss")
+    g = geom.c()
+    need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_GRAD))
+    ws, wp, wb = _ws_args(ws, need, h.device)
+    m = L.DOE_GRAD_L2_TARGET if mode == "l2" else L.DOE_GRAD_VJP
+    L.check(L.load().doe_grad(ctypes.byref(g), hp, ep, tp, m, gp, lp, int(bool(recompute)), wp, wb, _stream(stream)),
+            "doe_grad")
+    return out, loss
+
+
+def render(psf_t: torch.Tensor, img: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """Convolution of each image channel with its PSF (cropped at the axis, normalised)."""
+    C, H, W = img.shape
+    Py, Px = psf_t.shape[-2:]
+    pp = _dev_ptr(psf_t, torch.float32, (C, Py, Px), "psf")
+    ip = _dev_ptr(img, torch.float32, (C, H, W), "img")
+    if out is None:
+        out = torch.empty((C, H, W), dtype=torch.float32, device=img.device)
+    op = _dev_ptr(out, torch.float32, (C, H, W), "out")
+    need = int(L.load().doe_render_workspace_bytes(C, H, W))
+    ws, wp, wb = _ws_args(ws, need, img.device)
+    L.check(L.load().doe_render(C, H, W, pp, Py, Px, ip, op, wp, wb, _stream(stream)), "doe_render")
+    return out
+
+
+def band_limits(geom: Geometry):
+    """(kmax [L] int32, m_ev [L] int64): the integer band logic the kernels apply."""
+    k = np.zeros(geom.L, np.int32)
+    m = np.zeros(geom.L, np.int64)
+    g = geom.c()
+    L.check(L.load().doe_band_limits(ctypes.byref(g), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "doe_band_limits")
+    return k, m
+
+
+def debug_band_mask(geom: Geometry, j: int, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    P = geom.P
+    mask = torch.empty((P, P), dtype=torch.uint8, device="cuda")
+    g = geom.c()
+    need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PSF))
+    ws, wp, wb = _ws_args(ws, need, "cuda")
+    L.check(L.load().doe_debug_band_mask(ctypes.byref(g), j, ctypes.c_void_p(mask.data_ptr()), wp, wb, _stream(stream)),
+            "doe_debug_band_mask")
+    return mask
+
+
+class PSF(torch.autograd.Function):
+    """Differentiable h -> PSF [L, P, P].  Backward runs the library's adjoint kernels
+    (conjugate transfer function) with recomputation: no field is stored between passes."""
+
+    @staticmethod
+    def forward(ctx, h: torch.Tensor, geom: Geometry, e_in=None):
+        ctx.geom = geom
+        ctx.save_for_backward(h, e_in) if e_in is not None else ctx.save_for_backward(h)
+        return psf(h, geom, e_in)
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        saved = ctx.saved_tensors
+        h = saved[0]
+        e_in = saved[1] if len(saved) > 1 else None
+        g, _ = grad(h, ctx.geom, grad_out.contiguous().float(), mode="vjp", e_in=e_in, recompute=True)
+        return g, None, None
+
+
+def psf_autograd(h: torch.Tensor, geom: Geometry, e_in=None) -> torch.Tensor:
+    return PSF.apply(h, geom, e_in)

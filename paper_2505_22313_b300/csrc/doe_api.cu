@@ -1,0 +1,373 @@
+// doe_api.cu -- host side of libdoe: argument validation, per-device set-up, workspace
+// layout and launch sequencing of the passes (see doe_kernels.cuh).  Everything is
+// enqueued on the caller's stream; nothing here synchronises the device.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "doe.h"
+#include "doe_launch.h"
+
+using namespace doe;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxDevices = 64;
+
+std::mutex g_mu;
+bool g_dev_ready[kMaxDevices] = {};
+
+// Forward twiddles exp(-2 pi i m / n) in FP64, rounded to FP32.
+float2 twiddle(long m, long n) {
+  const double a = -2.0 * kPi * (double)(m % n) / (double)n;
+  return make_float2((float)std::cos(a), (float)std::sin(a));
+}
+
+const std::vector<float2>& host_stage_tables() {
+  static std::vector<float2> tw;
+  if (tw.empty()) {
+    tw.assign((size_t)kTwTotal, make_float2(0.f, 0.f));
+    for (int lg = kMinLog; lg <= kMaxLog; ++lg)
+      for (int inv = 0; inv < 2; ++inv)
+        for (int s = 0; s < plan_nst(lg); ++s) {
+          const long ns = plan_ns(lg, inv, s), R = plan_radix(lg, inv, s);
+          float2* p = tw.data() + tw_offset(lg, inv, s);
+          for (long k = 0; k < ns; ++k)
+            for (long r = 0; r < R; ++r) p[k * R + r] = twiddle(r * k, ns * R);
+        }
+  }
+  return tw;
+}
+
+const std::vector<float2>& host_big_table() {
+  static std::vector<float2> tw;
+  if (tw.empty()) {
+    tw.resize(1u << kBigLog);
+    for (long n = 0; n < (1L << kBigLog); ++n) tw[n] = twiddle(n, 1L << kBigLog);
+  }
+  return tw;
+}
+
+int ensure_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DOE_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_dev_ready[dev]) return DOE_OK;
+  const auto& a = host_stage_tables();
+  const auto& b = host_big_table();
+  if (upload_tables(a.data(), a.size(), b.data(), b.size()) != cudaSuccess) return DOE_ECUDA;
+  if (prepare_kernels() != cudaSuccess) return DOE_ECUDA;
+  g_dev_ready[dev] = true;
+  return DOE_OK;
+}
+
+bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(long n) { int l = 0; while ((1L << l) < n) ++l; return l; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+void split(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Integer band logic (see doe.h): the same FP64 expressions the specification states.
+long band_kmax(double lam, double dx, long P, double z, bool bandlimit) {
+  if (!bandlimit) return P / 2;
+  const double du = 1.0 / ((double)P * dx);
+  const double t = 2.0 * du * z;
+  const double flim = 1.0 / (lam * std::sqrt(t * t + 1.0));
+  long k = (long)std::ceil(flim / du) - 1;
+  if (k > P / 2) k = P / 2;
+  if (k < 0) k = 0;
+  return k;
+}
+long long band_mev(double lam, double dx, long P) {
+  const double du = 1.0 / ((double)P * dx);
+  const double ld = lam * du;
+  const double x = 1.0 / (ld * ld);
+  if (x > 9.0e18) return LLONG_MAX;
+  return (long long)std::ceil(x);
+}
+
+int check_geom(const doe_geom* g) {
+  if (!g) return DOE_EINVAL;
+  if (g->nx < 16 || g->ny < 16 || !is_pow2(g->nx) || !is_pow2(g->ny)) return DOE_EINVAL;
+  if (g->pad != 1 && g->pad != 2) return DOE_EINVAL;
+  if (!(g->dx > 0.0) || !(g->z > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->z)) return DOE_EINVAL;
+  if (g->n_lambda < 1 || g->n_lambda > kMaxSlices || !g->lambda || !g->n_index) return DOE_EINVAL;
+  for (int j = 0; j < g->n_lambda; ++j) {
+    if (!(g->lambda[j] > 0.0) || !std::isfinite(g->lambda[j])) return DOE_EINVAL;
+    if (!(g->n_index[j] >= 1.0) || !std::isfinite(g->n_index[j])) return DOE_EINVAL;
+  }
+  if (g->nx != g->ny) return DOE_EUNSUPPORTED;
+  if ((long)g->pad * g->nx > (1L << kMaxLog)) return DOE_EUNSUPPORTED;
+  return DOE_OK;
+}
+
+// Fills the per-slice constants of wavelength j of g.
+void fill_slice(Slice& s, const doe_geom* g, int j) {
+  const long P = (long)g->pad * g->nx;
+  const double lam = g->lambda[j];
+  const double du = 1.0 / ((double)P * g->dx);
+  const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
+  std::memset(&s, 0, sizeof(s));
+  s.kmax = (int)kmax;
+  s.w = (kmax >= P / 2) ? (int)P : (int)(2 * kmax + 1);
+  s.wp = (s.w + kTile - 1) / kTile * kTile;
+  s.hp = (int)kmax + 1;
+  s.mev = band_mev(lam, g->dx, P);
+  const double ld = lam * du;
+  split(ld * ld, s.c_hi, s.c_lo);
+  const double phi0 = 2.0 * kPi * g->z / lam;
+  split(phi0, s.phi0_hi, s.phi0_lo);
+  split(std::fmod(phi0, 2.0 * kPi), s.th0_hi, s.th0_lo);
+  split(2.0 * kPi * (g->n_index[j] - 1.0) / lam, s.kp_hi, s.kp_lo);
+}
+
+struct Layout {
+  size_t total = 0;
+  std::vector<size_t> buf, htab;
+  size_t loss = 0;
+};
+
+// Workspace: per slice a [P][wp] complex field buffer, then per slice a transfer table, then
+// (gradient) the per-row loss partials.  The PSF layout is a prefix of the gradient layout,
+// so a gradient-sized workspace used by doe_psf keeps its fields for doe_grad(recompute=0).
+Layout make_layout(const std::vector<Slice>& sl, long P, int op) {
+  Layout L;
+  size_t off = 0;
+  for (const auto& s : sl) {
+    L.buf.push_back(off);
+    off = align256(off + (size_t)P * s.wp * sizeof(float2));
+  }
+  for (const auto& s : sl) {
+    L.htab.push_back(off);
+    off = align256(off + (size_t)(s.kmax + 1) * s.hp * sizeof(float2));
+  }
+  if (op == DOE_OP_GRAD) {
+    L.loss = off;
+    off = align256(off + sl.size() * (size_t)P * sizeof(double));
+  }
+  L.total = off;
+  return L;
+}
+
+int collect_slices(int n_req, const doe_geom* geoms, std::vector<Slice>& sl, std::vector<int>& req_of) {
+  if (n_req < 1 || !geoms) return DOE_EINVAL;
+  for (int r = 0; r < n_req; ++r) {
+    const int rc = check_geom(&geoms[r]);
+    if (rc != DOE_OK) return rc;
+    if (geoms[r].nx != geoms[0].nx || geoms[r].pad != geoms[0].pad) return DOE_EINVAL;
+  }
+  for (int r = 0; r < n_req; ++r)
+    for (int j = 0; j < geoms[r].n_lambda; ++j) {
+      Slice s;
+      fill_slice(s, &geoms[r], j);
+      sl.push_back(s);
+      req_of.push_back(r);
+    }
+  if ((int)sl.size() > kMaxSlices) return DOE_EUNSUPPORTED;
+  return DOE_OK;
+}
+
+void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* ws, const Layout& lay) {
+  std::memset(&bt, 0, sizeof(bt));
+  bt.S = (int)sl.size();
+  bt.N = N;
+  bt.P = pad * N;
+  bt.off = (bt.P - N) / 2;
+  bt.inv_p2 = (float)(1.0 / ((double)bt.P * (double)bt.P));
+  int tiles = 0, kmx = 0;
+  for (int j = 0; j < bt.S; ++j) {
+    bt.s[j] = sl[j];
+    bt.s[j].buf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.buf[j]);
+    bt.s[j].htab = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.htab[j]);
+    if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P;
+    bt.s[j].tile_begin = tiles;
+    tiles += sl[j].wp / kTile;
+    if (sl[j].kmax > kmx) kmx = sl[j].kmax;
+  }
+  bt.total_tiles = tiles;
+  bt.max_kmax = kmx;
+}
+
+int ws_ok(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return DOE_OK;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u)) return DOE_ENOWS;
+  return DOE_OK;
+}
+
+int forward_passes(Batch& bt, cudaStream_t st) {
+  const int lg = ilog2(bt.P);
+  if (launch_htab(bt, st) != cudaSuccess) return DOE_ECUDA;
+  if (launch_pass_a(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  bt.mode = MODE_FWD;
+  if (launch_pass_b(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  return DOE_OK;
+}
+
+int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const float* const* e_in,
+                void* const* out, int out_kind, void* ws, size_t ws_bytes, void* stream) {
+  std::vector<Slice> sl;
+  std::vector<int> req_of;
+  int rc = collect_slices(n_req, geoms, sl, req_of);
+  if (rc != DOE_OK) return rc;
+  for (int r = 0; r < n_req; ++r)
+    if (!h[r] || !out[r]) return DOE_EINVAL;
+  const int N = geoms[0].nx, pad = geoms[0].pad;
+  const long P = (long)pad * N;
+  const Layout lay = make_layout(sl, P, DOE_OP_PSF);
+  if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
+  if ((rc = ensure_device()) != DOE_OK) return rc;
+  static thread_local Batch bt;
+  init_batch(bt, sl, N, pad, ws, lay);
+  int jr = 0, prev = -1;
+  for (int j = 0; j < bt.S; ++j) {
+    const int r = req_of[j];
+    jr = (r == prev) ? jr + 1 : 0;
+    prev = r;
+    bt.s[j].h = h[r];
+    bt.s[j].e_in = e_in ? reinterpret_cast<const float2*>(e_in[r]) : nullptr;
+    const size_t esz = out_kind == OUT_PSF ? sizeof(float) : sizeof(float2);
+    bt.s[j].out = static_cast<char*>(out[r]) + (size_t)jr * P * P * esz;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = forward_passes(bt, st)) != DOE_OK) return rc;
+  bt.mode = out_kind;
+  if (launch_pass_c(ilog2(P), bt, st) != cudaSuccess) return DOE_ECUDA;
+  return DOE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int doe_init(void) { return ensure_device(); }
+
+size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op) {
+  if (op != DOE_OP_PROPAGATE && op != DOE_OP_PSF && op != DOE_OP_GRAD) return 0;
+  std::vector<Slice> sl;
+  std::vector<int> req_of;
+  if (collect_slices(n_req, geoms, sl, req_of) != DOE_OK) return 0;
+  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, op).total;
+}
+
+size_t doe_workspace_bytes(const doe_geom* g, int op) { return doe_workspace_bytes_many(1, g, op); }
+
+int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
+                  size_t ws_bytes, void* stream) {
+  void* o = e_out;
+  return run_forward(1, g, &h, &e_in, &o, OUT_FIELD, ws, ws_bytes, stream);
+}
+
+int doe_psf(const doe_geom* g, const float* h, const float* e_in, float* psf, void* ws, size_t ws_bytes,
+            void* stream) {
+  void* o = psf;
+  return run_forward(1, g, &h, &e_in, &o, OUT_PSF, ws, ws_bytes, stream);
+}
+
+int doe_psf_many(int n_req, const doe_geom* geoms, const float* const* h, const float* const* e_in,
+                 float* const* psf, void* ws, size_t ws_bytes, void* stream) {
+  if (n_req < 1 || !h || !psf) return DOE_EINVAL;
+  std::vector<void*> o(psf, psf + n_req);
+  return run_forward(n_req, geoms, h, e_in, o.data(), OUT_PSF, ws, ws_bytes, stream);
+}
+
+int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* t_or_dldi, int mode,
+             float* grad_h, double* loss_dev, int recompute, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g);
+  if (rc != DOE_OK) return rc;
+  if (!h || !t_or_dldi || !grad_h) return DOE_EINVAL;
+  if (mode != DOE_GRAD_L2_TARGET && mode != DOE_GRAD_VJP) return DOE_EINVAL;
+  if (recompute != 0 && recompute != 1) return DOE_EINVAL;
+  std::vector<Slice> sl;
+  std::vector<int> req_of;
+  if ((rc = collect_slices(1, g, sl, req_of)) != DOE_OK) return rc;
+  const int N = g->nx, pad = g->pad;
+  const long P = (long)pad * N;
+  const Layout lay = make_layout(sl, P, DOE_OP_GRAD);
+  if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
+  if ((rc = ensure_device()) != DOE_OK) return rc;
+  static thread_local Batch bt;
+  init_batch(bt, sl, N, pad, ws, lay);
+  for (int j = 0; j < bt.S; ++j) {
+    bt.s[j].h = h;
+    bt.s[j].e_in = reinterpret_cast<const float2*>(e_in);
+    bt.s[j].tgt = t_or_dldi + (size_t)j * P * P;
+  }
+  bt.grad = grad_h;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int lg = ilog2(P);
+  if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
+  bt.mode = mode == DOE_GRAD_L2_TARGET ? GRAD_L2 : GRAD_VJP;
+  if (launch_pass_c_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  const int gmode = bt.mode;
+  bt.mode = MODE_ADJ;
+  if (launch_pass_b(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  if (launch_pass_a_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  if (loss_dev) {
+    bt.mode = gmode;
+    if (launch_loss_reduce(bt, loss_dev, st) != cudaSuccess) return DOE_ECUDA;
+  }
+  return DOE_OK;
+}
+
+int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev) {
+  const int rc = check_geom(g);
+  if (rc != DOE_OK && rc != DOE_EUNSUPPORTED) return rc;
+  if (!kmax || !m_ev) return DOE_EINVAL;
+  const long P = (long)g->pad * g->nx;
+  for (int j = 0; j < g->n_lambda; ++j) {
+    kmax[j] = (int32_t)band_kmax(g->lambda[j], g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
+    m_ev[j] = (int64_t)band_mev(g->lambda[j], g->dx, P);
+  }
+  return DOE_OK;
+}
+
+int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g);
+  if (rc != DOE_OK) return rc;
+  if (!mask || j < 0 || j >= g->n_lambda) return DOE_EINVAL;
+  doe_geom one = *g;
+  one.n_lambda = 1;
+  one.lambda = g->lambda + j;
+  one.n_index = g->n_index + j;
+  std::vector<Slice> sl;
+  std::vector<int> req_of;
+  if ((rc = collect_slices(1, &one, sl, req_of)) != DOE_OK) return rc;
+  const long P = (long)g->pad * g->nx;
+  const Layout lay = make_layout(sl, P, DOE_OP_PSF);
+  if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
+  if ((rc = ensure_device()) != DOE_OK) return rc;
+  static thread_local Batch bt;
+  init_batch(bt, sl, g->nx, g->pad, ws, lay);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (launch_htab(bt, st) != cudaSuccess) return DOE_ECUDA;
+  if (launch_band_mask(bt, mask, st) != cudaSuccess) return DOE_ECUDA;
+  return DOE_OK;
+}
+
+int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out, void* ws,
+               size_t ws_bytes, void* stream) {
+  return render_entry(C, H, W, psf, Py, Px, img, out, ws, ws_bytes, stream);
+}
+
+size_t doe_render_workspace_bytes(int C, int H, int W) { return render_workspace(C, H, W); }
+
+const char* doe_strerror(int code) {
+  switch (code) {
+    case DOE_OK: return "ok";
+    case DOE_EINVAL: return "invalid argument";
+    case DOE_EUNSUPPORTED: return "unsupported size or shape";
+    case DOE_ENOWS: return "workspace missing, too small or misaligned";
+    case DOE_ECUDA: return "CUDA runtime error";
+    case DOE_ETIMEDOUT: return "timed out";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

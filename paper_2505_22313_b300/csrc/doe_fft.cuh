@@ -1,0 +1,243 @@
+// doe_fft.cuh -- in-CTA Stockham FFT engine for sm_103a.
+//
+// One CTA transforms one vector of L = 2^LOG complex64 samples (16 <= L <= 16384).  Each of
+// the T = L / E threads keeps E samples in registers; a stage applies E / R radix-R
+// butterflies per thread, and consecutive stages exchange data through shared memory
+// (padded one float2 per 16 to avoid bank conflicts).  The formulation is the self-sorting
+// Stockham autosort: stage s with radix R and current sub-transform size Ns reads element
+//     j + r * (L / R)                        (j = butterfly index, r < R)
+// multiplies element r by W_{Ns R}^{r (j mod Ns)}, takes an R-point DFT and writes it to
+//     (j - j mod Ns) * R + (j mod Ns) + r * Ns,
+// which leaves the result in natural order after the last stage.  Thread t owns butterflies
+// j = t + b * T, b < E / R, so the first stage's reads and the last stage's writes
+// (both "j + r * L/R") are contiguous across a warp and go straight to/from global memory.
+//
+// Radix plans: forward = [r0, 16, 16, ...], inverse = [16, ..., 16, r0] (r0 = L / 16^k <= 16).
+// The forward plan ends and the inverse plan starts with radix 16, and the inverse plan ends
+// with the forward plan's first radix, so a forward -> pointwise -> inverse chain (the
+// transfer-function multiply) and an inverse -> pointwise -> forward chain (the adjoint row
+// pass) need no shared-memory round trip in between: the registers already hold the next
+// transform's first-stage inputs.
+//
+// Twiddles come from per-(L, direction, stage) tables in device memory, rows of R entries
+// W_{Ns R}^{r k} for k < Ns (entry 0 = 1), computed on the host in FP64 and rounded to FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "doe_plan.h"
+
+namespace doe {
+
+__device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
+
+// Tables live in static device memory, filled once per device at library set-up.  This header
+// is included by exactly one translation unit (doe_launch.cu), which owns these definitions.
+__device__ __align__(16) float2 g_tw[kTwTotal];
+__device__ __align__(16) float2 g_tw_big[1 << kBigLog];  // W_65536^n, n < 65536
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+template <bool INV>
+__device__ __forceinline__ float2 ctw(float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 cmi(float2 a) { return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ------------------------------------------------------------------ small DFTs in registers
+// Forward kernels use W_R = exp(-2 pi i / R); INV uses the conjugates.  In and out in place,
+// natural order.
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  float2 s13 = cadd(a1, a3), d13 = cmi<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+constexpr float kR2 = 0.70710678118654752440f;  // 1/sqrt(2)
+constexpr float kC8 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS8 = 0.38268343236508977173f;  // sin(pi/8)
+
+template <bool INV>
+__device__ __forceinline__ float2 w8(float2 a, int q) {  // a * W_8^q, q in 1..3
+  const float sg = INV ? 1.f : -1.f;
+  if (q == 1) return make_float2(kR2 * (a.x - sg * a.y), kR2 * (a.y + sg * a.x));
+  if (q == 2) return cmi<INV>(a);
+  return make_float2(kR2 * (-a.x - sg * a.y), kR2 * (-a.y + sg * a.x));
+}
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  dft4<INV>(v[0], v[2], v[4], v[6]);
+  dft4<INV>(v[1], v[3], v[5], v[7]);
+  v[3] = w8<INV>(v[3], 1);
+  v[5] = w8<INV>(v[5], 2);
+  v[7] = w8<INV>(v[7], 3);
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+// a * W_16^m for the m that occur in the 4 x 4 split: 1, 2, 3, 4, 6, 9
+template <bool INV>
+__device__ __forceinline__ float2 w16(float2 a, int m) {
+  const float sg = INV ? 1.f : -1.f;  // W_16^m = cos(2 pi m/16) + sg i sin(2 pi m/16)
+  float c, s;
+  switch (m) {
+    case 1: c = kC8; s = kS8; break;
+    case 2: c = kR2; s = kR2; break;
+    case 3: c = kS8; s = kC8; break;
+    case 4: return cmi<INV>(a);
+    case 6: c = -kR2; s = kR2; break;
+    default: c = -kC8; s = -kS8; break;  // m = 9
+  }
+  s *= sg;
+  return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+}
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  // n = 4 n1 + n2, q = q1 + 4 q2
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // now v[4 q1 + n2] = A_{n2}[q1]; twiddle by W_16^{n2 q1}
+  v[5] = w16<INV>(v[5], 1);
+  v[6] = w16<INV>(v[6], 2);
+  v[7] = w16<INV>(v[7], 3);
+  v[9] = w16<INV>(v[9], 2);
+  v[10] = w16<INV>(v[10], 4);
+  v[11] = w16<INV>(v[11], 6);
+  v[13] = w16<INV>(v[13], 3);
+  v[14] = w16<INV>(v[14], 6);
+  v[15] = w16<INV>(v[15], 9);
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1) dft4<INV>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+  // v[4 q1 + q2] = y[q1 + 4 q2]: transpose the 4 x 4 index
+  float2 t;
+  t = v[1]; v[1] = v[4]; v[4] = t;
+  t = v[2]; v[2] = v[8]; v[8] = t;
+  t = v[3]; v[3] = v[12]; v[12] = t;
+  t = v[6]; v[6] = v[9]; v[9] = t;
+  t = v[7]; v[7] = v[13]; v[13] = t;
+  t = v[11]; v[11] = v[14]; v[14] = t;
+}
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else dft16<INV>(v);
+}
+
+// ------------------------------------------------------------------ stages
+template <int L, int E>
+struct FftShape {
+  static constexpr int LOG = ilog2c(L);
+  static constexpr int T = L / E;
+  static constexpr int NST = plan_nst(LOG);
+  static_assert(L >= 16 && L <= (1 << kMaxLog) && (L & (L - 1)) == 0, "L must be a power of two in [16, 16384]");
+  static_assert(E % 16 == 0 || E == L, "E must be a multiple of every radix");
+};
+
+// Twiddle + DFT of stage S on registers (inputs already in place).
+template <int L, int E, bool INV, int S>
+__device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
+  using Sh = FftShape<L, E>;
+  constexpr int R = plan_radix(Sh::LOG, INV, S);
+  constexpr int NS = plan_ns(Sh::LOG, INV, S);
+  constexpr int B = E / R;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if constexpr (S > 0) {
+      const int j = t + b * Sh::T;
+      const int k = j & (NS - 1);
+      const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(Sh::LOG, INV, S) + (long)k * R);
+#pragma unroll
+      for (int r = 0; r < R; r += 2) {
+        float4 w = __ldg(tw + r / 2);
+        if (r > 0) v[b * R + r] = ctw<INV>(v[b * R + r], make_float2(w.x, w.y));
+        v[b * R + r + 1] = ctw<INV>(v[b * R + r + 1], make_float2(w.z, w.w));
+      }
+    }
+    dft<R, INV>(&v[b * R]);
+  }
+}
+
+// Write stage S's outputs to shared memory in Stockham order.
+template <int L, int E, bool INV, int S>
+__device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2* sm) {
+  using Sh = FftShape<L, E>;
+  constexpr int R = plan_radix(Sh::LOG, INV, S);
+  constexpr int NS = plan_ns(Sh::LOG, INV, S);
+  constexpr int B = E / R;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = t + b * Sh::T;
+    const int k = j & (NS - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[phys(base + r * NS)] = v[b * R + r];
+  }
+}
+
+// Read stage S's inputs ("j + r L/R") from shared memory.
+template <int L, int E, bool INV, int S>
+__device__ __forceinline__ void stage_load(float2 (&v)[E], int t, const float2* sm) {
+  using Sh = FftShape<L, E>;
+  constexpr int R = plan_radix(Sh::LOG, INV, S);
+  constexpr int B = E / R;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = t + b * Sh::T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b * R + r] = sm[phys(j + r * (L / R))];
+  }
+}
+
+// Runs stages S..NST-1: on entry v holds stage S's inputs; on exit v holds the final outputs
+// in the last stage's layout (element j + r L/R_last of the transform).  Stages exchange through
+// sm, each exchange preceded by a barrier, so sm may still be read by other threads on entry.
+template <int L, int E, bool INV, int S = 0>
+__device__ __forceinline__ void fft_run(float2 (&v)[E], int t, float2* sm) {
+  using Sh = FftShape<L, E>;
+  stage_compute<L, E, INV, S>(v, t);
+  if constexpr (S + 1 < Sh::NST) {
+    __syncthreads();
+    stage_store<L, E, INV, S>(v, t, sm);
+    __syncthreads();
+    stage_load<L, E, INV, S + 1>(v, t, sm);
+    fft_run<L, E, INV, S + 1>(v, t, sm);
+  }
+}
+
+// Index (within the transform) held by register b*R + r in the first stage's layout.
+template <int L, int E, bool INV>
+__device__ __forceinline__ int first_index(int t, int b, int r) {
+  constexpr int R = plan_radix(FftShape<L, E>::LOG, INV, 0);
+  return t + b * FftShape<L, E>::T + r * (L / R);
+}
+// Index held by register b*R + r after the last stage.
+template <int L, int E, bool INV>
+__device__ __forceinline__ int last_index(int t, int b, int r) {
+  constexpr int R = plan_radix(FftShape<L, E>::LOG, INV, FftShape<L, E>::NST - 1);
+  return t + b * FftShape<L, E>::T + r * (L / R);
+}
+
+
+}  // namespace doe

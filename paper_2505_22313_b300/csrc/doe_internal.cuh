@@ -1,0 +1,113 @@
+// doe_internal.cuh -- kernel parameter blocks and device helpers shared by the passes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "doe_fft.cuh"
+#include "doe_plan.h"
+
+namespace doe {
+
+// ------------------------------------------------------------------ double-float arithmetic
+// A value is hi + lo with |lo| <= ulp(hi) / 2 (about 48 significant bits).  Error-free
+// transformations: Knuth's two-sum, and the FMA two-product.  B300 runs FP64 at 1/64 of the
+// FP32 rate, so the transfer-function phase (up to ~1e6 rad) is evaluated in this format.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  dfl p = two_prod(x.hi, y.hi);
+  float e = __fadd_rn(p.lo, fmaf(x.hi, y.lo, __fmul_rn(x.lo, y.hi)));
+  return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dfl df_mul_f(dfl x, float f) {
+  dfl p = two_prod(x.hi, f);
+  float e = fmaf(x.lo, f, p.lo);
+  return fast_two_sum(p.hi, e);
+}
+
+constexpr float kTwoPiHi = 6.28318548202514648438f;        // float(2 pi)
+constexpr float kTwoPiLo = -1.7484555314695172e-07f;       // 2 pi - float(2 pi)
+constexpr float kInvTwoPi = 0.15915494309189533577f;
+
+// Transfer function H at integer frequencies with m = kt^2 + lt^2 (Eq. 3's H_lambda, the
+// band-limited angular spectrum: exp(+i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2))).  Written as
+// phi = phi0 sqrt(1 - q), q = c m, and evaluated as phi0 - phi0 q / (1 + sqrt(1 - q)) so that
+// no large phase is ever rounded to FP32: the drop phi0 g (g = q / (1 + sqrt(1 - q))) is kept
+// in double-float, reduced mod 2 pi in double-float, and subtracted from phi0 mod 2 pi
+// (computed on the host in FP64).  The caller has checked m < mev (propagating sample).
+__device__ __forceinline__ float2 transfer_value(unsigned int m, const Slice& s) {
+  const float m_hi = (float)(m & 0xFFFFF000u);  // exact: at most 20 significant bits
+  const float m_lo = (float)(m & 0x00000FFFu);  // exact
+  const dfl c = {s.c_hi, s.c_lo};
+  const dfl q = df_add(df_mul_f(c, m_hi), df_mul_f(c, m_lo));
+  const dfl u = df_add({1.f, 0.f}, df_neg(q));  // 1 - q in (0, 1]
+  // sqrt(u): one Newton step from the FP32 root doubles the precision
+  const float s0 = sqrtf(u.hi);
+  const dfl s0sq = two_prod(s0, s0);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(u.hi, s0sq.hi), s0sq.lo), u.lo);
+  const dfl sq = fast_two_sum(s0, __fmul_rn(r, __fdiv_rn(0.5f, s0)));
+  const dfl d = df_add({1.f, 0.f}, sq);  // in [1, 2]
+  // g = q / d: FP32 quotient corrected by one residual step
+  const float g0 = __fdiv_rn(q.hi, d.hi);
+  const dfl res = df_add(q, df_neg(df_mul_f(d, g0)));
+  const dfl g = fast_two_sum(g0, __fdiv_rn(res.hi, d.hi));
+  const dfl dphi = df_mul({s.phi0_hi, s.phi0_lo}, g);  // phase drop below the on-axis phase
+  const float n = rintf(__fmul_rn(dphi.hi, kInvTwoPi));
+  const dfl t = df_add(dphi, df_mul_f({-kTwoPiHi, -kTwoPiLo}, n));  // dphi mod 2 pi
+  const float th = __fadd_rn(__fsub_rn(s.th0_hi, t.hi), __fsub_rn(s.th0_lo, t.lo));
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// Transmittance exp(+i k' h) (Eq. 1-2).  k' h is formed exactly as a float pair (FMA
+// two-product), wrapped to (-pi, pi] in that format, then rounded once for sincosf.
+__device__ __forceinline__ float2 transmittance(float hv, float kp_hi, float kp_lo) {
+  const dfl p = two_prod(kp_hi, hv);
+  const float e = fmaf(kp_lo, hv, p.lo);
+  const float n = rintf(__fmul_rn(p.hi, kInvTwoPi));
+  const float r = fmaf(-n, kTwoPiHi, p.hi);  // exact (Sterbenz): |p.hi - n 2pi_hi| is small
+  const float th = __fadd_rn(r, fmaf(-n, kTwoPiLo, e));
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// Column position in the stored (band-compacted) spectrum of frequency index k in [0, P),
+// or -1 if k is outside the band.  With the band limit active the stored order is
+// k = 0..kmax, then k = P-kmax..P-1 (FFT order with the out-of-band middle removed).
+__device__ __forceinline__ int band_pos(int k, int P, int kmax, int w) {
+  if (w == P) return k;
+  if (k <= kmax) return k;
+  if (k >= P - kmax) return k - (P - w);
+  return -1;
+}
+__device__ __forceinline__ int pos_to_k(int pos, int P, int kmax, int w) {
+  if (w == P || pos <= kmax) return pos;
+  return pos + (P - w);
+}
+__device__ __forceinline__ int abs_signed(int k, int P) { return k < P / 2 ? k : P - k; }
+
+}  // namespace doe

@@ -1,0 +1,24 @@
+// doe_launch.h -- host-callable launchers of the device passes (defined in doe_launch.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "doe_plan.h"
+
+namespace doe {
+cudaError_t upload_tables(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big);
+cudaError_t prepare_kernels();
+cudaError_t launch_htab(const Batch& bt, cudaStream_t st);
+cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st);
+cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st);
+cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st);
+cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st);
+cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st);
+cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st);
+cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st);
+}  // namespace doe
+
+int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out, void* ws,
+                 size_t ws_bytes, void* stream);
+size_t render_workspace(int C, int H, int W);

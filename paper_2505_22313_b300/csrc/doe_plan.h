@@ -1,0 +1,88 @@
+// doe_plan.h -- compile-time FFT plans and the launch parameter blocks, usable from host
+// and device code.  Holds no device symbols.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace doe {
+
+
+constexpr int kMinLog = 4;   // L = 16
+constexpr int kMaxLog = 14;  // L = 16384 (one CTA)
+constexpr int kBigLog = 16;  // 65536-point table for the cross-CTA (four-step) twiddles
+
+__host__ __device__ constexpr int plan_r0(int lg) { return (lg % 4 == 0) ? 16 : (1 << (lg % 4)); }
+__host__ __device__ constexpr int plan_nst(int lg) { return (lg + 3) / 4; }
+__host__ __device__ constexpr int plan_radix(int lg, bool inv, int s) {
+  return inv ? (s == plan_nst(lg) - 1 ? plan_r0(lg) : 16) : (s == 0 ? plan_r0(lg) : 16);
+}
+__host__ __device__ constexpr int plan_ns(int lg, bool inv, int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= plan_radix(lg, inv, i);
+  return p;
+}
+__host__ __device__ constexpr long tw_plan_size(int lg, bool inv) {
+  long n = 0;
+  for (int s = 0; s < plan_nst(lg); ++s) n += (long)plan_ns(lg, inv, s) * plan_radix(lg, inv, s);
+  return n;
+}
+__host__ __device__ constexpr long tw_offset(int lg, bool inv, int s) {
+  long off = 0;
+  for (int l = kMinLog; l < lg; ++l) off += tw_plan_size(l, false) + tw_plan_size(l, true);
+  if (inv) off += tw_plan_size(lg, false);
+  for (int i = 0; i < s; ++i) off += (long)plan_ns(lg, inv, i) * plan_radix(lg, inv, i);
+  return off;
+}
+constexpr long kTwTotal = tw_offset(kMaxLog + 1, false, 0);
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__host__ __device__ constexpr int smem_words(int L) { return L + (L >> 4); }
+
+// Elements per thread used for a transform of length L.
+__host__ __device__ constexpr int elems_for(int L) { return L <= 8192 ? 16 : 32; }
+template <int L, bool INV>
+__host__ __device__ constexpr int first_radix() { return plan_radix(ilog2c(L), INV, 0); }
+template <int L, bool INV>
+__host__ __device__ constexpr int last_radix() { return plan_radix(ilog2c(L), INV, plan_nst(ilog2c(L)) - 1); }
+
+constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
+constexpr int kTile = 4;        // columns per column-pass cluster: 4 x 8 B = one 32-byte sector
+
+// One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
+// shared by the whole launch.
+struct Slice {
+  const float* h;        // [N][N] heights (m)
+  const float2* e_in;    // [N][N] incident field or nullptr
+  float2* buf;           // [P][wp] field buffer: I1 (rows < N), I2 / J1 (rows < P), J2 (rows < N)
+  float2* htab;          // [kmax + 1][hp] transfer function quarter table H(|kt|, |lt|)
+  const float* tgt;      // [P][P] target T or dL/dI (gradient)
+  void* out;             // [P][P] float PSF or float2 field
+  double* loss_part;     // [P] per-row loss partial sums (gradient)
+  float kp_hi, kp_lo;    // k' = 2 pi (n - 1) / lambda as a float pair
+  float c_hi, c_lo;      // (lambda du)^2
+  float phi0_hi, phi0_lo;  // 2 pi z / lambda
+  float th0_hi, th0_lo;    // (2 pi z / lambda) mod 2 pi
+  long long mev;         // propagating iff kt^2 + lt^2 < mev
+  int kmax;              // band limit index per axis
+  int w;                 // stored columns: P if the band limit is inactive, else 2 kmax + 1
+  int wp;                // row pitch of buf (w rounded up to kTile)
+  int hp;                // row pitch of htab (kmax + 1)
+  int tile_begin;        // first global column-tile index of this slice (column pass)
+};
+
+enum : int { OUT_PSF = 0, OUT_FIELD = 1 };
+enum : int { MODE_FWD = 0, MODE_ADJ = 1 };
+enum : int { GRAD_L2 = 0, GRAD_VJP = 1 };
+
+struct Batch {
+  int S;             // slices
+  int N, P, off;     // DOE side, padded side, DOE offset in the padded grid
+  int total_tiles;   // column tiles over all slices
+  int mode;          // MODE_FWD / MODE_ADJ (column pass), OUT_* (row inverse pass), GRAD_* (adjoint row pass)
+  int max_kmax;      // largest kmax over the slices (table builder grid)
+  float inv_p2;      // 1 / P^2 (inverse transform normalisation)
+  float* grad;       // [N][N] gradient output (DOE-row adjoint pass)
+  Slice s[kMaxSlices];
+};
+
+}  // namespace doe

@@ -1,0 +1,120 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry
+point include/doe.h declares, applies the band logic bit-exactly like the oracle, and
+rejects bad arguments before launching anything."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_22313_b300 import _lib as L
+from paper_2505_22313_b300 import build
+from paper_2505_22313_b300.api import Geometry, band_limits
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return L.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "doe.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(doe_\w+)\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(L.EXPORTS) | {"doe_render_workspace_bytes"}
+
+
+CASES = [
+    (256, 2, 2e-6, 20e-3, [550e-9]),
+    (4096, 2, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9]),
+    (8192, 2, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9]),
+    (32768, 2, 1e-6, 100e-3, [550e-9]),
+    (64, 2, 0.25e-6, 5e-6, [400e-9, 700e-9]),
+    (1024, 1, 1e-6, 10e-3, [520.6e-9]),
+]
+
+
+@pytest.mark.parametrize("N,pad,dx,z,lams", CASES)
+def test_band_limits_bit_exact_vs_oracle(lib, N, pad, dx, z, lams):
+    g = Geometry.make(N, dx, z, lams, pad=pad)
+    k, m = band_limits(g)
+    P = pad * N
+    for j, lam in enumerate(lams):
+        assert int(k[j]) == oracle.kmax(lam, dx, P, z)
+        assert int(m[j]) == oracle.m_ev(lam, dx, P)
+
+
+def test_band_limits_random_geometries(lib):
+    rng = np.random.default_rng(99)
+    for _ in range(200):
+        N = int(2 ** rng.integers(4, 15))
+        dx = float(rng.uniform(0.2e-6, 4e-6))
+        z = float(10 ** rng.uniform(-5, -0.5))
+        lam = float(rng.uniform(380e-9, 780e-9))
+        g = Geometry.make(N, dx, z, [lam])
+        k, m = band_limits(g)
+        assert int(k[0]) == oracle.kmax(lam, dx, 2 * N, z)
+        assert int(m[0]) == oracle.m_ev(lam, dx, 2 * N)
+
+
+def _geom(**kw):
+    base = dict(N=64, dx=1e-6, z=1e-3, lambdas=[550e-9])
+    base.update(kw)
+    return Geometry.make(**base)
+
+
+@pytest.mark.parametrize(
+    "g",
+    [_geom(N=48), _geom(N=8), _geom(dx=0.0), _geom(z=-1.0), _geom(lambdas=[0.0]), _geom(n_index=0.5),
+     _geom(lambdas=np.full(65, 5e-7))],
+)
+def test_invalid_geometry_rejected(lib, g):
+    c = g.c()
+    assert lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_PSF) == 0
+    rc = lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None)
+    assert rc in (L.DOE_EINVAL, L.DOE_EUNSUPPORTED)
+
+
+def test_bad_pad_and_unsupported_size(lib):
+    g = _geom()
+    c = g.c()
+    c.pad = 3
+    assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_EINVAL
+    big = _geom(N=32768).c()  # P = 65536 needs the multi-CTA transform
+    rc = lib.doe_psf(ctypes.byref(big), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None)
+    assert rc in (L.DOE_OK, L.DOE_ENOWS, L.DOE_EUNSUPPORTED)
+    rect = _geom().c()
+    rect.ny = 128
+    assert lib.doe_psf(ctypes.byref(rect), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_EUNSUPPORTED
+
+
+def test_workspace_checked_before_launch(lib):
+    g = _geom()
+    c = g.c()
+    need = lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_PSF)
+    assert need > 0
+    assert lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_GRAD) > need
+    # too small, NULL, misaligned: refused without touching the device
+    assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), ctypes.c_void_p(256), need - 1, None) == L.DOE_ENOWS
+    assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, need, None) == L.DOE_ENOWS
+    assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), ctypes.c_void_p(256 + 8), need, None) == L.DOE_ENOWS
+
+
+def test_null_pointers_and_bad_mode(lib):
+    c = _geom().c()
+    assert lib.doe_psf(ctypes.byref(c), None, None, ctypes.c_void_p(16), None, 0, None) == L.DOE_EINVAL
+    assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, None, None, 0, None) == L.DOE_EINVAL
+    assert lib.doe_grad(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), 7, ctypes.c_void_p(16), None, 1, None, 0, None) == L.DOE_EINVAL
+    assert lib.doe_grad(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), 0, ctypes.c_void_p(16), None, 2, None, 0, None) == L.DOE_EINVAL
+
+
+def test_strerror(lib):
+    for code in (0, -1, -2, -3, -4, -5, -99):
+        assert lib.doe_strerror(code)

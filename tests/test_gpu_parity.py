@@ -1,0 +1,188 @@
+"""GPU parity of libdoe against the FP64 oracle (element by element on seeded inputs), plus
+closed-form and property checks at sizes the oracle cannot finish quickly."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_22313_b300 import api, inputs
+from paper_2505_22313_b300.api import Geometry
+
+pytestmark = pytest.mark.gpu
+
+TOL_PSF = 1e-5   # relative L2, PSFs, fields and renders (FP32 path vs FP64 oracle)
+TOL_GRAD = 1e-4  # relative L2, gradients
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64) if not np.iscomplexobj(a) else np.asarray(a, np.complex128)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _init():
+    from paper_2505_22313_b300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    api.init()
+
+
+def _h(N, seed):
+    return inputs.heights(N, seed)
+
+
+# -------------------------------------------------------------- fields, every transform size
+@pytest.mark.parametrize("N,pad", [(16, 1), (16, 2), (32, 2), (64, 2), (128, 1), (128, 2), (256, 2),
+                                   (512, 2), (1024, 2), (2048, 1)])
+def test_propagate_matches_oracle_all_sizes(N, pad):
+    dx, z = 1e-6, 3e-3 * N / 256
+    lams = [450e-9, 633e-9]
+    h = _h(N, 1000 + N)
+    g = Geometry.make(N, dx, z, lams, pad=pad)
+    e = api.propagate(torch.from_numpy(h).cuda(), g).cpu().numpy()
+    for j, lam in enumerate(lams):
+        ref = oracle.propagate(h, dx, z, lam, pad=pad)
+        assert rel_l2(e[j], ref) < TOL_PSF, (N, pad, j, rel_l2(e[j], ref))
+
+
+def test_psf_config_small_full():
+    # 256 x 256 DOE, 2 um pitch, 550 nm, z = 20 mm, 2x padding -> 512 x 512 PSF
+    N, dx, z, lam = 256, 2e-6, 20e-3, 550e-9
+    h = _h(N, 1001)
+    g = Geometry.make(N, dx, z, [lam])
+    I = api.psf(torch.from_numpy(h).cuda(), g).cpu().numpy()
+    ref = oracle.psf(h, dx, z, [lam])
+    err = rel_l2(I, ref)
+    assert err < TOL_PSF, err
+
+
+def test_psf_with_incident_field():
+    N, dx, z, lam = 128, 1e-6, 2e-3, 532e-9
+    h = _h(N, 77)
+    rng = np.random.default_rng(5)
+    e_in = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    g = Geometry.make(N, dx, z, [lam])
+    I = api.psf(torch.from_numpy(h).cuda(), g, e_in=torch.from_numpy(e_in).cuda()).cpu().numpy()
+    ref = oracle.psf(h, dx, z, [lam], e_in=e_in.astype(np.complex128))
+    assert rel_l2(I, ref) < TOL_PSF
+
+
+@pytest.mark.parametrize("N", [512, 2048, 4096, 8192])
+def test_flat_plate_closed_form_every_size(N):
+    # h = c, pad = 1: E_out = exp(i (k' c + 2 pi z / lambda)) everywhere, I = 1
+    c, dx, z, lam = 0.37e-6, 1e-6, 0.1, 550e-9
+    h = torch.full((N, N), c, dtype=torch.float32, device="cuda")
+    g = Geometry.make(N, dx, z, [lam], pad=1)
+    e = api.propagate(h, g)[0]
+    phase = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z / lam
+    ref = complex(np.cos(np.fmod(phase, 2 * np.pi)), np.sin(np.fmod(phase, 2 * np.pi)))
+    err = (e - torch.tensor(ref, dtype=torch.complex64, device="cuda")).abs().max().item()
+    assert err < 2e-5, err
+
+
+@pytest.mark.parametrize("N,lams", [(4096, [450e-9, 550e-9, 650e-9]), (8192, [450e-9, 550e-9, 650e-9])])
+def test_psf_large_rows_vs_oracle(N, lams):
+    # full-size workloads: exact FP64 rows (seeded subset) from the oracle's row-subset mode
+    dx, z = 1e-6, 50e-3
+    P = 2 * N
+    h = _h(N, 1002 if N == 4096 else 1003)
+    g = Geometry.make(N, dx, z, lams)
+    I = api.psf(torch.from_numpy(h).cuda(), g)
+    rows = np.unique(np.concatenate([np.arange(0, P, P // 8), P // 2 + np.arange(-4, 4),
+                                     np.random.default_rng(N).integers(0, P, 8)]))
+    Ig = I[:, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    for j, lam in enumerate(lams[:1] if N == 8192 else lams):
+        ref = oracle.psf_rows(h, dx, z, lam, rows)
+        err = rel_l2(Ig[j], ref)
+        assert err < TOL_PSF, (j, err)
+    # Parseval over the band on every wavelength: sum I <= N^2 and close to it for smooth h
+    tot = I.double().sum(dim=(1, 2)).cpu().numpy()
+    assert np.all(tot <= N * N * (1 + 1e-5)) and np.all(tot > 0.5 * N * N)
+
+
+def test_band_mask_bit_exact():
+    for N, dx, z, lams in [(32, 0.25e-6, 5e-6, [400e-9, 700e-9]), (256, 2e-6, 20e-3, [550e-9]),
+                           (512, 1e-6, 50e-3, [450e-9, 650e-9])]:
+        g = Geometry.make(N, dx, z, lams)
+        for j, lam in enumerate(lams):
+            m = api.debug_band_mask(g, j).cpu().numpy()
+            ref = oracle.band_mask(2 * N, dx, z, lam)
+            assert np.array_equal(m, ref)
+
+
+def test_deterministic_and_batch_invariant():
+    N, dx, z = 256, 1e-6, 5e-3
+    h1 = torch.from_numpy(_h(N, 3)).cuda()
+    h2 = torch.from_numpy(_h(N, 4)).cuda()
+    g1 = Geometry.make(N, dx, z, [450e-9, 600e-9])
+    g2 = Geometry.make(N, dx, 2 * z, [700e-9])
+    a = api.psf(h1, g1)
+    b = api.psf(h1, g1)
+    assert torch.equal(a, b)
+    many = api.psf_many([h1, h2], [g1, g2])
+    assert torch.equal(many[0], a)
+    assert torch.equal(many[1], api.psf(h2, g2))
+
+
+# -------------------------------------------------------------- gradient
+def test_grad_matches_oracle_512():
+    # 256 x 256 DOE, 3 wavelengths, padded 512 x 512: full FP64 oracle gradient
+    N, dx, z = 256, 2e-6, 20e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = 2 * N
+    h = _h(N, 1001)
+    T = inputs.spot_target(P, N, 3, 2003)
+    g = Geometry.make(N, dx, z, lams)
+    gr, loss = api.grad(torch.from_numpy(h).cuda(), g, torch.from_numpy(T).cuda())
+    ref, ref_loss = oracle.grad(h, dx, z, lams, T)
+    err = rel_l2(gr.cpu().numpy(), ref)
+    assert err < TOL_GRAD, err
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+
+
+def test_grad_vjp_and_autograd():
+    N, dx, z = 128, 1e-6, 3e-3
+    lams = [500e-9, 620e-9]
+    P = 2 * N
+    h = _h(N, 9)
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((2, P, P)).astype(np.float32)
+    g = Geometry.make(N, dx, z, lams)
+    ht = torch.from_numpy(h).cuda().requires_grad_(True)
+    I = api.psf_autograd(ht, g)
+    I.backward(torch.from_numpy(G).cuda())
+    ref, _ = oracle.grad(h, dx, z, lams, G, mode="vjp")
+    assert rel_l2(ht.grad.cpu().numpy(), ref) < TOL_GRAD
+
+
+def test_grad_stored_fields_equal_recompute():
+    N, dx, z = 256, 1e-6, 5e-3
+    lams = [450e-9, 650e-9]
+    P = 2 * N
+    h = torch.from_numpy(_h(N, 12)).cuda()
+    T = torch.from_numpy(inputs.spot_target(P, N, 2, 2012)).cuda()
+    g = Geometry.make(N, dx, z, lams)
+    ws = api.workspace(api.workspace_bytes(g, 3))
+    a, la = api.grad(h, g, T, ws=ws, recompute=True)
+    api.psf(h, g, ws=ws)
+    b, lb = api.grad(h, g, T, ws=ws, recompute=False)
+    assert torch.equal(a, b) and torch.equal(la, lb)
+
+
+def test_grad_finite_differences_fd_exact():
+    # central differences of the FP64 loss (exact-difference form) on seeded pixels
+    N, dx, z = 512, 1e-6, 10e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = 2 * N
+    h = _h(N, 31)
+    T = inputs.spot_target(P, N, 3, 2031)
+    g = Geometry.make(N, dx, z, lams)
+    gr, _ = api.grad(torch.from_numpy(h).cuda(), g, torch.from_numpy(T).cuda())
+    gr = gr.cpu().numpy()
+    rng = np.random.default_rng(64)
+    py = rng.integers(0, N, 16)
+    px = rng.integers(0, N, 16)
+    fd = oracle.fd_exact(h, dx, z, lams, T, py, px, 1e-10)
+    scale = np.abs(fd).max()
+    assert np.all(np.abs(gr[py, px] - fd) <= 1e-3 * scale), np.abs(gr[py, px] - fd).max() / scale
