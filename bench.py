@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the DOE scalar-diffraction path on B300.
+
+Workload (RGB design evaluation): a 4096 x 4096 DOE at 1 um pitch, heights in [0, 1.2] um
+(seeded, smoothed), wavelengths 450/550/650 nm, n = 1.46, z = 50 mm, padded to 8192 x 8192:
+three PSFs, then the FFT convolution of a seeded 3 x 2048 x 2048 image with them.  One step
+is that whole chain.  Metric: field-samples/s = (wavelengths x 8192^2) per step / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one per GPU, weak scaling: the path has
+no exchange step between GPUs).  The reference arm is the FP64 CPU oracle.  Prints one JSON
+line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "DOE PSF field-samples/s & % HBM roofline at stated FP64 error; p50/p99 latency"
+UNIT = "field-samples/s"
+WL = dict(workload="rgb_design_eval_4096", N=4096, dx=1e-6, z=50e-3, lambdas=[450e-9, 550e-9, 650e-9],
+          n_index=1.46, pad=2, C=3, H=2048, W=2048, h_seed=1002, img_seed=2002)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _config(extra=None):
+    c = {"workload": WL["workload"], "doe": f"{WL['N']}x{WL['N']}", "pitch_um": 1.0,
+         "grid": f"{WL['pad'] * WL['N']}x{WL['pad'] * WL['N']}", "lambdas_nm": [450, 550, 650], "z_mm": 50,
+         "render": f"{WL['C']}x{WL['H']}x{WL['W']}", "l2_flush": "inputs larger than L2 (2.6 GB moved per step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def _band_w(kmax: int, P: int) -> int:
+    return P if kmax >= P // 2 else ((kmax + 2) & ~1) + ((kmax + 1) & ~1)
+
+
+def _algorithmic_bytes(kmax, P, N, C, H, W):
+    """Compulsory DRAM bytes of one launch of each pass (band-pruned storage)."""
+    S = len(kmax)
+    w = sum(_band_w(k, P) for k in kmax)
+    tab = sum((k + 1) ** 2 for k in kmax) * 8
+    return {
+        "transfer_table": tab,
+        "pass_a_rows": S * N * N * 4 + N * w * 8,
+        "pass_b_columns": N * w * 8 + P * w * 8 + tab,
+        "pass_c_rows": P * w * 8 + S * P * P * 4,
+        "render_rows": 2 * C * H * W * 4 + 2 * C * H * (W + 1) * 8,
+        "render_columns": 3 * C * H * (W + 1) * 8,
+        "render_output": C * H * (W + 1) * 8 + C * H * W * 4,
+    }
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2505_22313_b300" / "csrc").glob("*")):
+        if f.suffix in (".cu", ".cuh", ".h"):
+            h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != _source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class _Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(h, lam, img1, psf_gpu=None):
+    """FP64 oracle on a bounded sample of the workload: the 8192^2 PSF of one wavelength and
+    one render channel.  Returns (seconds, threads, rel L2 error of the GPU PSF if given)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    ref = oracle.psf(h, WL["dx"], WL["z"], [lam], n_index=WL["n_index"], pad=WL["pad"])
+    oracle.render(ref.astype(np.float32), img1)
+    dt = time.perf_counter() - t0
+    err = None
+    if psf_gpu is not None:
+        err = float(np.linalg.norm((psf_gpu.astype(np.float64) - ref[0]).ravel()) / np.linalg.norm(ref[0].ravel()))
+    return dt, oracle.num_threads(), err
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_22313_b300 import api, build, inputs
+    from paper_2505_22313_b300.api import Geometry
+
+    ws_n, rank, local = _dist()
+    if ws_n > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    build.build()
+    api.init()
+
+    N, P, C, H, W = WL["N"], WL["pad"] * WL["N"], WL["C"], WL["H"], WL["W"]
+    g = Geometry.make(N, WL["dx"], WL["z"], WL["lambdas"], n_index=WL["n_index"], pad=WL["pad"])
+    h_np = inputs.heights(N, WL["h_seed"])
+    img_np = inputs.image(C, H, W, WL["img_seed"])
+    h = torch.from_numpy(h_np).to(dev)
+    img = torch.from_numpy(img_np).to(dev)
+    ws = api.workspace(api.workspace_bytes(g, 2), dev)
+    from paper_2505_22313_b300 import _lib
+    ws_r = api.workspace(_lib.load().doe_render_workspace_bytes(C, H, W), dev)
+    psf = torch.empty((g.L, P, P), dtype=torch.float32, device=dev)
+    out = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+
+    def step():
+        api.psf(h, g, out=psf, ws=ws)
+        api.render(psf, img, out=out, ws=ws_r)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches_per_step = 7
+    api.trace_enable(K * launches_per_step)
+    n0 = api.launch_count()
+    if ws_n > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with _Clocks(dev.index if dev.index is not None else 0) as clk:
+        t0 = time.perf_counter()
+        for k in range(K):
+            ev[k][0].record()
+            step()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        if ws_n > 1:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+    launches = api.launch_count() - n0
+    recs = api.trace_read(K * launches_per_step)
+    api.trace_enable(0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    if ws_n > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = g.L * P * P
+    value = ws_n * units_per_step * K / (total_ms / 1e3)
+
+    # dominant kernel and its roofline (device time from the traced events)
+    per = {}
+    for name, ms in recs:
+        per.setdefault(name, []).append(ms)
+    kmax, _ = api.band_limits(g)
+    alg = _algorithmic_bytes([int(k) for k in kmax], P, N, C, H, W)
+    dom = max(per, key=lambda k: sum(per[k]))
+    avg_ms = sum(per[dom]) / len(per[dom])
+    peak, peak_kind = _peaks()
+    achieved = alg[dom] / (avg_ms / 1e3) / 1e9
+    trf = _traffic(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+            "traffic": trf, "algorithmic_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 4),
+            "passes_ms": {k: round(sum(v) / len(v), 4) for k, v in per.items()}}
+
+    # end to end through the public API: pinned host heights and image in, rendered image out
+    h_host = torch.from_numpy(h_np).pin_memory()
+    img_host = torch.from_numpy(img_np).pin_memory()
+    out_host = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        h.copy_(h_host, non_blocking=True)
+        img.copy_(img_host, non_blocking=True)
+        step()
+        out_host.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    Ke = max(3, min(K, 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(Ke):
+        step_e2e()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / Ke
+    if ws_n > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": ws_n * units_per_step / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": h_np.nbytes + img_np.nbytes, "d2h_bytes_per_step": C * H * W * 4,
+           "ms_per_step": round(e2e_ms, 4)}
+
+    cpu = None
+    fp64_err = None
+    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
+        psf1 = psf[1].cpu().numpy()
+        dt, cores, fp64_err = _oracle_sample(h_np, WL["lambdas"][1], img_np[1:2], psf1)
+        cpu = {"value": P * P / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle: the 8192^2 PSF of one wavelength (550 nm) and one 2048^2 render channel "
+                         f"({dt:.1f} s)"}
+    if ws_n > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws_n > 1:
+            dist.destroy_process_group()
+        return
+    srt = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": _config({"parallelism": f"replicas x{ws_n}" if ws_n > 1 else "single GPU"}),
+        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "fp64_rel_l2_psf_550nm": fp64_err,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+        "wall_s": round(wall, 3),
+    }
+    print(json.dumps(line), flush=True)
+    if ws_n > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step a bounded sample of the workload
+    (the PSF of one wavelength and one render channel) on the host cores.  One such sample
+    takes ~10 s on 16 cores, so the arm runs at most as many steps as fit in ~200 s and
+    reports both the requested and the executed step counts; warm-up is skipped (the oracle
+    has nothing to warm)."""
+    ws_n, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2505_22313_b300 import inputs
+
+    N, P, C, H, W = WL["N"], WL["pad"] * WL["N"], WL["C"], WL["H"], WL["W"]
+    h_np = inputs.heights(N, WL["h_seed"])
+    img1 = inputs.image(C, H, W, WL["img_seed"])[1:2]
+    times = []
+    cores = 0
+    budget_s = 200.0
+    while len(times) < args.steps:
+        dt, cores, _ = _oracle_sample(h_np, WL["lambdas"][1], img1)
+        times.append(dt)
+        if sum(times) + dt > budget_s:
+            break
+    tot = sum(times)
+    value = P * P * len(times) / tot
+    srt = sorted(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": len(times),
+        "steps_requested": args.steps, "warmup": 0, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config({"parallelism": "host cores"}),
+        "latency_ms": {"p50": 1e3 * srt[len(srt) // 2], "p99": 1e3 * srt[-1]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "FP64 oracle, per step: the 8192^2 PSF of one wavelength (550 nm) and one "
+                                   "2048^2 render channel"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

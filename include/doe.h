@@ -128,7 +128,7 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
  *   out_c[y][x] = sum_{u,v} img_c[y + H/2 - u][x + W/2 - v] k_c[u][v], zero outside the image
  *   (linear convolution, "same" window), computed with 2H x 2W transforms.
  *   psf  device float [C][Py][Px];  img, out  device float [C][H][W]
- * H and W are powers of two with 16 <= H <= Py, 16 <= W <= Px and 2H, 2W <= 16384.
+ * H and W are powers of two with 16 <= H <= Py, 16 <= W <= Px, 2H <= 8192 and 2W <= 16384.
  * Workspace: doe_render_workspace_bytes(C, H, W).  Errors: DOE_EINVAL, DOE_EUNSUPPORTED,
  * DOE_ENOWS, DOE_ECUDA. */
 int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out,
@@ -147,6 +147,18 @@ int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev);
  * uint8 [P][P] in FFT order, read back from the transfer table the kernels use. */
 int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_t ws_bytes,
                         void* stream);
+
+/* Tracing (optional).  doe_trace_enable(n) makes the library bracket each of the next n pass
+ * launches with a pair of CUDA events recorded on the launching stream (n = 0 turns tracing
+ * off); the events are host-side objects, no device memory is allocated.  doe_trace_read()
+ * waits for the recorded events, writes up to max (pass id, device milliseconds) records in
+ * launch order into the host arrays pass_ids / ms, clears them and returns how many it wrote
+ * (or a negative DOE_E* code).  doe_pass_name() names a pass id.  doe_launch_count() returns
+ * the number of kernels this library has launched in the process so far. */
+int doe_trace_enable(int max_records);
+int doe_trace_read(int max, int* pass_ids, float* ms);
+const char* doe_pass_name(int id);
+long long doe_launch_count(void);
 
 /* Human-readable text for a status code. */
 const char* doe_strerror(int code);

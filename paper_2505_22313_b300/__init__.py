@@ -17,7 +17,10 @@ from .api import (  # noqa: F401
     psf,
     psf_autograd,
     psf_many,
+    launch_count,
     render,
+    trace_enable,
+    trace_read,
     workspace,
     workspace_bytes,
 )

@@ -25,7 +25,8 @@ DOE_GRAD_L2_TARGET, DOE_GRAD_VJP = 0, 1
 EXPORTS = (
     "doe_init", "doe_workspace_bytes", "doe_propagate", "doe_psf", "doe_psf_many",
     "doe_workspace_bytes_many", "doe_grad", "doe_render", "doe_render_workspace_bytes",
-    "doe_band_limits", "doe_debug_band_mask", "doe_strerror",
+    "doe_band_limits", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
+    "doe_pass_name", "doe_launch_count",
 )
 
 
@@ -79,6 +80,10 @@ def load(path: Path | None = None) -> ctypes.CDLL:
         "doe_band_limits": ([G, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], I),
         "doe_debug_band_mask": ([G, I, F, V, S, V], I),
         "doe_strerror": ([I], ctypes.c_char_p),
+        "doe_trace_enable": ([I], I),
+        "doe_trace_read": ([I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)], I),
+        "doe_pass_name": ([I], ctypes.c_char_p),
+        "doe_launch_count": ([], ctypes.c_longlong),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

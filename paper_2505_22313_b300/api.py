@@ -225,3 +225,25 @@ class PSF(torch.autograd.Function):
 
 def psf_autograd(h: torch.Tensor, geom: Geometry, e_in=None) -> torch.Tensor:
     return PSF.apply(h, geom, e_in)
+
+
+# ---------------------------------------------------------------- tracing
+def trace_enable(max_records: int) -> None:
+    """Bracket each of the next max_records pass launches with CUDA events (0 disables)."""
+    L.check(L.load().doe_trace_enable(int(max_records)), "doe_trace_enable")
+
+
+def trace_read(max_records: int = 1 << 16) -> list[tuple[str, float]]:
+    """(pass name, device ms) of the traced launches since the last read, in launch order."""
+    ids = (ctypes.c_int * max_records)()
+    ms = (ctypes.c_float * max_records)()
+    n = L.load().doe_trace_read(max_records, ids, ms)
+    if n < 0:
+        raise L.DoeError(n, "doe_trace_read")
+    lib = L.load()
+    return [(lib.doe_pass_name(ids[i]).decode(), float(ms[i])) for i in range(n)]
+
+
+def launch_count() -> int:
+    """Number of kernels libdoe has launched in this process."""
+    return int(L.load().doe_launch_count())

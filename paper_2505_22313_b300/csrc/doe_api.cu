@@ -97,6 +97,7 @@ int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
   if (g->nx < 16 || g->ny < 16 || !is_pow2(g->nx) || !is_pow2(g->ny)) return DOE_EINVAL;
   if (g->pad != 1 && g->pad != 2) return DOE_EINVAL;
+  if ((long)g->pad * g->nx < (1L << kMinLog)) return DOE_EUNSUPPORTED;
   if (!(g->dx > 0.0) || !(g->z > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->z)) return DOE_EINVAL;
   if (g->n_lambda < 1 || g->n_lambda > kMaxSlices || !g->lambda || !g->n_index) return DOE_EINVAL;
   for (int j = 0; j < g->n_lambda; ++j) {
@@ -116,7 +117,13 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   std::memset(&s, 0, sizeof(s));
   s.kmax = (int)kmax;
-  s.w = (kmax >= P / 2) ? (int)P : (int)(2 * kmax + 1);
+  if (kmax >= P / 2) {
+    s.seg_a = (int)P;
+    s.w = (int)P;
+  } else {
+    s.seg_a = (int)((kmax + 2) & ~1L);  // kmax + 1 rounded up to even
+    s.w = s.seg_a + (int)((kmax + 1) & ~1L);  // + kmax rounded up to even
+  }
   s.wp = (s.w + kTile - 1) / kTile * kTile;
   s.hp = (int)kmax + 1;
   s.mev = band_mev(lam, g->dx, P);
@@ -244,6 +251,8 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
 
 }  // namespace
 
+int render_ensure_device() { return ensure_device(); }
+
 extern "C" {
 
 int doe_init(void) { return ensure_device(); }
@@ -357,6 +366,24 @@ int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const floa
 }
 
 size_t doe_render_workspace_bytes(int C, int H, int W) { return render_workspace(C, H, W); }
+
+int doe_trace_enable(int max_records) { return trace_enable(max_records) == 0 ? DOE_OK : DOE_ECUDA; }
+
+int doe_trace_read(int max, int* pass_ids, float* ms) {
+  if (max < 0 || (max > 0 && (!pass_ids || !ms))) return DOE_EINVAL;
+  const int n = trace_read(max, pass_ids, ms);
+  return n < 0 ? DOE_ECUDA : n;
+}
+
+const char* doe_pass_name(int id) {
+  static const char* names[TR_COUNT] = {"transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows",
+                                        "pass_c_adjoint_rows", "pass_b_adjoint_columns", "pass_a_adjoint_rows",
+                                        "loss_reduce", "render_rows", "render_columns", "render_output",
+                                        "band_mask"};
+  return (id >= 0 && id < TR_COUNT) ? names[id] : "unknown";
+}
+
+long long doe_launch_count(void) { return launch_count(); }
 
 const char* doe_strerror(int code) {
   switch (code) {

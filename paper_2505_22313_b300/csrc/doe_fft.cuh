@@ -1,9 +1,12 @@
 // doe_fft.cuh -- in-CTA Stockham FFT engine for sm_103a.
 //
-// One CTA transforms one vector of L = 2^LOG complex64 samples (16 <= L <= 16384).  Each of
-// the T = L / E threads keeps E samples in registers; a stage applies E / R radix-R
-// butterflies per thread, and consecutive stages exchange data through shared memory
-// (padded one float2 per 16 to avoid bank conflicts).  The formulation is the self-sorting
+// One CTA transforms one vector of L = 2^LOG complex64 samples (32 <= L <= 16384).  Each of
+// the T = L / 32 threads keeps E = 32 samples in registers; a stage applies E / R radix-R
+// butterflies per thread, always as pairs of adjacent butterflies (j, j + 1), so that every
+// shared-memory and global access moves two samples (16 bytes) at once.  Consecutive stages
+// exchange data through shared memory, addressed in 16-byte chunks with an XOR swizzle
+// (chunk c lives at c ^ ((c >> 4) & 7)) that keeps the strided patterns conflict-free without
+// padding, so an 8192-point vector takes exactly 64 KB.  The formulation is the self-sorting
 // Stockham autosort: stage s with radix R and current sub-transform size Ns reads element
 //     j + r * (L / R)                        (j = butterfly index, r < R)
 // multiplies element r by W_{Ns R}^{r (j mod Ns)}, takes an R-point DFT and writes it to
@@ -29,7 +32,9 @@
 
 namespace doe {
 
-__device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
+// 16-byte chunk swizzle of the exchange buffer, and the float2 slot of element e.
+__device__ __forceinline__ int swz(int c) { return c ^ ((c >> 4) & 7); }
+__device__ __forceinline__ int phys(int e) { return (swz(e >> 1) << 1) | (e & 1); }
 
 // Tables live in static device memory, filled once per device at library set-up.  This header
 // is included by exactly one translation unit (doe_launch.cu), which owns these definitions.
@@ -146,31 +151,36 @@ __device__ __forceinline__ void dft(float2* v) {
 }
 
 // ------------------------------------------------------------------ stages
-template <int L, int E>
-struct FftShape {
+template <int L, int E, bool INV, int S>
+struct St {
   static constexpr int LOG = ilog2c(L);
   static constexpr int T = L / E;
   static constexpr int NST = plan_nst(LOG);
-  static_assert(L >= 16 && L <= (1 << kMaxLog) && (L & (L - 1)) == 0, "L must be a power of two in [16, 16384]");
-  static_assert(E % 16 == 0 || E == L, "E must be a multiple of every radix");
+  static constexpr int R = plan_radix(LOG, INV, S);
+  static constexpr int NS = plan_ns(LOG, INV, S);
+  static constexpr int B = E / R;  // butterflies per thread (even)
+  static_assert(L >= 32 && L <= (1 << kMaxLog) && (L & (L - 1)) == 0, "L must be a power of two in [32, 16384]");
+  static_assert(E == 32 && B % 2 == 0, "butterflies are processed in adjacent pairs");
+  // butterfly index of register group b (b even: first of a pair)
+  __device__ static __forceinline__ int j(int t, int b) { return 2 * (t + (b >> 1) * T) + (b & 1); }
+  // transform index of register b*R + r in this stage's input layout (and, for the last
+  // stage, in its output layout)
+  __device__ static __forceinline__ int idx(int t, int b, int r) { return j(t, b) + r * (L / R); }
 };
 
 // Twiddle + DFT of stage S on registers (inputs already in place).
 template <int L, int E, bool INV, int S>
 __device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
-  using Sh = FftShape<L, E>;
-  constexpr int R = plan_radix(Sh::LOG, INV, S);
-  constexpr int NS = plan_ns(Sh::LOG, INV, S);
-  constexpr int B = E / R;
+  using X = St<L, E, INV, S>;
+  constexpr int R = X::R;
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
+  for (int b = 0; b < X::B; ++b) {
     if constexpr (S > 0) {
-      const int j = t + b * Sh::T;
-      const int k = j & (NS - 1);
-      const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(Sh::LOG, INV, S) + (long)k * R);
+      const int k = X::j(t, b) & (X::NS - 1);
+      const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(X::LOG, INV, S) + (long)k * R);
 #pragma unroll
       for (int r = 0; r < R; r += 2) {
-        float4 w = __ldg(tw + r / 2);
+        const float4 w = __ldg(tw + r / 2);
         if (r > 0) v[b * R + r] = ctw<INV>(v[b * R + r], make_float2(w.x, w.y));
         v[b * R + r + 1] = ctw<INV>(v[b * R + r + 1], make_float2(w.z, w.w));
       }
@@ -179,45 +189,61 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
   }
 }
 
-// Write stage S's outputs to shared memory in Stockham order.
+// Write stage S's outputs to shared memory in Stockham order, 16 bytes per access.
 template <int L, int E, bool INV, int S>
 __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2* sm) {
-  using Sh = FftShape<L, E>;
-  constexpr int R = plan_radix(Sh::LOG, INV, S);
-  constexpr int NS = plan_ns(Sh::LOG, INV, S);
-  constexpr int B = E / R;
+  using X = St<L, E, INV, S>;
+  constexpr int R = X::R, NS = X::NS;
+  float4* s4 = reinterpret_cast<float4*>(sm);
+  if constexpr (NS == 1) {
+    // butterfly j's outputs are the contiguous elements j R + r
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = t + b * Sh::T;
-    const int k = j & (NS - 1);
-    const int base = (j - k) * R + k;
+    for (int b = 0; b < X::B; ++b) {
+      const int c0 = X::j(t, b) * (R / 2);
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[phys(base + r * NS)] = v[b * R + r];
+      for (int r = 0; r < R; r += 2)
+        s4[swz(c0 + r / 2)] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
+    }
+  } else {
+    // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns
+#pragma unroll
+    for (int b = 0; b < X::B; b += 2) {
+      const int jj = X::j(t, b);
+      const int k = jj & (NS - 1);
+      const int c0 = ((jj - k) * R + k) >> 1;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        s4[swz(c0 + r * (NS / 2))] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
+    }
   }
 }
 
-// Read stage S's inputs ("j + r L/R") from shared memory.
+// Read stage S's inputs ("j + r L/R") from shared memory, 16 bytes per access.
 template <int L, int E, bool INV, int S>
 __device__ __forceinline__ void stage_load(float2 (&v)[E], int t, const float2* sm) {
-  using Sh = FftShape<L, E>;
-  constexpr int R = plan_radix(Sh::LOG, INV, S);
-  constexpr int B = E / R;
+  using X = St<L, E, INV, S>;
+  constexpr int R = X::R;
+  const float4* s4 = reinterpret_cast<const float4*>(sm);
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = t + b * Sh::T;
+  for (int b = 0; b < X::B; b += 2) {
+    const int c0 = X::j(t, b) >> 1;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b * R + r] = sm[phys(j + r * (L / R))];
+    for (int r = 0; r < R; ++r) {
+      const float4 q = s4[swz(c0 + r * (L / R / 2))];
+      v[b * R + r] = make_float2(q.x, q.y);
+      v[(b + 1) * R + r] = make_float2(q.z, q.w);
+    }
   }
 }
 
 // Runs stages S..NST-1: on entry v holds stage S's inputs; on exit v holds the final outputs
-// in the last stage's layout (element j + r L/R_last of the transform).  Stages exchange through
-// sm, each exchange preceded by a barrier, so sm may still be read by other threads on entry.
+// in the last stage's layout (element St<...,NST-1>::idx(t, b, r) of the transform).  Stages
+// exchange through sm, each exchange preceded by a barrier, so sm may still be read by other
+// threads on entry.
 template <int L, int E, bool INV, int S = 0>
 __device__ __forceinline__ void fft_run(float2 (&v)[E], int t, float2* sm) {
-  using Sh = FftShape<L, E>;
   stage_compute<L, E, INV, S>(v, t);
-  if constexpr (S + 1 < Sh::NST) {
+  if constexpr (S + 1 < St<L, E, INV, S>::NST) {
     __syncthreads();
     stage_store<L, E, INV, S>(v, t, sm);
     __syncthreads();
@@ -226,18 +252,12 @@ __device__ __forceinline__ void fft_run(float2 (&v)[E], int t, float2* sm) {
   }
 }
 
-// Index (within the transform) held by register b*R + r in the first stage's layout.
-template <int L, int E, bool INV>
-__device__ __forceinline__ int first_index(int t, int b, int r) {
-  constexpr int R = plan_radix(FftShape<L, E>::LOG, INV, 0);
-  return t + b * FftShape<L, E>::T + r * (L / R);
-}
-// Index held by register b*R + r after the last stage.
-template <int L, int E, bool INV>
-__device__ __forceinline__ int last_index(int t, int b, int r) {
-  constexpr int R = plan_radix(FftShape<L, E>::LOG, INV, FftShape<L, E>::NST - 1);
-  return t + b * FftShape<L, E>::T + r * (L / R);
-}
-
+// Layout helpers for the kernels: the first stage's input layout and the last stage's output
+// layout.  Register b*R + r holds transform element idx(t, b, r); registers (b, r) and
+// (b + 1, r) for even b hold the adjacent elements e, e + 1.
+template <int L, bool INV>
+using First = St<L, 32, INV, 0>;
+template <int L, bool INV>
+using Last = St<L, 32, INV, plan_nst(ilog2c(L)) - 1>;
 
 }  // namespace doe

@@ -95,18 +95,19 @@ __device__ __forceinline__ float2 transmittance(float hv, float kp_hi, float kp_
   return make_float2(cs, sn);
 }
 
-// Column position in the stored (band-compacted) spectrum of frequency index k in [0, P),
-// or -1 if k is outside the band.  With the band limit active the stored order is
-// k = 0..kmax, then k = P-kmax..P-1 (FFT order with the out-of-band middle removed).
-__device__ __forceinline__ int band_pos(int k, int P, int kmax, int w) {
-  if (w == P) return k;
-  if (k <= kmax) return k;
-  if (k >= P - kmax) return k - (P - w);
+// Stored (band-compacted) spectrum rows.  With the band limit active a row keeps the two
+// FFT-order segments [0, seg_a) and [P - (w - seg_a), P), seg_a = kmax + 1 and
+// w - seg_a = kmax, each rounded up to even length so that pairs of adjacent frequencies
+// (k, k + 1), k even, are always stored together at an even (16-byte aligned) position.  The
+// at most two stored entries outside the band (|kt| > kmax) hold zeros.  Without the band
+// limit w = P and positions equal frequency indices.
+__device__ __forceinline__ int band_pos(int k, int P, int seg_a, int w) {
+  if (k < seg_a) return k;
+  if (k >= P - (w - seg_a)) return k - (P - w);
   return -1;
 }
-__device__ __forceinline__ int pos_to_k(int pos, int P, int kmax, int w) {
-  if (w == P || pos <= kmax) return pos;
-  return pos + (P - w);
+__device__ __forceinline__ int pos_to_k(int pos, int P, int seg_a, int w) {
+  return pos < seg_a ? pos : pos + (P - w);
 }
 __device__ __forceinline__ int abs_signed(int k, int P) { return k < P / 2 ? k : P - k; }
 

@@ -13,6 +13,8 @@
 //          rows [off, off + N) -> buf rows [0, N)                                           (J2)
 //   A*     per DOE row i: row IFFT, crop to the DOE window, -2 k' Im(conj(g) E_doe), summed
 //          over the wavelengths of the request -> grad_h row i
+// Every transform uses the in-CTA engine of doe_fft.cuh (32 samples per thread, adjacent
+// pairs); global rows are read and written as 16-byte pairs of adjacent samples.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -35,41 +37,79 @@ __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch
   }
 }
 
-// ------------------------------------------------------------------ pass A: DOE rows
+// Writes the stored band positions of a spectrum held in the last-stage layout of a forward
+// row FFT (entries outside the band, at most one per segment, are written as zeros).
 template <int L>
-__global__ void __launch_bounds__(L / elems_for(L)) pass_a_kernel(const __grid_constant__ Batch bt) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int R0 = first_radix<L, false>(), B0 = E / R0;
-  constexpr int RL = last_radix<L, false>(), BL = E / RL;
+__device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, float2* row, const Slice& sl) {
+  using G = Last<L, false>;
+  float4* dst = reinterpret_cast<float4*>(row);
+#pragma unroll
+  for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) {
+      const int k = G::idx(t, b, r);
+      const int pos = band_pos(k, L, sl.seg_a, sl.w);
+      if (pos >= 0) {
+        float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
+        if (abs_signed(k, L) > sl.kmax) a = make_float2(0.f, 0.f);
+        if (abs_signed(k + 1, L) > sl.kmax) c = make_float2(0.f, 0.f);
+        dst[pos >> 1] = make_float4(a.x, a.y, c.x, c.y);
+      }
+    }
+}
+
+// Loads a stored band row into the first-stage registers of a row IFFT (16-byte pairs).
+template <int L>
+__device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const float2* src, const Slice& sl) {
+  using F = First<L, true>;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < F::R; ++r) {
+      const int pos = band_pos(F::idx(t, b, r), L, sl.seg_a, sl.w);
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (pos >= 0) q = s4[pos >> 1];
+      v[b * F::R + r] = make_float2(q.x, q.y);
+      v[(b + 1) * F::R + r] = make_float2(q.z, q.w);
+    }
+}
+
+// ------------------------------------------------------------------ pass A: DOE rows
+// One CTA per (DOE row i, slice).  The first stage's register pairs are adjacent padded
+// columns x, x + 1 (x even; the DOE offset is even), loaded as one float2 of heights.
+template <int L>
+__global__ void __launch_bounds__(L / 32) pass_a_kernel(const __grid_constant__ Batch bt) {
+  using F = First<L, false>;
   extern __shared__ float2 sm[];
   const Slice& sl = bt.s[blockIdx.y];
   const int i = blockIdx.x;
   const int t = threadIdx.x;
   const int N = bt.N, off = bt.off;
   const float* hrow = sl.h + (size_t)i * N;
-  const float2* erow = sl.e_in ? sl.e_in + (size_t)i * N : nullptr;
-  float2 v[E];
+  const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+  float2 v[32];
 #pragma unroll
-  for (int b = 0; b < B0; ++b)
+  for (int b = 0; b < F::B; b += 2)
 #pragma unroll
-    for (int r = 0; r < R0; ++r) {
-      const int x = t + b * T + r * (L / R0) - off;
-      float2 val = make_float2(0.f, 0.f);
+    for (int r = 0; r < F::R; ++r) {
+      const int x = F::idx(t, b, r) - off;  // even
+      float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
       if ((unsigned)x < (unsigned)N) {
-        val = transmittance(__ldg(hrow + x), sl.kp_hi, sl.kp_lo);
-        if (erow) val = cmul(val, erow[x]);
+        const float2 hv = __ldg(reinterpret_cast<const float2*>(hrow + x));
+        a = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+        c = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+        if (erow) {
+          const float4 ev = erow[x >> 1];
+          a = cmul(a, make_float2(ev.x, ev.y));
+          c = cmul(c, make_float2(ev.z, ev.w));
+        }
       }
-      v[b * R0 + r] = val;
+      v[b * F::R + r] = a;
+      v[(b + 1) * F::R + r] = c;
     }
-  fft_run<L, E, false>(v, t, sm);
-  float2* dst = sl.buf + (size_t)i * sl.wp;
-#pragma unroll
-  for (int b = 0; b < BL; ++b)
-#pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const int pos = band_pos(t + b * T + r * (L / RL), L, sl.kmax, sl.w);
-      if (pos >= 0) dst[pos] = v[b * RL + r];
-    }
+  fft_run<L, 32, false>(v, t, sm);
+  store_band_row<L>(v, t, sl.buf + (size_t)i * sl.wp, sl);
 }
 
 // ------------------------------------------------------------------ pass B / B*: columns
@@ -79,12 +119,12 @@ __global__ void __launch_bounds__(L / elems_for(L)) pass_a_kernel(const __grid_c
 // memory (distributed shared memory), and after the transforms gathers a quarter of the
 // output rows from all four CTAs.
 template <int L>
-__global__ void __launch_bounds__(L / elems_for(L)) pass_b_kernel(const __grid_constant__ Batch bt) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int RF = last_radix<L, false>(), BF = E / RF;  // forward's last = inverse's first (16)
-  constexpr int RL = last_radix<L, true>(), BL = E / RL;
+__global__ void __launch_bounds__(L / 32) pass_b_kernel(const __grid_constant__ Batch bt) {
+  using G = Last<L, false>;  // forward's last stage = inverse's first stage (radix 16)
+  using H = Last<L, true>;
+  constexpr int T = L / 32;
   constexpr int F4 = kTile / 2;
-  static_assert(last_radix<L, false>() == first_radix<L, true>(), "register hand-off needs equal radices");
+  static_assert(G::R == First<L, true>::R, "register hand-off needs equal radices");
   extern __shared__ float2 sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
@@ -99,6 +139,8 @@ __global__ void __launch_bounds__(L / elems_for(L)) pass_b_kernel(const __grid_c
   const int N = bt.N, off = bt.off;
   const int nin = adj ? L : N, yin0 = adj ? 0 : off;     // input rows (padded coordinates)
   const int nout = adj ? N : L, yout0 = adj ? off : 0;   // output rows (padded coordinates)
+  const int kcol = pos_to_k(mypos, L, sl.seg_a, sl.w);
+  const bool live = mypos < sl.w && abs_signed(kcol, L) <= sl.kmax;
 
   for (int y = t; y < L; y += T)
     if (y < yin0 || y >= yin0 + nin) sm[phys(y)] = make_float2(0.f, 0.f);
@@ -110,28 +152,23 @@ __global__ void __launch_bounds__(L / elems_for(L)) pass_b_kernel(const __grid_c
     for (int idx = t; idx < rows * F4; idx += T) {
       const int rr = rbeg + idx / F4, f = idx % F4;
       const float4 val = *reinterpret_cast<const float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f);
-      float2 a = make_float2(val.x, val.y), b = make_float2(val.z, val.w);
-      if (pos0 + 2 * f >= sl.w) a = make_float2(0.f, 0.f);
-      if (pos0 + 2 * f + 1 >= sl.w) b = make_float2(0.f, 0.f);
-      rsm[2 * f][phys(yin0 + rr)] = a;
-      rsm[2 * f + 1][phys(yin0 + rr)] = b;
+      rsm[2 * f][phys(yin0 + rr)] = make_float2(val.x, val.y);
+      rsm[2 * f + 1][phys(yin0 + rr)] = make_float2(val.z, val.w);
     }
   }
   cl.sync();
 
-  float2 v[E];
-  stage_load<L, E, false, 0>(v, t, sm);
-  fft_run<L, E, false>(v, t, sm);
+  float2 v[32];
+  stage_load<L, 32, false, 0>(v, t, sm);
+  fft_run<L, 32, false>(v, t, sm);
   {
-    const int bq = abs_signed(pos_to_k(mypos, L, sl.kmax, sl.w), L);
-    const bool live = mypos < sl.w;
-    const float2* hrow = sl.htab + (size_t)bq * sl.hp;
+    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, L) * sl.hp;
 #pragma unroll
-    for (int b = 0; b < BF; ++b)
+    for (int b = 0; b < G::B; ++b)
 #pragma unroll
-      for (int r = 0; r < RF; ++r) {
-        const int a = abs_signed(t + b * T + r * (L / RF), L);
-        float2& x = v[b * RF + r];
+      for (int r = 0; r < G::R; ++r) {
+        const int a = abs_signed(G::idx(t, b, r), L);
+        float2& x = v[b * G::R + r];
         if (live && a <= sl.kmax) {
           const float2 hv = hrow[a];
           x = adj ? cmulc(x, hv) : cmul(x, hv);
@@ -140,12 +177,18 @@ __global__ void __launch_bounds__(L / elems_for(L)) pass_b_kernel(const __grid_c
         }
       }
   }
-  fft_run<L, E, true>(v, t, sm);
+  fft_run<L, 32, true>(v, t, sm);
   __syncthreads();
+  {
+    float4* s4 = reinterpret_cast<float4*>(sm);
 #pragma unroll
-  for (int b = 0; b < BL; ++b)
+    for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-    for (int r = 0; r < RL; ++r) sm[phys(t + b * T + r * (L / RL))] = v[b * RL + r];
+      for (int r = 0; r < H::R; ++r) {
+        const float2 a = v[b * H::R + r], c = v[(b + 1) * H::R + r];
+        s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
+      }
+  }
   cl.sync();
   {
     const int rows = nout / kTile, rbeg = q * rows;
@@ -159,48 +202,36 @@ __global__ void __launch_bounds__(L / elems_for(L)) pass_b_kernel(const __grid_c
   cl.sync();
 }
 
-// Loads a stored band row into the first-stage registers of a row IFFT.
-template <int L>
-__device__ __forceinline__ void load_band_row(float2 (&v)[elems_for(L)], int t, const float2* src, const Slice& sl) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int R0 = first_radix<L, true>(), B0 = E / R0;
-#pragma unroll
-  for (int b = 0; b < B0; ++b)
-#pragma unroll
-    for (int r = 0; r < R0; ++r) {
-      const int pos = band_pos(t + b * T + r * (L / R0), L, sl.kmax, sl.w);
-      v[b * R0 + r] = pos >= 0 ? src[pos] : make_float2(0.f, 0.f);
-    }
-}
-
 // ------------------------------------------------------------------ pass C: output rows
 template <int L>
-__global__ void __launch_bounds__(L / elems_for(L)) pass_c_kernel(const __grid_constant__ Batch bt) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int RL = last_radix<L, true>(), BL = E / RL;
+__global__ void __launch_bounds__(L / 32) pass_c_kernel(const __grid_constant__ Batch bt) {
+  using H = Last<L, true>;
   extern __shared__ float2 sm[];
   const Slice& sl = bt.s[blockIdx.y];
   const int y = blockIdx.x;
   const int t = threadIdx.x;
-  float2 v[E];
+  float2 v[32];
   load_band_row<L>(v, t, sl.buf + (size_t)y * sl.wp, sl);
-  fft_run<L, E, true>(v, t, sm);
+  fft_run<L, 32, true>(v, t, sm);
   const float s = bt.inv_p2;
   if (bt.mode == OUT_PSF) {
-    float* dst = static_cast<float*>(sl.out) + (size_t)y * L;
+    float2* dst = reinterpret_cast<float2*>(static_cast<float*>(sl.out) + (size_t)y * L);
 #pragma unroll
-    for (int b = 0; b < BL; ++b)
+    for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const float2 e = cscale(v[b * RL + r], s);
-        dst[t + b * T + r * (L / RL)] = fmaf(e.x, e.x, e.y * e.y);
+      for (int r = 0; r < H::R; ++r) {
+        const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
+        dst[H::idx(t, b, r) >> 1] = make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(c.x, c.x, c.y * c.y));
       }
   } else {
-    float2* dst = static_cast<float2*>(sl.out) + (size_t)y * L;
+    float4* dst = reinterpret_cast<float4*>(static_cast<float2*>(sl.out) + (size_t)y * L);
 #pragma unroll
-    for (int b = 0; b < BL; ++b)
+    for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) dst[t + b * T + r * (L / RL)] = cscale(v[b * RL + r], s);
+      for (int r = 0; r < H::R; ++r) {
+        const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
+        dst[H::idx(t, b, r) >> 1] = make_float4(a.x, a.y, c.x, c.y);
+      }
   }
 }
 
@@ -237,94 +268,97 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
 
 // ------------------------------------------------------------------ pass C': adjoint rows
 template <int L>
-__global__ void __launch_bounds__(L / elems_for(L)) pass_c_adj_kernel(const __grid_constant__ Batch bt) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int RL = last_radix<L, true>(), BL = E / RL;
-  constexpr int RF = last_radix<L, false>(), BF = E / RF;
-  static_assert(last_radix<L, true>() == first_radix<L, false>(), "register hand-off needs equal radices");
+__global__ void __launch_bounds__(L / 32) pass_c_adj_kernel(const __grid_constant__ Batch bt) {
+  using H = Last<L, true>;
+  static_assert(H::R == First<L, false>::R, "register hand-off needs equal radices");
   extern __shared__ float2 sm[];
   __shared__ double red[32];
   const Slice& sl = bt.s[blockIdx.y];
   const int y = blockIdx.x;
   const int t = threadIdx.x;
   float2* row = sl.buf + (size_t)y * sl.wp;
-  float2 v[E];
+  float2 v[32];
   load_band_row<L>(v, t, row, sl);
-  fft_run<L, E, true>(v, t, sm);
+  fft_run<L, 32, true>(v, t, sm);
   const float s = bt.inv_p2;
-  const float* trow = sl.tgt + (size_t)y * L;
+  const float2* trow = reinterpret_cast<const float2*>(sl.tgt + (size_t)y * L);
   float acc = 0.f;
 #pragma unroll
-  for (int b = 0; b < BL; ++b)
+  for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const float2 e = cscale(v[b * RL + r], s);
-      const float tv = __ldg(trow + t + b * T + r * (L / RL));
-      float w;
-      if (bt.mode == GRAD_L2) {
-        const float d = fmaf(e.x, e.x, e.y * e.y) - tv;
-        acc = fmaf(d, d, acc);
-        w = 2.f * d;
-      } else {
-        w = tv;
+    for (int r = 0; r < H::R; ++r) {
+      const float2 tv = __ldg(trow + (H::idx(t, b, r) >> 1));
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float2 e = cscale(v[(b + u) * H::R + r], s);
+        const float tt = u ? tv.y : tv.x;
+        float w;
+        if (bt.mode == GRAD_L2) {
+          const float d = fmaf(e.x, e.x, e.y * e.y) - tt;
+          acc = fmaf(d, d, acc);
+          w = 2.f * d;
+        } else {
+          w = tt;
+        }
+        v[(b + u) * H::R + r] = cscale(e, w);
       }
-      v[b * RL + r] = cscale(e, w);
     }
-  fft_run<L, E, false>(v, t, sm);
+  fft_run<L, 32, false>(v, t, sm);
   // the row is re-written in place: every thread has finished reading it before fft_run's
-  // first barrier, and the band positions written are the ones read
-#pragma unroll
-  for (int b = 0; b < BF; ++b)
-#pragma unroll
-    for (int r = 0; r < RF; ++r) {
-      const int pos = band_pos(t + b * T + r * (L / RF), L, sl.kmax, sl.w);
-      if (pos >= 0) row[pos] = v[b * RF + r];
-    }
-  const double tot = block_sum<T>((double)acc, red);
+  // first barrier, and the stored positions written are the ones read
+  store_band_row<L>(v, t, row, sl);
+  const double tot = block_sum<L / 32>((double)acc, red);
   if (t == 0 && sl.loss_part) sl.loss_part[y] = tot;
 }
 
 // ------------------------------------------------------------------ pass A*: DOE-row adjoint
 // One CTA per DOE row; loops over the slices (wavelengths of one request) and sums.
 template <int L>
-__global__ void __launch_bounds__(L / elems_for(L)) pass_a_adj_kernel(const __grid_constant__ Batch bt) {
-  constexpr int E = elems_for(L), T = L / E;
-  constexpr int RL = last_radix<L, true>(), BL = E / RL;
+__global__ void __launch_bounds__(L / 32) pass_a_adj_kernel(const __grid_constant__ Batch bt) {
+  using H = Last<L, true>;
   extern __shared__ float2 sm[];
   const int i = blockIdx.x;
   const int t = threadIdx.x;
   const int N = bt.N, off = bt.off;
-  float acc[E];
+  float acc[32];
 #pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = 0.f;
+  for (int e = 0; e < 32; ++e) acc[e] = 0.f;
   for (int j = 0; j < bt.S; ++j) {
     const Slice& sl = bt.s[j];
-    float2 v[E];
+    float2 v[32];
     load_band_row<L>(v, t, sl.buf + (size_t)i * sl.wp, sl);
-    fft_run<L, E, true>(v, t, sm);
+    fft_run<L, 32, true>(v, t, sm);
     const float* hrow = sl.h + (size_t)i * N;
-    const float2* erow = sl.e_in ? sl.e_in + (size_t)i * N : nullptr;
+    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     const float k2 = -2.f * sl.kp_hi;
 #pragma unroll
-    for (int b = 0; b < BL; ++b)
+    for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const int x = t + b * T + r * (L / RL) - off;
+      for (int r = 0; r < H::R; ++r) {
+        const int x = H::idx(t, b, r) - off;  // even
         if ((unsigned)x < (unsigned)N) {
-          const float2 g = cscale(v[b * RL + r], bt.inv_p2);
-          float2 ed = transmittance(__ldg(hrow + x), sl.kp_hi, sl.kp_lo);
-          if (erow) ed = cmul(ed, erow[x]);
-          acc[b * RL + r] = fmaf(k2, fmaf(g.x, ed.y, -g.y * ed.x), acc[b * RL + r]);
+          const float2 hv = __ldg(reinterpret_cast<const float2*>(hrow + x));
+          float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+          float2 e1 = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          if (erow) {
+            const float4 ev = erow[x >> 1];
+            e0 = cmul(e0, make_float2(ev.x, ev.y));
+            e1 = cmul(e1, make_float2(ev.z, ev.w));
+          }
+          const float2 g0 = cscale(v[b * H::R + r], bt.inv_p2);
+          const float2 g1 = cscale(v[(b + 1) * H::R + r], bt.inv_p2);
+          acc[b * H::R + r] = fmaf(k2, fmaf(g0.x, e0.y, -g0.y * e0.x), acc[b * H::R + r]);
+          acc[(b + 1) * H::R + r] = fmaf(k2, fmaf(g1.x, e1.y, -g1.y * e1.x), acc[(b + 1) * H::R + r]);
         }
       }
   }
-  float* grow = bt.grad + (size_t)i * N;
+  float2* grow = reinterpret_cast<float2*>(bt.grad + (size_t)i * N);
 #pragma unroll
-  for (int b = 0; b < BL; ++b)
+  for (int b = 0; b < H::B; b += 2)
 #pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const int x = t + b * T + r * (L / RL) - off;
-      if ((unsigned)x < (unsigned)N) grow[x] = acc[b * RL + r];
+    for (int r = 0; r < H::R; ++r) {
+      const int x = H::idx(t, b, r) - off;
+      if ((unsigned)x < (unsigned)N) grow[x >> 1] = make_float2(acc[b * H::R + r], acc[(b + 1) * H::R + r]);
     }
 }
 

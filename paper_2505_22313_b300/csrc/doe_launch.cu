@@ -1,9 +1,72 @@
 // doe_launch.cu -- the single device translation unit: twiddle tables, every instantiation of
 // the passes for L = 16 .. 16384, and their launchers.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
 #include "doe_kernels.cuh"
 #include "doe_launch.h"
+#include "doe_render.cuh"
 
 namespace doe {
+
+// ------------------------------------------------------------------ tracing
+// When enabled, every pass launch is bracketed by two CUDA events recorded on the launching
+// stream; doe_trace_read() later reports each pass's device time.  A launch counter is kept
+// always.  Host-side bookkeeping only: no device memory is allocated.
+namespace {
+std::mutex g_tr_mu;
+std::vector<cudaEvent_t> g_ev;
+std::vector<int> g_tr_pass;
+int g_tr_cap = 0;
+std::atomic<long long> g_launches{0};
+
+struct Traced {
+  int pass;
+  cudaStream_t st;
+  int slot = -1;
+  Traced(int p, cudaStream_t s) : pass(p), st(s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_tr_mu);
+    if (g_tr_cap > 0 && (int)g_tr_pass.size() < g_tr_cap) {
+      slot = (int)g_tr_pass.size();
+      g_tr_pass.push_back(p);
+      cudaEventRecord(g_ev[2 * slot], st);
+    }
+  }
+  ~Traced() {
+    if (slot >= 0) cudaEventRecord(g_ev[2 * slot + 1], st);
+  }
+};
+}  // namespace
+
+int trace_enable(int max_records) {
+  std::lock_guard<std::mutex> lk(g_tr_mu);
+  for (auto e : g_ev) cudaEventDestroy(e);
+  g_ev.clear();
+  g_tr_pass.clear();
+  g_tr_cap = 0;
+  if (max_records <= 0) return 0;
+  g_ev.resize(2 * (size_t)max_records);
+  for (auto& e : g_ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+  g_tr_cap = max_records;
+  return 0;
+}
+
+int trace_read(int max, int* pass_ids, float* ms) {
+  std::lock_guard<std::mutex> lk(g_tr_mu);
+  const int n = (int)g_tr_pass.size() < max ? (int)g_tr_pass.size() : max;
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventSynchronize(g_ev[2 * i + 1]) != cudaSuccess) return -1;
+    pass_ids[i] = g_tr_pass[i];
+    if (cudaEventElapsedTime(&ms[i], g_ev[2 * i], g_ev[2 * i + 1]) != cudaSuccess) return -1;
+  }
+  g_tr_pass.clear();
+  return n;
+}
+
+long long launch_count() { return g_launches.load(); }
 
 cudaError_t upload_tables(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big) {
   cudaError_t e = cudaMemcpyToSymbol(g_tw, stage_tw, n_stage * sizeof(float2));
@@ -15,11 +78,10 @@ namespace {
 template <int L>
 constexpr size_t smem_bytes() { return (size_t)smem_words(L) * sizeof(float2); }
 template <int L>
-constexpr int threads() { return L / elems_for(L); }
+constexpr int threads() { return L / 32; }
 
 #define DOE_DISPATCH(lg, fn, ...)                   \
   switch (lg) {                                     \
-    case 4: return fn<16>(__VA_ARGS__);             \
     case 5: return fn<32>(__VA_ARGS__);             \
     case 6: return fn<64>(__VA_ARGS__);             \
     case 7: return fn<128>(__VA_ARGS__);            \
@@ -33,25 +95,39 @@ constexpr int threads() { return L / elems_for(L); }
     default: return cudaErrorInvalidValue;          \
   }
 
+// Dynamic shared memory above 48 KB must be opted into, and the carveout preference set to
+// the maximum so that several CTAs of a pass fit on one SM.
+template <typename K>
+cudaError_t prep_one(K* kern, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
 template <int L>
 cudaError_t prep_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<L>();
-  if ((e = cudaFuncSetAttribute(pass_a_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb))) return e;
-  if ((e = cudaFuncSetAttribute(pass_b_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb))) return e;
-  if ((e = cudaFuncSetAttribute(pass_c_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb))) return e;
-  if ((e = cudaFuncSetAttribute(pass_c_adj_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb))) return e;
-  if ((e = cudaFuncSetAttribute(pass_a_adj_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb))) return e;
+  if ((e = prep_one(pass_a_kernel<L>, sb))) return e;
+  if ((e = prep_one(pass_b_kernel<L>, sb))) return e;
+  if ((e = prep_one(pass_c_kernel<L>, sb))) return e;
+  if ((e = prep_one(pass_c_adj_kernel<L>, sb))) return e;
+  if ((e = prep_one(pass_a_adj_kernel<L>, sb))) return e;
+  if ((e = prep_one(render_rows_kernel<L>, sb))) return e;
+  if constexpr (L <= kRenderColsMax)  // two L-sample buffers must fit one CTA's shared memory
+    if ((e = prep_one(render_cols_kernel<L>, 2 * sb))) return e;
+  if ((e = prep_one(render_out_kernel<L>, sb))) return e;
   return cudaSuccess;
 }
 
 template <int L>
 cudaError_t pass_a_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_PASS_A, st);
   pass_a_kernel<L><<<dim3(bt.N, bt.S), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
 template <int L>
 cudaError_t pass_b_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(bt.total_tiles * kTile);
   cfg.blockDim = dim3(threads<L>());
@@ -70,24 +146,68 @@ cudaError_t pass_b_t(const Batch& bt, cudaStream_t st) {
 }
 template <int L>
 cudaError_t pass_c_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_PASS_C, st);
   pass_c_kernel<L><<<dim3(bt.P, bt.S), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
 template <int L>
 cudaError_t pass_c_adj_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_PASS_C_ADJ, st);
   pass_c_adj_kernel<L><<<dim3(bt.P, bt.S), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
 template <int L>
 cudaError_t pass_a_adj_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_PASS_A_ADJ, st);
   pass_a_adj_kernel<L><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
+template <int L>
+cudaError_t render_rows_t(const RenderArgs& ra, cudaStream_t st) {
+  Traced tr(TR_RENDER_ROWS, st);
+  render_rows_kernel<L><<<dim3(ra.H, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  return cudaGetLastError();
+}
+template <int L>
+cudaError_t render_cols_t(const RenderArgs& ra, cudaStream_t st) {
+  if constexpr (L > kRenderColsMax) return cudaErrorInvalidValue;
+  Traced tr(TR_RENDER_COLS, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ra.C * (ra.wpr / kTile) * kTile);
+  cfg.blockDim = dim3(threads<L>());
+  cfg.dynamicSmemBytes = 2 * smem_bytes<L>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kTile;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, render_cols_kernel<L>, ra);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template <int L>
+cudaError_t render_out_t(const RenderArgs& ra, cudaStream_t st) {
+  Traced tr(TR_RENDER_OUT, st);
+  render_out_kernel<L><<<dim3(ra.H / 2, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  return cudaGetLastError();
+}
+int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 }  // namespace
+
+cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st) {
+  cudaError_t e;
+  const int lw = ilog2i(2 * ra.W), lh = ilog2i(2 * ra.H);
+  if ((e = [&]() -> cudaError_t { DOE_DISPATCH(lw, render_rows_t, ra, st); }())) return e;
+  if ((e = [&]() -> cudaError_t { DOE_DISPATCH(lh, render_cols_t, ra, st); }())) return e;
+  return [&]() -> cudaError_t { DOE_DISPATCH(lw, render_out_t, ra, st); }();
+}
 
 cudaError_t prepare_kernels() {
   cudaError_t e;
-  if ((e = prep_t<16>()) || (e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
+  if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
       (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()))
     return e;
@@ -95,6 +215,7 @@ cudaError_t prepare_kernels() {
 }
 
 cudaError_t launch_htab(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_HTAB, st);
   htab_kernel<<<dim3(bt.max_kmax + 1, bt.S), 256, 0, st>>>(bt);
   return cudaGetLastError();
 }
@@ -104,10 +225,12 @@ cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPAT
 cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_c_adj_t, bt, st); }
 cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_a_adj_t, bt, st); }
 cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st) {
+  Traced tr(TR_LOSS, st);
   loss_reduce_kernel<<<1, 1024, 0, st>>>(bt, loss);
   return cudaGetLastError();
 }
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st) {
+  Traced tr(TR_MASK, st);
   band_mask_kernel<<<bt.P, 256, 0, st>>>(bt, mask);
   return cudaGetLastError();
 }

@@ -7,7 +7,7 @@
 namespace doe {
 
 
-constexpr int kMinLog = 4;   // L = 16
+constexpr int kMinLog = 5;   // L = 32
 constexpr int kMaxLog = 14;  // L = 16384 (one CTA)
 constexpr int kBigLog = 16;  // 65536-point table for the cross-CTA (four-step) twiddles
 
@@ -36,16 +36,17 @@ __host__ __device__ constexpr long tw_offset(int lg, bool inv, int s) {
 constexpr long kTwTotal = tw_offset(kMaxLog + 1, false, 0);
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
-__host__ __device__ constexpr int smem_words(int L) { return L + (L >> 4); }
+__host__ __device__ constexpr int smem_words(int L) { return L; }
 
 // Elements per thread used for a transform of length L.
-__host__ __device__ constexpr int elems_for(int L) { return L <= 8192 ? 16 : 32; }
+__host__ __device__ constexpr int elems_for(int) { return 32; }
 template <int L, bool INV>
 __host__ __device__ constexpr int first_radix() { return plan_radix(ilog2c(L), INV, 0); }
 template <int L, bool INV>
 __host__ __device__ constexpr int last_radix() { return plan_radix(ilog2c(L), INV, plan_nst(ilog2c(L)) - 1); }
 
 constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
+constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
 constexpr int kTile = 4;        // columns per column-pass cluster: 4 x 8 B = one 32-byte sector
 
 // One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
@@ -64,7 +65,8 @@ struct Slice {
   float th0_hi, th0_lo;    // (2 pi z / lambda) mod 2 pi
   long long mev;         // propagating iff kt^2 + lt^2 < mev
   int kmax;              // band limit index per axis
-  int w;                 // stored columns: P if the band limit is inactive, else 2 kmax + 1
+  int seg_a;             // length of the stored non-negative-frequency segment (even)
+  int w;                 // stored columns: P if the band limit is inactive, else seg_a + even(kmax)
   int wp;                // row pitch of buf (w rounded up to kTile)
   int hp;                // row pitch of htab (kmax + 1)
   int tile_begin;        // first global column-tile index of this slice (column pass)

@@ -1,0 +1,233 @@
+// doe_render.cuh -- image formation by PSF convolution (the imaging application's model
+// behind Eq. 9): out_c = img_c (*) k_c, linear convolution with zero boundary and a "same"
+// output window, computed with 2H x 2W transforms and real-data packing:
+//   R1  per image row u (channel c): z = img_c[u] + i k_c[u] (both real, zero-padded to 2W),
+//       one complex FFT of length 2W, then the two real spectra are separated in the CTA,
+//       X_img[k] = (Z[k] + conj Z[2W-k]) / 2, X_k[k] = (Z[k] - conj Z[2W-k]) / (2i), k <= W,
+//       and written to SA, SB ([H][wpr] complex).  The crop k_c is read straight from the PSF
+//       around the optical axis; its row sums go to ksum[c][u] (FP64).
+//   R2  per column k <= W (4-column cluster, as the propagation's column pass): column FFTs of
+//       SA and SB (zero-padded to 2H), product, column IFFT, rows [H/2, 3H/2) -> SA in place.
+//   R3  per pair of output rows: the two Hermitian half spectra are packed as X0 + i X1,
+//       extended to 2W by conjugate symmetry, one complex IFFT, real part = row y, imaginary
+//       part = row y + 1, window [W/2, 3W/2), scaled by 1 / (4 H W sum(k_c)).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "doe_internal.cuh"
+#include "doe_render_args.h"
+
+namespace doe {
+
+
+
+// R1: one CTA per (row u, channel c); transform length L = 2W.
+template <int L>
+__global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_constant__ RenderArgs ra) {
+  using F = First<L, false>;
+  using G = Last<L, false>;
+  constexpr int T = L / 32;
+  extern __shared__ float2 sm[];
+  __shared__ double red[32];
+  const int u = blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+  const int W = ra.W, H = ra.H;
+  const float* irow = ra.img + ((size_t)c * H + u) * W;
+  const float* krow = ra.psf + ((size_t)c * ra.Py + (ra.Py / 2 - H / 2 + u)) * ra.Px + (ra.Px / 2 - W / 2);
+  float2 v[32];
+  double ks = 0.0;
+#pragma unroll
+  for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < F::R; ++r) {
+      const int n = F::idx(t, b, r);  // even
+      float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+      if (n < W) {
+        const float2 iv = __ldcs(reinterpret_cast<const float2*>(irow + n));
+        const float2 kv = __ldcs(reinterpret_cast<const float2*>(krow + n));
+        a = make_float2(iv.x, kv.x);
+        d = make_float2(iv.y, kv.y);
+        ks += (double)kv.x + (double)kv.y;
+      }
+      v[b * F::R + r] = a;
+      v[(b + 1) * F::R + r] = d;
+    }
+  fft_run<L, 32, false>(v, t, sm);
+  __syncthreads();
+  float4* s4 = reinterpret_cast<float4*>(sm);
+#pragma unroll
+  for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) {
+      const float2 a = v[b * G::R + r], d = v[(b + 1) * G::R + r];
+      s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+    }
+  __syncthreads();
+  float2* sa = ra.sa + ((size_t)c * H + u) * ra.wpr;
+  float2* sb = ra.sb + ((size_t)c * H + u) * ra.wpr;
+  for (int k = t; k <= W; k += T) {
+    const float2 zk = sm[phys(k)];
+    const float2 zm = sm[phys((L - k) & (L - 1))];
+    // X_img = (Z[k] + conj Z[-k]) / 2, X_k = (Z[k] - conj Z[-k]) / (2i)
+    sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+  const double tot = block_sum<T>(ks, red);
+  if (t == 0) ra.ksum[(size_t)c * H + u] = tot;
+}
+
+// R2: cluster of kTile CTAs per 4 adjacent columns of one channel; transform length L = 2H.
+// Shared memory: two L-sample buffers (the image column and the kernel column).
+template <int L>
+__global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
+  using G = Last<L, false>;
+  using Hh = Last<L, true>;
+  constexpr int T = L / 32;
+  constexpr int F4 = kTile / 2;
+  extern __shared__ float2 sm[];
+  float2* sma = sm;
+  float2* smb = sm + L;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int t = threadIdx.x;
+  const int H = ra.H;
+  const int tiles = ra.wpr / kTile;
+  const int tile = (blockIdx.x / kTile) % tiles;
+  const int c = (blockIdx.x / kTile) / tiles;
+  const int pos0 = tile * kTile;
+  float2* baseA = ra.sa + (size_t)c * H * ra.wpr;
+  float2* baseB = ra.sb + (size_t)c * H * ra.wpr;
+  for (int y = H + t; y < L; y += T) {
+    sma[phys(y)] = make_float2(0.f, 0.f);
+    smb[phys(y)] = make_float2(0.f, 0.f);
+  }
+  float2* rsa[kTile];
+  float2* rsb[kTile];
+#pragma unroll
+  for (int cc = 0; cc < kTile; ++cc) {
+    rsa[cc] = cl.map_shared_rank(sma, cc);
+    rsb[cc] = cl.map_shared_rank(smb, cc);
+  }
+  {
+    const int rows = H / kTile, rbeg = q * rows;
+    for (int idx = t; idx < rows * F4; idx += T) {
+      const int rr = rbeg + idx / F4, f = idx % F4;
+      float4 va = __ldcs(reinterpret_cast<const float4*>(baseA + (size_t)rr * ra.wpr + pos0 + 2 * f));
+      float4 vb = __ldcs(reinterpret_cast<const float4*>(baseB + (size_t)rr * ra.wpr + pos0 + 2 * f));
+      if (pos0 + 2 * f > ra.W) va = vb = make_float4(0.f, 0.f, 0.f, 0.f);  // columns past W are unused
+      rsa[2 * f][phys(rr)] = make_float2(va.x, va.y);
+      rsa[2 * f + 1][phys(rr)] = make_float2(va.z, va.w);
+      rsb[2 * f][phys(rr)] = make_float2(vb.x, vb.y);
+      rsb[2 * f + 1][phys(rr)] = make_float2(vb.z, vb.w);
+    }
+  }
+  cl.sync();
+  float2 v[32];
+  // spectrum of the image column, kept in sma at its own register positions
+  stage_load<L, 32, false, 0>(v, t, sma);
+  fft_run<L, 32, false>(v, t, sma);
+  __syncthreads();
+  {
+    float4* s4 = reinterpret_cast<float4*>(sma);
+#pragma unroll
+    for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) {
+        const float2 a = v[b * G::R + r], d = v[(b + 1) * G::R + r];
+        s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+      }
+  }
+  // spectrum of the kernel column, times the image spectrum (same thread, same positions)
+  stage_load<L, 32, false, 0>(v, t, smb);
+  fft_run<L, 32, false>(v, t, smb);
+  {
+    const float4* s4 = reinterpret_cast<const float4*>(sma);
+#pragma unroll
+    for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) {
+        const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
+        v[b * G::R + r] = cmul(v[b * G::R + r], make_float2(a.x, a.y));
+        v[(b + 1) * G::R + r] = cmul(v[(b + 1) * G::R + r], make_float2(a.z, a.w));
+      }
+  }
+  fft_run<L, 32, true>(v, t, smb);
+  __syncthreads();
+  {
+    float4* s4 = reinterpret_cast<float4*>(smb);
+#pragma unroll
+    for (int b = 0; b < Hh::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < Hh::R; ++r) {
+        const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
+        s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+      }
+  }
+  cl.sync();
+  {
+    // rows [H/2, 3H/2) of the column IFFT -> SA rows [0, H)
+    const int rows = H / kTile, rbeg = q * rows;
+    for (int idx = t; idx < rows * F4; idx += T) {
+      const int rr = rbeg + idx / F4, f = idx % F4;
+      const float2 a = rsb[2 * f][phys(H / 2 + rr)];
+      const float2 d = rsb[2 * f + 1][phys(H / 2 + rr)];
+      *reinterpret_cast<float4*>(baseA + (size_t)rr * ra.wpr + pos0 + 2 * f) = make_float4(a.x, a.y, d.x, d.y);
+    }
+  }
+  cl.sync();
+}
+
+// R3: one CTA per (pair of output rows, channel); transform length L = 2W.
+template <int L>
+__global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constant__ RenderArgs ra) {
+  using F = First<L, true>;
+  using Hh = Last<L, true>;
+  constexpr int T = L / 32;
+  extern __shared__ float2 sm[];
+  __shared__ double red[32];
+  const int y = 2 * blockIdx.x, c = blockIdx.y, t = threadIdx.x;
+  const int W = ra.W, H = ra.H;
+  const float2* x0 = ra.sa + ((size_t)c * H + y) * ra.wpr;
+  const float2* x1 = x0 + ra.wpr;
+  // sum of the kernel crop (fixed order, FP64)
+  double ks = 0.0;
+  for (int u = t; u < H; u += T) ks += ra.ksum[(size_t)c * H + u];
+  ks = block_sum<T>(ks, red);
+  if (t == 0) red[0] = ks;
+  __syncthreads();
+  const float scale = (float)(1.0 / ((double)L * (2.0 * H) * red[0]));
+  float2 v[32];
+#pragma unroll
+  for (int b = 0; b < F::B; ++b)
+#pragma unroll
+    for (int r = 0; r < F::R; ++r) {
+      const int k = F::idx(t, b, r);
+      float2 a, d;  // X0[k], X1[k] with Hermitian extension above W
+      if (k <= W) {
+        a = x0[k];
+        d = x1[k];
+      } else {
+        a = x0[L - k];
+        d = x1[L - k];
+        a.y = -a.y;
+        d.y = -d.y;
+      }
+      v[b * F::R + r] = make_float2(a.x - d.y, a.y + d.x);  // X0 + i X1
+    }
+  fft_run<L, 32, true>(v, t, sm);
+  float* o0 = ra.out + ((size_t)c * H + y) * W;
+  float* o1 = o0 + W;
+#pragma unroll
+  for (int b = 0; b < Hh::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < Hh::R; ++r) {
+      const int n = Hh::idx(t, b, r) - W / 2;  // even
+      if ((unsigned)n < (unsigned)W) {
+        const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
+        __stcs(reinterpret_cast<float2*>(o0 + n), make_float2(a.x * scale, d.x * scale));
+        __stcs(reinterpret_cast<float2*>(o1 + n), make_float2(a.y * scale, d.y * scale));
+      }
+    }
+}
+
+}  // namespace doe

@@ -24,7 +24,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(ROOT, "include", "doe.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(doe_\w+)\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:int|size_t|long long|const char\*)\s+(doe_\w+)\(", hdr, re.M))
     assert declared, "no declarations parsed"
     for name in declared:
         assert hasattr(lib, name), name

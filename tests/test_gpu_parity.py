@@ -33,7 +33,7 @@ def _h(N, seed):
 
 
 # -------------------------------------------------------------- fields, every transform size
-@pytest.mark.parametrize("N,pad", [(16, 1), (16, 2), (32, 2), (64, 2), (128, 1), (128, 2), (256, 2),
+@pytest.mark.parametrize("N,pad", [(32, 1), (16, 2), (32, 2), (64, 2), (128, 1), (128, 2), (256, 2),
                                    (512, 2), (1024, 2), (2048, 1)])
 def test_propagate_matches_oracle_all_sizes(N, pad):
     dx, z = 1e-6, 3e-3 * N / 256
@@ -186,3 +186,43 @@ def test_grad_finite_differences_fd_exact():
     fd = oracle.fd_exact(h, dx, z, lams, T, py, px, 1e-10)
     scale = np.abs(fd).max()
     assert np.all(np.abs(gr[py, px] - fd) <= 1e-3 * scale), np.abs(gr[py, px] - fd).max() / scale
+
+
+# -------------------------------------------------------------- render
+@pytest.mark.parametrize("C,H,W,Pp", [(2, 16, 32, 64), (3, 64, 64, 128), (1, 128, 256, 512)])
+def test_render_small_vs_oracle(C, H, W, Pp):
+    rng = np.random.default_rng(H + W)
+    psf = rng.random((C, Pp, Pp)).astype(np.float32) ** 4
+    img = inputs.image(C, H, W, 2000 + H)
+    out = api.render(torch.from_numpy(psf).cuda(), torch.from_numpy(img).cuda()).cpu().numpy()
+    ref = oracle.render(psf, img)
+    assert rel_l2(out, ref) < TOL_PSF, rel_l2(out, ref)
+
+
+def test_render_rgb_workload_vs_oracle():
+    # the RGB design-evaluation workload: 3 PSFs of a 4096^2 DOE (8192^2 grid) convolved with
+    # a seeded 3 x 2048 x 2048 scene
+    N, dx, z = 4096, 1e-6, 50e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    h = torch.from_numpy(_h(N, 1002)).cuda()
+    g = Geometry.make(N, dx, z, lams)
+    I = api.psf(h, g)
+    img = inputs.image(3, 2048, 2048, 2002)
+    out = api.render(I, torch.from_numpy(img).cuda()).cpu().numpy()
+    ref = oracle.render(I.cpu().numpy(), img)  # the oracle convolves the GPU's PSFs
+    assert rel_l2(out, ref) < TOL_PSF, rel_l2(out, ref)
+
+
+def test_trace_and_launch_count():
+    N = 256
+    h = torch.from_numpy(_h(N, 5)).cuda()
+    g = Geometry.make(N, 1e-6, 5e-3, [500e-9])
+    api.psf(h, g)
+    n0 = api.launch_count()
+    api.trace_enable(16)
+    api.psf(h, g)
+    recs = api.trace_read()
+    api.trace_enable(0)
+    assert [r[0] for r in recs] == ["transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows"]
+    assert all(ms > 0 for _, ms in recs)
+    assert api.launch_count() - n0 == 4
