@@ -47,6 +47,7 @@ extern "C" {
 #define DOE_ENOWS (-3)        /* workspace missing, too small or not 256-byte aligned */
 #define DOE_ECUDA (-4)        /* a CUDA runtime call or kernel launch failed */
 #define DOE_ETIMEDOUT (-5)    /* a bounded host-side wait expired (serving layer) */
+#define DOE_ESCRATCH (-6)     /* the problem needs more scratch than doe_psf_noalloc's static buffer */
 
 /* ---- geometry flags ---- */
 #define DOE_BANDLIMIT 0x1u /* apply the band limit of the transfer function (default on) */
@@ -147,6 +148,19 @@ int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev);
  * uint8 [P][P] in FFT order, read back from the transfer table the kernels use. */
 int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_t ws_bytes,
                         void* stream);
+
+/* doe_psf without a workspace, for callers that cannot allocate device memory (for example a
+ * plugin inside an application that owns the device-memory budget and passes in only the
+ * input and output buffers, or a loop that must never call cudaMalloc).  No counterpart in
+ * the paper.  The scratch is a static device array of DOE_NOALLOC_SCRATCH_BYTES inside the
+ * library, held by every GPU that loads the library until the process exits; the call
+ * allocates nothing.  h, e_in, psf and the errors are as for doe_psf, plus DOE_ESCRATCH when
+ * doe_workspace_bytes(g, DOE_OP_PSF) exceeds DOE_NOALLOC_SCRATCH_BYTES.  The first call on a
+ * device looks up the array's device address (make it before any stream capture).  All calls
+ * share the one array: calls whose work overlaps on the GPU (different streams, or other
+ * host threads) race on it and must be serialised by the caller. */
+#define DOE_NOALLOC_SCRATCH_BYTES (32u << 20)
+int doe_psf_noalloc(const doe_geom* g, const float* h, const float* e_in, float* psf, void* stream);
 
 /* Tracing (optional).  doe_trace_enable(n) makes the library bracket each of the next n pass
  * launches with a pair of CUDA events recorded on the launching stream (n = 0 turns tracing

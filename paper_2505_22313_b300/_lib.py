@@ -17,6 +17,8 @@ DOE_EUNSUPPORTED = -2
 DOE_ENOWS = -3
 DOE_ECUDA = -4
 DOE_ETIMEDOUT = -5
+DOE_ESCRATCH = -6
+DOE_NOALLOC_SCRATCH_BYTES = 32 << 20
 DOE_BANDLIMIT = 0x1
 DOE_OP_PROPAGATE, DOE_OP_PSF, DOE_OP_GRAD = 1, 2, 3
 DOE_GRAD_L2_TARGET, DOE_GRAD_VJP = 0, 1
@@ -26,7 +28,7 @@ EXPORTS = (
     "doe_init", "doe_workspace_bytes", "doe_propagate", "doe_psf", "doe_psf_many",
     "doe_workspace_bytes_many", "doe_grad", "doe_render", "doe_render_workspace_bytes",
     "doe_band_limits", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
-    "doe_pass_name", "doe_launch_count",
+    "doe_pass_name", "doe_launch_count", "doe_psf_noalloc",
 )
 
 
@@ -84,6 +86,7 @@ def load(path: Path | None = None) -> ctypes.CDLL:
         "doe_trace_read": ([I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)], I),
         "doe_pass_name": ([I], ctypes.c_char_p),
         "doe_launch_count": ([], ctypes.c_longlong),
+        "doe_psf_noalloc": ([G, F, F, F, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -20,7 +20,7 @@ LIB = PKG / "libdoe.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
-SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu"]
+SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu", "doe_noalloc.cu"]
 
 
 def _deps() -> list[Path]:

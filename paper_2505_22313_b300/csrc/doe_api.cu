@@ -393,6 +393,7 @@ const char* doe_strerror(int code) {
     case DOE_ENOWS: return "workspace missing, too small or misaligned";
     case DOE_ECUDA: return "CUDA runtime error";
     case DOE_ETIMEDOUT: return "timed out";
+    case DOE_ESCRATCH: return "problem larger than the static no-alloc scratch (DOE_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown error";
   }
 }

@@ -1,0 +1,51 @@
+// doe_noalloc.cu -- doe_psf_noalloc: the PSF entry point for callers that cannot allocate.
+//
+// doe_psf needs a caller-provided device workspace.  Some callers cannot obtain one: a plugin
+// running inside a host application that owns the whole device-memory budget and hands out
+// only input and output buffers, a latency-critical loop that must never call cudaMalloc
+// (an allocation can block on the device or fail under memory pressure), or an embedding
+// that links only this library and has no allocator of its own.  For them this file keeps
+// the scratch in a file-scope static device array instead.  Every GPU that loads the library
+// holds the array (DOE_NOALLOC_SCRATCH_BYTES) until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "doe.h"
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DOE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the array's
+// name only stands in for the symbol; the address is looked up once per device, with that
+// device current.
+int scratch_for_current_device(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DOE_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DOE_ECUDA;
+    g_scratch[dev] = p;
+  }
+  *out = g_scratch[dev];
+  return DOE_OK;
+}
+}  // namespace
+
+extern "C" int doe_psf_noalloc(const doe_geom* g, const float* h, const float* e_in, float* psf, void* stream) {
+  const size_t need = doe_workspace_bytes(g, DOE_OP_PSF);
+  if (need == 0) return doe_psf(g, h, e_in, psf, nullptr, 0, stream);  // reports the validation error
+  if (need > DOE_NOALLOC_SCRATCH_BYTES) return DOE_ESCRATCH;
+  void* ws = nullptr;
+  const int rc = scratch_for_current_device(&ws);
+  if (rc != DOE_OK) return rc;
+  // Every location the passes read is written earlier in the same call (the padding columns
+  // of the field buffer are never read into a result), so the previous call's contents need
+  // no clearing.
+  return doe_psf(g, h, e_in, psf, ws, DOE_NOALLOC_SCRATCH_BYTES, stream);
+}
