@@ -105,7 +105,7 @@ int check_geom(const doe_geom* g) {
     if (!(g->n_index[j] >= 1.0) || !std::isfinite(g->n_index[j])) return DOE_EINVAL;
   }
   if (g->nx != g->ny) return DOE_EUNSUPPORTED;
-  if ((long)g->pad * g->nx > (1L << kMaxLog)) return DOE_EUNSUPPORTED;
+  if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
   return DOE_OK;
 }
 
@@ -117,7 +117,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   std::memset(&s, 0, sizeof(s));
   s.kmax = (int)kmax;
-  if (kmax >= P / 2) {
+  if (kmax >= P / 2 || P > (1L << kMaxLog)) {  // no compaction (split rows store sub-transform order)
     s.seg_a = (int)P;
     s.w = (int)P;
   } else {
@@ -157,7 +157,7 @@ Layout make_layout(const std::vector<Slice>& sl, long P, int op) {
   }
   if (op == DOE_OP_GRAD) {
     L.loss = off;
-    off = align256(off + sl.size() * (size_t)P * sizeof(double));
+    off = align256(off + sl.size() * (size_t)P * kMaxQf * sizeof(double));
   }
   L.total = off;
   return L;
@@ -188,14 +188,15 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
   bt.P = pad * N;
   bt.off = (bt.P - N) / 2;
   bt.inv_p2 = (float)(1.0 / ((double)bt.P * (double)bt.P));
+  bt.qf = bt.P > (1 << kMaxLog) ? bt.P >> kMaxLog : 1;
   int tiles = 0, kmx = 0;
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j] = sl[j];
     bt.s[j].buf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.buf[j]);
     bt.s[j].htab = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.htab[j]);
-    if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P;
+    if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P * kMaxQf;
     bt.s[j].tile_begin = tiles;
-    tiles += sl[j].wp / kTile;
+    tiles += sl[j].wp / (bt.qf > 1 ? 8 / bt.qf : kTile);
     if (sl[j].kmax > kmx) kmx = sl[j].kmax;
   }
   bt.total_tiles = tiles;

@@ -1,0 +1,410 @@
+// doe_big.cuh -- passes for padded grids longer than one CTA's transform, P = Q * 16384
+// (Q = 2: P = 32768; Q = 4: P = 65536, the large-area grid).
+//
+// A length-P transform is split across a cluster of Q CTAs, each running the in-CTA engine
+// on L = 16384 points (sub-transform s):
+//   forward (decimation in frequency)  x = n1 L + n2:
+//     y_s[n2] = W_P^{n2 s} sum_{n1} x[n1 L + n2] W_Q^{n1 s},  X[s + Q k2] = FFT_L(y_s)[k2]
+//   inverse (decimation in time)  output x = x2 + L q, input V_s[k2] = V[s + Q k2]:
+//     out[x2 + L q] = sum_s W_Q^{-s q} W_P^{-s x2} IFFT_L(V_s)[x2]
+// The radix-Q step is done once per element: each CTA takes a 1/Q share of n2 (or x2),
+// reads the Q values it needs from the other CTAs' shared memory (distributed shared memory)
+// or from global memory, and writes the Q results to their owners.  Spectra of rows are
+// stored in sub-transform order: position s L + k2 holds frequency k = s + Q k2 (no band
+// compaction; out-of-band columns are zeroed by the column pass).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "doe_kernels.cuh"
+
+namespace doe {
+
+constexpr int kBigL = 16384;
+
+// W_P^m (forward sign) for 0 <= m < P <= 65536, from the 65536-point table.
+template <int P>
+__device__ __forceinline__ float2 wbig(int m) {
+  return g_tw_big[(size_t)m * ((1 << kBigLog) / P)];
+}
+template <bool INV>
+__device__ __forceinline__ float2 tw_apply(float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); }
+
+__device__ __forceinline__ int big_pos_to_k(int pos, int Q) { return (pos % kBigL) * Q + pos / kBigL; }
+
+// ------------------------------------------------------------------ rows, forward (pass A)
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, 1) pass_a_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, P = L * Q, SH = L / Q;
+  using G = Last<L, false>;
+  extern __shared__ float2 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int s = (int)cl.block_rank();
+  const int i = blockIdx.x / Q;
+  const Slice& sl = bt.s[blockIdx.y];
+  const int t = threadIdx.x, N = bt.N, off = bt.off;
+  const float* hrow = sl.h + (size_t)i * N;
+  const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+  float4* rsm[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
+  cl.sync();  // every CTA of the cluster has started before its shared memory is written
+  for (int n2 = s * SH + 2 * t; n2 < (s + 1) * SH; n2 += 2 * T) {
+    float2 xa[Q], xb[Q];
+#pragma unroll
+    for (int n1 = 0; n1 < Q; ++n1) {
+      const int x = n1 * L + n2 - off;  // even
+      xa[n1] = xb[n1] = make_float2(0.f, 0.f);
+      if ((unsigned)x < (unsigned)N) {
+        const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
+        xa[n1] = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+        xb[n1] = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+        if (erow) {
+          const float4 ev = __ldcs(erow + (x >> 1));
+          xa[n1] = cmul(xa[n1], make_float2(ev.x, ev.y));
+          xb[n1] = cmul(xb[n1], make_float2(ev.z, ev.w));
+        }
+      }
+    }
+    dft<Q, false>(xa);
+    dft<Q, false>(xb);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float2 a = cmul(xa[q], wbig<P>(n2 * q)), b = cmul(xb[q], wbig<P>((n2 + 1) * q));
+      rsm[q][swz(n2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  cl.sync();
+  float2 v[32];
+  stage_load<L, 32, false, 0>(v, t, sm);
+  fft_run<L, 32, false>(v, t, sm);
+  float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)i * sl.wp + (size_t)s * L);
+#pragma unroll
+  for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) {
+      const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
+      __stcs(dst + (G::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
+    }
+}
+
+// Inverse sub-transform s of a stored row (positions s L .. s L + L - 1), result written to
+// this CTA's shared memory in natural order.
+template <int Q>
+__device__ __forceinline__ void big_row_inverse_to_smem(const float2* row, int s, int t, float2* sm) {
+  constexpr int L = kBigL;
+  using F = First<L, true>;
+  using H = Last<L, true>;
+  const float4* src = reinterpret_cast<const float4*>(row + (size_t)s * L);
+  float2 v[32];
+#pragma unroll
+  for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < F::R; ++r) {
+      const float4 q = __ldcs(src + (F::idx(t, b, r) >> 1));
+      v[b * F::R + r] = make_float2(q.x, q.y);
+      v[(b + 1) * F::R + r] = make_float2(q.z, q.w);
+    }
+  fft_run<L, 32, true>(v, t, sm);
+  __syncthreads();
+  float4* s4 = reinterpret_cast<float4*>(sm);
+#pragma unroll
+  for (int b = 0; b < H::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < H::R; ++r) {
+      const float2 a = v[b * H::R + r], c = v[(b + 1) * H::R + r];
+      s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
+    }
+}
+
+// Decimation-in-time combine for the pair (x2, x2 + 1): reads IFFT_L(V_s)[x2..] from every
+// CTA of the cluster and returns out[x2 + L q] in oa[q], out[x2 + 1 + L q] in ob[q].
+template <int Q>
+__device__ __forceinline__ void big_combine(float4* const (&rsm)[Q], int x2, float2 (&oa)[Q], float2 (&ob)[Q]) {
+  constexpr int P = kBigL * Q;
+#pragma unroll
+  for (int sp = 0; sp < Q; ++sp) {
+    const float4 q4 = rsm[sp][swz(x2 >> 1)];
+    oa[sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * x2));
+    ob[sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (x2 + 1)));
+  }
+  dft<Q, true>(oa);
+  dft<Q, true>(ob);
+}
+
+// ------------------------------------------------------------------ rows, inverse (pass C)
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, 1) pass_c_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, SH = L / Q;
+  extern __shared__ float2 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int s = (int)cl.block_rank();
+  const int y = blockIdx.x / Q;
+  const Slice& sl = bt.s[blockIdx.y];
+  const int t = threadIdx.x;
+  const int P = L * Q;
+  float4* rsm[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
+  big_row_inverse_to_smem<Q>(sl.buf + (size_t)y * sl.wp, s, t, sm);
+  cl.sync();
+  const float sc = bt.inv_p2;
+  for (int x2 = s * SH + 2 * t; x2 < (s + 1) * SH; x2 += 2 * T) {
+    float2 oa[Q], ob[Q];
+    big_combine<Q>(rsm, x2, oa, ob);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float2 a = cscale(oa[q], sc), b = cscale(ob[q], sc);
+      const size_t o = (size_t)y * P + (size_t)q * L + x2;
+      if (bt.mode == OUT_PSF)
+        __stcs(reinterpret_cast<float2*>(static_cast<float*>(sl.out) + o),
+               make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(b.x, b.x, b.y * b.y)));
+      else
+        __stcs(reinterpret_cast<float4*>(static_cast<float2*>(sl.out) + o), make_float4(a.x, a.y, b.x, b.y));
+    }
+  }
+  cl.sync();  // peers have finished reading this CTA's shared memory
+}
+
+// ------------------------------------------------------------------ columns (pass B / B*)
+// Cluster of 8 CTAs: TC = 8 / Q adjacent stored columns x Q sub-transforms; rank = c Q + s.
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, 1) pass_b_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, P = L * Q, TC = 8 / Q, CL = 8, SH = L / CL;
+  using G = Last<L, false>;
+  using Hh = Last<L, true>;
+  static_assert(G::R == First<L, true>::R, "register hand-off needs equal radices");
+  extern __shared__ float2 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int c = rank / Q, s = rank % Q;
+  const int t = threadIdx.x;
+  const int tile_g = blockIdx.x / CL;
+  int si = 0;
+  while (si + 1 < bt.S && bt.s[si + 1].tile_begin <= tile_g) ++si;
+  const Slice& sl = bt.s[si];
+  const int pos0 = (tile_g - sl.tile_begin) * TC;
+  const int kcol = big_pos_to_k(pos0 + c, Q);
+  const bool live = abs_signed(kcol, P) <= sl.kmax;
+  const bool adj = bt.mode == MODE_ADJ;
+  const int N = bt.N, off = bt.off;
+  const int nin = adj ? P : N, yin0 = adj ? 0 : off;
+  const int nout = adj ? N : P, yout0 = adj ? off : 0;
+  float2* rsm[CL];
+#pragma unroll
+  for (int k = 0; k < CL; ++k) rsm[k] = cl.map_shared_rank(sm, k);
+  cl.sync();
+  // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2
+  for (int y2 = rank * SH + t; y2 < (rank + 1) * SH; y2 += T) {
+    float2 col[TC][Q];
+#pragma unroll
+    for (int y1 = 0; y1 < Q; ++y1) {
+      const int y = y1 * L + y2;
+      if ((unsigned)(y - yin0) < (unsigned)nin) {
+        const float4* src = reinterpret_cast<const float4*>(sl.buf + (size_t)(y - yin0) * sl.wp + pos0);
+#pragma unroll
+        for (int f = 0; f < TC / 2; ++f) {
+          const float4 q4 = __ldcs(src + f);
+          col[2 * f][y1] = make_float2(q4.x, q4.y);
+          col[2 * f + 1][y1] = make_float2(q4.z, q4.w);
+        }
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < TC; ++cc) col[cc][y1] = make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int cc = 0; cc < TC; ++cc) {
+      dft<Q, false>(col[cc]);
+#pragma unroll
+      for (int sp = 0; sp < Q; ++sp) rsm[cc * Q + sp][phys(y2)] = cmul(col[cc][sp], wbig<P>(y2 * sp));
+    }
+  }
+  cl.sync();
+  float2 v[32];
+  stage_load<L, 32, false, 0>(v, t, sm);
+  fft_run<L, 32, false>(v, t, sm);
+  {
+    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, P) * sl.hp;
+#pragma unroll
+    for (int b = 0; b < G::B; ++b)
+#pragma unroll
+      for (int r = 0; r < G::R; ++r) {
+        const int a = abs_signed(s + Q * G::idx(t, b, r), P);
+        float2& x = v[b * G::R + r];
+        if (live && a <= sl.kmax) {
+          const float2 hv = hrow[a];
+          x = adj ? cmulc(x, hv) : cmul(x, hv);
+        } else {
+          x = make_float2(0.f, 0.f);
+        }
+      }
+  }
+  fft_run<L, 32, true>(v, t, sm);
+  __syncthreads();
+  {
+    float4* s4 = reinterpret_cast<float4*>(sm);
+#pragma unroll
+    for (int b = 0; b < Hh::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < Hh::R; ++r) {
+        const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
+        s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+      }
+  }
+  cl.sync();
+  // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2
+  for (int y2 = rank * SH + t; y2 < (rank + 1) * SH; y2 += T) {
+    float2 out[TC][Q];
+#pragma unroll
+    for (int cc = 0; cc < TC; ++cc) {
+#pragma unroll
+      for (int sp = 0; sp < Q; ++sp) out[cc][sp] = cmulc(rsm[cc * Q + sp][phys(y2)], wbig<P>(sp * y2));
+      dft<Q, true>(out[cc]);
+    }
+#pragma unroll
+    for (int y1 = 0; y1 < Q; ++y1) {
+      const int y = y1 * L + y2;
+      if ((unsigned)(y - yout0) < (unsigned)nout) {
+        float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
+#pragma unroll
+        for (int f = 0; f < TC / 2; ++f)
+          __stcs(dst + f, make_float4(out[2 * f][y1].x, out[2 * f][y1].y, out[2 * f + 1][y1].x, out[2 * f + 1][y1].y));
+      }
+    }
+  }
+  cl.sync();
+}
+
+// ------------------------------------------------------------------ rows, adjoint (pass C')
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, 1) pass_c_adj_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, P = L * Q, SH = L / Q, IT = SH / (2 * T);
+  using G = Last<L, false>;
+  extern __shared__ float2 sm[];
+  __shared__ double red[32];
+  cg::cluster_group cl = cg::this_cluster();
+  const int s = (int)cl.block_rank();
+  const int y = blockIdx.x / Q;
+  const Slice& sl = bt.s[blockIdx.y];
+  const int t = threadIdx.x;
+  float2* row = sl.buf + (size_t)y * sl.wp;
+  float4* rsm[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
+  big_row_inverse_to_smem<Q>(row, s, t, sm);
+  cl.sync();
+  float2 ga[IT][Q], gb[IT][Q];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) big_combine<Q>(rsm, s * SH + 2 * t + it * 2 * T, ga[it], gb[it]);
+  cl.sync();  // all reads of the inverse sub-transforms are done before they are overwritten
+  const float sc = bt.inv_p2;
+  const float* trow = sl.tgt + (size_t)y * P;
+  float acc = 0.f;
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int x2 = s * SH + 2 * t + it * 2 * T;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const float2 tv = __ldcs(reinterpret_cast<const float2*>(trow + (size_t)q * L + x2));
+      const float2 ea = cscale(ga[it][q], sc), eb = cscale(gb[it][q], sc);
+      float wa, wb;
+      if (bt.mode == GRAD_L2) {
+        const float da = fmaf(ea.x, ea.x, ea.y * ea.y) - tv.x, db = fmaf(eb.x, eb.x, eb.y * eb.y) - tv.y;
+        acc = fmaf(da, da, fmaf(db, db, acc));
+        wa = 2.f * da;
+        wb = 2.f * db;
+      } else {
+        wa = tv.x;
+        wb = tv.y;
+      }
+      ga[it][q] = cscale(ea, wa);
+      gb[it][q] = cscale(eb, wb);
+    }
+    // forward decimation-in-frequency split of g over the chunks q
+    dft<Q, false>(ga[it]);
+    dft<Q, false>(gb[it]);
+#pragma unroll
+    for (int sp = 0; sp < Q; ++sp) {
+      const float2 a = cmul(ga[it][sp], wbig<P>(x2 * sp)), b = cmul(gb[it][sp], wbig<P>((x2 + 1) * sp));
+      rsm[sp][swz(x2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  cl.sync();
+  float2 v[32];
+  stage_load<L, 32, false, 0>(v, t, sm);
+  fft_run<L, 32, false>(v, t, sm);
+  float4* dst = reinterpret_cast<float4*>(row + (size_t)s * L);
+#pragma unroll
+  for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < G::R; ++r) {
+      const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
+      __stcs(dst + (G::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
+    }
+  const double tot = block_sum<T>((double)acc, red);
+  if (t == 0 && sl.loss_part) sl.loss_part[(size_t)y * Q + s] = tot;
+}
+
+// ------------------------------------------------------------------ DOE rows, adjoint (pass A*)
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, 1) pass_a_adj_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, SH = L / Q, IT = SH / (2 * T);
+  extern __shared__ float2 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int s = (int)cl.block_rank();
+  const int i = blockIdx.x / Q;
+  const int t = threadIdx.x, N = bt.N, off = bt.off;
+  float4* rsm[Q];
+#pragma unroll
+  for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
+  float acc[IT][Q][2];
+#pragma unroll
+  for (int it = 0; it < IT; ++it)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[it][q][0] = acc[it][q][1] = 0.f;
+  for (int j = 0; j < bt.S; ++j) {
+    const Slice& sl = bt.s[j];
+    if (j > 0) cl.sync();  // peers finished reading the previous slice's sub-transforms
+    big_row_inverse_to_smem<Q>(sl.buf + (size_t)i * sl.wp, s, t, sm);
+    cl.sync();
+    const float* hrow = sl.h + (size_t)i * N;
+    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+    const float k2 = -2.f * sl.kp_hi;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int x2 = s * SH + 2 * t + it * 2 * T;
+      float2 oa[Q], ob[Q];
+      big_combine<Q>(rsm, x2, oa, ob);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int x = q * L + x2 - off;  // even
+        if ((unsigned)x < (unsigned)N) {
+          const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
+          float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+          float2 e1 = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          if (erow) {
+            const float4 ev = __ldcs(erow + (x >> 1));
+            e0 = cmul(e0, make_float2(ev.x, ev.y));
+            e1 = cmul(e1, make_float2(ev.z, ev.w));
+          }
+          const float2 g0 = cscale(oa[q], bt.inv_p2), g1 = cscale(ob[q], bt.inv_p2);
+          acc[it][q][0] = fmaf(k2, fmaf(g0.x, e0.y, -g0.y * e0.x), acc[it][q][0]);
+          acc[it][q][1] = fmaf(k2, fmaf(g1.x, e1.y, -g1.y * e1.x), acc[it][q][1]);
+        }
+      }
+    }
+  }
+  cl.sync();  // peers finished reading the last slice's sub-transforms
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int x2 = s * SH + 2 * t + it * 2 * T;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int x = q * L + x2 - off;
+      if ((unsigned)x < (unsigned)N)
+        *reinterpret_cast<float2*>(bt.grad + (size_t)i * N + x) = make_float2(acc[it][q][0], acc[it][q][1]);
+    }
+  }
+}
+
+}  // namespace doe

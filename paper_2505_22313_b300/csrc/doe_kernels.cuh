@@ -53,7 +53,7 @@ __device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, flo
         float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
         if (abs_signed(k, L) > sl.kmax) a = make_float2(0.f, 0.f);
         if (abs_signed(k + 1, L) > sl.kmax) c = make_float2(0.f, 0.f);
-        dst[pos >> 1] = make_float4(a.x, a.y, c.x, c.y);
+        __stcs(dst + (pos >> 1), make_float4(a.x, a.y, c.x, c.y));
       }
     }
 }
@@ -69,7 +69,7 @@ __device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const floa
     for (int r = 0; r < F::R; ++r) {
       const int pos = band_pos(F::idx(t, b, r), L, sl.seg_a, sl.w);
       float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (pos >= 0) q = s4[pos >> 1];
+      if (pos >= 0) q = __ldcs(s4 + (pos >> 1));
       v[b * F::R + r] = make_float2(q.x, q.y);
       v[(b + 1) * F::R + r] = make_float2(q.z, q.w);
     }
@@ -79,7 +79,7 @@ __device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const floa
 // One CTA per (DOE row i, slice).  The first stage's register pairs are adjacent padded
 // columns x, x + 1 (x even; the DOE offset is even), loaded as one float2 of heights.
 template <int L>
-__global__ void __launch_bounds__(L / 32) pass_a_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __grid_constant__ Batch bt) {
   using F = First<L, false>;
   extern __shared__ float2 sm[];
   const Slice& sl = bt.s[blockIdx.y];
@@ -96,11 +96,11 @@ __global__ void __launch_bounds__(L / 32) pass_a_kernel(const __grid_constant__ 
       const int x = F::idx(t, b, r) - off;  // even
       float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
       if ((unsigned)x < (unsigned)N) {
-        const float2 hv = __ldg(reinterpret_cast<const float2*>(hrow + x));
+        const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
         a = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
         c = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
         if (erow) {
-          const float4 ev = erow[x >> 1];
+          const float4 ev = __ldcs(erow + (x >> 1));
           a = cmul(a, make_float2(ev.x, ev.y));
           c = cmul(c, make_float2(ev.z, ev.w));
         }
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(L / 32) pass_a_kernel(const __grid_constant__ 
 // memory (distributed shared memory), and after the transforms gathers a quarter of the
 // output rows from all four CTAs.
 template <int L>
-__global__ void __launch_bounds__(L / 32) pass_b_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __grid_constant__ Batch bt) {
   using G = Last<L, false>;  // forward's last stage = inverse's first stage (radix 16)
   using H = Last<L, true>;
   constexpr int T = L / 32;
@@ -147,11 +147,12 @@ __global__ void __launch_bounds__(L / 32) pass_b_kernel(const __grid_constant__ 
   float2* rsm[kTile];
 #pragma unroll
   for (int c = 0; c < kTile; ++c) rsm[c] = cl.map_shared_rank(sm, c);
+  cl.sync();  // every CTA of the cluster has started before its shared memory is written
   {
     const int rows = nin / kTile, rbeg = q * rows;
     for (int idx = t; idx < rows * F4; idx += T) {
       const int rr = rbeg + idx / F4, f = idx % F4;
-      const float4 val = *reinterpret_cast<const float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f);
+      const float4 val = __ldcs(reinterpret_cast<const float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f));
       rsm[2 * f][phys(yin0 + rr)] = make_float2(val.x, val.y);
       rsm[2 * f + 1][phys(yin0 + rr)] = make_float2(val.z, val.w);
     }
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(L / 32) pass_b_kernel(const __grid_constant__ 
       const int rr = rbeg + idx / F4, f = idx % F4;
       const float2 a = rsm[2 * f][phys(yout0 + rr)];
       const float2 b = rsm[2 * f + 1][phys(yout0 + rr)];
-      *reinterpret_cast<float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f) = make_float4(a.x, a.y, b.x, b.y);
+      __stcs(reinterpret_cast<float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f), make_float4(a.x, a.y, b.x, b.y));
     }
   }
   cl.sync();
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(L / 32) pass_b_kernel(const __grid_constant__ 
 
 // ------------------------------------------------------------------ pass C: output rows
 template <int L>
-__global__ void __launch_bounds__(L / 32) pass_c_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_kernel(const __grid_constant__ Batch bt) {
   using H = Last<L, true>;
   extern __shared__ float2 sm[];
   const Slice& sl = bt.s[blockIdx.y];
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(L / 32) pass_c_kernel(const __grid_constant__ 
 #pragma unroll
       for (int r = 0; r < H::R; ++r) {
         const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
-        dst[H::idx(t, b, r) >> 1] = make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(c.x, c.x, c.y * c.y));
+        __stcs(dst + (H::idx(t, b, r) >> 1), make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(c.x, c.x, c.y * c.y)));
       }
   } else {
     float4* dst = reinterpret_cast<float4*>(static_cast<float2*>(sl.out) + (size_t)y * L);
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(L / 32) pass_c_kernel(const __grid_constant__ 
 #pragma unroll
       for (int r = 0; r < H::R; ++r) {
         const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
-        dst[H::idx(t, b, r) >> 1] = make_float4(a.x, a.y, c.x, c.y);
+        __stcs(dst + (H::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
       }
   }
 }
@@ -268,7 +269,7 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
 
 // ------------------------------------------------------------------ pass C': adjoint rows
 template <int L>
-__global__ void __launch_bounds__(L / 32) pass_c_adj_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const __grid_constant__ Batch bt) {
   using H = Last<L, true>;
   static_assert(H::R == First<L, false>::R, "register hand-off needs equal radices");
   extern __shared__ float2 sm[];
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(L / 32) pass_c_adj_kernel(const __grid_constan
   for (int b = 0; b < H::B; b += 2)
 #pragma unroll
     for (int r = 0; r < H::R; ++r) {
-      const float2 tv = __ldg(trow + (H::idx(t, b, r) >> 1));
+      const float2 tv = __ldcs(trow + (H::idx(t, b, r) >> 1));
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const float2 e = cscale(v[(b + u) * H::R + r], s);
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(L / 32) pass_c_adj_kernel(const __grid_constan
 // ------------------------------------------------------------------ pass A*: DOE-row adjoint
 // One CTA per DOE row; loops over the slices (wavelengths of one request) and sums.
 template <int L>
-__global__ void __launch_bounds__(L / 32) pass_a_adj_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const __grid_constant__ Batch bt) {
   using H = Last<L, true>;
   extern __shared__ float2 sm[];
   const int i = blockIdx.x;
@@ -366,8 +367,9 @@ __global__ void __launch_bounds__(L / 32) pass_a_adj_kernel(const __grid_constan
 __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant__ Batch bt, double* loss) {
   __shared__ double red[32];
   double acc = 0.0;
+  const int n = bt.P * bt.qf;  // per-row (and, for split rows, per-CTA) partials
   for (int j = 0; j < bt.S; ++j)
-    for (int y = threadIdx.x; y < bt.P; y += 1024) acc += bt.s[j].loss_part[y];
+    for (int y = threadIdx.x; y < n; y += 1024) acc += bt.s[j].loss_part[y];
   const double tot = block_sum<1024>(acc, red);
   if (threadIdx.x == 0) *loss = bt.mode == GRAD_L2 ? tot : 0.0;
 }

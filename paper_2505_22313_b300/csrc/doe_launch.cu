@@ -4,6 +4,7 @@
 #include <mutex>
 #include <vector>
 
+#include "doe_big.cuh"
 #include "doe_kernels.cuh"
 #include "doe_launch.h"
 #include "doe_render.cuh"
@@ -162,6 +163,52 @@ cudaError_t pass_a_adj_t(const Batch& bt, cudaStream_t st) {
   pass_a_adj_kernel<L><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
+// ---- grids longer than one CTA (P = Q * 16384): cluster launches
+cudaError_t launch_cluster(const void* fn, dim3 grid, int cluster, size_t smem, cudaStream_t st, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kBigL / 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template <int Q>
+cudaError_t big_rows_t(int which, const Batch& bt, cudaStream_t st) {
+  const void* fn = which == 0 ? (const void*)pass_a_big_kernel<Q>
+                 : which == 1 ? (const void*)pass_c_big_kernel<Q>
+                 : which == 2 ? (const void*)pass_c_adj_big_kernel<Q>
+                              : (const void*)pass_a_adj_big_kernel<Q>;
+  const int rows = (which == 0 || which == 3) ? bt.N : bt.P;
+  const dim3 grid(rows * Q, which == 3 ? 1 : bt.S);
+  void* args[] = {const_cast<Batch*>(&bt)};
+  return launch_cluster(fn, grid, Q, smem_bytes<kBigL>(), st, args);
+}
+template <int Q>
+cudaError_t big_cols_t(const Batch& bt, cudaStream_t st) {
+  void* args[] = {const_cast<Batch*>(&bt)};
+  return launch_cluster((const void*)pass_b_big_kernel<Q>, dim3(bt.total_tiles * 8), 8, smem_bytes<kBigL>(), st, args);
+}
+template <int Q>
+cudaError_t prep_big_t() {
+  cudaError_t e;
+  const int sb = (int)smem_bytes<kBigL>();
+  if ((e = prep_one(pass_a_big_kernel<Q>, sb))) return e;
+  if ((e = prep_one(pass_b_big_kernel<Q>, sb))) return e;
+  if ((e = prep_one(pass_c_big_kernel<Q>, sb))) return e;
+  if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb))) return e;
+  if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb))) return e;
+  return cudaSuccess;
+}
+
 template <int L>
 cudaError_t render_rows_t(const RenderArgs& ra, cudaStream_t st) {
   Traced tr(TR_RENDER_ROWS, st);
@@ -209,7 +256,8 @@ cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
-      (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()))
+      (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<2>()) ||
+      (e = prep_big_t<4>()))
     return e;
   return cudaSuccess;
 }
@@ -219,11 +267,33 @@ cudaError_t launch_htab(const Batch& bt, cudaStream_t st) {
   htab_kernel<<<dim3(bt.max_kmax + 1, bt.S), 256, 0, st>>>(bt);
   return cudaGetLastError();
 }
-cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_a_t, bt, st); }
-cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_b_t, bt, st); }
-cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_c_t, bt, st); }
-cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_c_adj_t, bt, st); }
-cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st) { DOE_DISPATCH(lg, pass_a_adj_t, bt, st); }
+// Grids longer than one CTA (lg = 15, 16) go to the cluster-split passes of doe_big.cuh.
+#define DOE_BIG_ROWS(which, trace)                                          \
+  if (lg == 15) { Traced tr(trace, st); return big_rows_t<2>(which, bt, st); } \
+  if (lg == 16) { Traced tr(trace, st); return big_rows_t<4>(which, bt, st); }
+cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
+  DOE_BIG_ROWS(0, TR_PASS_A)
+  DOE_DISPATCH(lg, pass_a_t, bt, st);
+}
+cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
+  if (lg == 15 || lg == 16) {
+    Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
+    return lg == 15 ? big_cols_t<2>(bt, st) : big_cols_t<4>(bt, st);
+  }
+  DOE_DISPATCH(lg, pass_b_t, bt, st);
+}
+cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) {
+  DOE_BIG_ROWS(1, TR_PASS_C)
+  DOE_DISPATCH(lg, pass_c_t, bt, st);
+}
+cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) {
+  DOE_BIG_ROWS(2, TR_PASS_C_ADJ)
+  DOE_DISPATCH(lg, pass_c_adj_t, bt, st);
+}
+cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st) {
+  DOE_BIG_ROWS(3, TR_PASS_A_ADJ)
+  DOE_DISPATCH(lg, pass_a_adj_t, bt, st);
+}
 cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st) {
   Traced tr(TR_LOSS, st);
   loss_reduce_kernel<<<1, 1024, 0, st>>>(bt, loss);

@@ -38,6 +38,11 @@ constexpr long kTwTotal = tw_offset(kMaxLog + 1, false, 0);
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 __host__ __device__ constexpr int smem_words(int L) { return L; }
 
+// Resident CTAs per SM requested from the register allocator for a row/column pass of length L.
+__host__ __device__ constexpr int min_blocks(int L) {
+  return (65536 / ((L / 32) * 128)) > 1 ? 65536 / ((L / 32) * 128) : 1;  // at most 128 registers per thread
+}
+
 // Elements per thread used for a transform of length L.
 __host__ __device__ constexpr int elems_for(int) { return 32; }
 template <int L, bool INV>
@@ -47,7 +52,8 @@ __host__ __device__ constexpr int last_radix() { return plan_radix(ilog2c(L), IN
 
 constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
 constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
-constexpr int kTile = 4;        // columns per column-pass cluster: 4 x 8 B = one 32-byte sector
+constexpr int kTile = 4;    // columns per column-pass cluster: 4 x 8 B = one 32-byte sector
+constexpr int kMaxQf = 4;   // sub-transforms per row at the largest grid (65536 = 4 x 16384)
 
 // One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
 // shared by the whole launch.
@@ -82,6 +88,7 @@ struct Batch {
   int total_tiles;   // column tiles over all slices
   int mode;          // MODE_FWD / MODE_ADJ (column pass), OUT_* (row inverse pass), GRAD_* (adjoint row pass)
   int max_kmax;      // largest kmax over the slices (table builder grid)
+  int qf;            // sub-transforms per row: P / 16384 for P > 16384, else 1
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient output (DOE-row adjoint pass)
   Slice s[kMaxSlices];

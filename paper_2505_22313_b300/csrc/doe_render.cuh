@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
     rsa[cc] = cl.map_shared_rank(sma, cc);
     rsb[cc] = cl.map_shared_rank(smb, cc);
   }
+  cl.sync();  // every CTA of the cluster has started before its shared memory is written
   {
     const int rows = H / kTile, rbeg = q * rows;
     for (int idx = t; idx < rows * F4; idx += T) {

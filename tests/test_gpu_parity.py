@@ -226,3 +226,110 @@ def test_trace_and_launch_count():
     assert [r[0] for r in recs] == ["transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows"]
     assert all(ms > 0 for _, ms in recs)
     assert api.launch_count() - n0 == 4
+
+
+# -------------------------------------------------------------- grids longer than one CTA
+def _h_closed(kt, lt, P, dx, z, lam):
+    """Transfer function at integer frequencies, FP64, from its definition (band + evanescent
+    rules as stated for the oracle)."""
+    du = 1.0 / (P * dx)
+    kmax = oracle.kmax(lam, dx, P, z)
+    if abs(kt) > kmax or abs(lt) > kmax or kt * kt + lt * lt >= oracle.m_ev(lam, dx, P):
+        return 0.0
+    ph = 2 * np.pi * z * np.sqrt(1.0 / lam**2 - (kt * du) ** 2 - (lt * du) ** 2)
+    return np.exp(1j * np.fmod(ph, 2 * np.pi))
+
+
+@pytest.mark.parametrize("P", [32768, 65536])
+def test_big_grid_flat_plate(P):
+    c, dx, z, lam = 0.37e-6, 1e-6, 0.1, 550e-9
+    h = torch.full((P, P), c, dtype=torch.float32, device="cuda")
+    g = Geometry.make(P, dx, z, [lam], pad=1)
+    e = api.propagate(h, g)[0]
+    phase = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z / lam
+    ref = torch.tensor(complex(np.cos(np.fmod(phase, 2 * np.pi)), np.sin(np.fmod(phase, 2 * np.pi))),
+                       dtype=torch.complex64, device="cuda")
+    err = (e - ref).abs().max().item()
+    assert err < 5e-5, err
+
+
+def test_big_grid_plane_waves_closed_form():
+    # pad 1, h = 0, E_in = sum_j c_j exp(2 pi i (a_j x + b_j y) / P): every wave is a single
+    # spectral line, so E_out = sum_j c_j H(a_j, b_j) exp(2 pi i (a_j x + b_j y) / P)
+    P, dx, z, lam = 65536, 1e-6, 0.1, 550e-9
+    rng = np.random.default_rng(65536)
+    waves = [(int(a), int(b), complex(rng.standard_normal(), rng.standard_normal()))
+             for a, b in rng.integers(-P // 2, P // 2, size=(6, 2))] + [(0, 0, 1.0 + 0.5j), (P // 2 - 1, -3, 0.7 - 0.2j)]
+    ys = torch.arange(P, device="cuda", dtype=torch.float64)
+
+    def field(coefs, rows=None):
+        yy = ys if rows is None else rows
+        out = torch.zeros((yy.numel(), P), dtype=torch.complex128, device="cuda")
+        for (a, b, _), cc in zip(waves, coefs):
+            px = torch.exp(2j * np.pi * ((a * ys) % P) / P)
+            py = torch.exp(2j * np.pi * ((b * yy) % P) / P)
+            out += cc * py[:, None] * px[None, :]
+        return out
+
+    e_in = torch.empty((P, P), dtype=torch.complex64, device="cuda")
+    for r0 in range(0, P, 4096):
+        e_in[r0:r0 + 4096] = field([w[2] for w in waves], ys[r0:r0 + 4096]).to(torch.complex64)
+    g = Geometry.make(P, dx, z, [lam], pad=1)
+    e = api.propagate(torch.zeros((P, P), dtype=torch.float32, device="cuda"), g, e_in=e_in)[0]
+    del e_in
+    rows = torch.tensor([0, 1, 777, P // 2, P - 1], device="cuda", dtype=torch.float64)
+    ref = field([w[2] * _h_closed(w[0], w[1], P, dx, z, lam) for w in waves], rows)
+    got = e[rows.long()].to(torch.complex128)
+    err = (torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref)).item()
+    assert err < TOL_PSF, err
+
+
+def test_big_grid_psf_rows_vs_oracle():
+    # 16384 x 16384 DOE padded to 32768 x 32768 (two-CTA rows and columns)
+    N, dx, z, lam = 16384, 1e-6, 50e-3, 550e-9
+    P = 2 * N
+    h = _h(N, 1005)
+    g = Geometry.make(N, dx, z, [lam])
+    I = api.psf(torch.from_numpy(h).cuda(), g)
+    rows = np.array([0, P // 4, P // 2 - 1, P // 2, P // 2 + 3, 3 * P // 4, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    ref = oracle.psf_rows(h, dx, z, lam, rows)
+    err = rel_l2(Ig, ref)
+    assert err < TOL_PSF, err
+
+
+def test_large_area_psf_rows_vs_oracle():
+    # the large-area workload: 32768 x 32768 DOE at 1 um, 550 nm, z = 100 mm, padded to
+    # 65536 x 65536 (band limit inactive); exact FP64 rows from the oracle's row-subset mode
+    N, dx, z, lam = 32768, 1e-6, 100e-3, 550e-9
+    P = 2 * N
+    h = _h(N, 1004)
+    g = Geometry.make(N, dx, z, [lam])
+    I = api.psf(torch.from_numpy(h).cuda(), g)
+    rows = np.array([0, P // 8, P // 2 - 1, P // 2, 5 * P // 8, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    tot = I.double().sum().item()
+    del I
+    ref = oracle.psf_rows(h, dx, z, lam, rows)
+    err = rel_l2(Ig, ref)
+    assert err < TOL_PSF, err
+    assert 0.5 * N * N < tot <= N * N * (1 + 1e-5)  # Parseval over the band
+
+
+def test_big_grid_gradient_fd_exact():
+    # two-CTA rows/columns adjoint (16384^2 DOE, 32768^2 grid) against exact-difference
+    # central differences of the FP64 loss on seeded pixels
+    N, dx, z = 16384, 1e-6, 50e-3
+    lams = [550e-9]
+    P = 2 * N
+    h = _h(N, 1006)
+    T = inputs.spot_target(P, N, 1, 2006)
+    g = Geometry.make(N, dx, z, lams)
+    gr, loss = api.grad(torch.from_numpy(h).cuda(), g, torch.from_numpy(T).cuda())
+    gr = gr.cpu().numpy()
+    rng = np.random.default_rng(16384)
+    py = np.concatenate([rng.integers(0, N, 6), [N // 2, N // 2 + 1]])
+    px = np.concatenate([rng.integers(0, N, 6), [N // 2, N // 2]])
+    fd = oracle.fd_exact(h, dx, z, lams, T, py, px, 1e-10)
+    scale = np.abs(fd).max()
+    assert np.all(np.abs(gr[py, px] - fd) <= 1e-3 * scale), np.abs(gr[py, px] - fd).max() / scale
