@@ -65,6 +65,26 @@ def heights(N: int, seed: int, hmax: float = HMAX, sigma: float = 2.0, radius: i
     return out
 
 
+def heights_device(N: int, seed: int, device, hmax: float = HMAX, sigma: float = 2.0, radius: int = 8):
+    """Seeded smoothed heights generated on a CUDA device (the serving workload's requests):
+    torch's device RNG U[0, 1), the same separable periodic Gaussian smoothing and affine
+    rescale to [0, hmax] as heights(), in float32.  Deterministic for a given seed and device
+    type; not bit-identical to heights() (different random generator)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    x = torch.rand((N, N), generator=g, device=device, dtype=torch.float32)
+    w = _gauss_weights(sigma, radius)
+    for dim in (1, 0):
+        acc = torch.zeros_like(x)
+        for i, wi in enumerate(w):
+            acc.add_(torch.roll(x, radius - i, dims=dim), alpha=float(wi))
+        x = acc
+    mn, mx = x.min(), x.max()
+    return ((x - mn) * (hmax / (mx - mn))).contiguous()
+
+
 def image(C: int, H: int, W: int, seed: int, n_disks: int = 64) -> np.ndarray:
     """C x H x W float32 test scene: iid uniform noise with filled disks painted on top."""
     rng = np.random.default_rng(seed)
