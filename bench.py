@@ -275,6 +275,47 @@ def run_ours(args):
            "h2d_bytes_per_step": h_np.nbytes + img_np.nbytes, "d2h_bytes_per_step": C * H * W * 4,
            "ms_per_step": round(e2e_ms, 4)}
 
+    # the unfused cuFFT chain on the same GPU (comparison only; libdoe does not use cuFFT)
+    cufft = None
+    try:
+        import ctypes
+
+        from paper_2505_22313_b300 import build as _b
+
+        clib = ctypes.CDLL(str(_b.COMPARE_LIB))
+        clib.doe_cufft_psf.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]
+        clib.doe_cufft_psf.restype = ctypes.c_int
+        cws = api.workspace(P * P * 8, dev)
+        cpsf = torch.empty_like(psf)
+        gc = g.c()
+        s_ = torch.cuda.current_stream()
+
+        def cstep():
+            rc = clib.doe_cufft_psf(ctypes.byref(gc), ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(cpsf.data_ptr()),
+                                    ctypes.c_void_p(cws.data_ptr()), cws.numel(), ctypes.c_void_p(s_.cuda_stream))
+            assert rc == 0, rc
+
+        for _ in range(3):
+            cstep()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(10):
+            cstep()
+        a1.record()
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(10):
+            api.psf(h, g, out=psf, ws=ws)
+        b1.record()
+        torch.cuda.synchronize()
+        diff = (torch.linalg.vector_norm((cpsf - psf).double()) / torch.linalg.vector_norm(psf.double())).item()
+        cufft = {"psf_ms": round(a0.elapsed_time(a1) / 10, 4), "ours_psf_ms": round(b0.elapsed_time(b1) / 10, 4),
+                 "rel_l2_vs_ours": diff}
+        del cws, cpsf
+    except (OSError, AttributeError, AssertionError) as exc:
+        cufft = {"unavailable": str(exc)[:200]}
+
     cpu = None
     fp64_err = None
     if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
@@ -298,6 +339,7 @@ def run_ours(args):
         "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
         "fp64_rel_l2_psf_550nm": fp64_err,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "gpu_launches": launches,
+        "cufft_chain_comparison": cufft,
         "wall_s": round(wall, 3),
     }
     print(json.dumps(line), flush=True)

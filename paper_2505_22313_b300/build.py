@@ -17,6 +17,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libdoe.so"
+COMPARE_LIB = PKG / "libdoe_cufft.so"  # cuFFT comparison chain, loaded only by the benchmark
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
@@ -25,6 +26,10 @@ SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu", "doe_noalloc.cu"]
 
 def _deps() -> list[Path]:
     return sorted(CSRC.glob("*.cu")) + sorted(CSRC.glob("*.cuh")) + sorted(CSRC.glob("*.h")) + [ROOT / "include" / "doe.h"]
+
+
+def _stale_all(deps) -> bool:
+    return _stale(LIB, deps) or _stale(COMPARE_LIB, deps)
 
 
 def _stale(target: Path, deps: list[Path]) -> bool:
@@ -36,7 +41,7 @@ def _stale(target: Path, deps: list[Path]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> Path:
     deps = _deps()
-    if not force and not _stale(LIB, deps):
+    if not force and not _stale_all(deps):
         return LIB
     BUILD.mkdir(exist_ok=True)
 
@@ -60,7 +65,25 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    _build_compare(verbose)
     return LIB
+
+
+def _build_compare(verbose: bool = False) -> Path:
+    """The cuFFT-based comparison chain (benchmark only; libdoe never loads it)."""
+    obj = BUILD / "compare_cufft.o"
+    cmd = [NVCC, *FLAGS, *ARCH, "-c", str(CSRC / "compare_cufft.cu"), "-o", str(obj)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for compare_cufft.cu:\n{r.stdout}\n{r.stderr}")
+    tmp = COMPARE_LIB.with_suffix(f".so.tmp{os.getpid()}")
+    cmd = [NVCC, "-shared", *ARCH, "-o", str(tmp), str(obj), f"-L{PKG}", "-ldoe", "-lcufft", "-lcudart",
+           "-Xlinker", "-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed for libdoe_cufft.so:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, COMPARE_LIB)
+    return COMPARE_LIB
 
 
 if __name__ == "__main__":

@@ -93,6 +93,9 @@ long long band_mev(double lam, double dx, long P) {
   return (long long)std::ceil(x);
 }
 
+// Columns per column-pass tile: 4, except 8 / Q for split columns (P = 32768: 4, 65536: 2).
+int col_tile(long P) { return P == 65536 ? 2 : kTile; }
+
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
   if (g->nx < 16 || g->ny < 16 || !is_pow2(g->nx) || !is_pow2(g->ny)) return DOE_EINVAL;
@@ -137,14 +140,16 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
 
 struct Layout {
   size_t total = 0;
-  std::vector<size_t> buf, htab;
+  std::vector<size_t> buf, htab, tbuf;
   size_t loss = 0;
 };
 
-// Workspace: per slice a [P][wp] complex field buffer, then per slice a transfer table, then
-// (gradient) the per-row loss partials.  The PSF layout is a prefix of the gradient layout,
-// so a gradient-sized workspace used by doe_psf keeps its fields for doe_grad(recompute=0).
-Layout make_layout(const std::vector<Slice>& sl, long P, int op) {
+// Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
+// table, then per slice a column-tiled buffer (N rows for the forward path, P rows when the
+// adjoint also runs), then (gradient) the per-row loss partials.  The field buffers and tables
+// sit at the same offsets in the PSF and gradient layouts, so a gradient-sized workspace used
+// by doe_psf keeps the fields and tables doe_grad(recompute=0) needs.
+Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op) {
   Layout L;
   size_t off = 0;
   for (const auto& s : sl) {
@@ -154,6 +159,11 @@ Layout make_layout(const std::vector<Slice>& sl, long P, int op) {
   for (const auto& s : sl) {
     L.htab.push_back(off);
     off = align256(off + (size_t)(s.kmax + 1) * s.hp * sizeof(float2));
+  }
+  const long R = op == DOE_OP_GRAD ? P : N;
+  for (const auto& s : sl) {
+    L.tbuf.push_back(off);
+    off = align256(off + (size_t)R * s.wp * sizeof(float2));
   }
   if (op == DOE_OP_GRAD) {
     L.loss = off;
@@ -194,9 +204,10 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
     bt.s[j] = sl[j];
     bt.s[j].buf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.buf[j]);
     bt.s[j].htab = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.htab[j]);
+    bt.s[j].tbuf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.tbuf[j]);
     if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P * kMaxQf;
     bt.s[j].tile_begin = tiles;
-    tiles += sl[j].wp / (bt.qf > 1 ? 8 / bt.qf : kTile);
+    tiles += sl[j].wp / col_tile(bt.P);
     if (sl[j].kmax > kmx) kmx = sl[j].kmax;
   }
   bt.total_tiles = tiles;
@@ -228,7 +239,7 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
     if (!h[r] || !out[r]) return DOE_EINVAL;
   const int N = geoms[0].nx, pad = geoms[0].pad;
   const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, DOE_OP_PSF);
+  const Layout lay = make_layout(sl, P, N, DOE_OP_PSF);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
@@ -263,7 +274,7 @@ size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op) {
   std::vector<Slice> sl;
   std::vector<int> req_of;
   if (collect_slices(n_req, geoms, sl, req_of) != DOE_OK) return 0;
-  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, op).total;
+  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, geoms[0].nx, op).total;
 }
 
 size_t doe_workspace_bytes(const doe_geom* g, int op) { return doe_workspace_bytes_many(1, g, op); }
@@ -299,7 +310,7 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   if ((rc = collect_slices(1, g, sl, req_of)) != DOE_OK) return rc;
   const int N = g->nx, pad = g->pad;
   const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, DOE_OP_GRAD);
+  const Layout lay = make_layout(sl, P, N, DOE_OP_GRAD);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
@@ -350,7 +361,7 @@ int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_
   std::vector<int> req_of;
   if ((rc = collect_slices(1, &one, sl, req_of)) != DOE_OK) return rc;
   const long P = (long)g->pad * g->nx;
-  const Layout lay = make_layout(sl, P, DOE_OP_PSF);
+  const Layout lay = make_layout(sl, P, g->nx, DOE_OP_PSF);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;

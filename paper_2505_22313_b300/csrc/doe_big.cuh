@@ -1,8 +1,10 @@
-// doe_big.cuh -- passes for padded grids longer than one CTA's transform, P = Q * 16384
-// (Q = 2: P = 32768; Q = 4: P = 65536, the large-area grid).
+// doe_big.cuh -- transforms split across a cluster: P = Q * LS with sub-transforms of LS points.
+// Rows of grids longer than one CTA's transform (P = 32768, 65536: LS = 16384, Q = 2, 4) and
+// the column pass of the 16384-point grid (LS = 8192, Q = 2: 64 KB of shared memory per CTA
+// instead of 128 KB, so several CTAs share an SM).
 //
 // A length-P transform is split across a cluster of Q CTAs, each running the in-CTA engine
-// on L = 16384 points (sub-transform s):
+// on L = LS points (sub-transform s):
 //   forward (decimation in frequency)  x = n1 L + n2:
 //     y_s[n2] = W_P^{n2 s} sum_{n1} x[n1 L + n2] W_Q^{n1 s},  X[s + Q k2] = FFT_L(y_s)[k2]
 //   inverse (decimation in time)  output x = x2 + L q, input V_s[k2] = V[s + Q k2]:
@@ -21,14 +23,18 @@ namespace doe {
 
 constexpr int kBigL = 16384;
 
-// W_P^m (forward sign) for 0 <= m < P <= 65536, from the 65536-point table.
+// W_P^m (forward sign) for 0 <= m < P <= 65536.  With n = m 65536 / P = 256 hi + lo,
+// W_65536^n = W_65536^{256 hi} W_65536^{lo}: two lookups in 256-entry tables (4 KB in all,
+// L1-resident) and one complex product, instead of a scattered read of a 512 KB table.
 template <int P>
 __device__ __forceinline__ float2 wbig(int m) {
-  return g_tw_big[(size_t)m * ((1 << kBigLog) / P)];
+  const int n = m * ((1 << kBigLog) / P);
+  return cmul(__ldg(g_tw_big + ((n >> 8) << 8)), __ldg(g_tw_big + (n & 255)));
 }
 template <bool INV>
 __device__ __forceinline__ float2 tw_apply(float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); }
 
+// frequency index of stored column position pos when rows are stored in sub-transform order
 __device__ __forceinline__ int big_pos_to_k(int pos, int Q) { return (pos % kBigL) * Q + pos / kBigL; }
 
 // ------------------------------------------------------------------ rows, forward (pass A)
@@ -77,13 +83,14 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_a_big_kernel(const __grid_
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)i * sl.wp + (size_t)s * L);
+  constexpr int TC = 8 / Q;
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
-      __stcs(dst + (G::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
+      const int pos = s * L + G::idx(t, b, r);
+      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, TC)), make_float4(a.x, a.y, c.x, c.y));
     }
 }
 
@@ -167,9 +174,10 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_c_big_kernel(const __grid_
 
 // ------------------------------------------------------------------ columns (pass B / B*)
 // Cluster of 8 CTAs: TC = 8 / Q adjacent stored columns x Q sub-transforms; rank = c Q + s.
-template <int Q>
-__global__ void __launch_bounds__(kBigL / 32, 1) pass_b_big_kernel(const __grid_constant__ Batch bt) {
-  constexpr int L = kBigL, T = L / 32, P = L * Q, TC = 8 / Q, CL = 8, SH = L / CL;
+// ROWSPLIT: rows are stored in sub-transform order (P > 16384); otherwise band-compacted.
+template <int LS, int Q, bool ROWSPLIT>
+__global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = LS, T = L / 32, P = L * Q, TC = 8 / Q, CL = 8, SH = L / CL;
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   static_assert(G::R == First<L, true>::R, "register hand-off needs equal radices");
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_b_big_kernel(const __grid_
   while (si + 1 < bt.S && bt.s[si + 1].tile_begin <= tile_g) ++si;
   const Slice& sl = bt.s[si];
   const int pos0 = (tile_g - sl.tile_begin) * TC;
-  const int kcol = big_pos_to_k(pos0 + c, Q);
-  const bool live = abs_signed(kcol, P) <= sl.kmax;
+  const int kcol = ROWSPLIT ? big_pos_to_k(pos0 + c, P / kBigL) : pos_to_k(pos0 + c, P, sl.seg_a, sl.w);
+  const bool live = pos0 + c < sl.w && abs_signed(kcol, P) <= sl.kmax;
   const bool adj = bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;
   const int nin = adj ? P : N, yin0 = adj ? 0 : off;
@@ -193,30 +201,37 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_b_big_kernel(const __grid_
 #pragma unroll
   for (int k = 0; k < CL; ++k) rsm[k] = cl.map_shared_rank(sm, k);
   cl.sync();
-  // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2
-  for (int y2 = rank * SH + t; y2 < (rank + 1) * SH; y2 += T) {
-    float2 col[TC][Q];
+  // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2; each
+  // thread takes the adjacent pair (y2, y2 + 1) so its shared-memory writes are 16 bytes
+  for (int y2 = rank * SH + 2 * t; y2 < (rank + 1) * SH; y2 += 2 * T) {
+    float2 col[2][TC][Q];
 #pragma unroll
-    for (int y1 = 0; y1 < Q; ++y1) {
-      const int y = y1 * L + y2;
-      if ((unsigned)(y - yin0) < (unsigned)nin) {
-        const float4* src = reinterpret_cast<const float4*>(sl.buf + (size_t)(y - yin0) * sl.wp + pos0);
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int f = 0; f < TC / 2; ++f) {
-          const float4 q4 = __ldcs(src + f);
-          col[2 * f][y1] = make_float2(q4.x, q4.y);
-          col[2 * f + 1][y1] = make_float2(q4.z, q4.w);
+      for (int y1 = 0; y1 < Q; ++y1) {
+        const int y = y1 * L + y2 + u;
+        if ((unsigned)(y - yin0) < (unsigned)nin) {
+          const float4* src = reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, TC));
+#pragma unroll
+          for (int f = 0; f < TC / 2; ++f) {
+            const float4 q4 = __ldcs(src + f);
+            col[u][2 * f][y1] = make_float2(q4.x, q4.y);
+            col[u][2 * f + 1][y1] = make_float2(q4.z, q4.w);
+          }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < TC; ++cc) col[u][cc][y1] = make_float2(0.f, 0.f);
         }
-      } else {
-#pragma unroll
-        for (int cc = 0; cc < TC; ++cc) col[cc][y1] = make_float2(0.f, 0.f);
       }
-    }
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {
-      dft<Q, false>(col[cc]);
+      dft<Q, false>(col[0][cc]);
+      dft<Q, false>(col[1][cc]);
 #pragma unroll
-      for (int sp = 0; sp < Q; ++sp) rsm[cc * Q + sp][phys(y2)] = cmul(col[cc][sp], wbig<P>(y2 * sp));
+      for (int sp = 0; sp < Q; ++sp) {
+        const float2 a = cmul(col[0][cc][sp], wbig<P>(y2 * sp)), d = cmul(col[1][cc][sp], wbig<P>((y2 + 1) * sp));
+        reinterpret_cast<float4*>(rsm[cc * Q + sp])[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+      }
     }
   }
   cl.sync();
@@ -252,25 +267,33 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_b_big_kernel(const __grid_
       }
   }
   cl.sync();
-  // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2
-  for (int y2 = rank * SH + t; y2 < (rank + 1) * SH; y2 += T) {
-    float2 out[TC][Q];
+  // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2 (pairs y2, y2 + 1)
+  for (int y2 = rank * SH + 2 * t; y2 < (rank + 1) * SH; y2 += 2 * T) {
+    float2 out[2][TC][Q];
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {
 #pragma unroll
-      for (int sp = 0; sp < Q; ++sp) out[cc][sp] = cmulc(rsm[cc * Q + sp][phys(y2)], wbig<P>(sp * y2));
-      dft<Q, true>(out[cc]);
-    }
-#pragma unroll
-    for (int y1 = 0; y1 < Q; ++y1) {
-      const int y = y1 * L + y2;
-      if ((unsigned)(y - yout0) < (unsigned)nout) {
-        float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
-#pragma unroll
-        for (int f = 0; f < TC / 2; ++f)
-          __stcs(dst + f, make_float4(out[2 * f][y1].x, out[2 * f][y1].y, out[2 * f + 1][y1].x, out[2 * f + 1][y1].y));
+      for (int sp = 0; sp < Q; ++sp) {
+        const float4 q4 = reinterpret_cast<const float4*>(rsm[cc * Q + sp])[swz(y2 >> 1)];
+        out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * y2));
+        out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (y2 + 1)));
       }
+      dft<Q, true>(out[0][cc]);
+      dft<Q, true>(out[1][cc]);
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int y1 = 0; y1 < Q; ++y1) {
+        const int y = y1 * L + y2 + u;
+        if ((unsigned)(y - yout0) < (unsigned)nout) {
+          float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
+#pragma unroll
+          for (int f = 0; f < TC / 2; ++f)
+            __stcs(dst + f, make_float4(out[u][2 * f][y1].x, out[u][2 * f][y1].y, out[u][2 * f + 1][y1].x,
+                                        out[u][2 * f + 1][y1].y));
+        }
+      }
   }
   cl.sync();
 }
@@ -333,13 +356,14 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_c_adj_big_kernel(const __g
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  float4* dst = reinterpret_cast<float4*>(row + (size_t)s * L);
+  constexpr int TC = 8 / Q;
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
-      __stcs(dst + (G::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
+      const int pos = s * L + G::idx(t, b, r);  // J1 row y of the column-tiled buffer (P rows)
+      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, TC)), make_float4(a.x, a.y, c.x, c.y));
     }
   const double tot = block_sum<T>((double)acc, red);
   if (t == 0 && sl.loss_part) sl.loss_part[(size_t)y * Q + s] = tot;

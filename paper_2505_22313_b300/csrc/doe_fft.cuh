@@ -142,12 +142,50 @@ __device__ __forceinline__ void dft16(float2* v) {
   t = v[7]; v[7] = v[13]; v[13] = t;
   t = v[11]; v[11] = v[14]; v[14] = t;
 }
+// cos and sin of 2 pi k / 32, k < 16
+__host__ __device__ constexpr float w32c(int k) {
+  constexpr float c[16] = {1.00000000000000000000f, 0.98078528040323043058f, 0.92387953251128673848f,
+                             0.83146961230254523567f, 0.70710678118654757274f, 0.55557023301960228867f,
+                             0.38268343236508983729f, 0.19509032201612833135f, 0.f, -0.19509032201612819257f,
+                             -0.38268343236508972627f, -0.55557023301960195560f, -0.70710678118654746172f,
+                             -0.83146961230254534669f, -0.92387953251128673848f, -0.98078528040323043058f};
+  return c[k];
+}
+__host__ __device__ constexpr float w32s(int k) {
+  constexpr float c[16] = {0.f, 0.19509032201612824808f, 0.38268343236508978178f, 0.55557023301960217765f,
+                             0.70710678118654746172f, 0.83146961230254523567f, 0.92387953251128673848f,
+                             0.98078528040323043058f, 1.f, 0.98078528040323043058f, 0.92387953251128673848f,
+                             0.83146961230254545772f, 0.70710678118654757274f, 0.55557023301960217765f,
+                             0.38268343236508989280f, 0.19509032201612860891f};
+  return c[k];
+}
+// 32-point DFT: two 16-point DFTs of the even and odd samples, then one radix-2 step with
+// W_32^k (decimation in time).
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* v) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float c = w32c(k), s = INV ? w32s(k) : -w32s(k);  // W_32^k = c + i s
+    const float2 t = k == 0 ? o[k] : (k == 8 ? cmi<INV>(o[k]) : make_float2(fmaf(o[k].x, c, -o[k].y * s), fmaf(o[k].x, s, o[k].y * c)));
+    v[k] = cadd(e[k], t);
+    v[k + 16] = csub(e[k], t);
+  }
+}
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) dft2<INV>(v[0], v[1]);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<INV>(v);
-  else dft16<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+  else dft32<INV>(v);
 }
 
 // ------------------------------------------------------------------ stages
@@ -158,11 +196,12 @@ struct St {
   static constexpr int NST = plan_nst(LOG);
   static constexpr int R = plan_radix(LOG, INV, S);
   static constexpr int NS = plan_ns(LOG, INV, S);
-  static constexpr int B = E / R;  // butterflies per thread (even)
+  static constexpr int B = E / R;  // butterflies per thread: even (adjacent pairs) or 1
+  static constexpr bool PAIRED = B >= 2;
   static_assert(L >= 32 && L <= (1 << kMaxLog) && (L & (L - 1)) == 0, "L must be a power of two in [32, 16384]");
-  static_assert(E == 32 && B % 2 == 0, "butterflies are processed in adjacent pairs");
+  static_assert(E == 32 && (B % 2 == 0 || B == 1), "butterflies are processed in adjacent pairs, or one per thread");
   // butterfly index of register group b (b even: first of a pair)
-  __device__ static __forceinline__ int j(int t, int b) { return 2 * (t + (b >> 1) * T) + (b & 1); }
+  __device__ static __forceinline__ int j(int t, int b) { return PAIRED ? 2 * (t + (b >> 1) * T) + (b & 1) : t; }
   // transform index of register b*R + r in this stage's input layout (and, for the last
   // stage, in its output layout)
   __device__ static __forceinline__ int idx(int t, int b, int r) { return j(t, b) + r * (L / R); }
@@ -195,7 +234,14 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
   using X = St<L, E, INV, S>;
   constexpr int R = X::R, NS = X::NS;
   float4* s4 = reinterpret_cast<float4*>(sm);
-  if constexpr (NS == 1) {
+  if constexpr (!X::PAIRED && NS > 1) {
+    // one butterfly per thread: its outputs base + r Ns are not adjacent, 8-byte accesses
+    const int jj = X::j(t, 0);
+    const int k = jj & (NS - 1);
+    const int base = (jj - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[phys(base + r * NS)] = v[r];
+  } else if constexpr (NS == 1) {
     // butterfly j's outputs are the contiguous elements j R + r
 #pragma unroll
     for (int b = 0; b < X::B; ++b) {
@@ -224,14 +270,19 @@ __device__ __forceinline__ void stage_load(float2 (&v)[E], int t, const float2* 
   using X = St<L, E, INV, S>;
   constexpr int R = X::R;
   const float4* s4 = reinterpret_cast<const float4*>(sm);
+  if constexpr (!X::PAIRED) {
 #pragma unroll
-  for (int b = 0; b < X::B; b += 2) {
-    const int c0 = X::j(t, b) >> 1;
+    for (int r = 0; r < R; ++r) v[r] = sm[phys(X::j(t, 0) + r * (L / R))];
+  } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float4 q = s4[swz(c0 + r * (L / R / 2))];
-      v[b * R + r] = make_float2(q.x, q.y);
-      v[(b + 1) * R + r] = make_float2(q.z, q.w);
+    for (int b = 0; b < X::B; b += 2) {
+      const int c0 = X::j(t, b) >> 1;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 q = s4[swz(c0 + r * (L / R / 2))];
+        v[b * R + r] = make_float2(q.x, q.y);
+        v[(b + 1) * R + r] = make_float2(q.z, q.w);
+      }
     }
   }
 }

@@ -111,4 +111,11 @@ __device__ __forceinline__ int pos_to_k(int pos, int P, int seg_a, int w) {
 }
 __device__ __forceinline__ int abs_signed(int k, int P) { return k < P / 2 ? k : P - k; }
 
+// Column-tiled layout of a spectrum with R rows: stored positions are grouped in tiles of TC
+// adjacent positions, and each tile holds its R rows contiguously (TC samples per row), so
+// the column pass reads one tile as a single contiguous block.  float2 index of (row, pos):
+__device__ __forceinline__ size_t tiled_at(int row, int pos, int R, int TC) {
+  return ((size_t)(pos / TC) * R + row) * TC + (pos % TC);
+}
+
 }  // namespace doe

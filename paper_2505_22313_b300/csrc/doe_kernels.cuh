@@ -38,11 +38,11 @@ __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch
 }
 
 // Writes the stored band positions of a spectrum held in the last-stage layout of a forward
-// row FFT (entries outside the band, at most one per segment, are written as zeros).
+// row FFT into row `row` of the slice's column-tiled buffer (R rows); entries outside the
+// band (at most one per segment) are written as zeros.
 template <int L>
-__device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, float2* row, const Slice& sl) {
+__device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, int row, int R, const Slice& sl) {
   using G = Last<L, false>;
-  float4* dst = reinterpret_cast<float4*>(row);
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
@@ -53,7 +53,7 @@ __device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, flo
         float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
         if (abs_signed(k, L) > sl.kmax) a = make_float2(0.f, 0.f);
         if (abs_signed(k + 1, L) > sl.kmax) c = make_float2(0.f, 0.f);
-        __stcs(dst + (pos >> 1), make_float4(a.x, a.y, c.x, c.y));
+        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(row, pos, R, kTile)), make_float4(a.x, a.y, c.x, c.y));
       }
     }
 }
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
       v[(b + 1) * F::R + r] = c;
     }
   fft_run<L, 32, false>(v, t, sm);
-  store_band_row<L>(v, t, sl.buf + (size_t)i * sl.wp, sl);
+  store_band_row<L>(v, t, i, N, sl);
 }
 
 // ------------------------------------------------------------------ pass B / B*: columns
@@ -144,17 +144,23 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
 
   for (int y = t; y < L; y += T)
     if (y < yin0 || y >= yin0 + nin) sm[phys(y)] = make_float2(0.f, 0.f);
-  float2* rsm[kTile];
+  float4* rsm[kTile];
 #pragma unroll
-  for (int c = 0; c < kTile; ++c) rsm[c] = cl.map_shared_rank(sm, c);
+  for (int c = 0; c < kTile; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
   cl.sync();  // every CTA of the cluster has started before its shared memory is written
   {
+    // thread = (pair of rows rr, rr + 1; column pair f): two 16-byte row loads, and for each
+    // of the two columns one 16-byte store of the adjacent elements (rr, rr + 1) to its owner
     const int rows = nin / kTile, rbeg = q * rows;
-    for (int idx = t; idx < rows * F4; idx += T) {
-      const int rr = rbeg + idx / F4, f = idx % F4;
-      const float4 val = __ldcs(reinterpret_cast<const float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f));
-      rsm[2 * f][phys(yin0 + rr)] = make_float2(val.x, val.y);
-      rsm[2 * f + 1][phys(yin0 + rr)] = make_float2(val.z, val.w);
+    const float2* tile = sl.tbuf + tiled_at(0, pos0, nin, kTile);  // this tile's nin rows, contiguous
+    for (int idx = t; idx < (rows / 2) * F4; idx += T) {
+      const int rr = rbeg + 2 * (idx / F4), f = idx % F4;
+      const float2* src = tile + (size_t)rr * kTile + 2 * f;
+      const float4 u0 = __ldcs(reinterpret_cast<const float4*>(src));
+      const float4 u1 = __ldcs(reinterpret_cast<const float4*>(src + kTile));
+      const int ch = swz((yin0 + rr) >> 1);
+      rsm[2 * f][ch] = make_float4(u0.x, u0.y, u1.x, u1.y);
+      rsm[2 * f + 1][ch] = make_float4(u0.z, u0.w, u1.z, u1.w);
     }
   }
   cl.sync();
@@ -193,11 +199,14 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
   cl.sync();
   {
     const int rows = nout / kTile, rbeg = q * rows;
-    for (int idx = t; idx < rows * F4; idx += T) {
-      const int rr = rbeg + idx / F4, f = idx % F4;
-      const float2 a = rsm[2 * f][phys(yout0 + rr)];
-      const float2 b = rsm[2 * f + 1][phys(yout0 + rr)];
-      __stcs(reinterpret_cast<float4*>(sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f), make_float4(a.x, a.y, b.x, b.y));
+    for (int idx = t; idx < (rows / 2) * F4; idx += T) {
+      const int rr = rbeg + 2 * (idx / F4), f = idx % F4;
+      const int ch = swz((yout0 + rr) >> 1);
+      const float4 a = rsm[2 * f][ch];      // column 2f, rows rr, rr + 1
+      const float4 b = rsm[2 * f + 1][ch];  // column 2f + 1
+      float2* dst = sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f;
+      __stcs(reinterpret_cast<float4*>(dst), make_float4(a.x, a.y, b.x, b.y));
+      __stcs(reinterpret_cast<float4*>(dst + sl.wp), make_float4(a.z, a.w, b.z, b.w));
     }
   }
   cl.sync();
@@ -305,9 +314,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const
       }
     }
   fft_run<L, 32, false>(v, t, sm);
-  // the row is re-written in place: every thread has finished reading it before fft_run's
-  // first barrier, and the stored positions written are the ones read
-  store_band_row<L>(v, t, row, sl);
+  store_band_row<L>(v, t, y, L, sl);  // J1 row y of the column-tiled buffer (P rows)
   const double tot = block_sum<L / 32>((double)acc, red);
   if (t == 0 && sl.loss_part) sl.loss_part[y] = tot;
 }

@@ -164,10 +164,11 @@ cudaError_t pass_a_adj_t(const Batch& bt, cudaStream_t st) {
   return cudaGetLastError();
 }
 // ---- grids longer than one CTA (P = Q * 16384): cluster launches
-cudaError_t launch_cluster(const void* fn, dim3 grid, int cluster, size_t smem, cudaStream_t st, void** args) {
+cudaError_t launch_cluster(const void* fn, dim3 grid, int cluster, size_t smem, cudaStream_t st, void** args,
+                           int threads = kBigL / 32) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(kBigL / 32);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -192,17 +193,18 @@ cudaError_t big_rows_t(int which, const Batch& bt, cudaStream_t st) {
   void* args[] = {const_cast<Batch*>(&bt)};
   return launch_cluster(fn, grid, Q, smem_bytes<kBigL>(), st, args);
 }
-template <int Q>
+template <int LS, int Q, bool ROWSPLIT>
 cudaError_t big_cols_t(const Batch& bt, cudaStream_t st) {
   void* args[] = {const_cast<Batch*>(&bt)};
-  return launch_cluster((const void*)pass_b_big_kernel<Q>, dim3(bt.total_tiles * 8), 8, smem_bytes<kBigL>(), st, args);
+  return launch_cluster((const void*)pass_b_big_kernel<LS, Q, ROWSPLIT>, dim3(bt.total_tiles * 8), 8,
+                        smem_bytes<LS>(), st, args, LS / 32);
 }
 template <int Q>
 cudaError_t prep_big_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<kBigL>();
   if ((e = prep_one(pass_a_big_kernel<Q>, sb))) return e;
-  if ((e = prep_one(pass_b_big_kernel<Q>, sb))) return e;
+  if ((e = prep_one(pass_b_big_kernel<kBigL, Q, true>, sb))) return e;
   if ((e = prep_one(pass_c_big_kernel<Q>, sb))) return e;
   if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb))) return e;
   if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb))) return e;
@@ -257,7 +259,7 @@ cudaError_t prepare_kernels() {
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
       (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<2>()) ||
-      (e = prep_big_t<4>()))
+      (e = prep_big_t<4>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>())))
     return e;
   return cudaSuccess;
 }
@@ -276,9 +278,10 @@ cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
   DOE_DISPATCH(lg, pass_a_t, bt, st);
 }
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
-  if (lg == 15 || lg == 16) {
+  if (lg >= 14) {  // 16384-point columns as 2 x 8192 sub-transforms; longer grids split by 16384
     Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
-    return lg == 15 ? big_cols_t<2>(bt, st) : big_cols_t<4>(bt, st);
+    if (lg == 14) return big_cols_t<8192, 2, false>(bt, st);
+    return lg == 15 ? big_cols_t<kBigL, 2, true>(bt, st) : big_cols_t<kBigL, 4, true>(bt, st);
   }
   DOE_DISPATCH(lg, pass_b_t, bt, st);
 }

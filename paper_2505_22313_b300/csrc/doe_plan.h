@@ -12,8 +12,11 @@ constexpr int kMaxLog = 14;  // L = 16384 (one CTA)
 constexpr int kBigLog = 16;  // 65536-point table for the cross-CTA (four-step) twiddles
 
 __host__ __device__ constexpr int plan_r0(int lg) { return (lg % 4 == 0) ? 16 : (1 << (lg % 4)); }
-__host__ __device__ constexpr int plan_nst(int lg) { return (lg + 3) / 4; }
+// 8192 points use the three-stage plan 16 x 32 x 16 (two exchanges); other lengths radix-16
+// stages plus one radix-2/4/8 stage.
+__host__ __device__ constexpr int plan_nst(int lg) { return lg == 13 ? 3 : (lg + 3) / 4; }
 __host__ __device__ constexpr int plan_radix(int lg, bool inv, int s) {
+  if (lg == 13) return s == 1 ? 32 : 16;
   return inv ? (s == plan_nst(lg) - 1 ? plan_r0(lg) : 16) : (s == 0 ? plan_r0(lg) : 16);
 }
 __host__ __device__ constexpr int plan_ns(int lg, bool inv, int s) {
@@ -60,7 +63,8 @@ constexpr int kMaxQf = 4;   // sub-transforms per row at the largest grid (65536
 struct Slice {
   const float* h;        // [N][N] heights (m)
   const float2* e_in;    // [N][N] incident field or nullptr
-  float2* buf;           // [P][wp] field buffer: I1 (rows < N), I2 / J1 (rows < P), J2 (rows < N)
+  float2* buf;           // [P][wp] natural-layout field buffer: I2 (rows < P), J2 (rows < N)
+  float2* tbuf;          // column-tiled buffer read by the column pass: I1 (N rows), J1 (P rows)
   float2* htab;          // [kmax + 1][hp] transfer function quarter table H(|kt|, |lt|)
   const float* tgt;      // [P][P] target T or dL/dI (gradient)
   void* out;             // [P][P] float PSF or float2 field

@@ -15,7 +15,7 @@ bool pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct RLayout {
-  size_t sa = 0, sb = 0, ks = 0, total = 0;
+  size_t sa = 0, sb = 0, sc = 0, ks = 0, total = 0;
   int wpr = 0;
 };
 
@@ -31,7 +31,8 @@ RLayout render_layout(int C, int H, int W) {
   const size_t plane = (size_t)C * H * L.wpr * sizeof(float2);
   L.sa = 0;
   L.sb = a256(plane);
-  L.ks = L.sb + a256(plane);
+  L.sc = L.sb + a256(plane);
+  L.ks = L.sc + a256(plane);
   L.total = L.ks + a256((size_t)C * H * sizeof(double));
   return L;
 }
@@ -66,6 +67,7 @@ int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const fl
   char* base = static_cast<char*>(ws);
   ra.sa = reinterpret_cast<float2*>(base + lay.sa);
   ra.sb = reinterpret_cast<float2*>(base + lay.sb);
+  ra.sc = reinterpret_cast<float2*>(base + lay.sc);
   ra.ksum = reinterpret_cast<double*>(base + lay.ks);
   if (doe::launch_render(ra, static_cast<cudaStream_t>(stream)) != cudaSuccess) return DOE_ECUDA;
   return DOE_OK;

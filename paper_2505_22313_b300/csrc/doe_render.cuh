@@ -4,10 +4,10 @@
 //   R1  per image row u (channel c): z = img_c[u] + i k_c[u] (both real, zero-padded to 2W),
 //       one complex FFT of length 2W, then the two real spectra are separated in the CTA,
 //       X_img[k] = (Z[k] + conj Z[2W-k]) / 2, X_k[k] = (Z[k] - conj Z[2W-k]) / (2i), k <= W,
-//       and written to SA, SB ([H][wpr] complex).  The crop k_c is read straight from the PSF
+//       and written to SA, SB (column-tiled, H rows).  The crop k_c is read straight from the PSF
 //       around the optical axis; its row sums go to ksum[c][u] (FP64).
 //   R2  per column k <= W (4-column cluster, as the propagation's column pass): column FFTs of
-//       SA and SB (zero-padded to 2H), product, column IFFT, rows [H/2, 3H/2) -> SA in place.
+//       SA and SB (zero-padded to 2H), product, column IFFT, rows [H/2, 3H/2) -> SC.
 //   R3  per pair of output rows: the two Hermitian half spectra are packed as X0 + i X1,
 //       extended to 2W by conjugate symmetry, one complex IFFT, real part = row y, imaginary
 //       part = row y + 1, window [W/2, 3W/2), scaled by 1 / (4 H W sum(k_c)).
@@ -62,14 +62,15 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
       s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
     }
   __syncthreads();
-  float2* sa = ra.sa + ((size_t)c * H + u) * ra.wpr;
-  float2* sb = ra.sb + ((size_t)c * H + u) * ra.wpr;
+  float2* sa = ra.sa + (size_t)c * H * ra.wpr;
+  float2* sb = ra.sb + (size_t)c * H * ra.wpr;
   for (int k = t; k <= W; k += T) {
     const float2 zk = sm[phys(k)];
     const float2 zm = sm[phys((L - k) & (L - 1))];
     // X_img = (Z[k] + conj Z[-k]) / 2, X_k = (Z[k] - conj Z[-k]) / (2i)
-    sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    sb[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    const size_t o = tiled_at(u, k, H, kTile);
+    sa[o] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    sb[o] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
   const double tot = block_sum<T>(ks, red);
   if (t == 0) ra.ksum[(size_t)c * H + u] = tot;
@@ -95,8 +96,9 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
   const int tile = (blockIdx.x / kTile) % tiles;
   const int c = (blockIdx.x / kTile) / tiles;
   const int pos0 = tile * kTile;
-  float2* baseA = ra.sa + (size_t)c * H * ra.wpr;
-  float2* baseB = ra.sb + (size_t)c * H * ra.wpr;
+  const float2* baseA = ra.sa + (size_t)c * H * ra.wpr + tiled_at(0, pos0, H, kTile);  // this tile, H rows
+  const float2* baseB = ra.sb + (size_t)c * H * ra.wpr + tiled_at(0, pos0, H, kTile);
+  float2* baseC = ra.sc + (size_t)c * H * ra.wpr;
   for (int y = H + t; y < L; y += T) {
     sma[phys(y)] = make_float2(0.f, 0.f);
     smb[phys(y)] = make_float2(0.f, 0.f);
@@ -113,8 +115,8 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
     const int rows = H / kTile, rbeg = q * rows;
     for (int idx = t; idx < rows * F4; idx += T) {
       const int rr = rbeg + idx / F4, f = idx % F4;
-      float4 va = __ldcs(reinterpret_cast<const float4*>(baseA + (size_t)rr * ra.wpr + pos0 + 2 * f));
-      float4 vb = __ldcs(reinterpret_cast<const float4*>(baseB + (size_t)rr * ra.wpr + pos0 + 2 * f));
+      float4 va = __ldcs(reinterpret_cast<const float4*>(baseA + (size_t)rr * kTile + 2 * f));
+      float4 vb = __ldcs(reinterpret_cast<const float4*>(baseB + (size_t)rr * kTile + 2 * f));
       if (pos0 + 2 * f > ra.W) va = vb = make_float4(0.f, 0.f, 0.f, 0.f);  // columns past W are unused
       rsa[2 * f][phys(rr)] = make_float2(va.x, va.y);
       rsa[2 * f + 1][phys(rr)] = make_float2(va.z, va.w);
@@ -166,13 +168,13 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
   }
   cl.sync();
   {
-    // rows [H/2, 3H/2) of the column IFFT -> SA rows [0, H)
+    // rows [H/2, 3H/2) of the column IFFT -> SC rows [0, H)
     const int rows = H / kTile, rbeg = q * rows;
     for (int idx = t; idx < rows * F4; idx += T) {
       const int rr = rbeg + idx / F4, f = idx % F4;
       const float2 a = rsb[2 * f][phys(H / 2 + rr)];
       const float2 d = rsb[2 * f + 1][phys(H / 2 + rr)];
-      *reinterpret_cast<float4*>(baseA + (size_t)rr * ra.wpr + pos0 + 2 * f) = make_float4(a.x, a.y, d.x, d.y);
+      __stcs(reinterpret_cast<float4*>(baseC + (size_t)rr * ra.wpr + pos0 + 2 * f), make_float4(a.x, a.y, d.x, d.y));
     }
   }
   cl.sync();
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
   __shared__ double red[32];
   const int y = 2 * blockIdx.x, c = blockIdx.y, t = threadIdx.x;
   const int W = ra.W, H = ra.H;
-  const float2* x0 = ra.sa + ((size_t)c * H + y) * ra.wpr;
+  const float2* x0 = ra.sc + ((size_t)c * H + y) * ra.wpr;
   const float2* x1 = x0 + ra.wpr;
   // sum of the kernel crop (fixed order, FP64)
   double ks = 0.0;

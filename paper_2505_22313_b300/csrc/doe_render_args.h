@@ -10,8 +10,9 @@ struct RenderArgs {
   const float* psf;     // [C][Py][Px]
   const float* img;     // [C][H][W]
   float* out;           // [C][H][W]
-  float2* sa;           // [C][H][wpr]
-  float2* sb;           // [C][H][wpr]
+  float2* sa;           // [C] column-tiled H x wpr: image row spectra
+  float2* sb;           // [C] column-tiled H x wpr: kernel row spectra
+  float2* sc;           // [C][H][wpr] natural layout: product after the column IFFT
   double* ksum;         // [C][H]
 };
 }  // namespace doe
