@@ -93,8 +93,9 @@ long long band_mev(double lam, double dx, long P) {
   return (long long)std::ceil(x);
 }
 
-// Columns per column-pass tile: 4, except 8 / Q for split columns (P = 32768: 4, 65536: 2).
-int col_tile(long P) { return P == 65536 ? 2 : kTile; }
+// Columns per column-pass tile: 4, except for rows split into Q = P / 8192 sub-transforms,
+// where a cluster holds 8 / Q columns (P = 32768: 2, P = 65536: 1).
+int col_tile(long P) { return P == 65536 ? 1 : (P == 32768 ? 2 : kTile); }
 
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
@@ -198,7 +199,7 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
   bt.P = pad * N;
   bt.off = (bt.P - N) / 2;
   bt.inv_p2 = (float)(1.0 / ((double)bt.P * (double)bt.P));
-  bt.qf = bt.P > (1 << kMaxLog) ? bt.P >> kMaxLog : 1;
+  bt.qf = bt.P > (1 << kMaxLog) ? bt.P / 8192 : 1;
   int tiles = 0, kmx = 0;
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j] = sl[j];

@@ -1,7 +1,8 @@
 // doe_big.cuh -- transforms split across a cluster: P = Q * LS with sub-transforms of LS points.
-// Rows of grids longer than one CTA's transform (P = 32768, 65536: LS = 16384, Q = 2, 4) and
-// the column pass of the 16384-point grid (LS = 8192, Q = 2: 64 KB of shared memory per CTA
-// instead of 128 KB, so several CTAs share an SM).
+// Grids longer than 16384 (P = 32768: Q = 4, P = 65536: Q = 8) and the column pass of the
+// 16384 grid (Q = 2) all use LS = 8192: 64 KB of shared memory and 256 threads per CTA, so
+// two CTAs share an SM and one CTA's global / distributed-shared-memory phases overlap
+// another's transforms.
 //
 // A length-P transform is split across a cluster of Q CTAs, each running the in-CTA engine
 // on L = LS points (sub-transform s):
@@ -21,7 +22,7 @@
 
 namespace doe {
 
-constexpr int kBigL = 16384;
+constexpr int kBigL = 8192;  // sub-transform length of split rows / columns
 
 // W_P^m (forward sign) for 0 <= m < P <= 65536.  With n = m 65536 / P = 256 hi + lo,
 // W_65536^n = W_65536^{256 hi} W_65536^{lo}: two lookups in 256-entry tables (4 KB in all,
@@ -36,10 +37,12 @@ __device__ __forceinline__ float2 tw_apply(float2 a, float2 w) { return INV ? cm
 
 // frequency index of stored column position pos when rows are stored in sub-transform order
 __device__ __forceinline__ int big_pos_to_k(int pos, int Q) { return (pos % kBigL) * Q + pos / kBigL; }
+// column tile of split grids: 8 / Q columns (one cluster = tile columns x Q sub-transforms)
+__host__ __device__ constexpr int big_tile(int Q) { return Q >= 8 ? 1 : 8 / Q; }
 
 // ------------------------------------------------------------------ rows, forward (pass A)
 template <int Q>
-__global__ void __launch_bounds__(kBigL / 32, 1) pass_a_big_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, P = L * Q, SH = L / Q;
   using G = Last<L, false>;
   extern __shared__ float2 sm[];
@@ -83,14 +86,19 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_a_big_kernel(const __grid_
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  constexpr int TC = 8 / Q;
+  constexpr int TC = big_tile(Q);
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);
-      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, TC)), make_float4(a.x, a.y, c.x, c.y));
+      if constexpr (TC >= 2) {
+        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, TC)), make_float4(a.x, a.y, c.x, c.y));
+      } else {  // one-column tiles: the two positions are in different tiles
+        __stcs(sl.tbuf + tiled_at(i, pos, N, 1), a);
+        __stcs(sl.tbuf + tiled_at(i, pos + 1, N, 1), c);
+      }
     }
 }
 
@@ -140,7 +148,7 @@ __device__ __forceinline__ void big_combine(float4* const (&rsm)[Q], int x2, flo
 
 // ------------------------------------------------------------------ rows, inverse (pass C)
 template <int Q>
-__global__ void __launch_bounds__(kBigL / 32, 1) pass_c_big_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, SH = L / Q;
   extern __shared__ float2 sm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -173,11 +181,12 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_c_big_kernel(const __grid_
 }
 
 // ------------------------------------------------------------------ columns (pass B / B*)
-// Cluster of 8 CTAs: TC = 8 / Q adjacent stored columns x Q sub-transforms; rank = c Q + s.
+// Cluster of TC x Q CTAs (TC = big_tile(Q) adjacent stored columns x Q sub-transforms, at
+// most 8); rank = c Q + s.
 // ROWSPLIT: rows are stored in sub-transform order (P > 16384); otherwise band-compacted.
 template <int LS, int Q, bool ROWSPLIT>
 __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
-  constexpr int L = LS, T = L / 32, P = L * Q, TC = 8 / Q, CL = 8, SH = L / CL;
+  constexpr int L = LS, T = L / 32, P = L * Q, TC = big_tile(Q), CL = TC * Q, SH = L / CL;
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   static_assert(G::R == First<L, true>::R, "register hand-off needs equal radices");
@@ -205,24 +214,38 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
   // thread takes the adjacent pair (y2, y2 + 1) so its shared-memory writes are 16 bytes
   for (int y2 = rank * SH + 2 * t; y2 < (rank + 1) * SH; y2 += 2 * T) {
     float2 col[2][TC][Q];
+    if constexpr (TC >= 2) {
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int y1 = 0; y1 < Q; ++y1) {
+          const int y = y1 * L + y2 + u;
+          if ((unsigned)(y - yin0) < (unsigned)nin) {
+            const float4* src = reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, TC));
+#pragma unroll
+            for (int f = 0; f < TC / 2; ++f) {
+              const float4 q4 = __ldcs(src + f);
+              col[u][2 * f][y1] = make_float2(q4.x, q4.y);
+              col[u][2 * f + 1][y1] = make_float2(q4.z, q4.w);
+            }
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < TC; ++cc) col[u][cc][y1] = make_float2(0.f, 0.f);
+          }
+        }
+    } else {
+      // one-column tile: rows y, y + 1 are adjacent samples; y - yin0 and nin are even, so
+      // the pair is 16-byte aligned and lies wholly inside or wholly outside the input rows
 #pragma unroll
       for (int y1 = 0; y1 < Q; ++y1) {
-        const int y = y1 * L + y2 + u;
-        if ((unsigned)(y - yin0) < (unsigned)nin) {
-          const float4* src = reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, TC));
-#pragma unroll
-          for (int f = 0; f < TC / 2; ++f) {
-            const float4 q4 = __ldcs(src + f);
-            col[u][2 * f][y1] = make_float2(q4.x, q4.y);
-            col[u][2 * f + 1][y1] = make_float2(q4.z, q4.w);
-          }
-        } else {
-#pragma unroll
-          for (int cc = 0; cc < TC; ++cc) col[u][cc][y1] = make_float2(0.f, 0.f);
-        }
+        const int y = y1 * L + y2;
+        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)(y - yin0) < (unsigned)nin)
+          q4 = __ldcs(reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, 1)));
+        col[0][0][y1] = make_float2(q4.x, q4.y);
+        col[1][0][y1] = make_float2(q4.z, q4.w);
       }
+    }
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {
       dft<Q, false>(col[0][cc]);
@@ -287,11 +310,15 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
       for (int y1 = 0; y1 < Q; ++y1) {
         const int y = y1 * L + y2 + u;
         if ((unsigned)(y - yout0) < (unsigned)nout) {
-          float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
+          if constexpr (TC >= 2) {
+            float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
 #pragma unroll
-          for (int f = 0; f < TC / 2; ++f)
-            __stcs(dst + f, make_float4(out[u][2 * f][y1].x, out[u][2 * f][y1].y, out[u][2 * f + 1][y1].x,
-                                        out[u][2 * f + 1][y1].y));
+            for (int f = 0; f < TC / 2; ++f)
+              __stcs(dst + f, make_float4(out[u][2 * f][y1].x, out[u][2 * f][y1].y, out[u][2 * f + 1][y1].x,
+                                          out[u][2 * f + 1][y1].y));
+          } else {
+            __stcs(sl.buf + (size_t)(y - yout0) * sl.wp + pos0, out[u][0][y1]);
+          }
         }
       }
   }
@@ -300,7 +327,7 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
 
 // ------------------------------------------------------------------ rows, adjoint (pass C')
 template <int Q>
-__global__ void __launch_bounds__(kBigL / 32, 1) pass_c_adj_big_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, P = L * Q, SH = L / Q, IT = SH / (2 * T);
   using G = Last<L, false>;
   extern __shared__ float2 sm[];
@@ -356,14 +383,19 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_c_adj_big_kernel(const __g
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  constexpr int TC = 8 / Q;
+  constexpr int TC = big_tile(Q);
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);  // J1 row y of the column-tiled buffer (P rows)
-      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, TC)), make_float4(a.x, a.y, c.x, c.y));
+      if constexpr (TC >= 2) {
+        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, TC)), make_float4(a.x, a.y, c.x, c.y));
+      } else {
+        __stcs(sl.tbuf + tiled_at(y, pos, P, 1), a);
+        __stcs(sl.tbuf + tiled_at(y, pos + 1, P, 1), c);
+      }
     }
   const double tot = block_sum<T>((double)acc, red);
   if (t == 0 && sl.loss_part) sl.loss_part[(size_t)y * Q + s] = tot;
@@ -371,7 +403,7 @@ __global__ void __launch_bounds__(kBigL / 32, 1) pass_c_adj_big_kernel(const __g
 
 // ------------------------------------------------------------------ DOE rows, adjoint (pass A*)
 template <int Q>
-__global__ void __launch_bounds__(kBigL / 32, 1) pass_a_adj_big_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, SH = L / Q, IT = SH / (2 * T);
   extern __shared__ float2 sm[];
   cg::cluster_group cl = cg::this_cluster();

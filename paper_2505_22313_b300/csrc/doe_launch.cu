@@ -163,7 +163,7 @@ cudaError_t pass_a_adj_t(const Batch& bt, cudaStream_t st) {
   pass_a_adj_kernel<L><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
-// ---- grids longer than one CTA (P = Q * 16384): cluster launches
+// ---- grids longer than one CTA (P = Q * 8192 sub-transforms): cluster launches
 cudaError_t launch_cluster(const void* fn, dim3 grid, int cluster, size_t smem, cudaStream_t st, void** args,
                            int threads = kBigL / 32) {
   cudaLaunchConfig_t cfg = {};
@@ -196,7 +196,8 @@ cudaError_t big_rows_t(int which, const Batch& bt, cudaStream_t st) {
 template <int LS, int Q, bool ROWSPLIT>
 cudaError_t big_cols_t(const Batch& bt, cudaStream_t st) {
   void* args[] = {const_cast<Batch*>(&bt)};
-  return launch_cluster((const void*)pass_b_big_kernel<LS, Q, ROWSPLIT>, dim3(bt.total_tiles * 8), 8,
+  constexpr int CL = big_tile(Q) * Q;
+  return launch_cluster((const void*)pass_b_big_kernel<LS, Q, ROWSPLIT>, dim3(bt.total_tiles * CL), CL,
                         smem_bytes<LS>(), st, args, LS / 32);
 }
 template <int Q>
@@ -258,8 +259,8 @@ cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
-      (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<2>()) ||
-      (e = prep_big_t<4>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>())))
+      (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<4>()) ||
+      (e = prep_big_t<8>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>())))
     return e;
   return cudaSuccess;
 }
@@ -271,17 +272,17 @@ cudaError_t launch_htab(const Batch& bt, cudaStream_t st) {
 }
 // Grids longer than one CTA (lg = 15, 16) go to the cluster-split passes of doe_big.cuh.
 #define DOE_BIG_ROWS(which, trace)                                          \
-  if (lg == 15) { Traced tr(trace, st); return big_rows_t<2>(which, bt, st); } \
-  if (lg == 16) { Traced tr(trace, st); return big_rows_t<4>(which, bt, st); }
+  if (lg == 15) { Traced tr(trace, st); return big_rows_t<4>(which, bt, st); } \
+  if (lg == 16) { Traced tr(trace, st); return big_rows_t<8>(which, bt, st); }
 cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
   DOE_BIG_ROWS(0, TR_PASS_A)
   DOE_DISPATCH(lg, pass_a_t, bt, st);
 }
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
-  if (lg >= 14) {  // 16384-point columns as 2 x 8192 sub-transforms; longer grids split by 16384
+  if (lg >= 14) {  // columns of 16384 and longer as Q = P / 8192 sub-transforms of 8192 points
     Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
     if (lg == 14) return big_cols_t<8192, 2, false>(bt, st);
-    return lg == 15 ? big_cols_t<kBigL, 2, true>(bt, st) : big_cols_t<kBigL, 4, true>(bt, st);
+    return lg == 15 ? big_cols_t<kBigL, 4, true>(bt, st) : big_cols_t<kBigL, 8, true>(bt, st);
   }
   DOE_DISPATCH(lg, pass_b_t, bt, st);
 }
