@@ -38,7 +38,7 @@ const std::vector<float2>& host_stage_tables() {
           const long ns = plan_ns(lg, inv, s), R = plan_radix(lg, inv, s);
           float2* p = tw.data() + tw_offset(lg, inv, s);
           for (long k = 0; k < ns; ++k)
-            for (long r = 0; r < R; ++r) p[k * R + r] = twiddle(r * k, ns * R);
+            for (long r = 0; r < R; ++r) p[2 * tw_quad((int)R, (int)ns, (int)k, (int)r) + (r & 1)] = twiddle(r * k, ns * R);
         }
   }
   return tw;

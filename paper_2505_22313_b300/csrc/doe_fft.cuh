@@ -216,10 +216,10 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
   for (int b = 0; b < X::B; ++b) {
     if constexpr (S > 0) {
       const int k = X::j(t, b) & (X::NS - 1);
-      const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(X::LOG, INV, S) + (long)k * R);
+      const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(X::LOG, INV && !tw_shared_dirs(X::LOG), S));
 #pragma unroll
       for (int r = 0; r < R; r += 2) {
-        const float4 w = __ldg(tw + r / 2);
+        const float4 w = __ldg(tw + tw_quad(R, X::NS, k, r));
         if (r > 0) v[b * R + r] = ctw<INV>(v[b * R + r], make_float2(w.x, w.y));
         v[b * R + r + 1] = ctw<INV>(v[b * R + r + 1], make_float2(w.z, w.w));
       }

@@ -99,24 +99,39 @@ constexpr int threads() { return L / 32; }
 // Dynamic shared memory above 48 KB must be opted into, and the carveout preference set to
 // the maximum so that several CTAs of a pass fit on one SM.
 template <typename K>
-cudaError_t prep_one(K* kern, int smem) {
+cudaError_t prep_one(K* kern, int smem, int threads) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)))
+    return e;
+  // Registers, not shared memory, bound the resident CTAs of these kernels; give shared memory
+  // only what those CTAs use, so the rest of the SM's 256 KB serves as L1 for the twiddle tables.
+  int dev = 0, blocks = 0, per_sm = 0, reserved = 0;
+  cudaFuncAttributes fa;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaFuncGetAttributes(&fa, kern)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem)) ||
+      (e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) ||
+      (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)))
+    return e;
+  if (blocks < 1 || per_sm <= 0) return cudaSuccess;
+  const long need = (long)blocks * ((long)smem + (long)fa.sharedSizeBytes + reserved);
+  const int pct = (int)((need * 100 + per_sm - 1) / per_sm);
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
 }
 template <int L>
 cudaError_t prep_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<L>();
-  if ((e = prep_one(pass_a_kernel<L>, sb))) return e;
-  if ((e = prep_one(pass_b_kernel<L>, sb))) return e;
-  if ((e = prep_one(pass_c_kernel<L>, sb))) return e;
-  if ((e = prep_one(pass_c_adj_kernel<L>, sb))) return e;
-  if ((e = prep_one(pass_a_adj_kernel<L>, sb))) return e;
-  if ((e = prep_one(render_rows_kernel<L>, sb))) return e;
+  const int nt = threads<L>();
+  if ((e = prep_one(pass_a_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_b_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_c_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_c_adj_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_adj_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(render_rows_kernel<L>, sb, nt))) return e;
   if constexpr (L <= kRenderColsMax)  // two L-sample buffers must fit one CTA's shared memory
-    if ((e = prep_one(render_cols_kernel<L>, 2 * sb))) return e;
-  if ((e = prep_one(render_out_kernel<L>, sb))) return e;
+    if ((e = prep_one(render_cols_kernel<L>, 2 * sb, nt))) return e;
+  if ((e = prep_one(render_out_kernel<L>, sb, nt))) return e;
   return cudaSuccess;
 }
 
@@ -204,11 +219,12 @@ template <int Q>
 cudaError_t prep_big_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<kBigL>();
-  if ((e = prep_one(pass_a_big_kernel<Q>, sb))) return e;
-  if ((e = prep_one(pass_b_big_kernel<kBigL, Q, true>, sb))) return e;
-  if ((e = prep_one(pass_c_big_kernel<Q>, sb))) return e;
-  if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb))) return e;
-  if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb))) return e;
+  constexpr int nt = kBigL / 32;
+  if ((e = prep_one(pass_a_big_kernel<Q>, sb, nt))) return e;
+  if ((e = prep_one(pass_b_big_kernel<kBigL, Q, true>, sb, nt))) return e;
+  if ((e = prep_one(pass_c_big_kernel<Q>, sb, nt))) return e;
+  if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb, nt))) return e;
   return cudaSuccess;
 }
 
@@ -260,7 +276,7 @@ cudaError_t prepare_kernels() {
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
       (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<4>()) ||
-      (e = prep_big_t<8>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>())))
+      (e = prep_big_t<8>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>(), 8192 / 32)))
     return e;
   return cudaSuccess;
 }

@@ -37,6 +37,17 @@ __host__ __device__ constexpr long tw_offset(int lg, bool inv, int s) {
   return off;
 }
 constexpr long kTwTotal = tw_offset(kMaxLog + 1, false, 0);
+// Forward and inverse plans of 8192 points are the same 16 x 32 x 16, so both directions read
+// the forward table (the inverse applies the conjugate): one 68 KB table stays in L1.
+__host__ __device__ constexpr bool tw_shared_dirs(int lg) { return lg == 13; }
+// Stage table layout, float4 units: entry (k, r) for even r holds (W^{k r}, W^{k (r + 1)}),
+// W = W_{Ns R}.  Stages with two butterflies per thread (R <= 16) hand lane t the butterflies
+// k = 2 t' + p, so their table is ordered (r / 2, p, k / 2); one-butterfly stages (R = 32)
+// hand lane t the butterfly k = t mod Ns, ordered (r / 2, k).  Either way the lanes of a warp
+// read one contiguous 512-byte run per load.
+__host__ __device__ constexpr long tw_quad(int R, int ns, int k, int r) {
+  return R <= 16 ? ((long)(r >> 1) * 2 + (k & 1)) * (ns >> 1) + (k >> 1) : (long)(r >> 1) * ns + k;
+}
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 __host__ __device__ constexpr int smem_words(int L) { return L; }
