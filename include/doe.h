@@ -28,7 +28,8 @@
  *  - Grid: N x N DOE samples (N a power of two, 16 <= N), padded to P = pad * N per axis with
  *    the DOE at offset (P - N) / 2; output sample (y, x) lies at the same physical position
  *    as padded input sample (y, x) (the optical axis is at (P/2, P/2)).  This build supports
- *    P <= 16384.
+ *    P <= 65536; above 16384 each row / column transform is split across a thread-block
+ *    cluster of P / 8192 CTAs.
  */
 #ifndef DOE_H
 #define DOE_H
@@ -85,7 +86,7 @@ size_t doe_workspace_bytes(const doe_geom* g, int op);
  *   h      device float [ny][nx]          heights in metres (Eq. 1)
  *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
  *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
- * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (P > 16384 or
+ * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (P > 65536 or
  * nx != ny), DOE_ENOWS (workspace), DOE_ECUDA. */
 int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
                   size_t ws_bytes, void* stream);
