@@ -62,6 +62,7 @@ def _load():
         "orc_propagate": ([L, L, D, D, D, D, Ii, P, P, P], Ii),
         "orc_psf": ([L, L, D, D, D, D, Ii, P, P, P], Ii),
         "orc_psf_rows": ([L, L, D, D, D, D, Ii, P, P, L, P, P], Ii),
+        "orc_grad_rows": ([L, L, D, D, D, D, Ii, P, P, L, P, P, L, P, P], Ii),
         "orc_grad": ([L, L, D, D, L, P, P, Ii, P, P, P, Ii, P, P], Ii),
         "orc_loss_l2": ([L, L, D, D, L, P, P, Ii, P, P, P, P], Ii),
         "orc_fd_exact": ([L, L, D, D, L, P, P, Ii, P, P, P, L, P, P, D, P], Ii),
@@ -184,6 +185,28 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
     _check(
         _load().orc_psf_rows(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows), _ptr(out)),
         "psf_rows",
+    )
+    return out
+
+
+def grad_rows(h, dx, z, lam, rows, g_rows, drows, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """Exact FP64 dL/dh on the DOE rows ``drows`` [len(drows)][N] for one wavelength, when
+    dL/dI is ``g_rows`` [len(rows)][P] on the output rows ``rows`` (distinct) and zero on every
+    other row, without holding the P x P field."""
+    h = _f32(h)
+    N = h.shape[0]
+    P = pad * N
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    drows = np.ascontiguousarray(drows, dtype=np.int64)
+    if np.unique(rows).size != rows.size:
+        raise ValueError("rows must be distinct")
+    g_rows = _f32(g_rows).reshape(rows.size, P)
+    out = np.empty((drows.size, N), np.float64)
+    e_in = _c128(e_in)
+    _check(
+        _load().orc_grad_rows(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows),
+                              _ptr(g_rows), drows.size, _ptr(drows), _ptr(out)),
+        "grad_rows",
     )
     return out
 

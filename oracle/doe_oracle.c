@@ -316,6 +316,106 @@ int orc_psf_rows(long N, long pad, double dx, double z, double lambda, double n_
 }
 
 /* ------------------------------------------------------------------------------------
+ * Row-masked adjoint for grids whose FP64 field does not fit host memory (Sec. 3.1, Eq. 4
+ * with dL/dI non-zero only on the output rows `rows`, one wavelength).  The output rows of
+ * E_out are formed as in orc_psf_rows; then
+ *   g_out = G E_out on those rows (G = dL/dI, zero on every other row),
+ *   g_pad = IFFT2( conj(H) FFT2(g_out) )  (numpy normalisation),
+ * where the column transforms see only the non-zero rows and keep only the requested DOE rows
+ * `drows` (0-based DOE row indices, padded row off + d), and
+ *   dL/dh[d][x] = -2 k' Im( conj(g_pad[off + d][off + x]) E_doe[d][x] ).
+ * rows must be distinct.  g_rows: float [nrows][P]; grad_rows: double [nd][N] (overwritten).
+ * ---------------------------------------------------------------------------------- */
+int orc_grad_rows(long N, long pad, double dx, double z, double lambda, double n_index,
+                  int bandlimit, const float *h, const cplx *e_in, long nrows, const long *rows,
+                  const float *g_rows, long nd, const long *drows, double *grad_rows) {
+    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    long P = pad * N, off = (P - N) / 2;
+    long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
+    int64_t mev = orc_mev(lambda, dx, P);
+    double du = 1.0 / ((double)P * dx);
+    double kp = orc_kprime(lambda, n_index);
+    double s = 1.0 / ((double)P * (double)P);
+    cplx *a = (cplx *)malloc((size_t)N * P * sizeof(cplx));
+    cplx *out = (cplx *)calloc((size_t)nrows * P, sizeof(cplx));
+    if (!a || !out) { free(a); free(out); return -2; }
+    /* forward: row FFT of the N DOE rows of E_pad */
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) {
+        cplx *row = a + i * P;
+        memset(row, 0, (size_t)P * sizeof(cplx));
+        for (long j = 0; j < N; ++j) {
+            double phi = kp * (double)h[i * N + j];
+            cplx t = cos(phi) + I * sin(phi);
+            row[off + j] = e_in ? e_in[i * N + j] * t : t;
+        }
+        orc_fft1d(row, P, -1);
+    }
+    /* forward: per column, FFT, x H, IFFT; keep the requested output rows */
+#pragma omp parallel
+    {
+        cplx *col = (cplx *)malloc((size_t)P * sizeof(cplx));
+#pragma omp for schedule(static)
+        for (long k = 0; k < P; ++k) {
+            memset(col, 0, (size_t)P * sizeof(cplx));
+            for (long i = 0; i < N; ++i) col[off + i] = a[i * P + k];
+            orc_fft1d(col, P, -1);
+            long kt = orc_signed_index(k, P);
+            for (long l = 0; l < P; ++l)
+                col[l] *= orc_transfer_value(kt, orc_signed_index(l, P), kmax, mev, du, lambda, z);
+            orc_fft1d(col, P, +1);
+            for (long r = 0; r < nrows; ++r) out[r * P + k] = col[rows[r]];
+        }
+        free(col);
+    }
+    free(a);
+    /* E_out on the rows (row IFFT, 1/P^2), g_out = G E_out, then the row FFT of g_out */
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < nrows; ++r) {
+        cplx *row = out + r * P;
+        orc_fft1d(row, P, +1);
+        for (long x = 0; x < P; ++x) row[x] *= s * (double)g_rows[r * P + x];
+        orc_fft1d(row, P, -1);
+    }
+    /* adjoint: per column, FFT over the (sparse) rows, x conj(H), IFFT; keep the DOE rows */
+    cplx *b = (cplx *)calloc((size_t)nd * P, sizeof(cplx));
+    if (!b) { free(out); return -2; }
+#pragma omp parallel
+    {
+        cplx *col = (cplx *)malloc((size_t)P * sizeof(cplx));
+#pragma omp for schedule(static)
+        for (long k = 0; k < P; ++k) {
+            memset(col, 0, (size_t)P * sizeof(cplx));
+            for (long r = 0; r < nrows; ++r) col[rows[r]] = out[r * P + k];
+            orc_fft1d(col, P, -1);
+            long kt = orc_signed_index(k, P);
+            for (long l = 0; l < P; ++l)
+                col[l] *= conj(orc_transfer_value(kt, orc_signed_index(l, P), kmax, mev, du, lambda, z));
+            orc_fft1d(col, P, +1);
+            for (long d = 0; d < nd; ++d) b[d * P + k] = col[off + drows[d]];
+        }
+        free(col);
+    }
+    free(out);
+    /* row IFFT of the kept DOE rows, 1/P^2, crop to the DOE window, dL/dh */
+#pragma omp parallel for schedule(static)
+    for (long d = 0; d < nd; ++d) {
+        cplx *row = b + d * P;
+        long i = drows[d];
+        orc_fft1d(row, P, +1);
+        for (long x = 0; x < N; ++x) {
+            cplx g = row[off + x] * s;
+            double phi = kp * (double)h[i * N + x];
+            cplx e = cos(phi) + I * sin(phi);
+            if (e_in) e *= e_in[i * N + x];
+            grad_rows[d * N + x] = -2.0 * kp * cimag(conj(g) * e);
+        }
+    }
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
  * Gradient (Eq. 4).  For each wavelength j:
  *   E_out = A_j E_pad with A_j = (1/P^2) F^H diag(H_j) F (F = unnormalised 2-D DFT);
  *   g_out = dL/d conj(E_out) = 2 (I - T) E_out      (mode 0: L = sum (I - T)^2)

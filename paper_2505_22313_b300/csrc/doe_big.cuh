@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
 #pragma unroll
   for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
   cl.sync();  // every CTA of the cluster has started before its shared memory is written
-  for (int n2 = s * SH + 2 * t; n2 < (s + 1) * SH; n2 += 2 * T) {
+#pragma unroll
+  for (int it = 0; it < SH / (2 * T); ++it) {  // compile-time count: loads of all items in flight together
+    const int n2 = s * SH + 2 * t + it * 2 * T;
     float2 xa[Q], xb[Q];
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
@@ -163,7 +165,9 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
   big_row_inverse_to_smem<Q>(sl.buf + (size_t)y * sl.wp, s, t, sm);
   cl.sync();
   const float sc = bt.inv_p2;
-  for (int x2 = s * SH + 2 * t; x2 < (s + 1) * SH; x2 += 2 * T) {
+#pragma unroll
+  for (int it = 0; it < SH / (2 * T); ++it) {
+    const int x2 = s * SH + 2 * t + it * 2 * T;
     float2 oa[Q], ob[Q];
     big_combine<Q>(rsm, x2, oa, ob);
 #pragma unroll
@@ -212,7 +216,9 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
   cl.sync();
   // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2; each
   // thread takes the adjacent pair (y2, y2 + 1) so its shared-memory writes are 16 bytes
-  for (int y2 = rank * SH + 2 * t; y2 < (rank + 1) * SH; y2 += 2 * T) {
+#pragma unroll
+  for (int it = 0; it < SH / (2 * T); ++it) {
+    const int y2 = rank * SH + 2 * t + it * 2 * T;
     float2 col[2][TC][Q];
     if constexpr (TC >= 2) {
 #pragma unroll
@@ -291,7 +297,9 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
   }
   cl.sync();
   // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2 (pairs y2, y2 + 1)
-  for (int y2 = rank * SH + 2 * t; y2 < (rank + 1) * SH; y2 += 2 * T) {
+#pragma unroll
+  for (int it = 0; it < SH / (2 * T); ++it) {
+    const int y2 = rank * SH + 2 * t + it * 2 * T;
     float2 out[2][TC][Q];
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {

@@ -113,11 +113,11 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
 }
 
 // ------------------------------------------------------------------ pass B / B*: columns
-// A cluster of kTile CTAs owns kTile adjacent stored columns; CTA q transforms column q in
-// its own shared memory.  Global rows are moved as whole 32-byte sectors (one float4 per 2
-// columns): each CTA loads a quarter of the rows and scatters them into the owners' shared
-// memory (distributed shared memory), and after the transforms gathers a quarter of the
-// output rows from all four CTAs.
+// A cluster of kTile CTAs owns kTile adjacent stored columns; CTA q transforms column q.
+// Input: each CTA reads its own column of the column-tiled buffer directly into registers
+// (the cluster's CTAs together consume whole 32-byte sectors).  Output: after the transforms
+// each CTA gathers a quarter of the output rows of all four columns from the cluster's shared
+// memory (distributed shared memory) and writes them as 32-byte row segments.
 template <int L>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __grid_constant__ Batch bt) {
   using G = Last<L, false>;  // forward's last stage = inverse's first stage (radix 16)
@@ -142,34 +142,40 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
   const int kcol = pos_to_k(mypos, L, sl.seg_a, sl.w);
   const bool live = mypos < sl.w && abs_signed(kcol, L) <= sl.kmax;
 
-  for (int y = t; y < L; y += T)
-    if (y < yin0 || y >= yin0 + nin) sm[phys(y)] = make_float2(0.f, 0.f);
   float4* rsm[kTile];
 #pragma unroll
   for (int c = 0; c < kTile; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
-  cl.sync();  // every CTA of the cluster has started before its shared memory is written
-  {
-    // thread = (pair of rows rr, rr + 1; column pair f): two 16-byte row loads, and for each
-    // of the two columns one 16-byte store of the adjacent elements (rr, rr + 1) to its owner
-    const int rows = nin / kTile, rbeg = q * rows;
-    const float2* tile = sl.tbuf + tiled_at(0, pos0, nin, kTile);  // this tile's nin rows, contiguous
-    for (int idx = t; idx < (rows / 2) * F4; idx += T) {
-      const int rr = rbeg + 2 * (idx / F4), f = idx % F4;
-      const float2* src = tile + (size_t)rr * kTile + 2 * f;
-      const float4 u0 = __ldcs(reinterpret_cast<const float4*>(src));
-      const float4 u1 = __ldcs(reinterpret_cast<const float4*>(src + kTile));
-      const int ch = swz((yin0 + rr) >> 1);
-      rsm[2 * f][ch] = make_float4(u0.x, u0.y, u1.x, u1.y);
-      rsm[2 * f + 1][ch] = make_float4(u0.z, u0.w, u1.z, u1.w);
-    }
+  const float2* hrow = sl.htab + (size_t)abs_signed(kcol, L) * sl.hp;
+  if (live) {  // this column's transfer-function row, into L1 ahead of the multiply
+    const char* hb = reinterpret_cast<const char*>(hrow);
+    for (int o = 128 * t; o < (sl.kmax + 1) * (int)sizeof(float2); o += 128 * T)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(hb + o));
   }
-  cl.sync();
-
+  // This CTA's column straight into the first stage's registers: rows e, e + 1 of the pair
+  // are two 8-byte loads 32 bytes apart in the tile (e - yin0 and nin are even, so both are
+  // inside or both outside the input rows).  The cluster's CTAs read the four columns of each
+  // 32-byte sector together, so DRAM still delivers every sector once.
   float2 v[32];
-  stage_load<L, 32, false, 0>(v, t, sm);
+  {
+    using F = First<L, false>;
+    static_assert(F::PAIRED, "first stage holds adjacent pairs");
+    const float2* col = sl.tbuf + tiled_at(0, mypos, nin, kTile);
+#pragma unroll
+    for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < F::R; ++r) {
+        const int y = F::idx(t, b, r) - yin0;
+        float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+        if (live && (unsigned)y < (unsigned)nin) {
+          a = __ldcs(col + (size_t)y * kTile);
+          c = __ldcs(col + (size_t)(y + 1) * kTile);
+        }
+        v[b * F::R + r] = a;
+        v[(b + 1) * F::R + r] = c;
+      }
+  }
   fft_run<L, 32, false>(v, t, sm);
   {
-    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, L) * sl.hp;
 #pragma unroll
     for (int b = 0; b < G::B; ++b)
 #pragma unroll
@@ -196,17 +202,32 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
         s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
       }
   }
-  cl.sync();
+  cl.sync();  // all four columns are in shared memory (and every CTA of the cluster has started)
   {
-    const int rows = nout / kTile, rbeg = q * rows;
-    for (int idx = t; idx < (rows / 2) * F4; idx += T) {
-      const int rr = rbeg + 2 * (idx / F4), f = idx % F4;
-      const int ch = swz((yout0 + rr) >> 1);
-      const float4 a = rsm[2 * f][ch];      // column 2f, rows rr, rr + 1
-      const float4 b = rsm[2 * f + 1][ch];  // column 2f + 1
-      float2* dst = sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f;
-      __stcs(reinterpret_cast<float4*>(dst), make_float4(a.x, a.y, b.x, b.y));
-      __stcs(reinterpret_cast<float4*>(dst + sl.wp), make_float4(a.z, a.w, b.z, b.w));
+    // item idx = (row pair, column pair f): IT items per thread, all remote loads issued
+    // before the first store so their latencies overlap
+    static_assert(F4 == 2, "two column pairs per tile");
+    constexpr int IT = (L / kTile / 2) * F4 / T;
+    const int rows = nout / kTile, rbeg = q * rows, lim = (rows / 2) * F4;
+    float4 a[IT], b[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = t + it * T, f = idx & 1;  // f = t & 1 whenever T is even
+      if (idx < lim) {
+        const int ch = swz((yout0 + rbeg + 2 * (idx / F4)) >> 1);
+        a[it] = (f ? rsm[2] : rsm[0])[ch];  // rows rr, rr + 1 of column 2f
+        b[it] = (f ? rsm[3] : rsm[1])[ch];  // of column 2f + 1
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = t + it * T, f = idx & 1;
+      if (idx < lim) {
+        const int rr = rbeg + 2 * (idx / F4);
+        float2* dst = sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f;
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
+        __stcs(reinterpret_cast<float4*>(dst + sl.wp), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+      }
     }
   }
   cl.sync();

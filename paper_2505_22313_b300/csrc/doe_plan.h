@@ -52,9 +52,11 @@ __host__ __device__ constexpr long tw_quad(int R, int ns, int k, int r) {
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 __host__ __device__ constexpr int smem_words(int L) { return L; }
 
-// Resident CTAs per SM requested from the register allocator for a row/column pass of length L.
+// Resident CTAs per SM requested from the register allocator for a row/column pass of length L
+// (L / 32 threads): at most 128 registers per thread.  Registers are allocated per warp, so a
+// CTA of fewer than 32 threads still takes a whole warp's share.
 __host__ __device__ constexpr int min_blocks(int L) {
-  return (65536 / ((L / 32) * 128)) > 1 ? 65536 / ((L / 32) * 128) : 1;  // at most 128 registers per thread
+  return 65536 / (((L / 32) < 32 ? 32 : (L / 32)) * 128) > 1 ? 65536 / (((L / 32) < 32 ? 32 : (L / 32)) * 128) : 1;
 }
 
 // Elements per thread used for a transform of length L.

@@ -316,6 +316,29 @@ def test_large_area_psf_rows_vs_oracle():
     assert 0.5 * N * N < tot <= N * N * (1 + 1e-5)  # Parseval over the band
 
 
+def test_large_area_gradient_rows_vs_oracle():
+    # the large-area gradient (32768^2 DOE, 65536^2 grid, adjoint with recomputed fields): a
+    # vector-Jacobian product whose dL/dI is non-zero on seeded output rows only, against the
+    # oracle's row-subset adjoint on seeded DOE rows (the FP64 field does not fit host memory)
+    N, dx, z, lam = 32768, 1e-6, 100e-3, 550e-9
+    P = 2 * N
+    h = _h(N, 1004)
+    g = Geometry.make(N, dx, z, [lam])
+    r = np.random.default_rng(4004)
+    rows = np.unique(np.concatenate([[P // 4, P // 2, P // 2 + 1, 3 * P // 4 - 1, P - 1], r.integers(0, P, 11)]))
+    g_rows = r.standard_normal((rows.size, P)).astype(np.float32)
+    G = torch.zeros((1, P, P), dtype=torch.float32, device="cuda")
+    G[0, torch.from_numpy(rows).cuda()] = torch.from_numpy(g_rows).cuda()
+    gr, _ = api.grad(torch.from_numpy(h).cuda(), g, G, mode="vjp", recompute=True)
+    drows = np.unique(np.concatenate([[0, N // 2, N - 1], r.integers(0, N, 13)]))
+    got = gr[torch.from_numpy(drows).cuda()].cpu().numpy()
+    del G, gr
+    torch.cuda.empty_cache()
+    ref = oracle.grad_rows(h, dx, z, lam, rows, g_rows, drows)
+    err = rel_l2(got, ref)
+    assert err < TOL_GRAD, err
+
+
 def test_big_grid_gradient_fd_exact():
     # two-CTA rows/columns adjoint (16384^2 DOE, 32768^2 grid) against exact-difference
     # central differences of the FP64 loss on seeded pixels
