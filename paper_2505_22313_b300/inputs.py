@@ -71,16 +71,15 @@ def heights_device(N: int, seed: int, device, hmax: float = HMAX, sigma: float =
     rescale to [0, hmax] as heights(), in float32.  Deterministic for a given seed and device
     type; not bit-identical to heights() (different random generator)."""
     import torch
+    import torch.nn.functional as F
 
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     x = torch.rand((N, N), generator=g, device=device, dtype=torch.float32)
-    w = _gauss_weights(sigma, radius)
-    for dim in (1, 0):
-        acc = torch.zeros_like(x)
-        for i, wi in enumerate(w):
-            acc.add_(torch.roll(x, radius - i, dims=dim), alpha=float(wi))
-        x = acc
+    w = torch.tensor(_gauss_weights(sigma, radius), dtype=torch.float32, device=device).view(1, 1, -1)
+    # periodic correlation along x (rows as a batch), then along y: out[j] = sum_i w[i] x[j + i - radius]
+    x = F.conv1d(F.pad(x.view(N, 1, N), (radius, radius), mode="circular"), w).view(N, N)
+    x = F.conv1d(F.pad(x.t().contiguous().view(N, 1, N), (radius, radius), mode="circular"), w).view(N, N).t()
     mn, mx = x.min(), x.max()
     return ((x - mn) * (hmax / (mx - mn))).contiguous()
 

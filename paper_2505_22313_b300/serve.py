@@ -6,8 +6,12 @@ is split into units of a few wavelengths each.  The scheduler:
     fits the HBM budget; admitted requests keep all their state on the device;
   * forms launches from pending units of one grid size P (oldest pending unit first), up to
     64 wavelengths or the per-stream workspace, so one set of kernels serves several
-    requests (doe_psf_many); launches go round-robin to several CUDA streams and overlap on
-    the device; requests that arrive while others run are admitted as memory frees up;
+    requests (doe_psf_many); requests that arrive while others run are admitted as memory
+    frees up;
+  * routes launches by grid size: one launch of a large grid (P >= 16384) fills the GPU, so
+    large-grid launches queue back to back on one stream in arrival order (served at full
+    speed, none time-shared with another large one), while smaller grids run on the other
+    streams beside them; small work also takes the large lane when no large work waits;
   * polls completion events without blocking and with a host deadline per request
     (a request past its deadline is reported as timed out, DOE_ETIMEDOUT);
   * hands each finished request to a consumer callback, which frees its PSFs.
@@ -81,14 +85,63 @@ class Stats:
                 "launches": self.launches, "peak_admitted_bytes": self.peak_bytes}
 
 
+class Arena:
+    """First-fit sub-allocator of byte ranges in one pre-allocated device buffer, so admitting
+    a request never calls the device allocator.  Ranges are 256-byte aligned; freed ranges
+    coalesce with their neighbours."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes: int):
+        self.size = int(nbytes)
+        self.free = [(0, self.size)]  # sorted, disjoint (offset, length)
+        self.used = 0
+
+    def _round(self, n: int) -> int:
+        return (int(n) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+
+    def fits(self, n: int) -> bool:
+        n = self._round(n)
+        return any(length >= n for _, length in self.free)
+
+    def alloc(self, n: int) -> int | None:
+        n = self._round(n)
+        for i, (off, length) in enumerate(self.free):
+            if length >= n:
+                if length == n:
+                    del self.free[i]
+                else:
+                    self.free[i] = (off + n, length - n)
+                self.used += n
+                return off
+        return None
+
+    def release(self, off: int, n: int) -> None:
+        n = self._round(n)
+        i = 0
+        while i < len(self.free) and self.free[i][0] < off:
+            i += 1
+        self.free.insert(i, (off, n))
+        self.used -= n
+        # coalesce with the following and the preceding range
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (self.free[i][0], self.free[i][1] + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+
 class Scheduler:
     """Continuous batching with admission by device-memory footprint.
 
     launcher: object with
-        n_slots                      -- concurrent launch slots (streams)
+        n_slots                      -- launch slots (a slot holds one launch in flight)
+        lanes (optional)             -- per slot "large", "small" or "any" (default: all "any")
         ws_bytes(units) -> int       -- workspace one launch of these units needs
         ws_limit                     -- workspace available per slot
         admit(req), release(req)     -- allocate / free a request's device state
+        fits(req) (optional)         -- whether admit(req) can place the request now
         launch(slot, units)          -- enqueue the units' PSFs on the slot's stream
         done(slot) -> bool           -- non-blocking completion test of the slot's last launch
     clock: callable returning seconds."""
@@ -96,8 +149,9 @@ class Scheduler:
     MAX_SLICES = 64
 
     def __init__(self, launcher, budget_bytes: int, clock=time.perf_counter, unit_lambdas: int = 8,
-                 consumer=None):
+                 consumer=None, large_P: int = 16384):
         self.L = launcher
+        self.large_P = int(large_P)
         self.budget = int(budget_bytes)
         self.clock = clock
         self.unit_lambdas = unit_lambdas
@@ -173,6 +227,8 @@ class Scheduler:
                     continue
                 if used[0] + r.footprint() > self.budget:
                     break
+                if hasattr(self.L, "fits") and not self.L.fits(r):
+                    break  # no contiguous range yet: wait for releases (keeps FIFO order)
                 waiting.popleft()
                 self.L.admit(r)
                 used[0] += r.footprint()
@@ -181,14 +237,27 @@ class Scheduler:
                 units = self._split(r)
                 remaining[r.rid] = len(units)
                 pending[r.P].extend(units)
-            # launches into free slots: the grid-size class holding the oldest pending unit
+            # launches into free slots: of the grid-size classes this slot's lane serves, the
+            # one holding the oldest pending unit
+            lanes = getattr(self.L, "lanes", None) or ["any"] * len(slots)
             for s in range(len(slots)):
                 if slots[s] is not None:
                     continue
                 live = [(q[0].req.arrival_s, q[0].req.rid, P) for P, q in pending.items() if q]
                 if not live:
                     break
-                P = min(live)[2]
+                if lanes[s] == "large":
+                    cand = [x for x in live if x[2] >= self.large_P]
+                    if not cand and not any(slots[k] is not None and lanes[k] == "large" and
+                                            slots[k][0].req.P >= self.large_P for k in range(len(slots))):
+                        cand = live  # no large work waiting or running: small work may use the lane
+                elif lanes[s] == "small":
+                    cand = [x for x in live if x[2] < self.large_P]
+                else:
+                    cand = live
+                if not cand:
+                    continue
+                P = min(cand)[2]
                 q = pending[P]
                 batch = [q.popleft()]
                 while q:
@@ -212,9 +281,13 @@ class Scheduler:
 
 class CudaLauncher:
     """Device side of the scheduler: per-stream workspaces, seeded heights generated on the
-    device at admission, doe_psf_many launches, completion events."""
+    device at admission, doe_psf_many launches, completion events.  Stream 0 is the large
+    lane: `large_depth` slots queue on it, so its launches run back to back; every other
+    stream has one small-lane slot.  Launches on one stream share its workspace (stream order
+    keeps them apart)."""
 
-    def __init__(self, n_streams: int = 3, ws_bytes: int = 24 << 30, device=None, keep_results: bool = False):
+    def __init__(self, n_streams: int = 3, ws_bytes: int = 24 << 30, device=None, keep_results: bool = False,
+                 large_depth: int = 2, psf_arena_bytes: int | None = None, heights_source=None):
         import torch
 
         from . import api
@@ -222,11 +295,19 @@ class CudaLauncher:
 
         self.torch, self.api, self.Geometry = torch, api, Geometry
         self.dev = torch.device(device or "cuda")
-        self.n_slots = n_streams
         self.ws_limit = int(ws_bytes)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(n_streams)]
         self.ws = [api.workspace(self.ws_limit, self.dev) for _ in range(n_streams)]
-        self.events = [None] * n_streams
+        self.slot_stream = [0] * large_depth + list(range(1, n_streams))
+        self.lanes = ["large"] * large_depth + ["small"] * (n_streams - 1)
+        self.n_slots = len(self.slot_stream)
+        self.events = [None] * self.n_slots
+        # heights_source(req) -> the request's heights: a device tensor, or a pinned host tensor
+        # copied in on the upload stream (default: seeded heights generated on the device)
+        self.heights_source = heights_source
+        # heights and PSFs live in one buffer allocated here (None: tensors per request)
+        self.arena = Arena(psf_arena_bytes) if psf_arena_bytes else None
+        self.arena_buf = torch.empty(psf_arena_bytes, dtype=torch.uint8, device=self.dev) if psf_arena_bytes else None
         self.state: dict[int, tuple] = {}
         self.keep = keep_results
         self.results: dict[int, "torch.Tensor"] = {}
@@ -245,34 +326,60 @@ class CudaLauncher:
         arr = (_lib.Geom * len(gs))(*[g.c() for g in gs])
         return int(_lib.load().doe_workspace_bytes_many(len(gs), arr, _lib.DOE_OP_PSF))
 
-    def admit(self, r: Req):
+    def fits(self, r: Req) -> bool:
+        return self.arena is None or self.arena.fits(r.footprint())
+
+    def _heights(self, r: Req):
+        if self.heights_source is not None:
+            return self.heights_source(r)
         from .inputs import heights_device
 
+        return heights_device(r.N, r.seed, self.dev)
+
+    def admit(self, r: Req):
         torch = self.torch
+        off = None
         with torch.cuda.stream(self.upload):
-            h = heights_device(r.N, r.seed, self.dev)
-            out = torch.empty((r.L, r.P, r.P), dtype=torch.float32, device=self.dev)
+            src = self._heights(r)
+            if self.arena is not None:
+                # one range: heights [N][N] then PSFs [L][P][P], both float32
+                off = self.arena.alloc(r.footprint())
+                if off is None:
+                    raise MemoryError("serving arena: no contiguous range (admit without fits)")
+                hb = 4 * r.N * r.N
+                h = self.arena_buf[off:off + hb].view(torch.float32).view(r.N, r.N)
+                h.copy_(src, non_blocking=True)
+                out = self.arena_buf[off + hb:off + r.footprint()].view(torch.float32).view(r.L, r.P, r.P)
+            else:
+                h = src if src.device.type == "cuda" else src.to(self.dev, non_blocking=True)
+                out = torch.empty((r.L, r.P, r.P), dtype=torch.float32, device=self.dev)
             ev = torch.cuda.Event()
             ev.record(self.upload)
-        self.state[r.rid] = (h, out, ev)
+        self.state[r.rid] = (h, out, ev, off, src)
 
     def release(self, r: Req):
-        h, out, _ = self.state.pop(r.rid)
+        h, out, _, off, _ = self.state.pop(r.rid)
         if self.keep:
-            self.results[r.rid] = out
+            # the range is reused by later requests: keep a copy, made before it can be
+            self.results[r.rid] = out.clone() if off is not None else out
+            if off is not None:
+                self.torch.cuda.synchronize(self.dev)
+        if off is not None:
+            self.arena.release(off, r.footprint())
 
     def launch(self, slot: int, units):
         torch = self.torch
-        st = self.streams[slot]
+        si = self.slot_stream[slot]
+        st = self.streams[si]
         hs, outs, gs = [], [], []
         for u in units:
-            h, out, ev = self.state[u.req.rid]
+            h, out, ev, _, _ = self.state[u.req.rid]
             st.wait_event(ev)
             hs.append(h)
             outs.append(out[u.j0:u.j1])
             gs.append(self._geom(u))
         with torch.cuda.stream(st):
-            self.api.psf_many(hs, gs, outs=outs, ws=self.ws[slot], stream=st)
+            self.api.psf_many(hs, gs, outs=outs, ws=self.ws[si], stream=st)
             for h, o in zip(hs, outs):
                 h.record_stream(st)
                 o.record_stream(st)
@@ -285,8 +392,10 @@ class CudaLauncher:
         return e is None or e.query()
 
 
-def serve_one_at_a_time(trace: list[Req], device=None, clock=time.perf_counter, keep_results=False):
-    """Baseline: arrival order, one wavelength per doe_psf launch, synchronous."""
+def serve_one_at_a_time(trace: list[Req], device=None, clock=time.perf_counter, keep_results=False,
+                        heights_source=None):
+    """Baseline: arrival order, one wavelength per doe_psf launch, synchronous (heights from
+    heights_source(req) as in CudaLauncher, default seeded on the device)."""
     import torch
 
     from . import api
@@ -301,7 +410,10 @@ def serve_one_at_a_time(trace: list[Req], device=None, clock=time.perf_counter, 
     for r in sorted(trace, key=lambda r: (r.arrival_s, r.rid)):
         while clock() - t0 < r.arrival_s:
             time.sleep(min(1e-3, max(0.0, r.arrival_s - (clock() - t0))))
-        h = heights_device(r.N, r.seed, dev)
+        if heights_source is not None:
+            h = heights_source(r).to(dev, non_blocking=True)
+        else:
+            h = heights_device(r.N, r.seed, dev)
         out = torch.empty((r.L, r.P, r.P), dtype=torch.float32, device=dev)
         for j in range(r.L):
             g = Geometry.make(r.N, r.dx, r.z, r.lambdas[j:j + 1], n_index=r.n_index)
@@ -319,6 +431,22 @@ def serve_one_at_a_time(trace: list[Req], device=None, clock=time.perf_counter, 
         del out, h
     st.makespan_s = clock() - t0
     return st, results
+
+
+class HostHeights:
+    """Heights as a client would send them: one seeded map per side N (generated once, kept in
+    pinned host memory) that every request of that side uploads."""
+
+    def __init__(self, sides, device=None):
+        import torch
+
+        from .inputs import heights_device
+
+        dev = torch.device(device or "cuda")
+        self.maps = {int(N): heights_device(int(N), 1000 + int(N), dev).cpu().pin_memory() for N in sides}
+
+    def __call__(self, r: Req):
+        return self.maps[r.N]
 
 
 def trace_from_stream(reqs) -> list[Req]:
@@ -347,20 +475,28 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=140.0)
     ap.add_argument("--ws-gb", type=float, default=20.0)
     ap.add_argument("--streams", type=int, default=3)
+    ap.add_argument("--large-p", type=int, default=16384, help="grids of at least this side use the large lane")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the one-request-at-a-time run")
     args = ap.parse_args()
     api.init()
     sides = tuple(int(s) for s in args.sides.split(","))
     trace = trace_from_stream(inputs.request_stream(args.requests, args.rate, sides=sides, max_lambda=args.max_lambda))
-    base, _ = serve_one_at_a_time(trace)
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    lau = CudaLauncher(n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)))
-    sched = Scheduler(lau, int(args.budget_gb * (1 << 30)))
+    hsrc = HostHeights(sides)
+    base = None
+    if not args.no_baseline:
+        base, _ = serve_one_at_a_time(trace, heights_source=hsrc)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    lau = CudaLauncher(n_streams=args.streams, ws_bytes=int(args.ws_gb * (1 << 30)),
+                       psf_arena_bytes=int(args.budget_gb * (1 << 30)), heights_source=hsrc)
+    sched = Scheduler(lau, int(args.budget_gb * (1 << 30)), large_P=args.large_p)
     st = sched.run(trace)
     torch.cuda.synchronize()
     print(json.dumps({"trace": {"requests": args.requests, "rate_hz": args.rate, "sides": sides,
                                 "max_lambda": args.max_lambda},
-                      "batched": st.summary(), "one_at_a_time": base.summary()}))
+                      "scheduler": {"streams": args.streams, "large_p": args.large_p, "budget_gb": args.budget_gb,
+                                    "ws_gb": args.ws_gb},
+                      "batched": st.summary(), "one_at_a_time": base.summary() if base else None}))
 
 
 if __name__ == "__main__":

@@ -1,7 +1,8 @@
 """Serving on the GPU: each request's PSFs computed in the continuous-batching mix (shared
 launches, several streams, admission under a memory budget) equal the same request computed
-alone, bit for bit (the kernels are batch-invariant), and the one-request-at-a-time baseline
-gives the same results."""
+alone, bit for bit (the kernels are batch-invariant), with PSFs in per-request tensors or in
+the launcher's pre-allocated arena, and the one-request-at-a-time baseline gives the same
+results."""
 import numpy as np
 import pytest
 import torch
@@ -36,10 +37,11 @@ def _alone(r):
     return api.psf(heights_device(r.N, r.seed, "cuda"), g)
 
 
-def test_mix_equals_alone():
+@pytest.mark.parametrize("arena", [False, True])
+def test_mix_equals_alone(arena):
     trace = _trace()
     budget = 3 * max(r.footprint() for r in trace)  # forces admission to wait for memory
-    lau = CudaLauncher(n_streams=3, ws_bytes=64 << 20, keep_results=True)
+    lau = CudaLauncher(n_streams=3, ws_bytes=64 << 20, keep_results=True, psf_arena_bytes=budget if arena else None)
     st = Scheduler(lau, budget, unit_lambdas=3).run(trace)
     torch.cuda.synchronize()
     assert st.summary()["completed"] == len(trace)

@@ -97,3 +97,85 @@ def test_oversize_request_refused():
     st = Scheduler(lau, 10 * max(r.footprint() for r in trace), clock=clk).run(trace + [big])
     assert st.status[99] == DOE_ENOMEM
     assert sum(1 for v in st.status.values() if v == 0) == len(trace)
+
+
+class LaneLauncher(FakeLauncher):
+    """Two large-lane slots and one small-lane slot; records the slot of every launch."""
+
+    lanes = ["large", "large", "small"]
+
+    def __init__(self, clock):
+        super().__init__(clock, n_slots=3)
+        self.slot_of = []
+
+    def launch(self, slot, units):
+        super().launch(slot, units)
+        self.slot_of.append((slot, units[0].req.P))
+
+
+def test_large_grids_use_the_large_lane_only():
+    clk = FakeClock()
+    trace = _trace(n=40, sides=(64, 128, 256), rate=2000.0)
+    lau = LaneLauncher(clk)
+    st = Scheduler(lau, 1 << 40, clock=clk, large_P=256).run(trace)  # P = 512 is "large"
+    assert st.summary()["completed"] == len(trace)
+    assert any(P >= 256 for _, P in lau.slot_of) and any(P < 256 for _, P in lau.slot_of)
+    for slot, P in lau.slot_of:
+        if P >= 256:
+            assert LaneLauncher.lanes[slot] == "large"
+    # small work reaches the large lane only when no large work waits: with the large requests
+    # removed, every slot serves small grids
+    lau2 = LaneLauncher(clk)
+    Scheduler(lau2, 1 << 40, clock=clk, large_P=1 << 20).run(_trace(n=40, sides=(64, 128), rate=2000.0))
+    assert {s for s, _ in lau2.slot_of} >= {0, 2}
+
+
+def test_arena_first_fit_and_coalescing():
+    from paper_2505_22313_b300.serve import Arena
+
+    a = Arena(10 * 256)
+    x = a.alloc(256)
+    y = a.alloc(300)        # rounds up to 512
+    z = a.alloc(256)
+    assert (x, y, z) == (0, 256, 768) and a.used == 1024
+    assert a.alloc(2000) is None and not a.fits(2000) and a.fits(1536)
+    a.release(y, 300)
+    assert a.alloc(512) == 256  # first fit reuses the hole
+    a.release(256, 512)
+    a.release(x, 256)
+    a.release(z, 256)
+    assert a.free == [(0, 10 * 256)] and a.used == 0  # everything coalesced
+
+
+class ArenaLauncher(FakeLauncher):
+    """Places each request's PSFs in an Arena; admission asks fits()."""
+
+    def __init__(self, clock, nbytes):
+        from paper_2505_22313_b300.serve import Arena
+
+        super().__init__(clock, n_slots=2)
+        self.arena = Arena(nbytes)
+        self.off = {}
+
+    def fits(self, r):
+        return self.arena.fits(r.footprint())
+
+    def admit(self, r):
+        super().admit(r)
+        self.off[r.rid] = self.arena.alloc(r.footprint())
+        assert self.off[r.rid] is not None
+
+    def release(self, r):
+        super().release(r)
+        self.arena.release(self.off.pop(r.rid), r.footprint())
+
+
+def test_admission_waits_for_a_contiguous_range():
+    clk = FakeClock()
+    trace = _trace(n=60, sides=(64, 128, 256), rate=5000.0)
+    biggest = max(r.footprint() for r in trace)
+    lau = ArenaLauncher(clk, 3 * biggest)
+    st = Scheduler(lau, 3 * biggest, clock=clk).run(trace)
+    assert st.summary()["completed"] == len(trace)
+    assert lau.order == sorted(lau.order)
+    assert lau.arena.used == 0 and lau.arena.free == [(0, lau.arena.size)]
