@@ -88,19 +88,14 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  constexpr int TC = big_tile(Q);
+  // column-tiled buffer, 4-wide tiles at every grid size: the pair (pos, pos + 1) is 16 bytes
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);
-      if constexpr (TC >= 2) {
-        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, TC)), make_float4(a.x, a.y, c.x, c.y));
-      } else {  // one-column tiles: the two positions are in different tiles
-        __stcs(sl.tbuf + tiled_at(i, pos, N, 1), a);
-        __stcs(sl.tbuf + tiled_at(i, pos + 1, N, 1), c);
-      }
+      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, kTile)), make_float4(a.x, a.y, c.x, c.y));
     }
 }
 
@@ -191,6 +186,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
 template <int LS, int Q, bool ROWSPLIT>
 __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = LS, T = L / 32, P = L * Q, TC = big_tile(Q), CL = TC * Q, SH = L / CL;
+  static_assert(kTile % TC == 0, "a cluster's columns lie inside one tile of the buffer");
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   static_assert(G::R == First<L, true>::R, "register hand-off needs equal radices");
@@ -220,38 +216,30 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
   for (int it = 0; it < SH / (2 * T); ++it) {
     const int y2 = rank * SH + 2 * t + it * 2 * T;
     float2 col[2][TC][Q];
-    if constexpr (TC >= 2) {
+    // this cluster's TC columns inside the buffer's 4-wide tiles (TC = 4: the whole tile row;
+    // TC = 2, 1: part of it, the rest read by the neighbouring clusters at the same time)
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int y1 = 0; y1 < Q; ++y1) {
-          const int y = y1 * L + y2 + u;
-          if ((unsigned)(y - yin0) < (unsigned)nin) {
-            const float4* src = reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, TC));
+      for (int y1 = 0; y1 < Q; ++y1) {
+        const int y = y1 * L + y2 + u;
+        if ((unsigned)(y - yin0) < (unsigned)nin) {
+          const float2* src = sl.tbuf + tiled_at(y - yin0, pos0, nin, kTile);
+          if constexpr (TC >= 2) {
 #pragma unroll
             for (int f = 0; f < TC / 2; ++f) {
-              const float4 q4 = __ldcs(src + f);
+              const float4 q4 = __ldcs(reinterpret_cast<const float4*>(src) + f);
               col[u][2 * f][y1] = make_float2(q4.x, q4.y);
               col[u][2 * f + 1][y1] = make_float2(q4.z, q4.w);
             }
           } else {
-#pragma unroll
-            for (int cc = 0; cc < TC; ++cc) col[u][cc][y1] = make_float2(0.f, 0.f);
+            col[u][0][y1] = __ldcs(src);
           }
-        }
-    } else {
-      // one-column tile: rows y, y + 1 are adjacent samples; y - yin0 and nin are even, so
-      // the pair is 16-byte aligned and lies wholly inside or wholly outside the input rows
+        } else {
 #pragma unroll
-      for (int y1 = 0; y1 < Q; ++y1) {
-        const int y = y1 * L + y2;
-        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)(y - yin0) < (unsigned)nin)
-          q4 = __ldcs(reinterpret_cast<const float4*>(sl.tbuf + tiled_at(y - yin0, pos0, nin, 1)));
-        col[0][0][y1] = make_float2(q4.x, q4.y);
-        col[1][0][y1] = make_float2(q4.z, q4.w);
+          for (int cc = 0; cc < TC; ++cc) col[u][cc][y1] = make_float2(0.f, 0.f);
+        }
       }
-    }
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {
       dft<Q, false>(col[0][cc]);
@@ -391,19 +379,13 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
   fft_run<L, 32, false>(v, t, sm);
-  constexpr int TC = big_tile(Q);
 #pragma unroll
   for (int b = 0; b < G::B; b += 2)
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);  // J1 row y of the column-tiled buffer (P rows)
-      if constexpr (TC >= 2) {
-        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, TC)), make_float4(a.x, a.y, c.x, c.y));
-      } else {
-        __stcs(sl.tbuf + tiled_at(y, pos, P, 1), a);
-        __stcs(sl.tbuf + tiled_at(y, pos + 1, P, 1), c);
-      }
+      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, kTile)), make_float4(a.x, a.y, c.x, c.y));
     }
   const double tot = block_sum<T>((double)acc, red);
   if (t == 0 && sl.loss_part) sl.loss_part[(size_t)y * Q + s] = tot;

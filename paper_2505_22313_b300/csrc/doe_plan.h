@@ -68,7 +68,7 @@ __host__ __device__ constexpr int last_radix() { return plan_radix(ilog2c(L), IN
 
 constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
 constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
-constexpr int kTile = 4;    // columns per column-pass cluster: 4 x 8 B = one 32-byte sector
+constexpr int kTile = 4;    // tile width of the column-tiled buffer (4 x 8 B = one 32-byte sector); columns per cluster for P <= 8192
 constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536 = 8 x 8192)
 
 // One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
