@@ -1,11 +1,10 @@
-// doe_big.cuh -- transforms split across a cluster: P = Q * LS with sub-transforms of LS points.
-// Grids longer than 16384 (P = 32768: Q = 4, P = 65536: Q = 8) and the column pass of the
-// 16384 grid (Q = 2) all use LS = 8192: 64 KB of shared memory and 256 threads per CTA, so
-// two CTAs share an SM and one CTA's global / distributed-shared-memory phases overlap
-// another's transforms.
+// doe_big.cuh -- transforms split across a cluster: P = Q * L with sub-transforms of L = 8192
+// points, for grids longer than one CTA's transform (P = 32768: Q = 4, P = 65536: Q = 8).
+// 64 KB of shared memory and 256 threads per CTA, so two CTAs share an SM and one CTA's
+// global / distributed-shared-memory phases overlap another's transforms.
 //
 // A length-P transform is split across a cluster of Q CTAs, each running the in-CTA engine
-// on L = LS points (sub-transform s):
+// on L points (sub-transform s):
 //   forward (decimation in frequency)  x = n1 L + n2:
 //     y_s[n2] = W_P^{n2 s} sum_{n1} x[n1 L + n2] W_Q^{n1 s},  X[s + Q k2] = FFT_L(y_s)[k2]
 //   inverse (decimation in time)  output x = x2 + L q, input V_s[k2] = V[s + Q k2]:
@@ -182,10 +181,10 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
 // ------------------------------------------------------------------ columns (pass B / B*)
 // Cluster of TC x Q CTAs (TC = big_tile(Q) adjacent stored columns x Q sub-transforms, at
 // most 8); rank = c Q + s.
-// ROWSPLIT: rows are stored in sub-transform order (P > 16384); otherwise band-compacted.
-template <int LS, int Q, bool ROWSPLIT>
-__global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
-  constexpr int L = LS, T = L / 32, P = L * Q, TC = big_tile(Q), CL = TC * Q, SH = L / CL;
+// Rows are stored in sub-transform order (the row passes above).
+template <int Q>
+__global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
+  constexpr int L = kBigL, T = L / 32, P = L * Q, TC = big_tile(Q), CL = TC * Q, SH = L / CL;
   static_assert(kTile % TC == 0, "a cluster's columns lie inside one tile of the buffer");
   using G = Last<L, false>;
   using Hh = Last<L, true>;
@@ -200,7 +199,7 @@ __global__ void __launch_bounds__(LS / 32, min_blocks(LS)) pass_b_big_kernel(con
   while (si + 1 < bt.S && bt.s[si + 1].tile_begin <= tile_g) ++si;
   const Slice& sl = bt.s[si];
   const int pos0 = (tile_g - sl.tile_begin) * TC;
-  const int kcol = ROWSPLIT ? big_pos_to_k(pos0 + c, P / kBigL) : pos_to_k(pos0 + c, P, sl.seg_a, sl.w);
+  const int kcol = big_pos_to_k(pos0 + c, Q);
   const bool live = pos0 + c < sl.w && abs_signed(kcol, P) <= sl.kmax;
   const bool adj = bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;

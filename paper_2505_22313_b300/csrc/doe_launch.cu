@@ -208,12 +208,12 @@ cudaError_t big_rows_t(int which, const Batch& bt, cudaStream_t st) {
   void* args[] = {const_cast<Batch*>(&bt)};
   return launch_cluster(fn, grid, Q, smem_bytes<kBigL>(), st, args);
 }
-template <int LS, int Q, bool ROWSPLIT>
+template <int Q>
 cudaError_t big_cols_t(const Batch& bt, cudaStream_t st) {
   void* args[] = {const_cast<Batch*>(&bt)};
   constexpr int CL = big_tile(Q) * Q;
-  return launch_cluster((const void*)pass_b_big_kernel<LS, Q, ROWSPLIT>, dim3(bt.total_tiles * CL), CL,
-                        smem_bytes<LS>(), st, args, LS / 32);
+  return launch_cluster((const void*)pass_b_big_kernel<Q>, dim3(bt.total_tiles * CL), CL, smem_bytes<kBigL>(), st,
+                        args, kBigL / 32);
 }
 template <int Q>
 cudaError_t prep_big_t() {
@@ -221,7 +221,7 @@ cudaError_t prep_big_t() {
   const int sb = (int)smem_bytes<kBigL>();
   constexpr int nt = kBigL / 32;
   if ((e = prep_one(pass_a_big_kernel<Q>, sb, nt))) return e;
-  if ((e = prep_one(pass_b_big_kernel<kBigL, Q, true>, sb, nt))) return e;
+  if ((e = prep_one(pass_b_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_c_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb, nt))) return e;
@@ -276,7 +276,7 @@ cudaError_t prepare_kernels() {
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
       (e = prep_t<256>()) || (e = prep_t<512>()) || (e = prep_t<1024>()) || (e = prep_t<2048>()) ||
       (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<4>()) ||
-      (e = prep_big_t<8>()) || (e = prep_one(pass_b_big_kernel<8192, 2, false>, (int)smem_bytes<8192>(), 8192 / 32)))
+      (e = prep_big_t<8>()))
     return e;
   return cudaSuccess;
 }
@@ -295,10 +295,9 @@ cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
   DOE_DISPATCH(lg, pass_a_t, bt, st);
 }
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
-  if (lg >= 14) {  // columns of 16384 and longer as Q = P / 8192 sub-transforms of 8192 points
+  if (lg >= 15) {  // columns longer than one CTA's transform: Q = P / 8192 sub-transforms of 8192 points
     Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
-    if (lg == 14) return big_cols_t<8192, 2, false>(bt, st);
-    return lg == 15 ? big_cols_t<kBigL, 4, true>(bt, st) : big_cols_t<kBigL, 8, true>(bt, st);
+    return lg == 15 ? big_cols_t<4>(bt, st) : big_cols_t<8>(bt, st);
   }
   DOE_DISPATCH(lg, pass_b_t, bt, st);
 }

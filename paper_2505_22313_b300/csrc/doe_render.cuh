@@ -6,8 +6,9 @@
 //       X_img[k] = (Z[k] + conj Z[2W-k]) / 2, X_k[k] = (Z[k] - conj Z[2W-k]) / (2i), k <= W,
 //       and written to SA, SB (column-tiled, H rows).  The crop k_c is read straight from the PSF
 //       around the optical axis; its row sums go to ksum[c][u] (FP64).
-//   R2  per column k <= W (4-column cluster, as the propagation's column pass): column FFTs of
-//       SA and SB (zero-padded to 2H), product, column IFFT, rows [H/2, 3H/2) -> SC.
+//   R2  per column k <= W (4-column cluster, as the propagation's column pass): each CTA reads
+//       its columns of SA and SB directly, column FFTs (zero-padded to 2H), product, column
+//       IFFT, rows [H/2, 3H/2) gathered across the cluster -> SC.
 //   R3  per pair of output rows: the two Hermitian half spectra are packed as X0 + i X1,
 //       extended to 2W by conjugate symmetry, one complex IFFT, real part = row y, imaginary
 //       part = row y + 1, window [W/2, 3W/2), scaled by 1 / (4 H W sum(k_c)).
@@ -76,14 +77,39 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
   if (t == 0) ra.ksum[(size_t)c * H + u] = tot;
 }
 
+// Loads column `col` of a column-tiled buffer (n rows, 4-wide tiles) into the first-stage
+// registers of a length-L forward transform; rows n..L-1 are zero padding.  A register pair
+// (rows e, e + 1; e even, n even) is two 8-byte loads 32 bytes apart.
+template <int L>
+__device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const float2* col, int n, bool live) {
+  using F = First<L, false>;
+  static_assert(F::PAIRED, "first stage holds adjacent pairs");
+#pragma unroll
+  for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+    for (int r = 0; r < F::R; ++r) {
+      const int y = F::idx(t, b, r);
+      float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+      if (live && y < n) {
+        a = __ldcs(col + (size_t)y * kTile);
+        d = __ldcs(col + (size_t)(y + 1) * kTile);
+      }
+      v[b * F::R + r] = a;
+      v[(b + 1) * F::R + r] = d;
+    }
+}
+
 // R2: cluster of kTile CTAs per 4 adjacent columns of one channel; transform length L = 2H.
-// Shared memory: two L-sample buffers (the image column and the kernel column).
+// CTA q reads its own column of SA and of SB straight into registers, keeps the image column's
+// spectrum in sma while the kernel column is transformed in smb, multiplies, inverse-transforms,
+// and the cluster gathers rows [H/2, 3H/2) of its four columns as 32-byte row segments of SC.
 template <int L>
 __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   constexpr int T = L / 32;
   constexpr int F4 = kTile / 2;
+  static_assert(F4 == 2, "two column pairs per tile");
   extern __shared__ float2 sm[];
   float2* sma = sm;
   float2* smb = sm + L;
@@ -95,39 +121,14 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
   const int tiles = ra.wpr / kTile;
   const int tile = (blockIdx.x / kTile) % tiles;
   const int c = (blockIdx.x / kTile) / tiles;
-  const int pos0 = tile * kTile;
-  const float2* baseA = ra.sa + (size_t)c * H * ra.wpr + tiled_at(0, pos0, H, kTile);  // this tile, H rows
-  const float2* baseB = ra.sb + (size_t)c * H * ra.wpr + tiled_at(0, pos0, H, kTile);
+  const int pos0 = tile * kTile, mypos = pos0 + q;
+  const bool live = mypos <= ra.W;  // columns past W are unused
+  const float2* colA = ra.sa + (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile);
+  const float2* colB = ra.sb + (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile);
   float2* baseC = ra.sc + (size_t)c * H * ra.wpr;
-  for (int y = H + t; y < L; y += T) {
-    sma[phys(y)] = make_float2(0.f, 0.f);
-    smb[phys(y)] = make_float2(0.f, 0.f);
-  }
-  float2* rsa[kTile];
-  float2* rsb[kTile];
-#pragma unroll
-  for (int cc = 0; cc < kTile; ++cc) {
-    rsa[cc] = cl.map_shared_rank(sma, cc);
-    rsb[cc] = cl.map_shared_rank(smb, cc);
-  }
-  cl.sync();  // every CTA of the cluster has started before its shared memory is written
-  {
-    const int rows = H / kTile, rbeg = q * rows;
-    for (int idx = t; idx < rows * F4; idx += T) {
-      const int rr = rbeg + idx / F4, f = idx % F4;
-      float4 va = __ldcs(reinterpret_cast<const float4*>(baseA + (size_t)rr * kTile + 2 * f));
-      float4 vb = __ldcs(reinterpret_cast<const float4*>(baseB + (size_t)rr * kTile + 2 * f));
-      if (pos0 + 2 * f > ra.W) va = vb = make_float4(0.f, 0.f, 0.f, 0.f);  // columns past W are unused
-      rsa[2 * f][phys(rr)] = make_float2(va.x, va.y);
-      rsa[2 * f + 1][phys(rr)] = make_float2(va.z, va.w);
-      rsb[2 * f][phys(rr)] = make_float2(vb.x, vb.y);
-      rsb[2 * f + 1][phys(rr)] = make_float2(vb.z, vb.w);
-    }
-  }
-  cl.sync();
   float2 v[32];
   // spectrum of the image column, kept in sma at its own register positions
-  stage_load<L, 32, false, 0>(v, t, sma);
+  load_tiled_col<L>(v, t, colA, H, live);
   fft_run<L, 32, false>(v, t, sma);
   __syncthreads();
   {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
       }
   }
   // spectrum of the kernel column, times the image spectrum (same thread, same positions)
-  stage_load<L, 32, false, 0>(v, t, smb);
+  load_tiled_col<L>(v, t, colB, H, live);
   fft_run<L, 32, false>(v, t, smb);
   {
     const float4* s4 = reinterpret_cast<const float4*>(sma);
@@ -166,18 +167,36 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
         s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
-  cl.sync();
+  const float4* rsb[kTile];
+#pragma unroll
+  for (int cc = 0; cc < kTile; ++cc) rsb[cc] = reinterpret_cast<const float4*>(cl.map_shared_rank(smb, cc));
+  cl.sync();  // all four columns are in shared memory (and every CTA of the cluster has started)
   {
-    // rows [H/2, 3H/2) of the column IFFT -> SC rows [0, H)
-    const int rows = H / kTile, rbeg = q * rows;
-    for (int idx = t; idx < rows * F4; idx += T) {
-      const int rr = rbeg + idx / F4, f = idx % F4;
-      const float2 a = rsb[2 * f][phys(H / 2 + rr)];
-      const float2 d = rsb[2 * f + 1][phys(H / 2 + rr)];
-      __stcs(reinterpret_cast<float4*>(baseC + (size_t)rr * ra.wpr + pos0 + 2 * f), make_float4(a.x, a.y, d.x, d.y));
+    // rows [H/2, 3H/2) of the column IFFT -> SC rows [0, H); item = (pair of output rows,
+    // column pair f), all remote loads issued before the first store
+    constexpr int IT = (L / 2 / kTile / 2) * F4 / T;
+    const int rows = H / kTile, rbeg = q * rows, lim = (rows / 2) * F4;
+    float4 a[IT], b[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = t + it * T, f = idx & 1;
+      if (idx < lim) {
+        const int ch = swz((H / 2 + rbeg + 2 * (idx / F4)) >> 1);
+        a[it] = (f ? rsb[2] : rsb[0])[ch];  // rows rr, rr + 1 of column 2f
+        b[it] = (f ? rsb[3] : rsb[1])[ch];  // of column 2f + 1
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = t + it * T, f = idx & 1;
+      if (idx < lim) {
+        float2* dst = baseC + (size_t)(rbeg + 2 * (idx / F4)) * ra.wpr + pos0 + 2 * f;
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
+        __stcs(reinterpret_cast<float4*>(dst + ra.wpr), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+      }
     }
   }
-  cl.sync();
+  cl.sync();  // peers have finished reading this CTA's shared memory
 }
 
 // R3: one CTA per (pair of output rows, channel); transform length L = 2W.

@@ -1,0 +1,91 @@
+"""Per-configuration timing of the library's passes (PSF and gradient).
+
+    python -m paper_2505_22313_b300.sweep [--configs small,rgb,gradient,large_area] [--reps K]
+
+Each configuration runs the PSF (and, where listed, the L2 gradient against the spot-array
+target with recomputed fields) K times after warm-up, timed with CUDA events on the current
+stream, and prints one JSON line: wall time per call, field-samples/s, and the median device
+time of every traced pass.  Inputs are the seeded synthetic heights and targets of
+``inputs``; nothing here checks results (the tests do).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+CONFIGS = {
+    # name: (N, pitch m, z m, wavelengths m, gradient?)
+    "small": (256, 2e-6, 20e-3, [550e-9], True),
+    "rgb": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True),
+    "gradient": (8192, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True),
+    "grid_16384": (8192, 1e-6, 50e-3, [550e-9], False),  # one wavelength: ~3.3 GB on the device
+    "grid_32768": (16384, 1e-6, 50e-3, [550e-9], True),
+    "large_area": (32768, 1e-6, 100e-3, [550e-9], True),
+}
+
+
+def run(name: str, reps: int, grad: bool = True) -> dict:
+    import torch
+
+    from . import _lib, api, inputs
+    from .api import Geometry
+
+    N, dx, z, lams, do_grad = CONFIGS[name]
+    do_grad = do_grad and grad
+    P = 2 * N
+    g = Geometry.make(N, dx, z, lams)
+    h = inputs.heights_device(N, 1000 + N, "cuda")
+    ws = api.workspace(api.workspace_bytes(g, _lib.DOE_OP_GRAD if do_grad else _lib.DOE_OP_PSF))
+    out = torch.empty((g.L, P, P), device="cuda")
+    for _ in range(2):
+        api.psf(h, g, out=out, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.trace_enable(reps * 8 + 64)
+    e0.record()
+    for _ in range(reps):
+        api.psf(h, g, out=out, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    psf_ms = e0.elapsed_time(e1) / reps
+    row = {"config": name, "N": N, "P": P, "wavelengths": g.L, "psf_ms": round(psf_ms, 3),
+           "field_samples_per_s": g.L * P * P / (psf_ms / 1e3)}
+    recs = api.trace_read()
+    del out
+    if do_grad:
+        T = torch.from_numpy(inputs.spot_target(P, N, g.L, 2000 + N)).cuda()
+        api.grad(h, g, T, ws=ws)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            api.grad(h, g, T, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        row["grad_ms"] = round(e0.elapsed_time(e1) / reps, 3)
+        recs += api.trace_read()
+        del T
+    api.trace_enable(0)
+    per: dict[str, list[float]] = {}
+    for n, ms in recs:
+        per.setdefault(n, []).append(ms)
+    row["passes_ms"] = {k: round(sorted(v)[len(v) // 2], 3) for k, v in per.items()}
+    del ws, h
+    torch.cuda.empty_cache()
+    return row
+
+
+def main():
+    from . import api
+
+    ap = argparse.ArgumentParser(description="per-configuration pass timing")
+    ap.add_argument("--configs", default=",".join(CONFIGS))
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--no-grad", action="store_true", help="time the PSF only")
+    args = ap.parse_args()
+    api.init()
+    for name in args.configs.split(","):
+        print(json.dumps(run(name.strip(), args.reps, grad=not args.no_grad)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
