@@ -76,40 +76,77 @@ __device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const floa
 }
 
 // ------------------------------------------------------------------ pass A: DOE rows
-// One CTA per (DOE row i, slice).  The first stage's register pairs are adjacent padded
-// columns x, x + 1 (x even; the DOE offset is even), loaded as one float2 of heights.
+// 16-byte asynchronous copies of a height row into shared memory (cp.async, L2 only).
+__device__ __forceinline__ void stage_heights(float* dst, const float* src, int n, int t, int nt) {
+  const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+  for (int k = t; k < n / 4; k += nt)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * k), "l"(src + 4 * k) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void wait_staged() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Persistent: CTA b transforms the (slice, DOE row) items k = b, b + gridDim.x, ... of all
+// S x N items (slice k / N, row k mod N).  The first stage's register pairs are adjacent padded
+// columns x, x + 1 (x even; the DOE offset is even).  When a height row fits behind the
+// exchange buffer (N <= L / 2, i.e. pad 2) the next item's heights are copied into shared
+// memory while the current row is transformed; otherwise they are read from global memory.
 template <int L>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __grid_constant__ Batch bt) {
   using F = First<L, false>;
+  constexpr int T = L / 32;
   extern __shared__ float2 sm[];
-  const Slice& sl = bt.s[blockIdx.y];
-  const int i = blockIdx.x;
+  float* hs = reinterpret_cast<float*>(sm + L);  // staged height row (N floats)
   const int t = threadIdx.x;
   const int N = bt.N, off = bt.off;
-  const float* hrow = sl.h + (size_t)i * N;
-  const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
-  float2 v[32];
-#pragma unroll
-  for (int b = 0; b < F::B; b += 2)
-#pragma unroll
-    for (int r = 0; r < F::R; ++r) {
-      const int x = F::idx(t, b, r) - off;  // even
-      float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-      if ((unsigned)x < (unsigned)N) {
-        const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
-        a = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-        c = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
-        if (erow) {
-          const float4 ev = __ldcs(erow + (x >> 1));
-          a = cmul(a, make_float2(ev.x, ev.y));
-          c = cmul(c, make_float2(ev.z, ev.w));
-        }
-      }
-      v[b * F::R + r] = a;
-      v[(b + 1) * F::R + r] = c;
+  const bool staged = 2 * N <= L;
+  const int items = bt.S * N, k0 = blockIdx.x, dk = gridDim.x;
+  if (staged && k0 < items) stage_heights(hs, bt.s[k0 / N].h + (size_t)(k0 % N) * N, N, t, T);
+  for (int k = k0; k < items; k += dk) {
+    const Slice& sl = bt.s[k / N];
+    const int i = k % N;
+    const float* hrow = sl.h + (size_t)i * N;
+    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+    float2 hv[F::B / 2][F::R];
+    if (staged) {
+      wait_staged();
+      __syncthreads();  // row i is in hs for every thread
     }
-  fft_run<L, 32, false>(v, t, sm);
-  store_band_row<L>(v, t, i, N, sl);
+#pragma unroll
+    for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < F::R; ++r) {
+        const int x = F::idx(t, b, r) - off;  // even
+        hv[b / 2][r] = make_float2(0.f, 0.f);
+        if ((unsigned)x < (unsigned)N)
+          hv[b / 2][r] = staged ? *reinterpret_cast<const float2*>(hs + x) : __ldcs(reinterpret_cast<const float2*>(hrow + x));
+      }
+    if (staged) {
+      __syncthreads();  // every thread has read hs
+      const int kn = k + dk;
+      if (kn < items) stage_heights(hs, bt.s[kn / N].h + (size_t)(kn % N) * N, N, t, T);
+    }
+    float2 v[32];
+#pragma unroll
+    for (int b = 0; b < F::B; b += 2)
+#pragma unroll
+      for (int r = 0; r < F::R; ++r) {
+        const int x = F::idx(t, b, r) - off;
+        float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+        if ((unsigned)x < (unsigned)N) {
+          a = transmittance(hv[b / 2][r].x, sl.kp_hi, sl.kp_lo);
+          c = transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);
+          if (erow) {
+            const float4 ev = __ldcs(erow + (x >> 1));
+            a = cmul(a, make_float2(ev.x, ev.y));
+            c = cmul(c, make_float2(ev.z, ev.w));
+          }
+        }
+        v[b * F::R + r] = a;
+        v[(b + 1) * F::R + r] = c;
+      }
+    fft_run<L, 32, false>(v, t, sm);  // its first exchange waits for every thread's previous row
+    store_band_row<L>(v, t, i, N, sl);
+  }
 }
 
 // ------------------------------------------------------------------ pass B / B*: columns

@@ -80,6 +80,9 @@ template <int L>
 constexpr size_t smem_bytes() { return (size_t)smem_words(L) * sizeof(float2); }
 template <int L>
 constexpr int threads() { return L / 32; }
+// pass A: exchange buffer plus the staged height row (at most L / 2 floats)
+template <int L>
+constexpr int pass_a_smem() { return (int)(smem_bytes<L>() + (size_t)(L / 2) * sizeof(float)); }
 
 #define DOE_DISPATCH(lg, fn, ...)                   \
   switch (lg) {                                     \
@@ -123,7 +126,7 @@ cudaError_t prep_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<L>();
   const int nt = threads<L>();
-  if ((e = prep_one(pass_a_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_kernel<L>, pass_a_smem<L>(), nt))) return e;
   if ((e = prep_one(pass_b_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_kernel<L>, sb, nt))) return e;
@@ -138,7 +141,18 @@ cudaError_t prep_t() {
 template <int L>
 cudaError_t pass_a_t(const Batch& bt, cudaStream_t st) {
   Traced tr(TR_PASS_A, st);
-  pass_a_kernel<L><<<dim3(bt.N, bt.S), threads<L>(), smem_bytes<L>(), st>>>(bt);
+  // persistent: about as many CTAs per slice as are resident at once, each looping over rows
+  static const int resident = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_a_kernel<L>, threads<L>(), pass_a_smem<L>()))
+      return 0;
+    return sms * per_sm;
+  }();
+  const long items = (long)bt.S * bt.N;
+  const int grid = (int)(resident > 0 && resident < items ? resident : items);
+  const size_t smem = smem_bytes<L>() + (2 * bt.N <= L ? (size_t)bt.N * sizeof(float) : 0);
+  pass_a_kernel<L><<<dim3(grid), threads<L>(), smem, st>>>(bt);
   return cudaGetLastError();
 }
 template <int L>
