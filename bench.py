@@ -171,6 +171,7 @@ def run_ours(args):
 
     from paper_2505_22313_b300 import api, build, inputs
     from paper_2505_22313_b300.api import Geometry
+    from paper_2505_22313_b300.replicas import max_over_ranks
 
     ws_n, rank, local = _dist()
     if ws_n > 1:
@@ -221,11 +222,7 @@ def run_ours(args):
     recs = api.trace_read(K * launches_per_step)
     api.trace_enable(0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = ev[0][0].elapsed_time(ev[-1][1])
-    if ws_n > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]))
     units_per_step = g.L * P * P
     value = ws_n * units_per_step * K / (total_ms / 1e3)
 
@@ -290,11 +287,7 @@ def run_ours(args):
         step_e2e(k)
     e1.record(s_out)  # after the last copy-out, which follows every earlier step's work
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / Ke
-    if ws_n > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke)
     e2e = {"value": ws_n * units_per_step / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h_np.nbytes + img_np.nbytes, "d2h_bytes_per_step": C * H * W * 4,
            "ms_per_step": round(e2e_ms, 4), "overlap": "copy-in / compute / copy-out streams, 2 slots"}
