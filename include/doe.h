@@ -130,12 +130,27 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
  *   out_c[y][x] = sum_{u,v} img_c[y + H/2 - u][x + W/2 - v] k_c[u][v], zero outside the image
  *   (linear convolution, "same" window), computed with 2H x 2W transforms.
  *   psf  device float [C][Py][Px];  img, out  device float [C][H][W]
- * H and W are powers of two with 16 <= H <= Py, 16 <= W <= Px, 2H <= 8192 and 2W <= 16384.
+ * H and W are powers of two with 16 <= H <= Py, 16 <= W <= Px, 2H <= 8192 and 2W <= 16384;
+ * Py is even and Px a multiple of 4.
  * Workspace: doe_render_workspace_bytes(C, H, W).  Errors: DOE_EINVAL, DOE_EUNSUPPORTED,
  * DOE_ENOWS, DOE_ECUDA. */
 int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out,
                void* ws, size_t ws_bytes, void* stream);
 size_t doe_render_workspace_bytes(int C, int H, int W);
+
+/* Wiener deconvolution with the simulated PSF (Eq. 9, the imaging application's
+ * reconstruction): per channel c,
+ *   out_c = real( IFFT2( conj(K_c) / (|K_c|^2 + gamma) * FFT2(y_c) ) ),
+ * with K_c = FFT2 of the PSF crop of size H x W centred at (Py/2, Px/2), normalised to sum 1
+ * and placed with its centre at the origin of the H x W grid (circular model, no padding);
+ * FFT2 unnormalised, IFFT2 with 1 / (H W).
+ *   psf  device float [C][Py][Px];  y (blurred images), out  device float [C][H][W]
+ * H and W are powers of two with 32 <= H <= min(Py, 8192), 32 <= W <= min(Px, 16384); Py
+ * even, Px a multiple of 4; gamma >= 0.  Workspace: doe_wiener_workspace_bytes(C, H, W).
+ * Errors: DOE_EINVAL, DOE_EUNSUPPORTED, DOE_ENOWS, DOE_ECUDA. */
+int doe_wiener(int C, int H, int W, const float* psf, int Py, int Px, const float* y, double gamma,
+               float* out, void* ws, size_t ws_bytes, void* stream);
+size_t doe_wiener_workspace_bytes(int C, int H, int W);
 
 /* Integer band logic of the transfer function, computed on the host exactly as the kernels
  * use it (for bit-exact checks).  For wavelength j: kmax[j] = the largest signed frequency

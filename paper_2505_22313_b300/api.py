@@ -183,6 +183,23 @@ def render(psf_t: torch.Tensor, img: torch.Tensor, out: torch.Tensor | None = No
     return out
 
 
+def wiener(psf_t: torch.Tensor, y: torch.Tensor, gamma: float, out: torch.Tensor | None = None,
+           ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Wiener deconvolution of each blurred channel with its PSF (Eq. 9; crop at the axis,
+    normalised, circular model)."""
+    C, H, W = y.shape
+    Py, Px = psf_t.shape[-2:]
+    pp = _dev_ptr(psf_t, torch.float32, (C, Py, Px), "psf")
+    yp = _dev_ptr(y, torch.float32, (C, H, W), "y")
+    if out is None:
+        out = torch.empty((C, H, W), dtype=torch.float32, device=y.device)
+    op = _dev_ptr(out, torch.float32, (C, H, W), "out")
+    need = int(L.load().doe_wiener_workspace_bytes(C, H, W))
+    ws, wp, wb = _ws_args(ws, need, y.device)
+    L.check(L.load().doe_wiener(C, H, W, pp, Py, Px, yp, float(gamma), op, wp, wb, _stream(stream)), "doe_wiener")
+    return out
+
+
 def band_limits(geom: Geometry):
     """(kmax [L] int32, m_ev [L] int64): the integer band logic the kernels apply."""
     k = np.zeros(geom.L, np.int32)

@@ -380,6 +380,13 @@ int doe_render(int C, int H, int W, const float* psf, int Py, int Px, const floa
 
 size_t doe_render_workspace_bytes(int C, int H, int W) { return render_workspace(C, H, W); }
 
+int doe_wiener(int C, int H, int W, const float* psf, int Py, int Px, const float* y, double gamma, float* out,
+               void* ws, size_t ws_bytes, void* stream) {
+  return wiener_entry(C, H, W, psf, Py, Px, y, gamma, out, ws, ws_bytes, stream);
+}
+
+size_t doe_wiener_workspace_bytes(int C, int H, int W) { return wiener_workspace(C, H, W); }
+
 int doe_trace_enable(int max_records) { return trace_enable(max_records) == 0 ? DOE_OK : DOE_ECUDA; }
 
 int doe_trace_read(int max, int* pass_ids, float* ms) {

@@ -279,7 +279,9 @@ int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st) {
   cudaError_t e;
-  const int lw = ilog2i(2 * ra.W), lh = ilog2i(2 * ra.H);
+  // linear render: 2W x 2H transforms; Wiener (circular): W x H
+  const int f = ra.mode == RENDER_WIENER ? 1 : 2;
+  const int lw = ilog2i(f * ra.W), lh = ilog2i(f * ra.H);
   if ((e = [&]() -> cudaError_t { DOE_DISPATCH(lw, render_rows_t, ra, st); }())) return e;
   if ((e = [&]() -> cudaError_t { DOE_DISPATCH(lh, render_cols_t, ra, st); }())) return e;
   return [&]() -> cudaError_t { DOE_DISPATCH(lw, render_out_t, ra, st); }();

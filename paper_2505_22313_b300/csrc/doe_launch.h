@@ -34,3 +34,6 @@ cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st);
 int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out, void* ws,
                  size_t ws_bytes, void* stream);
 size_t render_workspace(int C, int H, int W);
+int wiener_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* y, double gamma, float* out,
+                 void* ws, size_t ws_bytes, void* stream);
+size_t wiener_workspace(int C, int H, int W);

@@ -1,5 +1,5 @@
-// doe_render.cu -- host side of doe_render: validation, workspace layout, launch sequence
-// (kernels in doe_render.cuh).
+// doe_render.cu -- host side of doe_render and doe_wiener: validation, workspace layout,
+// launch sequence (kernels in doe_render.cuh).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,15 +19,17 @@ struct RLayout {
   int wpr = 0;
 };
 
-int render_check(int C, int H, int W) {
-  if (C < 1 || !pow2(H) || !pow2(W) || H < 16 || W < 16) return DOE_EINVAL;
-  if (2L * H > doe::kRenderColsMax || 2L * W > (1L << doe::kMaxLog)) return DOE_EUNSUPPORTED;
+// f = 2: linear render on 2H x 2W transforms; f = 1: circular Wiener on H x W transforms.
+int render_check(int C, int H, int W, int f) {
+  if (C < 1 || !pow2(H) || !pow2(W) || f * H < 32 || f * W < 32) return DOE_EINVAL;
+  if ((long)f * H > doe::kRenderColsMax || (long)f * W > (1L << doe::kMaxLog)) return DOE_EUNSUPPORTED;
   return DOE_OK;
 }
 
-RLayout render_layout(int C, int H, int W) {
+// nk = stored columns of a row spectrum (f W / 2 + 1)
+RLayout render_layout(int C, int H, int nk) {
   RLayout L;
-  L.wpr = (W + 1 + doe::kTile - 1) / doe::kTile * doe::kTile;
+  L.wpr = (nk + doe::kTile - 1) / doe::kTile * doe::kTile;
   const size_t plane = (size_t)C * H * L.wpr * sizeof(float2);
   L.sa = 0;
   L.sb = a256(plane);
@@ -41,25 +43,38 @@ RLayout render_layout(int C, int H, int W) {
 int render_ensure_device();
 
 size_t render_workspace(int C, int H, int W) {
-  if (render_check(C, H, W) != DOE_OK) return 0;
-  return render_layout(C, H, W).total;
+  if (render_check(C, H, W, 2) != DOE_OK) return 0;
+  return render_layout(C, H, W + 1).total;
 }
 
-int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out, void* ws,
-                 size_t ws_bytes, void* stream) {
-  int rc = render_check(C, H, W);
+size_t wiener_workspace(int C, int H, int W) {
+  if (render_check(C, H, W, 1) != DOE_OK) return 0;
+  return render_layout(C, H, W / 2 + 1).total;
+}
+
+namespace {
+int run(int mode, int C, int H, int W, const float* psf, int Py, int Px, const float* img, double gamma, float* out,
+        void* ws, size_t ws_bytes, void* stream) {
+  const int f = mode == doe::RENDER_WIENER ? 1 : 2;
+  int rc = render_check(C, H, W, f);
   if (rc != DOE_OK) return rc;
   if (!psf || !img || !out) return DOE_EINVAL;
-  if (Py < H || Px < W || (Py & 1) || (Px & 1)) return DOE_EINVAL;
-  const RLayout lay = render_layout(C, H, W);
+  // the crop's rows start at column Px/2 - W/2 and are read as 8-byte pairs: Px % 4 == 0
+  if (Py < H || Px < W || (Py & 1) || (Px & 3)) return DOE_EINVAL;
+  if (mode == doe::RENDER_WIENER && !(gamma >= 0.0)) return DOE_EINVAL;
+  const int nk = f * W / 2 + 1;
+  const RLayout lay = render_layout(C, H, nk);
   if (!ws || ws_bytes < lay.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) return DOE_ENOWS;
   if ((rc = render_ensure_device()) != DOE_OK) return rc;
   doe::RenderArgs ra;
+  ra.mode = mode;
+  ra.gamma = (float)gamma;
   ra.C = C;
   ra.H = H;
   ra.W = W;
   ra.Py = Py;
   ra.Px = Px;
+  ra.nk = nk;
   ra.wpr = lay.wpr;
   ra.psf = psf;
   ra.img = img;
@@ -71,4 +86,15 @@ int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const fl
   ra.ksum = reinterpret_cast<double*>(base + lay.ks);
   if (doe::launch_render(ra, static_cast<cudaStream_t>(stream)) != cudaSuccess) return DOE_ECUDA;
   return DOE_OK;
+}
+}  // namespace
+
+int render_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* img, float* out, void* ws,
+                 size_t ws_bytes, void* stream) {
+  return run(doe::RENDER_LINEAR, C, H, W, psf, Py, Px, img, 0.0, out, ws, ws_bytes, stream);
+}
+
+int wiener_entry(int C, int H, int W, const float* psf, int Py, int Px, const float* y, double gamma, float* out,
+                 void* ws, size_t ws_bytes, void* stream) {
+  return run(doe::RENDER_WIENER, C, H, W, psf, Py, Px, y, gamma, out, ws, ws_bytes, stream);
 }

@@ -12,6 +12,11 @@
 //   R3  per pair of output rows: the two Hermitian half spectra are packed as X0 + i X1,
 //       extended to 2W by conjugate symmetry, one complex IFFT, real part = row y, imaginary
 //       part = row y + 1, window [W/2, 3W/2), scaled by 1 / (4 H W sum(k_c)).
+// The same three kernels run Wiener deconvolution (Eq. 9, circular model, RENDER_WIENER) on
+// H x W transforms without padding: R1 packs the blurred row with the (unshifted) crop row;
+// R2 replaces the product by the filter conj(K) Y / (|K|^2 + gamma) with K = FFT2(crop) /
+// sum(crop) times (-1)^(l + k) (the crop's centre moved to the origin), and keeps all H rows;
+// R3 keeps all W columns and scales by 1 / (H W).
 #pragma once
 #include <cooperative_groups.h>
 
@@ -65,7 +70,7 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
   __syncthreads();
   float2* sa = ra.sa + (size_t)c * H * ra.wpr;
   float2* sb = ra.sb + (size_t)c * H * ra.wpr;
-  for (int k = t; k <= W; k += T) {
+  for (int k = t; k <= L / 2; k += T) {
     const float2 zk = sm[phys(k)];
     const float2 zm = sm[phys((L - k) & (L - 1))];
     // X_img = (Z[k] + conj Z[-k]) / 2, X_k = (Z[k] - conj Z[-k]) / (2i)
@@ -103,8 +108,9 @@ __device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const flo
 // CTA q reads its own column of SA and of SB straight into registers, keeps the image column's
 // spectrum in sma while the kernel column is transformed in smb, multiplies, inverse-transforms,
 // and the cluster gathers rows [H/2, 3H/2) of its four columns as 32-byte row segments of SC.
+// Up to 4096 points two 32 KB buffers let 3 CTAs share an SM, so registers are capped to match.
 template <int L>
-__global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
+__global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   constexpr int T = L / 32;
@@ -122,7 +128,18 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
   const int tile = (blockIdx.x / kTile) % tiles;
   const int c = (blockIdx.x / kTile) / tiles;
   const int pos0 = tile * kTile, mypos = pos0 + q;
-  const bool live = mypos <= ra.W;  // columns past W are unused
+  const bool live = mypos < ra.nk;  // columns past the half spectrum are unused
+  const bool wiener = ra.mode == RENDER_WIENER;
+  float ks = 0.f;  // Wiener: sum of the crop, in a fixed order (FP64)
+  if (wiener) {
+    __shared__ double red[32];
+    double a = 0.0;
+    for (int u = t; u < H; u += T) a += ra.ksum[(size_t)c * H + u];
+    a = block_sum<T>(a, red);  // the total is in thread 0
+    if (t == 0) red[0] = a;
+    __syncthreads();
+    ks = (float)red[0];
+  }
   const float2* colA = ra.sa + (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile);
   const float2* colB = ra.sb + (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile);
   float2* baseC = ra.sc + (size_t)c * H * ra.wpr;
@@ -141,18 +158,31 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
         s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
-  // spectrum of the kernel column, times the image spectrum (same thread, same positions)
+  // spectrum of the kernel column, times the image spectrum (same thread, same positions), or
+  // the Wiener filter sign conj(K) ks Y / (|K|^2 + gamma ks^2) with K unnormalised
   load_tiled_col<L>(v, t, colB, H, live);
   fft_run<L, 32, false>(v, t, smb);
   {
     const float4* s4 = reinterpret_cast<const float4*>(sma);
+    const float g2 = ra.gamma * ks * ks;
 #pragma unroll
     for (int b = 0; b < G::B; b += 2)
 #pragma unroll
       for (int r = 0; r < G::R; ++r) {
         const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
-        v[b * G::R + r] = cmul(v[b * G::R + r], make_float2(a.x, a.y));
-        v[(b + 1) * G::R + r] = cmul(v[(b + 1) * G::R + r], make_float2(a.z, a.w));
+        float2& k0 = v[b * G::R + r];
+        float2& k1 = v[(b + 1) * G::R + r];
+        if (!wiener) {
+          k0 = cmul(k0, make_float2(a.x, a.y));
+          k1 = cmul(k1, make_float2(a.z, a.w));
+        } else {
+          // rows l = idx (even) and idx + 1, column mypos: signs (-1)^(l + k) alternate
+          const float s0 = (mypos & 1) ? -ks : ks;
+          const float f0 = s0 / fmaf(k0.x, k0.x, fmaf(k0.y, k0.y, g2));
+          const float f1 = -s0 / fmaf(k1.x, k1.x, fmaf(k1.y, k1.y, g2));
+          k0 = cscale(cmulc(make_float2(a.x, a.y), k0), f0);
+          k1 = cscale(cmulc(make_float2(a.z, a.w), k1), f1);
+        }
       }
   }
   fft_run<L, 32, true>(v, t, smb);
@@ -172,27 +202,32 @@ __global__ void __launch_bounds__(L / 32) render_cols_kernel(const __grid_consta
   for (int cc = 0; cc < kTile; ++cc) rsb[cc] = reinterpret_cast<const float4*>(cl.map_shared_rank(smb, cc));
   cl.sync();  // all four columns are in shared memory (and every CTA of the cluster has started)
   {
-    // rows [H/2, 3H/2) of the column IFFT -> SC rows [0, H); item = (pair of output rows,
-    // column pair f), all remote loads issued before the first store
-    constexpr int IT = (L / 2 / kTile / 2) * F4 / T;
+    // rows [H/2, 3H/2) (render) or [0, H) (Wiener) of the column IFFT -> SC rows [0, H); item
+    // = (pair of output rows, column pair f), all remote loads issued before the first store
+    constexpr int IT = (L / kTile / 2) * F4 / T;  // Wiener; the render uses the first half
+    constexpr int CH = IT < 4 ? IT : 4;           // items whose loads are in flight together
     const int rows = H / kTile, rbeg = q * rows, lim = (rows / 2) * F4;
-    float4 a[IT], b[IT];
+    const int r0 = wiener ? 0 : H / 2;
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = t + it * T, f = idx & 1;
-      if (idx < lim) {
-        const int ch = swz((H / 2 + rbeg + 2 * (idx / F4)) >> 1);
-        a[it] = (f ? rsb[2] : rsb[0])[ch];  // rows rr, rr + 1 of column 2f
-        b[it] = (f ? rsb[3] : rsb[1])[ch];  // of column 2f + 1
+    for (int c0 = 0; c0 < IT; c0 += CH) {
+      float4 a[CH], b[CH];
+#pragma unroll
+      for (int it = 0; it < CH; ++it) {
+        const int idx = t + (c0 + it) * T, f = idx & 1;
+        if (idx < lim) {
+          const int ch = swz((r0 + rbeg + 2 * (idx / F4)) >> 1);
+          a[it] = (f ? rsb[2] : rsb[0])[ch];  // rows rr, rr + 1 of column 2f
+          b[it] = (f ? rsb[3] : rsb[1])[ch];  // of column 2f + 1
+        }
       }
-    }
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = t + it * T, f = idx & 1;
-      if (idx < lim) {
-        float2* dst = baseC + (size_t)(rbeg + 2 * (idx / F4)) * ra.wpr + pos0 + 2 * f;
-        __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
-        __stcs(reinterpret_cast<float4*>(dst + ra.wpr), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+      for (int it = 0; it < CH; ++it) {
+        const int idx = t + (c0 + it) * T, f = idx & 1;
+        if (idx < lim) {
+          float2* dst = baseC + (size_t)(rbeg + 2 * (idx / F4)) * ra.wpr + pos0 + 2 * f;
+          __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
+          __stcs(reinterpret_cast<float4*>(dst + ra.wpr), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+        }
       }
     }
   }
@@ -211,21 +246,26 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
   const int W = ra.W, H = ra.H;
   const float2* x0 = ra.sc + ((size_t)c * H + y) * ra.wpr;
   const float2* x1 = x0 + ra.wpr;
-  // sum of the kernel crop (fixed order, FP64)
-  double ks = 0.0;
-  for (int u = t; u < H; u += T) ks += ra.ksum[(size_t)c * H + u];
-  ks = block_sum<T>(ks, red);
-  if (t == 0) red[0] = ks;
-  __syncthreads();
-  const float scale = (float)(1.0 / ((double)L * (2.0 * H) * red[0]));
+  const bool wiener = ra.mode == RENDER_WIENER;
+  // render: sum of the kernel crop (fixed order, FP64); Wiener: normalised in R2 already
+  double ks = 1.0;
+  if (!wiener) {
+    ks = 0.0;
+    for (int u = t; u < H; u += T) ks += ra.ksum[(size_t)c * H + u];
+    ks = block_sum<T>(ks, red);
+    if (t == 0) red[0] = ks;
+    __syncthreads();
+    ks = red[0];
+  }
+  const float scale = (float)(1.0 / ((double)L * (wiener ? (double)H : 2.0 * H) * ks));
   float2 v[32];
 #pragma unroll
   for (int b = 0; b < F::B; ++b)
 #pragma unroll
     for (int r = 0; r < F::R; ++r) {
       const int k = F::idx(t, b, r);
-      float2 a, d;  // X0[k], X1[k] with Hermitian extension above W
-      if (k <= W) {
+      float2 a, d;  // X0[k], X1[k] with Hermitian extension above L / 2
+      if (k <= L / 2) {
         a = x0[k];
         d = x1[k];
       } else {
@@ -243,7 +283,7 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
   for (int b = 0; b < Hh::B; b += 2)
 #pragma unroll
     for (int r = 0; r < Hh::R; ++r) {
-      const int n = Hh::idx(t, b, r) - W / 2;  // even
+      const int n = Hh::idx(t, b, r) - (L - W) / 2;  // even; window offset W/2 (render) or 0
       if ((unsigned)n < (unsigned)W) {
         const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
         __stcs(reinterpret_cast<float2*>(o0 + n), make_float2(a.x * scale, d.x * scale));

@@ -1,6 +1,6 @@
 """Per-configuration timing of the library's passes (PSF and gradient).
 
-    python -m paper_2505_22313_b300.sweep [--configs small,rgb,gradient,large_area] [--reps K]
+    python -m paper_2505_22313_b300.sweep [--configs small,rgb,gradient,large_area,wiener] [--reps K]
 
 Each configuration runs the PSF (and, where listed, the L2 gradient against the spot-array
 target with recomputed fields) K times after warm-up, timed with CUDA events on the current
@@ -74,6 +74,38 @@ def run(name: str, reps: int, grad: bool = True) -> dict:
     return row
 
 
+def run_wiener(reps: int, C: int = 3, H: int = 2048, W: int = 2048, P: int = 8192) -> dict:
+    """Wiener deconvolution (Eq. 9) of C seeded H x W images with seeded P x P PSFs."""
+    import numpy as np
+    import torch
+
+    from . import _lib, api, inputs
+
+    rng = np.random.default_rng(2048)
+    psf = torch.from_numpy(rng.random((C, P, P), dtype=np.float32) ** 4).cuda()
+    y = torch.from_numpy(inputs.image(C, H, W, 2002)).cuda()
+    out = torch.empty_like(y)
+    ws = api.workspace(int(_lib.load().doe_wiener_workspace_bytes(C, H, W)))
+    for _ in range(3):
+        out = api.wiener(psf, y, 5e-4, out=out, ws=ws)
+    torch.cuda.synchronize()
+    api.trace_enable(reps * 4 + 16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        api.wiener(psf, y, 5e-4, out=out, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    recs = api.trace_read()
+    api.trace_enable(0)
+    per: dict[str, list[float]] = {}
+    for n, ms in recs:
+        per.setdefault(n, []).append(ms)
+    ms = e0.elapsed_time(e1) / reps
+    return {"config": f"wiener_{C}x{H}x{W}", "wiener_ms": round(ms, 4), "pixels_per_s": C * H * W / (ms / 1e3),
+            "passes_ms": {k: round(sorted(v)[len(v) // 2], 4) for k, v in per.items()}}
+
+
 def main():
     from . import api
 
@@ -84,7 +116,9 @@ def main():
     args = ap.parse_args()
     api.init()
     for name in args.configs.split(","):
-        print(json.dumps(run(name.strip(), args.reps, grad=not args.no_grad)), flush=True)
+        name = name.strip()
+        row = run_wiener(args.reps) if name == "wiener" else run(name, args.reps, grad=not args.no_grad)
+        print(json.dumps(row), flush=True)
 
 
 if __name__ == "__main__":

@@ -199,18 +199,58 @@ def test_render_small_vs_oracle(C, H, W, Pp):
     assert rel_l2(out, ref) < TOL_PSF, rel_l2(out, ref)
 
 
+def _rgb_workload_psfs():
+    # the oracle's FP64 PSFs of the RGB workload's 4096^2 DOE (8192^2 grid, 450/550/650 nm),
+    # rounded to float32: the input both sides of the render and Wiener tests receive
+    N, dx, z = 4096, 1e-6, 50e-3
+    return oracle.psf(_h(N, 1002), dx, z, [450e-9, 550e-9, 650e-9]).astype(np.float32)
+
+
 def test_render_rgb_workload_vs_oracle():
     # the RGB design-evaluation workload: 3 PSFs of a 4096^2 DOE (8192^2 grid) convolved with
     # a seeded 3 x 2048 x 2048 scene
-    N, dx, z = 4096, 1e-6, 50e-3
-    lams = [450e-9, 550e-9, 650e-9]
-    h = torch.from_numpy(_h(N, 1002)).cuda()
-    g = Geometry.make(N, dx, z, lams)
-    I = api.psf(h, g)
+    psf = _rgb_workload_psfs()
     img = inputs.image(3, 2048, 2048, 2002)
-    out = api.render(I, torch.from_numpy(img).cuda()).cpu().numpy()
-    ref = oracle.render(I.cpu().numpy(), img)  # the oracle convolves the GPU's PSFs
+    out = api.render(torch.from_numpy(psf).cuda(), torch.from_numpy(img).cuda()).cpu().numpy()
+    ref = oracle.render(psf, img)
     assert rel_l2(out, ref) < TOL_PSF, rel_l2(out, ref)
+
+
+# -------------------------------------------------------------- Wiener deconvolution (Eq. 9)
+GAMMA = 5e-4  # the regulariser of the imaging application
+# FP32 transforms (rel L2 <= TOL_PSF, as for the PSF) amplified by at most the filter's gain
+# max |conj(K) / (|K|^2 + gamma)| = 1 / (2 sqrt(gamma))
+TOL_WIENER = TOL_PSF / (2.0 * np.sqrt(GAMMA))
+
+
+@pytest.mark.parametrize("C,H,W,Pp", [(2, 32, 32, 64), (3, 64, 128, 128), (1, 256, 64, 512)])
+def test_wiener_small_vs_oracle(C, H, W, Pp):
+    rng = np.random.default_rng(7 * H + W)
+    psf = rng.random((C, Pp, Pp)).astype(np.float32) ** 4
+    y = inputs.image(C, H, W, 2100 + H)
+    out = api.wiener(torch.from_numpy(psf).cuda(), torch.from_numpy(y).cuda(), GAMMA).cpu().numpy()
+    ref = oracle.wiener(psf, y, GAMMA)
+    assert rel_l2(out, ref) < TOL_WIENER, rel_l2(out, ref)
+
+
+def test_wiener_rgb_workload_vs_oracle():
+    # the RGB workload's PSFs deconvolving a scene the oracle blurred with them
+    psf = _rgb_workload_psfs()
+    y = oracle.render(psf, inputs.image(3, 2048, 2048, 2002)).astype(np.float32)
+    out = api.wiener(torch.from_numpy(psf).cuda(), torch.from_numpy(y).cuda(), GAMMA).cpu().numpy()
+    ref = oracle.wiener(psf, y, GAMMA)
+    err = rel_l2(out, ref)
+    print(f"wiener rgb rel_l2 {err:.3e}")
+    assert err < TOL_WIENER, err
+
+
+def test_wiener_rejects_bad_arguments():
+    psf = torch.zeros((1, 64, 66), device="cuda")  # Px not a multiple of 4
+    y = torch.zeros((1, 32, 32), device="cuda")
+    with pytest.raises(Exception):
+        api.wiener(psf, y, GAMMA)
+    with pytest.raises(Exception):
+        api.wiener(torch.zeros((1, 64, 64), device="cuda"), y, -1.0)
 
 
 def test_trace_and_launch_count():
