@@ -131,10 +131,14 @@ cudaError_t prep_t() {
   if ((e = prep_one(pass_c_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_a_adj_kernel<L>, sb, nt))) return e;
-  if ((e = prep_one(render_rows_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(render_rows_kernel<L, false>, sb, nt)) || (e = prep_one(render_rows_kernel<L, true>, sb, nt)))
+    return e;
   if constexpr (L <= kRenderColsMax)  // two L-sample buffers must fit one CTA's shared memory
-    if ((e = prep_one(render_cols_kernel<L>, 2 * sb, nt))) return e;
-  if ((e = prep_one(render_out_kernel<L>, sb, nt))) return e;
+    if ((e = prep_one(render_cols_kernel<L, false>, 2 * sb, nt)) ||
+        (e = prep_one(render_cols_kernel<L, true>, 2 * sb, nt)))
+      return e;
+  if ((e = prep_one(render_out_kernel<L, false>, sb, nt)) || (e = prep_one(render_out_kernel<L, true>, sb, nt)))
+    return e;
   return cudaSuccess;
 }
 
@@ -245,7 +249,10 @@ cudaError_t prep_big_t() {
 template <int L>
 cudaError_t render_rows_t(const RenderArgs& ra, cudaStream_t st) {
   Traced tr(TR_RENDER_ROWS, st);
-  render_rows_kernel<L><<<dim3(ra.H, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  if (ra.mode == RENDER_WIENER)
+    render_rows_kernel<L, true><<<dim3(ra.H, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  else
+    render_rows_kernel<L, false><<<dim3(ra.H, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
   return cudaGetLastError();
 }
 template <int L>
@@ -264,14 +271,18 @@ cudaError_t render_cols_t(const RenderArgs& ra, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, render_cols_kernel<L>, ra);
+  cudaError_t e = ra.mode == RENDER_WIENER ? cudaLaunchKernelEx(&cfg, render_cols_kernel<L, true>, ra)
+                                            : cudaLaunchKernelEx(&cfg, render_cols_kernel<L, false>, ra);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 template <int L>
 cudaError_t render_out_t(const RenderArgs& ra, cudaStream_t st) {
   Traced tr(TR_RENDER_OUT, st);
-  render_out_kernel<L><<<dim3(ra.H / 2, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  if (ra.mode == RENDER_WIENER)
+    render_out_kernel<L, true><<<dim3(ra.H / 2, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
+  else
+    render_out_kernel<L, false><<<dim3(ra.H / 2, ra.C), threads<L>(), smem_bytes<L>(), st>>>(ra);
   return cudaGetLastError();
 }
 int ilog2i(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }

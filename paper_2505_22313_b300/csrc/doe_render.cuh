@@ -28,7 +28,7 @@ namespace doe {
 
 
 // R1: one CTA per (row u, channel c); transform length L = 2W.
-template <int L>
+template <int L, bool WIENER>
 __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_constant__ RenderArgs ra) {
   using F = First<L, false>;
   using G = Last<L, false>;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
   __syncthreads();
   float2* sa = ra.sa + (size_t)c * H * ra.wpr;
   float2* sb = ra.sb + (size_t)c * H * ra.wpr;
-  for (int k = t; k <= L / 2; k += T) {
+  for (int k = t; k <= (WIENER ? W / 2 : W); k += T) {  // the L / 2 + 1 stored columns
     const float2 zk = sm[phys(k)];
     const float2 zm = sm[phys((L - k) & (L - 1))];
     // X_img = (Z[k] + conj Z[-k]) / 2, X_k = (Z[k] - conj Z[-k]) / (2i)
@@ -108,9 +108,10 @@ __device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const flo
 // CTA q reads its own column of SA and of SB straight into registers, keeps the image column's
 // spectrum in sma while the kernel column is transformed in smb, multiplies, inverse-transforms,
 // and the cluster gathers rows [H/2, 3H/2) of its four columns as 32-byte row segments of SC.
-// Up to 4096 points two 32 KB buffers let 3 CTAs share an SM, so registers are capped to match.
-template <int L>
-__global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
+// Up to 4096 points two 32 KB buffers let 3 CTAs share an SM; the Wiener filter would push
+// registers past that, so its instantiation is capped to match.
+template <int L, bool WIENER>
+__global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   constexpr int T = L / 32;
@@ -129,9 +130,9 @@ __global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(
   const int c = (blockIdx.x / kTile) / tiles;
   const int pos0 = tile * kTile, mypos = pos0 + q;
   const bool live = mypos < ra.nk;  // columns past the half spectrum are unused
-  const bool wiener = ra.mode == RENDER_WIENER;
+  constexpr bool wiener = WIENER;
   float ks = 0.f;  // Wiener: sum of the crop, in a fixed order (FP64)
-  if (wiener) {
+  if constexpr (wiener) {
     __shared__ double red[32];
     double a = 0.0;
     for (int u = t; u < H; u += T) a += ra.ksum[(size_t)c * H + u];
@@ -164,26 +165,31 @@ __global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(
   fft_run<L, 32, false>(v, t, smb);
   {
     const float4* s4 = reinterpret_cast<const float4*>(sma);
-    const float g2 = ra.gamma * ks * ks;
+    if constexpr (!wiener) {
 #pragma unroll
-    for (int b = 0; b < G::B; b += 2)
+      for (int b = 0; b < G::B; b += 2)
 #pragma unroll
-      for (int r = 0; r < G::R; ++r) {
-        const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
-        float2& k0 = v[b * G::R + r];
-        float2& k1 = v[(b + 1) * G::R + r];
-        if (!wiener) {
-          k0 = cmul(k0, make_float2(a.x, a.y));
-          k1 = cmul(k1, make_float2(a.z, a.w));
-        } else {
-          // rows l = idx (even) and idx + 1, column mypos: signs (-1)^(l + k) alternate
-          const float s0 = (mypos & 1) ? -ks : ks;
+        for (int r = 0; r < G::R; ++r) {
+          const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
+          v[b * G::R + r] = cmul(v[b * G::R + r], make_float2(a.x, a.y));
+          v[(b + 1) * G::R + r] = cmul(v[(b + 1) * G::R + r], make_float2(a.z, a.w));
+        }
+    } else {
+      const float g2 = ra.gamma * ks * ks;
+      const float s0 = (mypos & 1) ? -ks : ks;  // rows l even, column mypos: sign (-1)^(l + k)
+#pragma unroll
+      for (int b = 0; b < G::B; b += 2)
+#pragma unroll
+        for (int r = 0; r < G::R; ++r) {
+          const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
+          float2& k0 = v[b * G::R + r];        // row l = idx (even)
+          float2& k1 = v[(b + 1) * G::R + r];  // row l + 1: opposite sign
           const float f0 = s0 / fmaf(k0.x, k0.x, fmaf(k0.y, k0.y, g2));
           const float f1 = -s0 / fmaf(k1.x, k1.x, fmaf(k1.y, k1.y, g2));
           k0 = cscale(cmulc(make_float2(a.x, a.y), k0), f0);
           k1 = cscale(cmulc(make_float2(a.z, a.w), k1), f1);
         }
-      }
+    }
   }
   fft_run<L, 32, true>(v, t, smb);
   __syncthreads();
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(
   {
     // rows [H/2, 3H/2) (render) or [0, H) (Wiener) of the column IFFT -> SC rows [0, H); item
     // = (pair of output rows, column pair f), all remote loads issued before the first store
-    constexpr int IT = (L / kTile / 2) * F4 / T;  // Wiener; the render uses the first half
+    constexpr int IT = ((WIENER ? L : L / 2) / kTile / 2) * F4 / T;  // H = L (Wiener) or L / 2 rows
     constexpr int CH = IT < 4 ? IT : 4;           // items whose loads are in flight together
     const int rows = H / kTile, rbeg = q * rows, lim = (rows / 2) * F4;
     const int r0 = wiener ? 0 : H / 2;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(L / 32, L <= 4096 ? 3 : 1) render_cols_kernel(
 }
 
 // R3: one CTA per (pair of output rows, channel); transform length L = 2W.
-template <int L>
+template <int L, bool WIENER>
 __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constant__ RenderArgs ra) {
   using F = First<L, true>;
   using Hh = Last<L, true>;
@@ -246,10 +252,10 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
   const int W = ra.W, H = ra.H;
   const float2* x0 = ra.sc + ((size_t)c * H + y) * ra.wpr;
   const float2* x1 = x0 + ra.wpr;
-  const bool wiener = ra.mode == RENDER_WIENER;
+  constexpr bool wiener = WIENER;
   // render: sum of the kernel crop (fixed order, FP64); Wiener: normalised in R2 already
   double ks = 1.0;
-  if (!wiener) {
+  if constexpr (!wiener) {
     ks = 0.0;
     for (int u = t; u < H; u += T) ks += ra.ksum[(size_t)c * H + u];
     ks = block_sum<T>(ks, red);

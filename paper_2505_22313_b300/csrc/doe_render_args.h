@@ -6,11 +6,8 @@ namespace doe {
 constexpr int RENDER_LINEAR = 0;  // doe_render: linear convolution, 2H x 2W transforms
 constexpr int RENDER_WIENER = 1;  // doe_wiener: circular Wiener deconvolution, H x W transforms
 struct RenderArgs {
-  int mode;             // RENDER_LINEAR or RENDER_WIENER
-  float gamma;          // Wiener regulariser (RENDER_WIENER)
   int C, H, W;          // channels, image rows, image columns
   int Py, Px;           // PSF grid
-  int nk;               // stored row-spectrum columns: row transform length / 2 + 1
   int wpr;              // row pitch of SA / SB (complex), >= nk, multiple of kTile
   const float* psf;     // [C][Py][Px]
   const float* img;     // [C][H][W]: scene (render) or blurred image (Wiener)
@@ -19,5 +16,8 @@ struct RenderArgs {
   float2* sb;           // [C] column-tiled H x wpr: kernel row spectra
   float2* sc;           // [C][H][wpr] natural layout: product / filtered spectrum after the column IFFT
   double* ksum;         // [C][H]
+  int mode;             // RENDER_LINEAR or RENDER_WIENER
+  float gamma;          // Wiener regulariser (RENDER_WIENER)
+  int nk;               // stored row-spectrum columns: row transform length / 2 + 1
 };
 }  // namespace doe
