@@ -52,6 +52,12 @@ extern "C" {
 
 /* ---- geometry flags ---- */
 #define DOE_BANDLIMIT 0x1u /* apply the band limit of the transfer function (default on) */
+/* Super-resolved design input: the heights h are a layout of (ny / f) x (nx / f) cells at
+ * pitch f dx, nearest-upsampled by f = 2^u (u = 0..3) onto the dx simulation grid inside the
+ * first pass (h_sim[i][x] = h[i / f][x / f]); gradients are returned on the layout (the sum
+ * over each f x f block, the adjoint of the upsampling).  nx / f >= 4. */
+#define DOE_UPSAMPLE_SHIFT 4
+#define DOE_UPSAMPLE(u) (((uint32_t)(u) & 3u) << DOE_UPSAMPLE_SHIFT)
 
 /* ---- operations, for doe_workspace_bytes ---- */
 #define DOE_OP_PROPAGATE 1
@@ -71,7 +77,7 @@ typedef struct doe_geom {
     int32_t n_lambda;      /* number of wavelengths, 1..64 */
     const double* lambda;  /* HOST [n_lambda] wavelengths [m], > 0 */
     const double* n_index; /* HOST [n_lambda] refractive index n_lambda of the DOE material, >= 1 */
-    uint32_t flags;        /* DOE_BANDLIMIT */
+    uint32_t flags;        /* DOE_BANDLIMIT | DOE_UPSAMPLE(u) */
 } doe_geom;
 
 /* Per-device set-up (uploads the twiddle tables).  Optional: the first call of any entry
@@ -83,7 +89,7 @@ int doe_init(void);
 size_t doe_workspace_bytes(const doe_geom* g, int op);
 
 /* Destination field E_dest (Eq. 3) for every wavelength.
- *   h      device float [ny][nx]          heights in metres (Eq. 1)
+ *   h      device float [ny/f][nx/f]      heights in metres (Eq. 1); f = 1 unless DOE_UPSAMPLE
  *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
  *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
  * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (P > 65536 or
@@ -113,7 +119,7 @@ size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op);
  *   g_pad = IFFT2( conj(H) FFT2(g_out) ); g_doe = g_pad on the DOE window;
  *   dL/dh = sum_lambda -2 k'_lambda Im(conj(g_doe) E_doe), k' = 2 pi (n - 1) / lambda.
  *   t_or_dldi  device float [n_lambda][P][P]: the target T or dL/dI
- *   grad_h     device float [ny][nx], overwritten (per metre of height)
+ *   grad_h     device float [ny/f][nx/f], overwritten (per metre of height, on the layout)
  *   loss_dev   device double[1] or NULL: receives sum (I - T)^2 in DOE_GRAD_L2_TARGET mode
  *              (summed in FP64 from FP32 per-row partials), 0 in DOE_GRAD_VJP mode
  *   recompute  1: the forward field is recomputed inside the call (no stored field);

@@ -189,6 +189,22 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
     return out
 
 
+# ---------------------------------------------------------------- super-resolved design input
+def upsample_nearest(h_layout, f: int) -> np.ndarray:
+    """Heights on the simulation grid from a layout at f times its pitch by nearest (zero-order)
+    upsampling, the interpolation the paper's conventional large-area designs use (Sec. 4, toy
+    example; Sec. 5: 8x and 4x nearest upsampling): h[i][x] = h_layout[i // f][x // f]."""
+    return np.repeat(np.repeat(np.asarray(h_layout, np.float32), f, axis=0), f, axis=1)
+
+
+def layout_grad(g_sim, f: int) -> np.ndarray:
+    """Gradient on the layout from the gradient on the simulation grid: the adjoint of
+    upsample_nearest, i.e. the sum over each f x f block."""
+    g = np.asarray(g_sim, np.float64)
+    n = g.shape[0] // f
+    return g.reshape(n, f, n, f).sum(axis=(1, 3))
+
+
 def grad_rows(h, dx, z, lam, rows, g_rows, drows, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
     """Exact FP64 dL/dh on the DOE rows ``drows`` [len(drows)][N] for one wavelength, when
     dL/dI is ``g_rows`` [len(rows)][P] on the output rows ``rows`` (distinct) and zero on every

@@ -18,7 +18,9 @@ from . import _lib as L
 @dataclass
 class Geometry:
     """One DOE evaluation: N x N samples at pitch dx, padded to P = pad * N, at distance z,
-    for the wavelengths `lambdas` with refractive indices `n_index`."""
+    for the wavelengths `lambdas` with refractive indices `n_index`.  With upsample = f > 1 the
+    heights (and the gradient) live on an (N / f) x (N / f) layout at pitch f dx, nearest-
+    upsampled onto the simulation grid inside the first pass."""
 
     N: int
     dx: float
@@ -27,12 +29,20 @@ class Geometry:
     n_index: np.ndarray
     pad: int = 2
     bandlimit: bool = True
+    upsample: int = 1
 
     @staticmethod
-    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True) -> "Geometry":
+    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1) -> "Geometry":
         lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, np.float64)))
         nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
-        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit))
+        if upsample not in (1, 2, 4, 8):
+            raise ValueError("upsample must be 1, 2, 4 or 8")
+        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample))
+
+    @property
+    def NL(self) -> int:
+        """Side of the height layout (N / upsample)."""
+        return self.N // self.upsample
 
     @property
     def P(self) -> int:
@@ -51,7 +61,7 @@ class Geometry:
         g.n_lambda = self.L
         g.lambda_ = self.lambdas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         g.n_index = self.n_index.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        g.flags = L.DOE_BANDLIMIT if self.bandlimit else 0
+        g.flags = (L.DOE_BANDLIMIT if self.bandlimit else 0) | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
         return g
 
 
@@ -100,7 +110,7 @@ def psf(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: 
         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """PSFs I_lambda = |E_dest|^2 on the padded grid: float32 [L, P, P]."""
     N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
     ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
     if out is None:
         out = torch.empty((geom.L, P, P), dtype=torch.float32, device=h.device)
@@ -116,7 +126,7 @@ def propagate(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None,
               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Destination fields E_dest (Eq. 3): complex64 [L, P, P]."""
     N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
     ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
     if out is None:
         out = torch.empty((geom.L, P, P), dtype=torch.complex64, device=h.device)
@@ -134,7 +144,7 @@ def psf_many(hs, geoms, e_ins=None, outs=None, ws: torch.Tensor | None = None, s
     gs = (L.Geom * n)(*[g.c() for g in geoms])
     if outs is None:
         outs = [torch.empty((g.L, g.P, g.P), dtype=torch.float32, device=hs[0].device) for g in geoms]
-    hp = (ctypes.c_void_p * n)(*[_dev_ptr(h, torch.float32, (g.N, g.N), "h").value for h, g in zip(hs, geoms)])
+    hp = (ctypes.c_void_p * n)(*[_dev_ptr(h, torch.float32, (g.NL, g.NL), "h").value for h, g in zip(hs, geoms)])
     ep = (ctypes.c_void_p * n)(*[(e.data_ptr() if e is not None else None) for e in (e_ins or [None] * n)])
     op = (ctypes.c_void_p * n)(*[_dev_ptr(o, torch.float32, (g.L, g.P, g.P), "out").value for o, g in zip(outs, geoms)])
     need = int(L.load().doe_workspace_bytes_many(n, gs, L.DOE_OP_PSF))
@@ -149,12 +159,12 @@ def grad(h: torch.Tensor, geom: Geometry, t_or_dldi: torch.Tensor, mode: str = "
     """(dL/dh float32 [N, N], loss float64 [1]) for L = sum (I - T)^2 (mode 'l2') or the
     vector-Jacobian product with dL/dI (mode 'vjp'; loss is then 0)."""
     N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (N, N), "h")
+    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
     ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
     tp = _dev_ptr(t_or_dldi, torch.float32, (geom.L, P, P), "t_or_dldi")
     if out is None:
-        out = torch.empty((N, N), dtype=torch.float32, device=h.device)
-    gp = _dev_ptr(out, torch.float32, (N, N), "grad")
+        out = torch.empty((geom.NL, geom.NL), dtype=torch.float32, device=h.device)
+    gp = _dev_ptr(out, torch.float32, (geom.NL, geom.NL), "grad")
     if loss is None:
         loss = torch.empty((1,), dtype=torch.float64, device=h.device)
     lp = _dev_ptr(loss, torch.float64, (1,), "loss")

@@ -97,6 +97,8 @@ long long band_mev(double lam, double dx, long P) {
 // where a cluster holds 8 / Q columns (P = 32768: 2, P = 65536: 1).
 int col_tile(long P) { return P == 65536 ? 1 : (P == 32768 ? 2 : kTile); }
 
+int upsample_log2(const doe_geom* g) { return (int)((g->flags >> DOE_UPSAMPLE_SHIFT) & 3u); }
+
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
   if (g->nx < 16 || g->ny < 16 || !is_pow2(g->nx) || !is_pow2(g->ny)) return DOE_EINVAL;
@@ -110,6 +112,7 @@ int check_geom(const doe_geom* g) {
   }
   if (g->nx != g->ny) return DOE_EUNSUPPORTED;
   if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
+  if ((g->nx >> upsample_log2(g)) < 4) return DOE_EINVAL;
   return DOE_OK;
 }
 
@@ -120,6 +123,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   const double du = 1.0 / ((double)P * g->dx);
   const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   std::memset(&s, 0, sizeof(s));
+  s.uf = upsample_log2(g);
   s.kmax = (int)kmax;
   if (kmax >= P / 2 || P > (1L << kMaxLog)) {  // no compaction (split rows store sub-transform order)
     s.seg_a = (int)P;
@@ -143,6 +147,7 @@ struct Layout {
   size_t total = 0;
   std::vector<size_t> buf, htab, tbuf;
   size_t loss = 0;
+  size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint (uf > 0)
 };
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
@@ -169,6 +174,10 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op) {
   if (op == DOE_OP_GRAD) {
     L.loss = off;
     off = align256(off + sl.size() * (size_t)P * kMaxQf * sizeof(double));
+    if (!sl.empty() && sl[0].uf > 0) {
+      L.gsim = off;
+      off = align256(off + (size_t)N * N * sizeof(float));
+    }
   }
   L.total = off;
   return L;
@@ -321,7 +330,8 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
     bt.s[j].e_in = reinterpret_cast<const float2*>(e_in);
     bt.s[j].tgt = t_or_dldi + (size_t)j * P * P;
   }
-  bt.grad = grad_h;
+  const int uf = upsample_log2(g);
+  bt.grad = uf ? reinterpret_cast<float*>(static_cast<char*>(ws) + lay.gsim) : grad_h;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int lg = ilog2(P);
   if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
@@ -331,6 +341,7 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   bt.mode = MODE_ADJ;
   if (launch_pass_b(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_pass_a_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
+  if (uf && launch_upsample_adjoint(bt.grad, grad_h, N, uf, st) != cudaSuccess) return DOE_ECUDA;
   if (loss_dev) {
     bt.mode = gmode;
     if (launch_loss_reduce(bt, loss_dev, st) != cudaSuccess) return DOE_ECUDA;
@@ -399,7 +410,7 @@ const char* doe_pass_name(int id) {
   static const char* names[TR_COUNT] = {"transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows",
                                         "pass_c_adjoint_rows", "pass_b_adjoint_columns", "pass_a_adjoint_rows",
                                         "loss_reduce", "render_rows", "render_columns", "render_output",
-                                        "band_mask"};
+                                        "band_mask", "upsample_adjoint"};
   return (id >= 0 && id < TR_COUNT) ? names[id] : "unknown";
 }
 

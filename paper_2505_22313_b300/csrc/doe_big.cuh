@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
   const int i = blockIdx.x / Q;
   const Slice& sl = bt.s[blockIdx.y];
   const int t = threadIdx.x, N = bt.N, off = bt.off;
-  const float* hrow = sl.h + (size_t)i * N;
+  const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
   const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
   float4* rsm[Q];
 #pragma unroll
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
       const int x = n1 * L + n2 - off;  // even
       xa[n1] = xb[n1] = make_float2(0.f, 0.f);
       if ((unsigned)x < (unsigned)N) {
-        const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
+        const float2 hv = heights_pair(hrow, x, sl.uf);
         xa[n1] = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-        xb[n1] = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+        xb[n1] = sl.uf ? xa[n1] : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
         if (erow) {
           const float4 ev = __ldcs(erow + (x >> 1));
           xa[n1] = cmul(xa[n1], make_float2(ev.x, ev.y));
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
     if (j > 0) cl.sync();  // peers finished reading the previous slice's sub-transforms
     big_row_inverse_to_smem<Q>(sl.buf + (size_t)i * sl.wp, s, t, sm);
     cl.sync();
-    const float* hrow = sl.h + (size_t)i * N;
+    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     const float k2 = -2.f * sl.kp_hi;
 #pragma unroll
@@ -424,9 +424,9 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
       for (int q = 0; q < Q; ++q) {
         const int x = q * L + x2 - off;  // even
         if ((unsigned)x < (unsigned)N) {
-          const float2 hv = __ldcs(reinterpret_cast<const float2*>(hrow + x));
+          const float2 hv = heights_pair(hrow, x, sl.uf);
           float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-          float2 e1 = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          float2 e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
           if (erow) {
             const float4 ev = __ldcs(erow + (x >> 1));
             e0 = cmul(e0, make_float2(ev.x, ev.y));

@@ -95,6 +95,15 @@ __device__ __forceinline__ float2 transmittance(float hv, float kp_hi, float kp_
   return make_float2(cs, sn);
 }
 
+// Heights of the adjacent simulation samples (x, x + 1), x even, of the DOE row whose layout
+// row starts at hrow: without upsampling one 8-byte load; with nearest upsampling by 2^uf
+// (uf >= 1) both samples lie in the same layout cell x >> uf.
+__device__ __forceinline__ float2 heights_pair(const float* hrow, int x, int uf) {
+  if (uf == 0) return __ldcs(reinterpret_cast<const float2*>(hrow + x));
+  const float h = __ldcs(hrow + (x >> uf));
+  return make_float2(h, h);
+}
+
 // Stored (band-compacted) spectrum rows.  With the band limit active a row keeps the two
 // FFT-order segments [0, seg_a) and [P - (w - seg_a), P), seg_a = kmax + 1 and
 // w - seg_a = kmax, each rounded up to even length so that pairs of adjacent frequencies

@@ -100,11 +100,14 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
   const int N = bt.N, off = bt.off;
   const bool staged = 2 * N <= L;
   const int items = bt.S * N, k0 = blockIdx.x, dk = gridDim.x;
-  if (staged && k0 < items) stage_heights(hs, bt.s[k0 / N].h + (size_t)(k0 % N) * N, N, t, T);
+  // height layout row of DOE row i: row i >> uf of the (N >> uf)-wide layout
+  auto layout_row = [&](int kk) { const Slice& q = bt.s[kk / N]; return q.h + (size_t)((kk % N) >> q.uf) * (N >> q.uf); };
+  auto layout_n = [&](int kk) { return N >> bt.s[kk / N].uf; };
+  if (staged && k0 < items) stage_heights(hs, layout_row(k0), layout_n(k0), t, T);
   for (int k = k0; k < items; k += dk) {
     const Slice& sl = bt.s[k / N];
-    const int i = k % N;
-    const float* hrow = sl.h + (size_t)i * N;
+    const int i = k % N, uf = sl.uf;
+    const float* hrow = layout_row(k);
     const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     float2 hv[F::B / 2][F::R];
     if (staged) {
@@ -117,13 +120,16 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
       for (int r = 0; r < F::R; ++r) {
         const int x = F::idx(t, b, r) - off;  // even
         hv[b / 2][r] = make_float2(0.f, 0.f);
-        if ((unsigned)x < (unsigned)N)
-          hv[b / 2][r] = staged ? *reinterpret_cast<const float2*>(hs + x) : __ldcs(reinterpret_cast<const float2*>(hrow + x));
+        if ((unsigned)x < (unsigned)N) {
+          if (!staged) hv[b / 2][r] = heights_pair(hrow, x, uf);
+          else if (uf == 0) hv[b / 2][r] = *reinterpret_cast<const float2*>(hs + x);
+          else hv[b / 2][r] = make_float2(hs[x >> uf], hs[x >> uf]);
+        }
       }
     if (staged) {
       __syncthreads();  // every thread has read hs
       const int kn = k + dk;
-      if (kn < items) stage_heights(hs, bt.s[kn / N].h + (size_t)(kn % N) * N, N, t, T);
+      if (kn < items) stage_heights(hs, layout_row(kn), layout_n(kn), t, T);
     }
     float2 v[32];
 #pragma unroll
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
         if ((unsigned)x < (unsigned)N) {
           a = transmittance(hv[b / 2][r].x, sl.kp_hi, sl.kp_lo);
-          c = transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);
+          c = uf ? a : transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);  // one layout cell
           if (erow) {
             const float4 ev = __ldcs(erow + (x >> 1));
             a = cmul(a, make_float2(ev.x, ev.y));
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
     float2 v[32];
     load_band_row<L>(v, t, sl.buf + (size_t)i * sl.wp, sl);
     fft_run<L, 32, true>(v, t, sm);
-    const float* hrow = sl.h + (size_t)i * N;
+    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     const float k2 = -2.f * sl.kp_hi;
 #pragma unroll
@@ -403,9 +409,9 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
       for (int r = 0; r < H::R; ++r) {
         const int x = H::idx(t, b, r) - off;  // even
         if ((unsigned)x < (unsigned)N) {
-          const float2 hv = __ldg(reinterpret_cast<const float2*>(hrow + x));
+          const float2 hv = heights_pair(hrow, x, sl.uf);
           float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-          float2 e1 = transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          float2 e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
           if (erow) {
             const float4 ev = erow[x >> 1];
             e0 = cmul(e0, make_float2(ev.x, ev.y));
@@ -426,6 +432,22 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
       const int x = H::idx(t, b, r) - off;
       if ((unsigned)x < (unsigned)N) grow[x >> 1] = make_float2(acc[b * H::R + r], acc[(b + 1) * H::R + r]);
     }
+}
+
+// Adjoint of nearest upsampling by f = 2^uf: the layout gradient is the sum of the simulation-
+// grid gradient over each f x f block, in a fixed order.  One thread per layout cell.
+__global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __restrict__ g, float* __restrict__ gc,
+                                                              int N, int uf) {
+  const int nc = N >> uf, f = 1 << uf;
+  const long long cell = blockIdx.x * 256LL + threadIdx.x;
+  if (cell >= (long long)nc * nc) return;
+  const int ic = (int)(cell / nc), xc = (int)(cell % nc);
+  float acc = 0.f;
+  for (int di = 0; di < f; ++di) {
+    const float* row = g + (size_t)(ic * f + di) * N + (size_t)xc * f;
+    for (int dx = 0; dx < f; ++dx) acc += row[dx];
+  }
+  gc[cell] = acc;
 }
 
 // Sum of the per-row loss partials of all slices, in a fixed order (one CTA).

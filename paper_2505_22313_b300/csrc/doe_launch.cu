@@ -353,6 +353,12 @@ cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st) {
   loss_reduce_kernel<<<1, 1024, 0, st>>>(bt, loss);
   return cudaGetLastError();
 }
+cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st) {
+  Traced tr(TR_UPSAMPLE_ADJ, st);
+  const long long cells = (long long)(N >> uf) * (N >> uf);
+  upsample_adjoint_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, gc, N, uf);
+  return cudaGetLastError();
+}
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st) {
   Traced tr(TR_MASK, st);
   band_mask_kernel<<<bt.P, 256, 0, st>>>(bt, mask);

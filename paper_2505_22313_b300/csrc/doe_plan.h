@@ -74,7 +74,7 @@ constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536
 // One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
 // shared by the whole launch.
 struct Slice {
-  const float* h;        // [N][N] heights (m)
+  const float* h;        // [N >> uf][N >> uf] heights (m): the layout at pitch 2^uf dx
   const float2* e_in;    // [N][N] incident field or nullptr
   float2* buf;           // [P][wp] natural-layout field buffer: I2 (rows < P), J2 (rows < N)
   float2* tbuf;          // column-tiled buffer read by the column pass: I1 (N rows), J1 (P rows)
@@ -93,6 +93,7 @@ struct Slice {
   int wp;                // row pitch of buf (w rounded up to kTile)
   int hp;                // row pitch of htab (kmax + 1)
   int tile_begin;        // first global column-tile index of this slice (column pass)
+  int uf;                // log2 of the nearest-upsampling factor of the heights (0: none)
 };
 
 enum : int { OUT_PSF = 0, OUT_FIELD = 1 };
@@ -107,7 +108,7 @@ struct Batch {
   int max_kmax;      // largest kmax over the slices (table builder grid)
   int qf;            // sub-transforms per row: P / 16384 for P > 16384, else 1
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
-  float* grad;       // [N][N] gradient output (DOE-row adjoint pass)
+  float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
   Slice s[kMaxSlices];
 };
 

@@ -415,3 +415,52 @@ def test_gradient_workload_fd_exact():
     fd = oracle.fd_exact(h, dx, z, lams, T, py, px, 1e-10)
     scale = np.abs(fd).max()
     assert np.all(np.abs(gr[py, px] - fd) <= 1e-3 * scale), np.abs(gr[py, px] - fd).max() / scale
+
+
+# -------------------------------------------------------------- super-resolved design input
+@pytest.mark.parametrize("N,f,pad", [(256, 2, 2), (256, 4, 2), (256, 8, 2), (128, 4, 1)])
+def test_upsampled_layout_psf_and_grad_vs_oracle(N, f, pad):
+    # heights on an (N / f)^2 layout at pitch f dx, nearest-upsampled inside the first pass;
+    # the oracle gets the upsampled heights and returns the layout gradient as block sums
+    dx, z = 0.5e-6, 2e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = pad * N
+    hl = _h(N // f, 5000 + f)
+    g = Geometry.make(N, dx, z, lams, pad=pad, upsample=f)
+    hs = oracle.upsample_nearest(hl, f)
+    I = api.psf(torch.from_numpy(hl).cuda(), g).cpu().numpy()
+    ref = oracle.psf(hs, dx, z, lams, pad=pad)
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    T = inputs.spot_target(P, N, 3, 6000 + f)
+    gr, loss = api.grad(torch.from_numpy(hl).cuda(), g, torch.from_numpy(T).cuda())
+    assert gr.shape == (N // f, N // f)
+    gref, lref = oracle.grad(hs, dx, z, lams, T, pad=pad)
+    err = rel_l2(gr.cpu().numpy(), oracle.layout_grad(gref, f))
+    assert err < TOL_GRAD, err
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_upsampled_layout_big_grid_rows_vs_oracle():
+    # 4096^2 layout, 4x nearest upsampling onto a 16384^2 DOE, 32768^2 grid (cluster-split rows)
+    N, f, dx, z, lam = 16384, 4, 0.5e-6, 20e-3, 550e-9
+    P = 2 * N
+    hl = _h(N // f, 5100)
+    g = Geometry.make(N, dx, z, [lam], upsample=f)
+    I = api.psf(torch.from_numpy(hl).cuda(), g)
+    rows = np.array([0, P // 4, P // 2 - 1, P // 2, 3 * P // 4 + 5, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    del I
+    ref = oracle.psf_rows(oracle.upsample_nearest(hl, f), dx, z, lam, rows)
+    err = rel_l2(Ig, ref)
+    assert err < TOL_PSF, err
+
+
+def test_upsampled_and_plain_requests_share_a_launch():
+    N, dx, z = 256, 0.5e-6, 2e-3
+    h1 = torch.from_numpy(_h(N, 5200)).cuda()
+    h2 = torch.from_numpy(_h(N // 4, 5201)).cuda()
+    g1 = Geometry.make(N, dx, z, [500e-9])
+    g2 = Geometry.make(N, dx, z, [600e-9, 700e-9], upsample=4)
+    many = api.psf_many([h1, h2], [g1, g2])
+    assert torch.equal(many[0], api.psf(h1, g1))
+    assert torch.equal(many[1], api.psf(h2, g2))

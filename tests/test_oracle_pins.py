@@ -289,6 +289,26 @@ def test_grad_rows_equal_masked_full_gradient(z, with_ein):
     assert np.abs(part - full[drows]).max() <= 1e-12 * np.abs(full).max()
 
 
+def test_upsample_nearest_and_its_adjoint():
+    # brute force on a small layout, and <up(a), b> = <a, up^T(b)> (dot-product test)
+    r = np.random.default_rng(40)
+    for f in (1, 2, 4, 8):
+        a = r.random((3, 3)).astype(np.float32)
+        up = oracle.upsample_nearest(a, f)
+        assert up.shape == (3 * f, 3 * f)
+        for i in range(3 * f):
+            for x in range(3 * f):
+                assert up[i, x] == a[i // f, x // f]
+        b = r.standard_normal((3 * f, 3 * f))
+        lhs = float((up.astype(np.float64) * b).sum())
+        rhs = float((a.astype(np.float64) * oracle.layout_grad(b, f)).sum())
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs) + 1e-12
+        bs = oracle.layout_grad(b, f)
+        for ic in range(3):
+            for xc in range(3):
+                assert abs(bs[ic, xc] - b[ic * f:(ic + 1) * f, xc * f:(xc + 1) * f].sum()) < 1e-12
+
+
 def test_table2_grids_are_twice_the_design_sample_count():
     rows = np.loadtxt(os.path.join(GOLD, "table2_grids.txt"))
     for ay, ax, pitch, gy, gx in rows:
