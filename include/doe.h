@@ -158,6 +158,19 @@ int doe_wiener(int C, int H, int W, const float* psf, int Py, int Px, const floa
                float* out, void* ws, size_t ws_bytes, void* stream);
 size_t doe_wiener_workspace_bytes(int C, int H, int W);
 
+/* One step of the design optimiser: Adam (Kingma & Ba 2015; the optimiser of the paper's
+ * designs, Sec. 4 and 5) on the heights with the gradient of doe_grad, then projection onto
+ * the fabricable range [h_min, h_max]:
+ *   m = beta1 m + (1 - beta1) g;  v = beta2 v + (1 - beta2) g^2;
+ *   h = clamp(h - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps), h_min, h_max)
+ *   h, m, v  device float [n], updated in place (m = v = 0 before step t = 1)
+ *   grad     device float [n]
+ * t >= 1 is the step number; 0 <= beta1, beta2 < 1, eps > 0, lr >= 0, h_min <= h_max.  The
+ * caller schedules lr (the paper decays it with a cosine schedule).  Errors: DOE_EINVAL,
+ * DOE_ECUDA. */
+int doe_adam_step(float* h, const float* grad, float* m, float* v, long long n, double lr, double beta1,
+                  double beta2, double eps, int t, double h_min, double h_max, void* stream);
+
 /* Integer band logic of the transfer function, computed on the host exactly as the kernels
  * use it (for bit-exact checks).  For wavelength j: kmax[j] = the largest signed frequency
  * index kept per axis (ceil(f_lim / du) - 1 capped at P/2, with

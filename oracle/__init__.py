@@ -189,6 +189,24 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
     return out
 
 
+# ---------------------------------------------------------------- design optimiser
+def adam_step(h, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, h_min=0.0, h_max=np.inf):
+    """One Adam step (Kingma & Ba 2015, the optimiser of the paper's designs, Sec. 4) in FP64,
+    then projection onto [h_min, h_max]; returns (h, m, v)."""
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1**t)
+    v_hat = v / (1.0 - beta2**t)
+    h = np.asarray(h, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return np.clip(h, h_min, h_max), m, v
+
+
+def cosine_lr(lr0, t, iters):
+    """Cosine decay of the learning rate to zero over iters steps (Sec. 4's schedule), t = 1.."""
+    return 0.5 * lr0 * (1.0 + np.cos(np.pi * (t - 1) / iters))
+
+
 # ---------------------------------------------------------------- super-resolved design input
 def upsample_nearest(h_layout, f: int) -> np.ndarray:
     """Heights on the simulation grid from a layout at f times its pitch by nearest (zero-order)

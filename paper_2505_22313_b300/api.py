@@ -210,6 +210,18 @@ def wiener(psf_t: torch.Tensor, y: torch.Tensor, gamma: float, out: torch.Tensor
     return out
 
 
+def adam_step(h: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, t: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, h_min: float = 0.0,
+              h_max: float = float("inf"), stream=None) -> torch.Tensor:
+    """One Adam step (step number t >= 1) on the heights h in place, then h clamped to
+    [h_min, h_max]; m and v are the optimiser state (zeros before t = 1)."""
+    n = h.numel()
+    ptrs = [_dev_ptr(x, torch.float32, tuple(h.shape), name) for x, name in ((h, "h"), (grad, "grad"), (m, "m"), (v, "v"))]
+    L.check(L.load().doe_adam_step(*ptrs, n, float(lr), float(beta1), float(beta2), float(eps), int(t), float(h_min),
+                                   float(h_max), _stream(stream)), "doe_adam_step")
+    return h
+
+
 def band_limits(geom: Geometry):
     """(kmax [L] int32, m_ev [L] int64): the integer band logic the kernels apply."""
     k = np.zeros(geom.L, np.int32)

@@ -21,7 +21,7 @@ COMPARE_LIB = PKG / "libdoe_cufft.so"  # cuFFT comparison chain, loaded only by 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
-SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu", "doe_noalloc.cu"]
+SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu", "doe_noalloc.cu", "doe_design.cu"]
 
 
 def _deps() -> list[Path]:

@@ -450,6 +450,25 @@ __global__ void __launch_bounds__(256) upsample_adjoint_kernel(const float* __re
   gc[cell] = acc;
 }
 
+// One Adam step on the height map (Kingma & Ba 2015), then projection onto [h_min, h_max]:
+//   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+//   h = clamp(h - lr_hat m / (sqrt(v) + eps_hat))
+// with the bias corrections folded into lr_hat and eps_hat by the caller.
+__global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ h, const float* __restrict__ g,
+                                                   float* __restrict__ m, float* __restrict__ v, long long n,
+                                                   float lr_hat, float beta1, float beta2, float eps_hat,
+                                                   float h_min, float h_max) {
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = fmaf(beta1, m[i] - gi, gi);            // beta1 m + (1 - beta1) g
+  const float vi = fmaf(beta2, v[i] - gi * gi, gi * gi);  // beta2 v + (1 - beta2) g^2
+  m[i] = mi;
+  v[i] = vi;
+  const float hi = h[i] - lr_hat * mi / (sqrtf(vi) + eps_hat);
+  h[i] = fminf(fmaxf(hi, h_min), h_max);
+}
+
 // Sum of the per-row loss partials of all slices, in a fixed order (one CTA).
 __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant__ Batch bt, double* loss) {
   __shared__ double red[32];

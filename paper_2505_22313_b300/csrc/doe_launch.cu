@@ -353,6 +353,12 @@ cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st) {
   loss_reduce_kernel<<<1, 1024, 0, st>>>(bt, loss);
   return cudaGetLastError();
 }
+cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long n, float lr_hat, float beta1,
+                        float beta2, float eps_hat, float h_min, float h_max, cudaStream_t st) {
+  Traced tr(TR_ADAM, st);
+  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h, g, m, v, n, lr_hat, beta1, beta2, eps_hat, h_min, h_max);
+  return cudaGetLastError();
+}
 cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st) {
   Traced tr(TR_UPSAMPLE_ADJ, st);
   const long long cells = (long long)(N >> uf) * (N >> uf);

@@ -109,6 +109,35 @@ def run_wiener(reps: int, C: int = 3, H: int = 2048, W: int = 2048, P: int = 819
             "passes_ms": {k: round(sorted(v)[len(v) // 2], 4) for k, v in per.items()}}
 
 
+def run_design(reps: int, name: str = "gradient") -> dict:
+    """Design-loop iterations (doe_grad + doe_adam_step) per second on a gradient workload."""
+    import torch
+
+    from . import api, design, inputs
+    from .api import Geometry
+
+    N, dx, z, lams, _, *rest = CONFIGS[name]
+    P = 2 * N
+    g = Geometry.make(N, dx, z, lams)
+    h0 = inputs.heights_device(N, 1000 + N, "cuda")
+    T = torch.from_numpy(inputs.spot_target(P, N, g.L, 2000 + N)).cuda()
+    design.optimize(h0, g, T, 2)
+    torch.cuda.synchronize()
+    api.trace_enable(reps * 16 + 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, losses = design.optimize(h0, g, T, reps)
+    e1.record()
+    torch.cuda.synchronize()
+    recs = api.trace_read()
+    api.trace_enable(0)
+    adam = [ms for n, ms in recs if n == "adam_step"]
+    ms = e0.elapsed_time(e1) / reps
+    return {"config": f"design_{name}", "iteration_ms": round(ms, 3), "iterations_per_s": round(1e3 / ms, 2),
+            "adam_step_ms": round(sorted(adam)[len(adam) // 2], 4) if adam else None,
+            "loss_first_last": [float(losses[0]), float(losses[-1])]}
+
+
 def main():
     from . import api
 
@@ -120,7 +149,12 @@ def main():
     api.init()
     for name in args.configs.split(","):
         name = name.strip()
-        row = run_wiener(args.reps) if name == "wiener" else run(name, args.reps, grad=not args.no_grad)
+        if name == "wiener":
+            row = run_wiener(args.reps)
+        elif name.startswith("design"):
+            row = run_design(args.reps)
+        else:
+            row = run(name, args.reps, grad=not args.no_grad)
         print(json.dumps(row), flush=True)
 
 

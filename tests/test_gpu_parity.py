@@ -464,3 +464,42 @@ def test_upsampled_and_plain_requests_share_a_launch():
     many = api.psf_many([h1, h2], [g1, g2])
     assert torch.equal(many[0], api.psf(h1, g1))
     assert torch.equal(many[1], api.psf(h2, g2))
+
+
+# -------------------------------------------------------------- design optimiser
+def test_adam_step_matches_oracle():
+    r = np.random.default_rng(50)
+    n = 4096
+    h0 = (r.random(n) * 1.2e-6).astype(np.float32)
+    ht, mt, vt = torch.from_numpy(h0).cuda(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    ho, mo, vo = h0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 7):
+        g = (r.standard_normal(n) * 1e3).astype(np.float32)
+        api.adam_step(ht, torch.from_numpy(g).cuda(), mt, vt, 2e-8, t, h_max=1.2e-6)
+        ho, mo, vo = oracle.adam_step(ho, g, mo, vo, 2e-8, t, h_max=1.2e-6)
+    assert rel_l2(ht.cpu().numpy(), ho) < 1e-6
+
+
+def test_design_loop_matches_oracle():
+    # Adam + cosine schedule on the L2 gradient (64^2 DOE, 2 wavelengths, 6 steps), the GPU
+    # library against the same loop on the FP64 oracle's gradient and Adam
+    from paper_2505_22313_b300 import design
+
+    N, dx, z = 64, 1e-6, 2e-3
+    lams = [500e-9, 600e-9]
+    P = 2 * N
+    iters, lr0 = 6, 1.2e-8
+    h0 = _h(N, 7000)
+    T = inputs.spot_target(P, N, 2, 7001)
+    g = Geometry.make(N, dx, z, lams)
+    h, losses = design.optimize(torch.from_numpy(h0).cuda(), g, torch.from_numpy(T).cuda(), iters, lr0=lr0)
+    ho, mo, vo = h0.astype(np.float64), np.zeros((N, N)), np.zeros((N, N))
+    lo = []
+    for t in range(1, iters + 1):
+        gr, loss = oracle.grad(ho.astype(np.float32), dx, z, lams, T)
+        lo.append(loss)
+        ho, mo, vo = oracle.adam_step(ho, gr, mo, vo, oracle.cosine_lr(lr0, t, iters), t, h_max=inputs.HMAX)
+    lg = losses.cpu().numpy()
+    assert np.all(np.abs(lg - np.array(lo)) <= 1e-4 * np.abs(lo)), (lg, lo)
+    assert lo[-1] < lo[0]  # the loop descends
+    assert rel_l2(h.cpu().numpy(), ho) < 1e-3

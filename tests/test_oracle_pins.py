@@ -309,6 +309,37 @@ def test_upsample_nearest_and_its_adjoint():
                 assert abs(bs[ic, xc] - b[ic * f:(ic + 1) * f, xc * f:(xc + 1) * f].sum()) < 1e-12
 
 
+def test_adam_first_step_scale_invariance_and_descent():
+    r = np.random.default_rng(41)
+    g = r.standard_normal(64)
+    z = np.zeros(64)
+    lr, eps = 1e-3, 1e-12
+    # first step from zero moments: the bias-corrected step is lr g / (|g| + eps) = lr sign(g)
+    free = dict(h_min=-np.inf, h_max=np.inf)  # no projection for these checks
+    h1, _, _ = oracle.adam_step(z, g, z, z, lr, 1, eps=eps, **free)
+    assert np.allclose(h1, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+    # scaling every gradient by c > 0 leaves the steps unchanged (eps negligible)
+    ha, ma, va = z, z, z
+    hb, mb, vb = z, z, z
+    for t in range(1, 6):
+        gt = r.standard_normal(64)
+        ha, ma, va = oracle.adam_step(ha, gt, ma, va, lr, t, eps=eps, **free)
+        hb, mb, vb = oracle.adam_step(hb, 1e3 * gt, mb, vb, lr, t, eps=eps, **free)
+    # (the eps term moves each step by at most ~lr eps / sqrt(v_hat) ~ 1e-15 here)
+    assert np.abs(ha - hb).max() <= 1e-12
+    # on f(x) = x^2 / 2 from x = 1 the iterates decrease towards the minimiser
+    x, m, v = np.array([1.0]), np.zeros(1), np.zeros(1)
+    for t in range(1, 201):
+        x_new, m, v = oracle.adam_step(x, x, m, v, 1e-2, t, **free)
+        assert x_new[0] < x[0] or x[0] < 2e-2
+        x = x_new
+    assert abs(x[0]) < 2e-2
+    # projection onto the fabricable range
+    hc, _, _ = oracle.adam_step(np.array([0.0, 1.0]), np.array([1.0, -1.0]), np.zeros(2), np.zeros(2), 0.5, 1,
+                                h_min=0.0, h_max=1.2)
+    assert hc[0] == 0.0 and abs(hc[1] - 1.2) < 1e-12
+
+
 def test_table2_grids_are_twice_the_design_sample_count():
     rows = np.loadtxt(os.path.join(GOLD, "table2_grids.txt"))
     for ay, ax, pitch, gy, gx in rows:
