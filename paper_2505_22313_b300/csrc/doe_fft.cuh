@@ -234,7 +234,21 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
   using X = St<L, E, INV, S>;
   constexpr int R = X::R, NS = X::NS;
   float4* s4 = reinterpret_cast<float4*>(sm);
-  if constexpr (!X::PAIRED && NS > 1) {
+  if constexpr (!X::PAIRED && NS == 16) {
+    // one butterfly per thread (the radix-32 stage of 8192 points): outputs base + 16 r, chunk
+    // c0 + 8 r with c0 = base / 2 and c0 mod 16 < 8, so the swizzle term ((c0 + 8 r) >> 4) & 7
+    // = ((c0 >> 4) + (r >> 1)) & 7 is shared by r = 2q, 2q + 1 and only touches the low 3 bits
+    const int jj = X::j(t, 0);
+    const int k = jj & (NS - 1);
+    const int base = (jj - k) * R + k;
+    const int c0 = base >> 1, odd = base & 1;
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+      const int ch = (c0 & ~7) + 16 * q + ((c0 & 7) ^ (((c0 >> 4) + q) & 7));
+      sm[(ch << 1) | odd] = v[2 * q];
+      sm[((ch + 8) << 1) | odd] = v[2 * q + 1];
+    }
+  } else if constexpr (!X::PAIRED && NS > 1) {
     // one butterfly per thread: its outputs base + r Ns are not adjacent, 8-byte accesses
     const int jj = X::j(t, 0);
     const int k = jj & (NS - 1);
@@ -270,16 +284,20 @@ __device__ __forceinline__ void stage_load(float2 (&v)[E], int t, const float2* 
   using X = St<L, E, INV, S>;
   constexpr int R = X::R;
   const float4* s4 = reinterpret_cast<const float4*>(sm);
+  // with a stride of a multiple of 128 chunks the swizzle term is the same for every r, so
+  // the addresses are the first one plus constants
+  constexpr bool kFlat = (L / R / 2) % 128 == 0;
   if constexpr (!X::PAIRED) {
+    const int p0 = phys(X::j(t, 0));
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[phys(X::j(t, 0) + r * (L / R))];
+    for (int r = 0; r < R; ++r) v[r] = sm[kFlat ? p0 + r * (L / R) : phys(X::j(t, 0) + r * (L / R))];
   } else {
 #pragma unroll
     for (int b = 0; b < X::B; b += 2) {
-      const int c0 = X::j(t, b) >> 1;
+      const int c0 = X::j(t, b) >> 1, q0 = swz(c0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float4 q = s4[swz(c0 + r * (L / R / 2))];
+        const float4 q = s4[kFlat ? q0 + r * (L / R / 2) : swz(c0 + r * (L / R / 2))];
         v[b * R + r] = make_float2(q.x, q.y);
         v[(b + 1) * R + r] = make_float2(q.z, q.w);
       }
