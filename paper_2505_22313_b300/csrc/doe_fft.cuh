@@ -256,24 +256,34 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
 #pragma unroll
     for (int r = 0; r < R; ++r) sm[phys(base + r * NS)] = v[r];
   } else if constexpr (NS == 1) {
-    // butterfly j's outputs are the contiguous elements j R + r
+    // butterfly j's outputs are the contiguous elements j R + r: chunks c0 + d, d < R / 2, all
+    // inside one 16-chunk row of the swizzle (c0 = j R / 2), so the swizzle term is fixed
 #pragma unroll
     for (int b = 0; b < X::B; ++b) {
-      const int c0 = X::j(t, b) * (R / 2);
+      const int c0 = X::j(t, b) * (R / 2), x = (c0 >> 4) & 7;
 #pragma unroll
       for (int r = 0; r < R; r += 2)
-        s4[swz(c0 + r / 2)] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
+        s4[(c0 + r / 2) ^ x] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
     }
   } else {
-    // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns
+    // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns: chunks c0 + S r,
+    // S = Ns / 2.  Closed forms of swz(c0 + S r): S a multiple of 128 leaves the swizzle term
+    // unchanged; S = 16 a adds a r to it; S = 8 (c0 mod 16 < 8 here) adds r >> 1.
+    constexpr int S = NS / 2;
 #pragma unroll
     for (int b = 0; b < X::B; b += 2) {
       const int jj = X::j(t, b);
       const int k = jj & (NS - 1);
-      const int c0 = ((jj - k) * R + k) >> 1;
+      const int c0 = ((jj - k) * R + k) >> 1, x0 = c0 >> 4, q0 = swz(c0);
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        s4[swz(c0 + r * (NS / 2))] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
+      for (int r = 0; r < R; ++r) {
+        int ch;
+        if constexpr (S % 128 == 0) ch = q0 + S * r;
+        else if constexpr (S % 16 == 0) ch = (c0 ^ ((x0 + (S / 16) * r) & 7)) + S * r;
+        else if constexpr (S == 8) ch = (c0 & ~7) + 8 * r + ((c0 & 7) ^ ((x0 + (r >> 1)) & 7));
+        else ch = swz(c0 + S * r);
+        s4[ch] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
+      }
     }
   }
 }
