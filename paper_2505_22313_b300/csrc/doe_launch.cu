@@ -118,7 +118,7 @@ cudaError_t prep_one(K* kern, int smem, int threads) {
     return e;
   if (blocks < 1 || per_sm <= 0) return cudaSuccess;
   const long need = (long)blocks * ((long)smem + (long)fa.sharedSizeBytes + reserved);
-  // the driver rounds the percentage up to the next shared-memory configuration, so start
+  // the CUDA driver rounds the percentage up to the next shared-memory configuration, so start
   // from the rounded-down percentage and step up only if the resident CTAs would drop
   for (int pct = (int)(need * 100 / per_sm); pct <= 100; ++pct) {
     int b = 0;

@@ -31,7 +31,8 @@ def _device():
 
 
 def max_over_ranks(x: float) -> float:
-    """Maximum of a per-rank scalar (the driver's timing rule); identity without a process group."""
+    """Maximum of a per-rank scalar (a multi-GPU step ends when its slowest rank ends); identity
+    without a process group."""
     import torch
     import torch.distributed as dist
 
