@@ -266,10 +266,10 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
         s4[(c0 + r / 2) ^ x] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
     }
   } else {
-    // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns: chunks c0 + S r,
-    // S = Ns / 2.  Closed forms of swz(c0 + S r): S a multiple of 128 leaves the swizzle term
-    // unchanged; S = 16 a adds a r to it; S = 8 (c0 mod 16 < 8 here) adds r >> 1.
-    constexpr int S = NS / 2;
+    // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns: chunks c0 + C r,
+    // C = Ns / 2.  Closed forms of swz(c0 + C r): C a multiple of 128 leaves the swizzle term
+    // unchanged; C = 16 a adds a r to it; C = 8 (c0 mod 16 < 8 here) adds r >> 1.
+    constexpr int C = NS / 2;
 #pragma unroll
     for (int b = 0; b < X::B; b += 2) {
       const int jj = X::j(t, b);
@@ -278,10 +278,10 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         int ch;
-        if constexpr (S % 128 == 0) ch = q0 + S * r;
-        else if constexpr (S % 16 == 0) ch = (c0 ^ ((x0 + (S / 16) * r) & 7)) + S * r;
-        else if constexpr (S == 8) ch = (c0 & ~7) + 8 * r + ((c0 & 7) ^ ((x0 + (r >> 1)) & 7));
-        else ch = swz(c0 + S * r);
+        if constexpr (C % 128 == 0) ch = q0 + C * r;
+        else if constexpr (C % 16 == 0) ch = (c0 ^ ((x0 + (C / 16) * r) & 7)) + C * r;
+        else if constexpr (C == 8) ch = (c0 & ~7) + 8 * r + ((c0 & 7) ^ ((x0 + (r >> 1)) & 7));
+        else ch = swz(c0 + C * r);
         s4[ch] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
       }
     }
