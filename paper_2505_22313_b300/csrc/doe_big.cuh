@@ -201,6 +201,13 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   const int pos0 = (tile_g - sl.tile_begin) * TC;
   const int kcol = big_pos_to_k(pos0 + c, Q);
   const bool live = pos0 + c < sl.w && abs_signed(kcol, P) <= sl.kmax;
+  if (live) {
+    // this column's transfer-function row (up to 256 KB, read at a stride of Q entries after
+    // the forward transform): the column's Q CTAs bring its lines into L2 now
+    const char* hb = reinterpret_cast<const char*>(sl.htab + (size_t)abs_signed(kcol, P) * sl.hp);
+    for (int o = 128 * (s * T + t); o < (sl.kmax + 1) * (int)sizeof(float2); o += 128 * T * Q)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(hb + o));
+  }
   const bool adj = bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;
   const int nin = adj ? P : N, yin0 = adj ? 0 : off;
