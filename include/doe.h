@@ -58,6 +58,14 @@ extern "C" {
  * over each f x f block, the adjoint of the upsampling).  nx / f >= 4. */
 #define DOE_UPSAMPLE_SHIFT 4
 #define DOE_UPSAMPLE(u) (((uint32_t)(u) & 3u) << DOE_UPSAMPLE_SHIFT)
+/* With DOE_UPSAMPLE(u), u >= 1: Lanczos-3 interpolation instead of nearest (the smooth kernel
+ * the paper compares against, Sec. 4):
+ *   h_sim[i][x] = sum_{m,n} w(i, m) w(x, n) h[m][n],
+ *   w(x, n) = K(u_x - n) / sum_n' K(u_x - n'),  u_x = (x + 1/2) / f - 1/2 (cell centres),
+ *   K(t) = sinc(t) sinc(t / 3) for |t| < 3, else 0,  cells clamped to the layout at its edges;
+ * gradients are returned on the layout through the transpose.  The interpolation is a pre-pass
+ * into the workspace (N^2 floats per Lanczos request, counted by doe_workspace_bytes*). */
+#define DOE_UPSAMPLE_LANCZOS3 0x40u
 
 /* ---- operations, for doe_workspace_bytes ---- */
 #define DOE_OP_PROPAGATE 1
@@ -77,7 +85,7 @@ typedef struct doe_geom {
     int32_t n_lambda;      /* number of wavelengths, 1..64 */
     const double* lambda;  /* HOST [n_lambda] wavelengths [m], > 0 */
     const double* n_index; /* HOST [n_lambda] refractive index n_lambda of the DOE material, >= 1 */
-    uint32_t flags;        /* DOE_BANDLIMIT | DOE_UPSAMPLE(u) */
+    uint32_t flags;        /* DOE_BANDLIMIT | DOE_UPSAMPLE(u) [| DOE_UPSAMPLE_LANCZOS3] */
 } doe_geom;
 
 /* Per-device set-up (uploads the twiddle tables).  Optional: the first call of any entry

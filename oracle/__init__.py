@@ -223,6 +223,39 @@ def layout_grad(g_sim, f: int) -> np.ndarray:
     return g.reshape(n, f, n, f).sum(axis=(1, 3))
 
 
+def lanczos3_matrix(n_layout: int, f: int) -> np.ndarray:
+    """[n_layout f][n_layout] FP64 interpolation matrix of Lanczos-3 upsampling by f, the
+    smooth kernel the paper compares nearest upsampling against (Sec. 4, toy example), read
+    as: sample x at layout coordinate u = (x + 1/2) / f - 1/2 (cell centres), weights
+    K(u - n) = sinc(u - n) sinc((u - n) / 3) for |u - n| < 3 normalised to sum 1, cells
+    clamped to the layout at its edges."""
+    n = n_layout * f
+    W = np.zeros((n, n_layout))
+    for x in range(n):
+        u = (x + 0.5) / f - 0.5
+        taps = np.arange(int(np.floor(u)) - 2, int(np.floor(u)) + 4)
+        t = u - taps
+        k = np.where(np.abs(t) < 3.0, np.sinc(t) * np.sinc(t / 3.0), 0.0)
+        k /= k.sum()
+        for tap, wgt in zip(taps, k):
+            W[x, min(max(tap, 0), n_layout - 1)] += wgt
+    return W
+
+
+def upsample_lanczos3(h_layout, f: int) -> np.ndarray:
+    """Heights on the simulation grid from the layout by separable Lanczos-3 interpolation."""
+    hl = np.asarray(h_layout, np.float64)
+    W = lanczos3_matrix(hl.shape[0], f)
+    return (W @ hl @ W.T).astype(np.float32)
+
+
+def layout_grad_lanczos3(g_sim, f: int) -> np.ndarray:
+    """Layout gradient: the transpose of upsample_lanczos3 applied to the simulation-grid one."""
+    g = np.asarray(g_sim, np.float64)
+    W = lanczos3_matrix(g.shape[0] // f, f)
+    return W.T @ g @ W
+
+
 def grad_rows(h, dx, z, lam, rows, g_rows, drows, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
     """Exact FP64 dL/dh on the DOE rows ``drows`` [len(drows)][N] for one wavelength, when
     dL/dI is ``g_rows`` [len(rows)][P] on the output rows ``rows`` (distinct) and zero on every

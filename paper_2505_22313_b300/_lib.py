@@ -20,7 +20,8 @@ DOE_ETIMEDOUT = -5
 DOE_ESCRATCH = -6
 DOE_NOALLOC_SCRATCH_BYTES = 32 << 20
 DOE_BANDLIMIT = 0x1
-DOE_UPSAMPLE_SHIFT = 4  # flags bits 4-5: log2 of the nearest-upsampling factor of the heights
+DOE_UPSAMPLE_SHIFT = 4  # flags bits 4-5: log2 of the upsampling factor of the heights
+DOE_UPSAMPLE_LANCZOS3 = 0x40  # Lanczos-3 instead of nearest upsampling
 DOE_OP_PROPAGATE, DOE_OP_PSF, DOE_OP_GRAD = 1, 2, 3
 DOE_GRAD_L2_TARGET, DOE_GRAD_VJP = 0, 1
 

@@ -30,14 +30,15 @@ class Geometry:
     pad: int = 2
     bandlimit: bool = True
     upsample: int = 1
+    lanczos: bool = False  # Lanczos-3 instead of nearest upsampling of the layout
 
     @staticmethod
-    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1) -> "Geometry":
+    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1, lanczos=False) -> "Geometry":
         lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, np.float64)))
         nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
         if upsample not in (1, 2, 4, 8):
             raise ValueError("upsample must be 1, 2, 4 or 8")
-        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample))
+        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample), bool(lanczos))
 
     @property
     def NL(self) -> int:
@@ -61,7 +62,8 @@ class Geometry:
         g.n_lambda = self.L
         g.lambda_ = self.lambdas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         g.n_index = self.n_index.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        g.flags = (L.DOE_BANDLIMIT if self.bandlimit else 0) | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
+        g.flags = ((L.DOE_BANDLIMIT if self.bandlimit else 0) | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
+                   | (L.DOE_UPSAMPLE_LANCZOS3 if self.lanczos else 0))
         return g
 
 

@@ -98,6 +98,32 @@ long long band_mev(double lam, double dx, long P) {
 int col_tile(long P) { return P == 65536 ? 1 : (P == 32768 ? 2 : kTile); }
 
 int upsample_log2(const doe_geom* g) { return (int)((g->flags >> DOE_UPSAMPLE_SHIFT) & 3u); }
+// Lanczos-3 interpolation of the layout (a pre-pass) instead of nearest (fused into pass A)
+bool lanczos(const doe_geom* g) { return (g->flags & DOE_UPSAMPLE_LANCZOS3) && upsample_log2(g) > 0; }
+
+// Tap table of the Lanczos-3 interpolation by f = 2^u (FP64 on the host): sample x = f xc + r
+// sits at layout coordinate u = xc + (r + 1/2) / f - 1/2; its taps are the cells
+// floor(u) - 2 .. floor(u) + 3 with weights K(u - n), K(t) = sinc(t) sinc(t / 3), normalised.
+LanczosTab lanczos_table(int N, int u) {
+  LanczosTab tb;
+  std::memset(&tb, 0, sizeof(tb));
+  tb.f = 1 << u;
+  tb.nl = N >> u;
+  auto sinc = [](double x) { return x == 0.0 ? 1.0 : std::sin(kPi * x) / (kPi * x); };
+  for (int r = 0; r < tb.f; ++r) {
+    const double fr = (r + 0.5) / tb.f - 0.5;  // u - xc
+    const int n0 = (int)std::floor(fr) - 2;
+    double w[6], sum = 0.0;
+    for (int d = 0; d < 6; ++d) {
+      const double tt = fr - (n0 + d);
+      w[d] = std::fabs(tt) < 3.0 ? sinc(tt) * sinc(tt / 3.0) : 0.0;
+      sum += w[d];
+    }
+    tb.off[r] = n0;
+    for (int d = 0; d < 6; ++d) tb.w[r][d] = (float)(w[d] / sum);
+  }
+  return tb;
+}
 
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
@@ -123,7 +149,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   const double du = 1.0 / ((double)P * g->dx);
   const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   std::memset(&s, 0, sizeof(s));
-  s.uf = upsample_log2(g);
+  s.uf = lanczos(g) ? 0 : upsample_log2(g);  // Lanczos: the passes read pre-interpolated heights
   s.kmax = (int)kmax;
   if (kmax >= P / 2 || P > (1L << kMaxLog)) {  // no compaction (split rows store sub-transform order)
     s.seg_a = (int)P;
@@ -147,7 +173,8 @@ struct Layout {
   size_t total = 0;
   std::vector<size_t> buf, htab, tbuf;
   size_t loss = 0;
-  size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint (uf > 0)
+  size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint
+  std::vector<size_t> hsim;  // per request, Lanczos-3: heights interpolated onto the simulation grid
 };
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
@@ -155,7 +182,7 @@ struct Layout {
 // adjoint also runs), then (gradient) the per-row loss partials.  The field buffers and tables
 // sit at the same offsets in the PSF and gradient layouts, so a gradient-sized workspace used
 // by doe_psf keeps the fields and tables doe_grad(recompute=0) needs.
-Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op) {
+Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_req, const doe_geom* geoms) {
   Layout L;
   size_t off = 0;
   for (const auto& s : sl) {
@@ -174,11 +201,17 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op) {
   if (op == DOE_OP_GRAD) {
     L.loss = off;
     off = align256(off + sl.size() * (size_t)P * kMaxQf * sizeof(double));
-    if (!sl.empty() && sl[0].uf > 0) {
+    if (upsample_log2(&geoms[0]) > 0) {
       L.gsim = off;
       off = align256(off + (size_t)N * N * sizeof(float));
     }
   }
+  L.hsim.assign(n_req, 0);
+  for (int r = 0; r < n_req; ++r)
+    if (lanczos(&geoms[r])) {
+      L.hsim[r] = off;
+      off = align256(off + (size_t)N * N * sizeof(float));
+    }
   L.total = off;
   return L;
 }
@@ -249,22 +282,31 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
     if (!h[r] || !out[r]) return DOE_EINVAL;
   const int N = geoms[0].nx, pad = geoms[0].pad;
   const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, N, DOE_OP_PSF);
+  const Layout lay = make_layout(sl, P, N, DOE_OP_PSF, n_req, geoms);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
   init_batch(bt, sl, N, pad, ws, lay);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Lanczos-3 requests: interpolate their layouts onto the simulation grid first
+  std::vector<const float*> hr(h, h + n_req);
+  for (int r = 0; r < n_req; ++r)
+    if (lanczos(&geoms[r])) {
+      float* hs = reinterpret_cast<float*>(static_cast<char*>(ws) + lay.hsim[r]);
+      if (launch_lanczos_up(h[r], hs, N, lanczos_table(N, upsample_log2(&geoms[r])), st) != cudaSuccess)
+        return DOE_ECUDA;
+      hr[r] = hs;
+    }
   int jr = 0, prev = -1;
   for (int j = 0; j < bt.S; ++j) {
     const int r = req_of[j];
     jr = (r == prev) ? jr + 1 : 0;
     prev = r;
-    bt.s[j].h = h[r];
+    bt.s[j].h = hr[r];
     bt.s[j].e_in = e_in ? reinterpret_cast<const float2*>(e_in[r]) : nullptr;
     const size_t esz = out_kind == OUT_PSF ? sizeof(float) : sizeof(float2);
     bt.s[j].out = static_cast<char*>(out[r]) + (size_t)jr * P * P * esz;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((rc = forward_passes(bt, st)) != DOE_OK) return rc;
   bt.mode = out_kind;
   if (launch_pass_c(ilog2(P), bt, st) != cudaSuccess) return DOE_ECUDA;
@@ -284,7 +326,7 @@ size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op) {
   std::vector<Slice> sl;
   std::vector<int> req_of;
   if (collect_slices(n_req, geoms, sl, req_of) != DOE_OK) return 0;
-  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, geoms[0].nx, op).total;
+  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, geoms[0].nx, op, n_req, geoms).total;
 }
 
 size_t doe_workspace_bytes(const doe_geom* g, int op) { return doe_workspace_bytes_many(1, g, op); }
@@ -320,19 +362,24 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   if ((rc = collect_slices(1, g, sl, req_of)) != DOE_OK) return rc;
   const int N = g->nx, pad = g->pad;
   const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, N, DOE_OP_GRAD);
+  const Layout lay = make_layout(sl, P, N, DOE_OP_GRAD, 1, g);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
   init_batch(bt, sl, N, pad, ws, lay);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool lz = lanczos(g);
+  const float* hsim = lz ? reinterpret_cast<const float*>(static_cast<char*>(ws) + lay.hsim[0]) : nullptr;
+  // the adjoint row pass reads the heights too, so the interpolation runs with stored fields as well
+  if (lz && launch_lanczos_up(h, const_cast<float*>(hsim), N, lanczos_table(N, upsample_log2(g)), st) != cudaSuccess)
+    return DOE_ECUDA;
   for (int j = 0; j < bt.S; ++j) {
-    bt.s[j].h = h;
+    bt.s[j].h = lz ? hsim : h;
     bt.s[j].e_in = reinterpret_cast<const float2*>(e_in);
     bt.s[j].tgt = t_or_dldi + (size_t)j * P * P;
   }
   const int uf = upsample_log2(g);
   bt.grad = uf ? reinterpret_cast<float*>(static_cast<char*>(ws) + lay.gsim) : grad_h;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int lg = ilog2(P);
   if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
   bt.mode = mode == DOE_GRAD_L2_TARGET ? GRAD_L2 : GRAD_VJP;
@@ -341,7 +388,11 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   bt.mode = MODE_ADJ;
   if (launch_pass_b(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_pass_a_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
-  if (uf && launch_upsample_adjoint(bt.grad, grad_h, N, uf, st) != cudaSuccess) return DOE_ECUDA;
+  if (lz) {
+    if (launch_lanczos_adjoint(bt.grad, grad_h, N, lanczos_table(N, uf), st) != cudaSuccess) return DOE_ECUDA;
+  } else if (uf && launch_upsample_adjoint(bt.grad, grad_h, N, uf, st) != cudaSuccess) {
+    return DOE_ECUDA;
+  }
   if (loss_dev) {
     bt.mode = gmode;
     if (launch_loss_reduce(bt, loss_dev, st) != cudaSuccess) return DOE_ECUDA;
@@ -373,7 +424,7 @@ int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_
   std::vector<int> req_of;
   if ((rc = collect_slices(1, &one, sl, req_of)) != DOE_OK) return rc;
   const long P = (long)g->pad * g->nx;
-  const Layout lay = make_layout(sl, P, g->nx, DOE_OP_PSF);
+  const Layout lay = make_layout(sl, P, g->nx, DOE_OP_PSF, 1, g);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
@@ -410,7 +461,7 @@ const char* doe_pass_name(int id) {
   static const char* names[TR_COUNT] = {"transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows",
                                         "pass_c_adjoint_rows", "pass_b_adjoint_columns", "pass_a_adjoint_rows",
                                         "loss_reduce", "render_rows", "render_columns", "render_output",
-                                        "band_mask", "upsample_adjoint", "adam_step"};
+                                        "band_mask", "upsample_adjoint", "adam_step", "lanczos_upsample", "lanczos_adjoint"};
   return (id >= 0 && id < TR_COUNT) ? names[id] : "unknown";
 }
 

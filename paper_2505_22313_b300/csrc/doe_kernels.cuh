@@ -469,6 +469,59 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ h, const 
   h[i] = fminf(fmaxf(hi, h_min), h_max);
 }
 
+// Lanczos-3 interpolation of the (nl x nl) height layout onto the N x N simulation grid,
+// separable with the tap table tb; one thread per simulation sample.
+__global__ void __launch_bounds__(256) lanczos_up_kernel(const float* __restrict__ hl, float* __restrict__ hs, int N,
+                                                        const __grid_constant__ LanczosTab tb) {
+  const long long idx = blockIdx.x * 256LL + threadIdx.x;
+  if (idx >= (long long)N * N) return;
+  const int i = (int)(idx / N), x = (int)(idx % N);
+  const int f = tb.f, nl = tb.nl, ri = i & (f - 1), rx = x & (f - 1);
+  const int my = i / f + tb.off[ri], mx = x / f + tb.off[rx];
+  float acc = 0.f;
+#pragma unroll
+  for (int dy = 0; dy < 6; ++dy) {
+    const float* row = hl + (size_t)min(max(my + dy, 0), nl - 1) * nl;
+    float s = 0.f;
+#pragma unroll
+    for (int dx = 0; dx < 6; ++dx) s = fmaf(tb.w[rx][dx], __ldg(row + min(max(mx + dx, 0), nl - 1)), s);
+    acc = fmaf(tb.w[ri][dy], s, acc);
+  }
+  hs[idx] = acc;
+}
+
+// Weight of layout cell m in simulation sample i's interpolation (taps clamped to the layout).
+__device__ __forceinline__ float lanczos_coef(const LanczosTab& tb, int i, int m) {
+  const int r = i & (tb.f - 1), n0 = i / tb.f + tb.off[r];
+  float c = 0.f;
+#pragma unroll
+  for (int d = 0; d < 6; ++d)
+    if (min(max(n0 + d, 0), tb.nl - 1) == m) c += tb.w[r][d];
+  return c;
+}
+
+// Adjoint of lanczos_up_kernel: the layout gradient of cell (m, n) gathers the simulation-grid
+// gradient over the samples whose taps reach it (rows and columns [f (m - 3), f (m + 4)) cover
+// them, edge clamping included), in a fixed order.  One thread per layout cell.
+__global__ void __launch_bounds__(256) lanczos_adjoint_kernel(const float* __restrict__ g, float* __restrict__ gl,
+                                                             int N, const __grid_constant__ LanczosTab tb) {
+  const long long cell = blockIdx.x * 256LL + threadIdx.x;
+  if (cell >= (long long)tb.nl * tb.nl) return;
+  const int m = (int)(cell / tb.nl), n = (int)(cell % tb.nl), f = tb.f;
+  const int i0 = max(0, f * (m - 3)), i1 = min(N, f * (m + 4));
+  const int x0 = max(0, f * (n - 3)), x1 = min(N, f * (n + 4));
+  float acc = 0.f;
+  for (int i = i0; i < i1; ++i) {
+    const float cy = lanczos_coef(tb, i, m);
+    if (cy == 0.f) continue;
+    const float* gr = g + (size_t)i * N;
+    float s = 0.f;
+    for (int x = x0; x < x1; ++x) s = fmaf(lanczos_coef(tb, x, n), gr[x], s);
+    acc = fmaf(cy, s, acc);
+  }
+  gl[cell] = acc;
+}
+
 // Sum of the per-row loss partials of all slices, in a fixed order (one CTA).
 __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant__ Batch bt, double* loss) {
   __shared__ double red[32];

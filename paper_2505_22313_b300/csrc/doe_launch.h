@@ -18,6 +18,8 @@ cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st);
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st);
+cudaError_t launch_lanczos_up(const float* hl, float* hs, int N, const LanczosTab& tb, cudaStream_t st);
+cudaError_t launch_lanczos_adjoint(const float* g, float* gl, int N, const LanczosTab& tb, cudaStream_t st);
 cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long n, float lr_hat, float beta1,
                         float beta2, float eps_hat, float h_min, float h_max, cudaStream_t st);
 
@@ -26,7 +28,7 @@ struct RenderArgs;
 // pass identifiers reported by the tracer (doe_trace_read / doe_pass_name)
 enum : int {
   TR_HTAB = 0, TR_PASS_A, TR_PASS_B, TR_PASS_C, TR_PASS_C_ADJ, TR_PASS_B_ADJ, TR_PASS_A_ADJ, TR_LOSS,
-  TR_RENDER_ROWS, TR_RENDER_COLS, TR_RENDER_OUT, TR_MASK, TR_UPSAMPLE_ADJ, TR_ADAM, TR_COUNT
+  TR_RENDER_ROWS, TR_RENDER_COLS, TR_RENDER_OUT, TR_MASK, TR_UPSAMPLE_ADJ, TR_ADAM, TR_LANCZOS, TR_LANCZOS_ADJ, TR_COUNT
 };
 int trace_enable(int max_records);
 int trace_read(int max, int* pass_ids, float* ms);

@@ -96,6 +96,15 @@ struct Slice {
   int uf;                // log2 of the nearest-upsampling factor of the heights (0: none)
 };
 
+// Lanczos-3 interpolation of a height layout onto the simulation grid (upsampling factor f):
+// simulation sample x = f xc + r reads layout cells xc + off[r] + d, d = 0..5, with weights
+// w[r][d] (normalised to sum 1; cells clamped to the layout).
+struct LanczosTab {
+  int f, nl;          // factor, layout side
+  int off[8];         // first tap relative to xc, per residue r
+  float w[8][6];      // tap weights per residue r
+};
+
 enum : int { OUT_PSF = 0, OUT_FIELD = 1 };
 enum : int { MODE_FWD = 0, MODE_ADJ = 1 };
 enum : int { GRAD_L2 = 0, GRAD_VJP = 1 };

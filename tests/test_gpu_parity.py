@@ -466,6 +466,63 @@ def test_upsampled_and_plain_requests_share_a_launch():
     assert torch.equal(many[1], api.psf(h2, g2))
 
 
+@pytest.mark.parametrize("N,f,pad", [(256, 2, 2), (256, 4, 2), (256, 8, 2), (128, 4, 1)])
+def test_lanczos_layout_psf_and_grad_vs_oracle(N, f, pad):
+    # Lanczos-3 interpolation of an (N / f)^2 layout (a pre-pass), then the PSF and the layout
+    # gradient (the transpose of the interpolation applied to the grid gradient)
+    dx, z = 0.5e-6, 2e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = pad * N
+    hl = _h(N // f, 5300 + f)
+    g = Geometry.make(N, dx, z, lams, pad=pad, upsample=f, lanczos=True)
+    hs = oracle.upsample_lanczos3(hl, f)
+    I = api.psf(torch.from_numpy(hl).cuda(), g).cpu().numpy()
+    ref = oracle.psf(hs, dx, z, lams, pad=pad)
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    T = inputs.spot_target(P, N, 3, 6300 + f)
+    for recompute in (True, False):
+        if not recompute:
+            ws = api.workspace(api.workspace_bytes(g, 3))  # gradient-sized: the PSF call keeps its fields
+            api.psf(torch.from_numpy(hl).cuda(), g, ws=ws)
+        else:
+            ws = None
+        gr, loss = api.grad(torch.from_numpy(hl).cuda(), g, torch.from_numpy(T).cuda(), recompute=recompute, ws=ws)
+        assert gr.shape == (N // f, N // f)
+        gref, lref = oracle.grad(hs, dx, z, lams, T, pad=pad)
+        err = rel_l2(gr.cpu().numpy(), oracle.layout_grad_lanczos3(gref, f))
+        assert err < TOL_GRAD, err
+        assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_lanczos_layout_rows_at_4096_vs_oracle():
+    # 1024^2 layout, Lanczos-3 by 4 onto a 4096^2 DOE, 8192^2 grid: sampled output rows
+    N, f, dx, z, lam = 4096, 4, 0.5e-6, 5e-3, 550e-9
+    P = 2 * N
+    hl = _h(N // f, 5400)
+    g = Geometry.make(N, dx, z, [lam], upsample=f, lanczos=True)
+    I = api.psf(torch.from_numpy(hl).cuda(), g)
+    rows = np.array([0, P // 4, P // 2 - 1, P // 2, 3 * P // 4 + 5, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    ref = oracle.psf_rows(oracle.upsample_lanczos3(hl, f), dx, z, lam, rows)
+    err = rel_l2(Ig, ref)
+    assert err < TOL_PSF, err
+
+
+def test_lanczos_nearest_and_plain_requests_share_a_launch():
+    N, dx, z = 256, 0.5e-6, 2e-3
+    h1 = torch.from_numpy(_h(N, 5500)).cuda()
+    h2 = torch.from_numpy(_h(N // 4, 5501)).cuda()
+    h3 = torch.from_numpy(_h(N // 2, 5502)).cuda()
+    h4 = torch.from_numpy(_h(N // 8, 5503)).cuda()
+    gs = [Geometry.make(N, dx, z, [500e-9]),
+          Geometry.make(N, dx, z, [600e-9, 700e-9], upsample=4, lanczos=True),
+          Geometry.make(N, dx, z, [450e-9], upsample=2),
+          Geometry.make(N, dx, z, [550e-9, 650e-9], upsample=8, lanczos=True)]
+    many = api.psf_many([h1, h2, h3, h4], gs)
+    for h, g, m in zip([h1, h2, h3, h4], gs, many):
+        assert torch.equal(m, api.psf(h, g))
+
+
 # -------------------------------------------------------------- design optimiser
 def test_adam_step_matches_oracle():
     r = np.random.default_rng(50)

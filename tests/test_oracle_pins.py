@@ -340,6 +340,33 @@ def test_adam_first_step_scale_invariance_and_descent():
     assert hc[0] == 0.0 and abs(hc[1] - 1.2) < 1e-12
 
 
+def test_lanczos3_upsampling_properties():
+    r = np.random.default_rng(42)
+    # f = 1 is the identity (the kernel vanishes at non-zero integers and is 1 at 0)
+    a = r.random((8, 8))
+    assert np.abs(oracle.upsample_lanczos3(a, 1) - a.astype(np.float32)).max() == 0.0
+    for f in (2, 4, 8):
+        n = 64
+        # a constant layout stays constant (normalised weights, clamped edges)
+        assert np.abs(oracle.upsample_lanczos3(np.full((n, n), 0.7), f) - np.float32(0.7)).max() < 1e-6
+        # a slowly varying layout (periods of 32 and 40 cells) is interpolated at the
+        # cell-centre positions to within Lanczos-3's own error there (3.6e-3 at most);
+        # sampling it half a fine sample off, or with another kernel, misses by 1.6e-2 or more
+        c = np.arange(n)
+        lay = np.cos(2 * np.pi * c / 32.0)[:, None] * np.cos(2 * np.pi * c / 40.0)[None, :]
+        up = oracle.upsample_lanczos3(lay, f)
+        u = (np.arange(n * f) + 0.5) / f - 0.5
+        exact = np.cos(2 * np.pi * u / 32.0)[:, None] * np.cos(2 * np.pi * u / 40.0)[None, :]
+        inner = slice(4 * f, (n - 4) * f)
+        assert np.abs(up[inner, inner] - exact[inner, inner]).max() < 5e-3
+        # the layout gradient is the transpose: <up(a), b> = <a, up^T(b)>
+        a = r.standard_normal((n, n))
+        b = r.standard_normal((n * f, n * f))
+        lhs = float((oracle.upsample_lanczos3(a, f).astype(np.float64) * b).sum())
+        rhs = float((a * oracle.layout_grad_lanczos3(b, f)).sum())
+        assert abs(lhs - rhs) <= 1e-5 * abs(lhs)  # the forward output is rounded to float32
+
+
 def test_table2_grids_are_twice_the_design_sample_count():
     rows = np.loadtxt(os.path.join(GOLD, "table2_grids.txt"))
     for ay, ax, pitch, gy, gx in rows:
