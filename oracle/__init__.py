@@ -189,6 +189,26 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
     return out
 
 
+# ---------------------------------------------------------------- incident fields
+def incident(N: int, dx: float, lam: float, theta_x: float = 0.0, theta_y: float = 0.0, d: float = 0.0) -> np.ndarray:
+    """E_in [N][N] complex128 of Eq. 2 for a plane or spherical incident wave (Sec. 3.1 names
+    both; Sec. 2.3 scales over incidence angles), read as: sample (i, j) at x = (j - N/2) dx,
+    y = (i - N/2) dx (the optical axis at padded index P/2);
+        tilt:   exp(+i 2 pi (x sin theta_x + y sin theta_y) / lambda)
+        sphere: 1 if d == 0, else (|d| / r) exp(+i sgn(d) 2 pi (r - |d|) / lambda),
+                r = sqrt(x^2 + y^2 + d^2)
+    and E_in = tilt * sphere.  d > 0 is a point source |d| before the DOE (diverging wave),
+    d < 0 a wave converging to the point |d| behind it; phases are referenced to the axis."""
+    c = (np.arange(N, dtype=np.float64) - N // 2) * dx
+    y = c[:, None]
+    x = c[None, :]
+    e = np.exp(2j * np.pi * (x * np.sin(theta_x) + y * np.sin(theta_y)) / lam)
+    if d != 0.0:
+        r = np.sqrt(x * x + y * y + d * d)
+        e = e * (abs(d) / r) * np.exp(1j * np.sign(d) * 2 * np.pi * (r - abs(d)) / lam)
+    return e
+
+
 # ---------------------------------------------------------------- design optimiser
 def adam_step(h, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, h_min=0.0, h_max=np.inf):
     """One Adam step (Kingma & Ba 2015, the optimiser of the paper's designs, Sec. 4) in FP64,

@@ -133,6 +133,66 @@ def test_gaussian_beam_paraxial():
     assert rel_l2(e, ref) < 5e-6  # measured 8.2e-7; non-paraxial terms ~1e-6
 
 
+# ------------------------------------------------------------------ incident fields
+def test_incident_tilt_is_one_spectral_line():
+    # sin(theta) = m lambda / (N dx) puts the tilted plane wave on DFT bin m of each axis, with
+    # value N^2 (-1)^(mx + my) (phase referenced to sample N/2); numpy's FFT, not the oracle's
+    N, dx, lam = 64, 1e-6, 550e-9
+    for mx, my in ((5, 0), (0, -3), (7, -2)):
+        e = oracle.incident(N, dx, lam, np.arcsin(mx * lam / (N * dx)), np.arcsin(my * lam / (N * dx)))
+        F = np.fft.fft2(e)
+        ref = np.zeros((N, N), np.complex128)
+        ref[my % N, mx % N] = N * N * (-1.0) ** (mx + my)
+        assert np.abs(F - ref).max() < 1e-9 * N * N
+
+
+def test_incident_tilted_flat_plate_closed_form():
+    # pad = 1, flat plate, a plane wave on an exact spectral line: ASM multiplies it by
+    # H(fx, fy) = exp(i 2 pi z sqrt(1 / lambda^2 - fx^2 - fy^2)) and nothing else
+    N, dx, lam, z, c = 64, 1e-6, 550e-9, 200e-6, 0.3e-6
+    du = 1.0 / (N * dx)
+    for mx, my in ((5, -3), (-12, 9)):
+        e_in = oracle.incident(N, dx, lam, np.arcsin(mx * lam / (N * dx)), np.arcsin(my * lam / (N * dx)))
+        e = oracle.propagate(np.full((N, N), c, np.float32), dx, z, lam, n_index=1.46, pad=1, e_in=e_in)
+        ph = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z * np.sqrt(1 / lam**2 - (mx * du) ** 2 - (my * du) ** 2)
+        assert np.abs(e - np.exp(1j * ph) * e_in).max() < 1e-9
+
+
+def test_incident_spherical_paraxial_limit_and_conjugate():
+    # near the axis the spherical wave is the Fresnel quadratic phase with amplitude ~ 1:
+    # |phase - pi rho^2 / (lambda d)| <= k rho^4 / (8 d^3), |amp - 1 + rho^2 / (2 d^2)| <= 3 rho^4 / (8 d^4)
+    N, dx, lam, d = 64, 1e-6, 550e-9, 10e-3
+    e = oracle.incident(N, dx, lam, d=d)
+    c = (np.arange(N) - N // 2) * dx
+    rho2 = c[:, None] ** 2 + c[None, :] ** 2
+    k = 2 * np.pi / lam
+    dph = np.angle(e * np.exp(-1j * np.pi * rho2 / (lam * d)))
+    # (+1e-10: FP64 rounding of r - |d| is k ulp(d) ~ 2e-11 rad)
+    assert np.all(np.abs(dph) <= k * rho2**2 / (8 * d**3) * 1.001 + 1e-10)
+    assert np.abs(dph).max() > 1e-6  # the quartic term is visible: the wave is not the paraxial one
+    assert np.all(np.abs(np.abs(e) - 1 + rho2 / (2 * d * d)) <= 3 * rho2**2 / (8 * d**4) + 1e-15)
+    # a converging wave is the conjugate of the diverging one
+    assert np.array_equal(oracle.incident(N, dx, lam, d=-d), np.conj(e))
+
+
+def test_converging_wave_focuses_where_geometry_says():
+    # flat DOE lit by a wave converging to distance z: the PSF at z peaks on the optical axis
+    # (padded index P/2); a tilt of the same wave moves the focus to z tan(theta) on its axis
+    N, dx, lam, z = 256, 1e-6, 550e-9, 2e-3
+    P = 2 * N
+    h = np.zeros((N, N), np.float32)
+    I0 = oracle.psf(h, dx, z, [lam], e_in=oracle.incident(N, dx, lam, d=-z))[0]
+    assert np.unravel_index(I0.argmax(), I0.shape) == (P // 2, P // 2)
+    Id = oracle.psf(h, dx, z, [lam], e_in=oracle.incident(N, dx, lam, d=z))[0]
+    assert I0.max() > 20 * Id.max()  # the diverging wave does not focus
+    tx, ty = 0.02, -0.015
+    It = oracle.psf(h, dx, z, [lam], e_in=oracle.incident(N, dx, lam, np.arcsin(tx), np.arcsin(ty), d=-z))[0]
+    py, px = np.unravel_index(It.argmax(), It.shape)
+    ex = z * tx / np.sqrt(1 - tx * tx) / dx
+    ey = z * ty / np.sqrt(1 - ty * ty) / dx
+    assert abs(px - P // 2 - ex) <= 1.0 and abs(py - P // 2 - ey) <= 1.0
+
+
 def test_parseval_over_band():
     N, dx, z, lam = 128, 1e-6, 5e-3, 550e-9
     P = 2 * N
