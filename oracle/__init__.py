@@ -209,6 +209,30 @@ def incident(N: int, dx: float, lam: float, theta_x: float = 0.0, theta_y: float
     return e
 
 
+# ---------------------------------------------------------------- radial parameterisation
+def radial_s(N: int) -> np.ndarray:
+    """[N][N] squared normalised radius s = rho^2 / R^2 of each sample, rho measured from the
+    optical axis at sample (N/2, N/2) and R = N dx / 2 the half-aperture (dx cancels)."""
+    c = np.arange(N, dtype=np.float64) - N // 2
+    return (c[:, None] ** 2 + c[None, :] ** 2) / (N / 2.0) ** 2
+
+
+def radial_heights(c, N: int) -> np.ndarray:
+    """Radially symmetric height map of Sec. 5's broadband design (radial symmetry through a
+    16th-order polynomial), read as an even polynomial in rho / R:
+    h = sum_k c[k] s^k, s = (rho / R)^2, k = 0 .. len(c) - 1 <= 8 (degree <= 16).  FP64."""
+    c = np.asarray(c, np.float64)
+    s = radial_s(N)
+    return sum(ck * s**k for k, ck in enumerate(c))
+
+
+def radial_grad(g, n_c: int) -> np.ndarray:
+    """dL/dc[k] = sum over the grid of dL/dh * s^k (the transpose of radial_heights). FP64."""
+    g = np.asarray(g, np.float64)
+    s = radial_s(g.shape[0])
+    return np.array([(g * s**k).sum() for k in range(n_c)])
+
+
 # ---------------------------------------------------------------- design optimiser
 def adam_step(h, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, h_min=0.0, h_max=np.inf):
     """One Adam step (Kingma & Ba 2015, the optimiser of the paper's designs, Sec. 4) in FP64,

@@ -18,6 +18,8 @@ Recipes (seeds: heights 1000 + c, images and targets 2000 + c, request stream 30
            Sec. 5.2): pitch P/32, sigma 8 px, each centre jittered by U[-P/256, P/256] in
            both axes, lattice centred at (P/2, P/2), scaled so that each wavelength's
            target sums to N^2 (the energy of a unit-amplitude N x N aperture).
+  flat-top 8 x 8 regular lattice of equal-intensity discs (Sec. 5.2's flat-top spot array),
+           pitch P/32, radius pitch/4, centred at (P/2, P/2), summing to N^2.
   requests Poisson arrivals at a given rate; side N uniform in {1024, ..., 16384};
            1..31 wavelengths uniform in [400, 700] nm; z uniform in [10, 100] mm;
            pitch 1 um; per-request heights seed 100000 + request id.
@@ -132,6 +134,26 @@ def spot_target(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: 
         for y0, y1, x0, x1, g in tiles:
             T[j, y0:y1, x0:x1] += (g * scale).astype(np.float32)
     return T
+
+
+def flat_top_target(P: int, N: int, n_lambda: int, grid: int = 8, pitch: float | None = None,
+                    radius: float | None = None) -> np.ndarray:
+    """[L][P][P] float32 beam-splitter targets: a regular grid x grid lattice of flat-top,
+    equal-intensity discs (pitch P/32 and radius pitch/4 by default) centred at (P/2, P/2),
+    each wavelength's target summing to N^2."""
+    pitch = P / 32.0 if pitch is None else float(pitch)
+    radius = pitch / 4.0 if radius is None else float(radius)
+    offs = (np.arange(grid) - (grid - 1) / 2.0) * pitch + P / 2.0
+    ys = np.arange(P, dtype=np.float64)[:, None]
+    xs = np.arange(P, dtype=np.float64)[None, :]
+    m = np.zeros((P, P), bool)
+    for cy in offs:
+        for cx in offs:
+            y0, y1 = max(0, int(cy - radius) - 1), min(P, int(cy + radius) + 2)
+            x0, x1 = max(0, int(cx - radius) - 1), min(P, int(cx + radius) + 2)
+            m[y0:y1, x0:x1] |= (ys[y0:y1] - cy) ** 2 + (xs[:, x0:x1] - cx) ** 2 <= radius * radius
+    T = np.where(m, float(N) * float(N) / m.sum(), 0.0).astype(np.float32)
+    return np.broadcast_to(T, (n_lambda, P, P)).copy()
 
 
 def gaussian_beam(N: int, dx: float, w0: float) -> np.ndarray:

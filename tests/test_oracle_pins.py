@@ -427,6 +427,28 @@ def test_lanczos3_upsampling_properties():
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs)  # the forward output is rounded to float32
 
 
+def test_radial_parameterisation():
+    N = 64
+    r = np.random.default_rng(44)
+    c = r.standard_normal(9) * 1e-7
+    h = oracle.radial_heights(c, N)
+    # the axis sample is the piston, the edge midpoints (rho = R) sum the coefficients and the
+    # corner (rho^2 = 2 R^2) weighs them by 2^k
+    assert h[N // 2, N // 2] == c[0]
+    for y, x in ((N // 2, 0), (0, N // 2)):
+        assert abs(h[y, x] - c.sum()) <= 1e-22
+    assert abs(h[0, 0] - (c * 2.0 ** np.arange(9)).sum()) <= 1e-20
+    # symmetric under the 90-degree rotation and the reflections about the axis sample
+    a = h[1:, 1:]  # the samples symmetric about (N/2, N/2)
+    assert np.array_equal(a, np.rot90(a)) and np.array_equal(a, a[::-1, :]) and np.array_equal(a, a.T)
+    # s^1 along the centre row is ((x - N/2) / (N/2))^2
+    e1 = oracle.radial_heights([0.0, 1.0], N)
+    assert np.allclose(e1[N // 2], ((np.arange(N) - N / 2) / (N / 2)) ** 2, rtol=0, atol=1e-15)
+    # the gradient is the transpose: <heights(c), g> = <c, grad(g)>
+    g = r.standard_normal((N, N))
+    assert abs((h * g).sum() - (c * oracle.radial_grad(g, 9)).sum()) <= 1e-12 * np.abs(h * g).sum()
+
+
 def test_table2_grids_are_twice_the_design_sample_count():
     rows = np.loadtxt(os.path.join(GOLD, "table2_grids.txt"))
     for ay, ax, pitch, gy, gx in rows:
