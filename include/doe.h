@@ -86,6 +86,16 @@ typedef struct doe_geom {
     const double* lambda;  /* HOST [n_lambda] wavelengths [m], > 0 */
     const double* n_index; /* HOST [n_lambda] refractive index n_lambda of the DOE material, >= 1 */
     uint32_t flags;        /* DOE_BANDLIMIT | DOE_UPSAMPLE(u) [| DOE_UPSAMPLE_LANCZOS3] */
+    /* Parametric incident field E_in (Eq. 2: a plane or spherical wave; Sec. 2.3 scales over
+     * incidence angles), per wavelength, at sample (i, j), x = (j - nx/2) dx, y = (i - ny/2) dx
+     * (the optical axis at padded index P/2):
+     *   E_in = exp(+i 2 pi (x sin theta_x + y sin theta_y) / lambda)
+     *        * [src_d == 0 ? 1 : (|d| / r) exp(+i sgn(d) 2 pi (r - |d|) / lambda)],
+     *   r = sqrt(x^2 + y^2 + d^2), d = src_d.
+     * All zero (the default): a unit plane wave at normal incidence.  Multiplies the e_in array
+     * when both are given; evaluated inside the DOE-row passes (no E_in array in memory). */
+    double theta_x, theta_y; /* incidence angles [rad], |theta| < pi/2 */
+    double src_d;            /* [m]: > 0 point source |d| before the DOE, < 0 focus |d| behind it */
 } doe_geom;
 
 /* Per-device set-up (uploads the twiddle tables).  Optional: the first call of any entry

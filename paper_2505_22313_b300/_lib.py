@@ -53,6 +53,9 @@ class Geom(ctypes.Structure):
         ("lambda_", ctypes.POINTER(ctypes.c_double)),
         ("n_index", ctypes.POINTER(ctypes.c_double)),
         ("flags", ctypes.c_uint32),
+        ("theta_x", ctypes.c_double),
+        ("theta_y", ctypes.c_double),
+        ("src_d", ctypes.c_double),
     ]
 
 

@@ -31,14 +31,19 @@ class Geometry:
     bandlimit: bool = True
     upsample: int = 1
     lanczos: bool = False  # Lanczos-3 instead of nearest upsampling of the layout
+    theta_x: float = 0.0   # incident plane-wave tilt [rad]
+    theta_y: float = 0.0
+    src_d: float = 0.0     # spherical incident wave: source |d| before (> 0) / focus behind (< 0) [m]
 
     @staticmethod
-    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1, lanczos=False) -> "Geometry":
+    def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1, lanczos=False,
+             theta_x=0.0, theta_y=0.0, src_d=0.0) -> "Geometry":
         lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, np.float64)))
         nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
         if upsample not in (1, 2, 4, 8):
             raise ValueError("upsample must be 1, 2, 4 or 8")
-        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample), bool(lanczos))
+        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample), bool(lanczos),
+                        float(theta_x), float(theta_y), float(src_d))
 
     @property
     def NL(self) -> int:
@@ -64,6 +69,7 @@ class Geometry:
         g.n_index = self.n_index.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         g.flags = ((L.DOE_BANDLIMIT if self.bandlimit else 0) | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
                    | (L.DOE_UPSAMPLE_LANCZOS3 if self.lanczos else 0))
+        g.theta_x, g.theta_y, g.src_d = self.theta_x, self.theta_y, self.src_d
         return g
 
 

@@ -139,6 +139,8 @@ int check_geom(const doe_geom* g) {
   if (g->nx != g->ny) return DOE_EUNSUPPORTED;
   if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
   if ((g->nx >> upsample_log2(g)) < 4) return DOE_EINVAL;
+  if (!(std::fabs(g->theta_x) < 0.5 * kPi) || !(std::fabs(g->theta_y) < 0.5 * kPi) || !std::isfinite(g->src_d))
+    return DOE_EINVAL;
   return DOE_OK;
 }
 
@@ -167,6 +169,19 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   split(phi0, s.phi0_hi, s.phi0_lo);
   split(std::fmod(phi0, 2.0 * kPi), s.th0_hi, s.th0_lo);
   split(2.0 * kPi * (g->n_index[j] - 1.0) / lam, s.kp_hi, s.kp_lo);
+  // parametric incident field: tilt in cycles per sample, spherical wave as (dx/d)^2 and |d|/lambda
+  if (g->theta_x != 0.0 || g->theta_y != 0.0) {
+    s.illum |= ILLUM_TILT;
+    split(g->dx * std::sin(g->theta_x) / lam, s.ta_hi, s.ta_lo);
+    split(g->dx * std::sin(g->theta_y) / lam, s.tb_hi, s.tb_lo);
+  }
+  if (g->src_d != 0.0) {
+    s.illum |= ILLUM_SPHERE;
+    const double q = g->dx / g->src_d;
+    split(q * q, s.sc_hi, s.sc_lo);
+    split(std::fabs(g->src_d) / lam, s.sk_hi, s.sk_lo);
+    s.ssgn = g->src_d > 0.0 ? 1.f : -1.f;
+  }
 }
 
 struct Layout {
@@ -252,6 +267,7 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
     bt.s[j].tile_begin = tiles;
     tiles += sl[j].wp / col_tile(bt.P);
     if (sl[j].kmax > kmx) kmx = sl[j].kmax;
+    if (sl[j].illum) bt.illum = 1;
   }
   bt.total_tiles = tiles;
   bt.max_kmax = kmx;

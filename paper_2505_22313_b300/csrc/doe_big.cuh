@@ -40,7 +40,7 @@ __device__ __forceinline__ int big_pos_to_k(int pos, int Q) { return (pos % kBig
 __host__ __device__ constexpr int big_tile(int Q) { return Q >= 8 ? 1 : 8 / Q; }
 
 // ------------------------------------------------------------------ rows, forward (pass A)
-template <int Q>
+template <int Q, bool ILLUM>
 __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, P = L * Q, SH = L / Q;
   using G = Last<L, false>;
@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
   const int t = threadIdx.x, N = bt.N, off = bt.off;
   const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
   const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+  IncRow ir = {0.f, 0u};
+  if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
   float4* rsm[Q];
 #pragma unroll
   for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
@@ -66,8 +68,13 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
       xa[n1] = xb[n1] = make_float2(0.f, 0.f);
       if ((unsigned)x < (unsigned)N) {
         const float2 hv = heights_pair(hrow, x, sl.uf);
-        xa[n1] = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-        xb[n1] = sl.uf ? xa[n1] : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+        if (ILLUM && sl.illum) {
+          xa[n1] = transmittance_inc(hv.x, sl, ir, x - N / 2);
+          xb[n1] = transmittance_inc(hv.y, sl, ir, x + 1 - N / 2);
+        } else {
+          xa[n1] = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+          xb[n1] = sl.uf ? xa[n1] : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+        }
         if (erow) {
           const float4 ev = __ldcs(erow + (x >> 1));
           xa[n1] = cmul(xa[n1], make_float2(ev.x, ev.y));
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
 }
 
 // ------------------------------------------------------------------ DOE rows, adjoint (pass A*)
-template <int Q>
+template <int Q, bool ILLUM>
 __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, SH = L / Q, IT = SH / (2 * T);
   extern __shared__ float2 sm[];
@@ -422,6 +429,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
     const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     const float k2 = -2.f * sl.kp_hi;
+    IncRow ir = {0.f, 0u};
+    if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
       const int x2 = s * SH + 2 * t + it * 2 * T;
@@ -432,8 +441,14 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
         const int x = q * L + x2 - off;  // even
         if ((unsigned)x < (unsigned)N) {
           const float2 hv = heights_pair(hrow, x, sl.uf);
-          float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-          float2 e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          float2 e0, e1;
+          if (ILLUM && sl.illum) {
+            e0 = transmittance_inc(hv.x, sl, ir, x - N / 2);
+            e1 = transmittance_inc(hv.y, sl, ir, x + 1 - N / 2);
+          } else {
+            e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+            e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          }
           if (erow) {
             const float4 ev = __ldcs(erow + (x >> 1));
             e0 = cmul(e0, make_float2(ev.x, ev.y));

@@ -82,17 +82,89 @@ __device__ __forceinline__ float2 transfer_value(unsigned int m, const Slice& s)
   return make_float2(cs, sn);
 }
 
-// Transmittance exp(+i k' h) (Eq. 1-2).  k' h is formed exactly as a float pair (FMA
-// two-product), wrapped to (-pi, pi] in that format, then rounded once for sincosf.
-__device__ __forceinline__ float2 transmittance(float hv, float kp_hi, float kp_lo) {
+// Phase of the transmittance exp(+i k' h) (Eq. 1-2).  k' h is formed exactly as a float pair
+// (FMA two-product) and wrapped to (-pi, pi] in that format, then rounded once.
+__device__ __forceinline__ float trans_phase(float hv, float kp_hi, float kp_lo) {
   const dfl p = two_prod(kp_hi, hv);
   const float e = fmaf(kp_lo, hv, p.lo);
   const float n = rintf(__fmul_rn(p.hi, kInvTwoPi));
   const float r = fmaf(-n, kTwoPiHi, p.hi);  // exact (Sterbenz): |p.hi - n 2pi_hi| is small
-  const float th = __fadd_rn(r, fmaf(-n, kTwoPiLo, e));
+  return __fadd_rn(r, fmaf(-n, kTwoPiLo, e));
+}
+__device__ __forceinline__ float2 transmittance(float hv, float kp_hi, float kp_lo) {
+  float sn, cs;
+  sincosf(trans_phase(hv, kp_hi, kp_lo), &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// ------------------------------------------------------------------ parametric incident field
+// E_in of Eq. 2 as a tilted plane wave times an on-axis spherical wave, at DOE sample
+// (yy, xx) = (i - N/2, x - N/2) (the optical axis at padded index P/2):
+//   tilt:   exp(+i 2 pi (a xx + b yy)),  a = dx sin(theta_x) / lambda, b = dx sin(theta_y) / lambda
+//   sphere: (|d| / r) exp(+i sgn(d) 2 pi (r - |d|) / lambda),  r = sqrt(rho^2 + d^2)
+// Phases are kept in cycles and reduced to their fractional parts in double-float, so that
+// tens of thousands of cycles across a large aperture cost no accuracy.
+
+// Fractional part of a n (a = a_hi + a_lo, n an integer with |n| <= 2^24), in cycles,
+// |result| <= 1/2 + |a_lo n|.
+__device__ __forceinline__ float frac_cycles(float a_hi, float a_lo, float n) {
+  const dfl p = two_prod(a_hi, n);
+  const float r = __fsub_rn(p.hi, rintf(p.hi));  // exact: p.hi and its nearest integer share a binade grid
+  return __fadd_rn(r, fmaf(a_lo, n, p.lo));
+}
+
+// The part of the incident field shared by DOE row yy: its tilt cycles and yy^2.
+struct IncRow {
+  float cy;
+  unsigned int yy2;
+};
+__device__ __forceinline__ IncRow incident_row(const Slice& s, int yy) {
+  IncRow r;
+  r.cy = (s.illum & ILLUM_TILT) ? frac_cycles(s.tb_hi, s.tb_lo, (float)yy) : 0.f;
+  r.yy2 = (unsigned int)(yy * yy);
+  return r;
+}
+
+// Phase (radians, |th| <= pi) and amplitude of the incident field at column xx of row r.
+// Spherical term: with u = (dx / d)^2 (xx^2 + yy^2) = rho^2 / d^2, (r - |d|) / lambda =
+// (|d| / lambda) u / (1 + sqrt(1 + u)) (no cancellation), evaluated in double-float.
+__device__ __forceinline__ float incident_phase(const Slice& s, IncRow r, int xx, float& amp) {
+  float cyc = r.cy;
+  if (s.illum & ILLUM_TILT) cyc = __fadd_rn(cyc, frac_cycles(s.ta_hi, s.ta_lo, (float)xx));
+  amp = 1.f;
+  if (s.illum & ILLUM_SPHERE) {
+    const unsigned int m = r.yy2 + (unsigned int)(xx * xx);  // < 2^31 + 2^30
+    const float m_hi = (float)(m & 0xFFFFF000u);                // exact: at most 20 significant bits
+    const float m_lo = (float)(m & 0x00000FFFu);                // exact
+    const dfl c = {s.sc_hi, s.sc_lo};
+    const dfl u = df_add(df_mul_f(c, m_hi), df_mul_f(c, m_lo));
+    const dfl w = df_add({1.f, 0.f}, u);  // 1 + u
+    // sqrt(1 + u): one Newton step from the FP32 root
+    const float s0 = sqrtf(w.hi);
+    const dfl s0sq = two_prod(s0, s0);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(w.hi, s0sq.hi), s0sq.lo), w.lo);
+    const dfl sq = fast_two_sum(s0, __fmul_rn(res, __fdiv_rn(0.5f, s0)));
+    const dfl den = df_add({1.f, 0.f}, sq);  // >= 2
+    // q = u / (1 + sqrt(1 + u)): FP32 quotient corrected by one residual step
+    const float q0 = __fdiv_rn(u.hi, den.hi);
+    const dfl rq = df_add(u, df_neg(df_mul_f(den, q0)));
+    const dfl q = fast_two_sum(q0, __fdiv_rn(rq.hi, den.hi));
+    const dfl t = df_mul({s.sk_hi, s.sk_lo}, q);  // (r - |d|) / lambda, cycles
+    const float f = __fadd_rn(__fsub_rn(t.hi, rintf(t.hi)), t.lo);
+    cyc = fmaf(s.ssgn, f, cyc);
+    amp = __fdiv_rn(1.f, sq.hi);  // |d| / r
+  }
+  cyc = __fsub_rn(cyc, rintf(cyc));  // exact
+  return fmaf(cyc, kTwoPiHi, __fmul_rn(cyc, kTwoPiLo));
+}
+
+// Transmittance times the parametric incident field, one sincosf for both phases.
+__device__ __forceinline__ float2 transmittance_inc(float hv, const Slice& s, IncRow r, int xx) {
+  float amp;
+  const float th = __fadd_rn(trans_phase(hv, s.kp_hi, s.kp_lo), incident_phase(s, r, xx, amp));
   float sn, cs;
   sincosf(th, &sn, &cs);
-  return make_float2(cs, sn);
+  return make_float2(amp * cs, amp * sn);
 }
 
 // Heights of the adjacent simulation samples (x, x + 1), x even, of the DOE row whose layout

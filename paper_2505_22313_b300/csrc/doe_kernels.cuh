@@ -90,7 +90,8 @@ __device__ __forceinline__ void wait_staged() { asm volatile("cp.async.wait_all;
 // columns x, x + 1 (x even; the DOE offset is even).  When a height row fits behind the
 // exchange buffer (N <= L / 2, i.e. pad 2) the next item's heights are copied into shared
 // memory while the current row is transformed; otherwise they are read from global memory.
-template <int L>
+// ILLUM: some slice has a parametric incident field (evaluated per sample with the phase).
+template <int L, bool ILLUM>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __grid_constant__ Batch bt) {
   using F = First<L, false>;
   constexpr int T = L / 32;
@@ -132,6 +133,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
       if (kn < items) stage_heights(hs, layout_row(kn), layout_n(kn), t, T);
     }
     float2 v[32];
+    IncRow ir = {0.f, 0u};
+    if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
 #pragma unroll
     for (int b = 0; b < F::B; b += 2)
 #pragma unroll
@@ -139,8 +142,13 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
         const int x = F::idx(t, b, r) - off;
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
         if ((unsigned)x < (unsigned)N) {
-          a = transmittance(hv[b / 2][r].x, sl.kp_hi, sl.kp_lo);
-          c = uf ? a : transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);  // one layout cell
+          if (ILLUM && sl.illum) {
+            a = transmittance_inc(hv[b / 2][r].x, sl, ir, x - N / 2);
+            c = transmittance_inc(hv[b / 2][r].y, sl, ir, x + 1 - N / 2);
+          } else {
+            a = transmittance(hv[b / 2][r].x, sl.kp_hi, sl.kp_lo);
+            c = uf ? a : transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);  // one layout cell
+          }
           if (erow) {
             const float4 ev = __ldcs(erow + (x >> 1));
             a = cmul(a, make_float2(ev.x, ev.y));
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const
 
 // ------------------------------------------------------------------ pass A*: DOE-row adjoint
 // One CTA per DOE row; loops over the slices (wavelengths of one request) and sums.
-template <int L>
+template <int L, bool ILLUM>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const __grid_constant__ Batch bt) {
   using H = Last<L, true>;
   extern __shared__ float2 sm[];
@@ -403,6 +411,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
     const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
     const float k2 = -2.f * sl.kp_hi;
+    IncRow ir = {0.f, 0u};
+    if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
 #pragma unroll
     for (int b = 0; b < H::B; b += 2)
 #pragma unroll
@@ -410,8 +420,14 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
         const int x = H::idx(t, b, r) - off;  // even
         if ((unsigned)x < (unsigned)N) {
           const float2 hv = heights_pair(hrow, x, sl.uf);
-          float2 e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
-          float2 e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          float2 e0, e1;
+          if (ILLUM && sl.illum) {
+            e0 = transmittance_inc(hv.x, sl, ir, x - N / 2);
+            e1 = transmittance_inc(hv.y, sl, ir, x + 1 - N / 2);
+          } else {
+            e0 = transmittance(hv.x, sl.kp_hi, sl.kp_lo);
+            e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
+          }
           if (erow) {
             const float4 ev = erow[x >> 1];
             e0 = cmul(e0, make_float2(ev.x, ev.y));

@@ -134,11 +134,14 @@ cudaError_t prep_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<L>();
   const int nt = threads<L>();
-  if ((e = prep_one(pass_a_kernel<L>, pass_a_smem<L>(), nt))) return e;
+  if ((e = prep_one(pass_a_kernel<L, false>, pass_a_smem<L>(), nt)) ||
+      (e = prep_one(pass_a_kernel<L, true>, pass_a_smem<L>(), nt)))
+    return e;
   if ((e = prep_one(pass_b_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_kernel<L>, sb, nt))) return e;
-  if ((e = prep_one(pass_a_adj_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_adj_kernel<L, false>, sb, nt)) || (e = prep_one(pass_a_adj_kernel<L, true>, sb, nt)))
+    return e;
   if ((e = prep_one(render_rows_kernel<L, false>, sb, nt)) || (e = prep_one(render_rows_kernel<L, true>, sb, nt)))
     return e;
   if constexpr (L <= kRenderColsMax)  // two L-sample buffers must fit one CTA's shared memory
@@ -150,22 +153,27 @@ cudaError_t prep_t() {
   return cudaSuccess;
 }
 
-template <int L>
-cudaError_t pass_a_t(const Batch& bt, cudaStream_t st) {
-  Traced tr(TR_PASS_A, st);
-  // persistent: about as many CTAs per slice as are resident at once, each looping over rows
+template <int L, bool ILLUM>
+cudaError_t pass_a_run(const Batch& bt, cudaStream_t st) {
+  // persistent: about as many CTAs as are resident at once, each looping over (slice, row) items
   static const int resident = [] {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_a_kernel<L>, threads<L>(), pass_a_smem<L>()))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_a_kernel<L, ILLUM>, threads<L>(),
+                                                      pass_a_smem<L>()))
       return 0;
     return sms * per_sm;
   }();
   const long items = (long)bt.S * bt.N;
   const int grid = (int)(resident > 0 && resident < items ? resident : items);
   const size_t smem = smem_bytes<L>() + (2 * bt.N <= L ? (size_t)bt.N * sizeof(float) : 0);
-  pass_a_kernel<L><<<dim3(grid), threads<L>(), smem, st>>>(bt);
+  pass_a_kernel<L, ILLUM><<<dim3(grid), threads<L>(), smem, st>>>(bt);
   return cudaGetLastError();
+}
+template <int L>
+cudaError_t pass_a_t(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_PASS_A, st);
+  return bt.illum ? pass_a_run<L, true>(bt, st) : pass_a_run<L, false>(bt, st);
 }
 template <int L>
 cudaError_t pass_b_t(const Batch& bt, cudaStream_t st) {
@@ -201,7 +209,10 @@ cudaError_t pass_c_adj_t(const Batch& bt, cudaStream_t st) {
 template <int L>
 cudaError_t pass_a_adj_t(const Batch& bt, cudaStream_t st) {
   Traced tr(TR_PASS_A_ADJ, st);
-  pass_a_adj_kernel<L><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
+  if (bt.illum)
+    pass_a_adj_kernel<L, true><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
+  else
+    pass_a_adj_kernel<L, false><<<dim3(bt.N), threads<L>(), smem_bytes<L>(), st>>>(bt);
   return cudaGetLastError();
 }
 // ---- grids longer than one CTA (P = Q * 8192 sub-transforms): cluster launches
@@ -225,10 +236,11 @@ cudaError_t launch_cluster(const void* fn, dim3 grid, int cluster, size_t smem, 
 }
 template <int Q>
 cudaError_t big_rows_t(int which, const Batch& bt, cudaStream_t st) {
-  const void* fn = which == 0 ? (const void*)pass_a_big_kernel<Q>
+  const void* fn = which == 0 ? (bt.illum ? (const void*)pass_a_big_kernel<Q, true> : (const void*)pass_a_big_kernel<Q, false>)
                  : which == 1 ? (const void*)pass_c_big_kernel<Q>
                  : which == 2 ? (const void*)pass_c_adj_big_kernel<Q>
-                              : (const void*)pass_a_adj_big_kernel<Q>;
+                 : bt.illum   ? (const void*)pass_a_adj_big_kernel<Q, true>
+                              : (const void*)pass_a_adj_big_kernel<Q, false>;
   const int rows = (which == 0 || which == 3) ? bt.N : bt.P;
   const dim3 grid(rows * Q, which == 3 ? 1 : bt.S);
   void* args[] = {const_cast<Batch*>(&bt)};
@@ -246,11 +258,14 @@ cudaError_t prep_big_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<kBigL>();
   constexpr int nt = kBigL / 32;
-  if ((e = prep_one(pass_a_big_kernel<Q>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_big_kernel<Q, false>, sb, nt)) || (e = prep_one(pass_a_big_kernel<Q, true>, sb, nt)))
+    return e;
   if ((e = prep_one(pass_b_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_c_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb, nt))) return e;
-  if ((e = prep_one(pass_a_adj_big_kernel<Q>, sb, nt))) return e;
+  if ((e = prep_one(pass_a_adj_big_kernel<Q, false>, sb, nt)) ||
+      (e = prep_one(pass_a_adj_big_kernel<Q, true>, sb, nt)))
+    return e;
   return cudaSuccess;
 }
 

@@ -94,7 +94,14 @@ struct Slice {
   int hp;                // row pitch of htab (kmax + 1)
   int tile_begin;        // first global column-tile index of this slice (column pass)
   int uf;                // log2 of the nearest-upsampling factor of the heights (0: none)
+  int illum;             // parametric incident field: ILLUM_TILT | ILLUM_SPHERE (0: none)
+  float ta_hi, ta_lo;    // tilt: cycles per sample along x, dx sin(theta_x) / lambda
+  float tb_hi, tb_lo;    // tilt: cycles per sample along y, dx sin(theta_y) / lambda
+  float sc_hi, sc_lo;    // spherical wave: (dx / d)^2
+  float sk_hi, sk_lo;    // spherical wave: |d| / lambda
+  float ssgn;            // spherical wave: +1 diverging (d > 0), -1 converging
 };
+enum : int { ILLUM_TILT = 1, ILLUM_SPHERE = 2 };
 
 // Lanczos-3 interpolation of a height layout onto the simulation grid (upsampling factor f):
 // simulation sample x = f xc + r reads layout cells xc + off[r] + d, d = 0..5, with weights
@@ -116,6 +123,7 @@ struct Batch {
   int mode;          // MODE_FWD / MODE_ADJ (column pass), OUT_* (row inverse pass), GRAD_* (adjoint row pass)
   int max_kmax;      // largest kmax over the slices (table builder grid)
   int qf;            // sub-transforms per row: P / 16384 for P > 16384, else 1
+  int illum;         // some slice has a parametric incident field (selects the DOE-row kernels)
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
   Slice s[kMaxSlices];

@@ -14,7 +14,8 @@ import argparse
 import json
 
 CONFIGS = {
-    # name: (N, pitch m, z m, wavelengths m, gradient?[, nearest-upsampling factor of the heights])
+    # name: (N, pitch m, z m, wavelengths m, gradient?[, nearest-upsampling factor of the heights
+    #        [, parametric incident field]])
     "small": (256, 2e-6, 20e-3, [550e-9], True),
     "rgb": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True),
     "gradient": (8192, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True),
@@ -23,6 +24,9 @@ CONFIGS = {
     "large_area": (32768, 1e-6, 100e-3, [550e-9], True),
     # the RGB geometry designed on a 1024^2 layout at 4 um, nearest-upsampled 4x in pass A
     "rgb_layout4": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 4),
+    # the RGB geometry lit by a tilted wave converging to 200 mm (evaluated in the DOE-row passes)
+    "rgb_tilted_converging": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 1,
+                              dict(theta_x=0.01, theta_y=-0.005, src_d=-0.2)),
 }
 
 
@@ -34,9 +38,10 @@ def run(name: str, reps: int, grad: bool = True) -> dict:
 
     N, dx, z, lams, do_grad, *rest = CONFIGS[name]
     f = rest[0] if rest else 1
+    illum = rest[1] if len(rest) > 1 else {}
     do_grad = do_grad and grad
     P = 2 * N
-    g = Geometry.make(N, dx, z, lams, upsample=f)
+    g = Geometry.make(N, dx, z, lams, upsample=f, **illum)
     h = inputs.heights_device(N // f, 1000 + N, "cuda")
     ws = api.workspace(api.workspace_bytes(g, _lib.DOE_OP_GRAD if do_grad else _lib.DOE_OP_PSF))
     out = torch.empty((g.L, P, P), device="cuda")
@@ -51,7 +56,7 @@ def run(name: str, reps: int, grad: bool = True) -> dict:
     e1.record()
     torch.cuda.synchronize()
     psf_ms = e0.elapsed_time(e1) / reps
-    row = {"config": name, "N": N, "P": P, "wavelengths": g.L, "upsample": f, "psf_ms": round(psf_ms, 3),
+    row = {"config": name, "N": N, "P": P, "wavelengths": g.L, "upsample": f, "illum": illum, "psf_ms": round(psf_ms, 3),
            "field_samples_per_s": g.L * P * P / (psf_ms / 1e3)}
     recs = api.trace_read()
     del out

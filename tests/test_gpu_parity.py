@@ -523,6 +523,111 @@ def test_lanczos_nearest_and_plain_requests_share_a_launch():
         assert torch.equal(m, api.psf(h, g))
 
 
+# -------------------------------------------------------------- parametric incident fields
+ILLUM_CASES = {
+    "tilt": dict(theta_x=0.1, theta_y=-0.05),
+    "converging": dict(src_d=-2e-3),
+    "diverging": dict(src_d=5e-3),
+    "tilted_converging": dict(theta_x=-0.08, theta_y=0.03, src_d=-3e-3),
+}
+
+
+def _illum_oracle(hs, N, dx, z, lams, kw, T=None, pad=2, e_arr=None):
+    """Per-wavelength oracle PSFs (and the gradient summed over wavelengths) with E_in the
+    oracle's incident field of each wavelength, times e_arr if given."""
+    I, g, loss = [], 0.0, 0.0
+    for j, lam in enumerate(lams):
+        e = oracle.incident(N, dx, lam, kw.get("theta_x", 0.0), kw.get("theta_y", 0.0), kw.get("src_d", 0.0))
+        if e_arr is not None:
+            e = e * e_arr
+        I.append(oracle.psf(hs, dx, z, [lam], pad=pad, e_in=e)[0])
+        if T is not None:
+            gj, lj = oracle.grad(hs, dx, z, [lam], T[j:j + 1], pad=pad, e_in=e)
+            g, loss = g + gj, loss + lj
+    return np.stack(I), g, loss
+
+
+@pytest.mark.parametrize("case", sorted(ILLUM_CASES))
+@pytest.mark.parametrize("N,pad", [(256, 2), (128, 1)])
+def test_incident_field_psf_and_grad_vs_oracle(case, N, pad):
+    dx, z = 0.5e-6, 2e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = pad * N
+    kw = ILLUM_CASES[case]
+    h = _h(N, 8000 + N)
+    T = inputs.spot_target(P, N, 3, 8100 + N)
+    g = Geometry.make(N, dx, z, lams, pad=pad, **kw)
+    I = api.psf(torch.from_numpy(h).cuda(), g).cpu().numpy()
+    gr, loss = api.grad(torch.from_numpy(h).cuda(), g, torch.from_numpy(T).cuda())
+    Iref, gref, lref = _illum_oracle(h, N, dx, z, lams, kw, T, pad=pad)
+    assert rel_l2(I, Iref) < TOL_PSF, rel_l2(I, Iref)
+    err = rel_l2(gr.cpu().numpy(), gref)
+    assert err < TOL_GRAD, err
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_incident_field_with_array_and_upsampling_vs_oracle():
+    # the parametric field multiplies an E_in array; heights on a 4x nearest-upsampled layout
+    N, f, dx, z = 256, 4, 0.5e-6, 2e-3
+    lams = [500e-9, 620e-9]
+    kw = dict(theta_x=0.06, src_d=-4e-3)
+    hl = _h(N // f, 8200)
+    hs = oracle.upsample_nearest(hl, f)
+    e_arr = inputs.gaussian_beam(N, dx, 40e-6).astype(np.complex64)
+    T = inputs.spot_target(2 * N, N, 2, 8201)
+    g = Geometry.make(N, dx, z, lams, upsample=f, **kw)
+    et = torch.from_numpy(e_arr).cuda()
+    I = api.psf(torch.from_numpy(hl).cuda(), g, e_in=et).cpu().numpy()
+    gr, loss = api.grad(torch.from_numpy(hl).cuda(), g, torch.from_numpy(T).cuda(), e_in=et)
+    Iref, gref, lref = _illum_oracle(hs, N, dx, z, lams, kw, T, e_arr=e_arr.astype(np.complex128))
+    assert rel_l2(I, Iref) < TOL_PSF, rel_l2(I, Iref)
+    err = rel_l2(gr.cpu().numpy(), oracle.layout_grad(gref, f))
+    assert err < TOL_GRAD, err
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_incident_field_requests_share_a_launch():
+    # tilted, spherical and plain requests in one batched launch equal their separate calls
+    N, dx, z = 256, 0.5e-6, 2e-3
+    hs = [torch.from_numpy(_h(N, 8300 + k)).cuda() for k in range(3)]
+    gs = [Geometry.make(N, dx, z, [500e-9]),
+          Geometry.make(N, dx, z, [600e-9, 700e-9], theta_x=0.05),
+          Geometry.make(N, dx, z, [450e-9], src_d=-2e-3)]
+    many = api.psf_many(hs, gs)
+    for h, g, m in zip(hs, gs, many):
+        assert torch.equal(m, api.psf(h, g))
+
+
+def test_incident_field_big_grid_rows_vs_oracle():
+    # 16384^2 DOE, 32768^2 grid (cluster-split rows): a tilted wave converging to 200 mm,
+    # sampled PSF rows and the row-subset gradient against the oracle
+    N, dx, z, lam = 16384, 1e-6, 50e-3, 550e-9
+    P = 2 * N
+    kw = dict(theta_x=0.01, theta_y=-0.005, src_d=-0.2)
+    h = _h(N, 8400)
+    g = Geometry.make(N, dx, z, [lam], **kw)
+    e = oracle.incident(N, dx, lam, theta_x=0.01, theta_y=-0.005, d=-0.2)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g)
+    rows = np.array([0, P // 4, P // 2 - 1, P // 2, 3 * P // 4 + 5, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    del I
+    err = rel_l2(Ig, oracle.psf_rows(h, dx, z, lam, rows, e_in=e))
+    assert err < TOL_PSF, err
+    r = np.random.default_rng(8401)
+    grows = np.unique(np.concatenate([[P // 2, P // 2 + 1], r.integers(0, P, 6)]))
+    g_rows = r.standard_normal((grows.size, P)).astype(np.float32)
+    G = torch.zeros((1, P, P), dtype=torch.float32, device="cuda")
+    G[0, torch.from_numpy(grows).cuda()] = torch.from_numpy(g_rows).cuda()
+    gr, _ = api.grad(ht, g, G, mode="vjp", recompute=True)
+    drows = np.unique(np.concatenate([[0, N // 2, N - 1], r.integers(0, N, 5)]))
+    got = gr[torch.from_numpy(drows).cuda()].cpu().numpy()
+    del G, gr
+    torch.cuda.empty_cache()
+    err = rel_l2(got, oracle.grad_rows(h, dx, z, lam, grows, g_rows, drows, e_in=e))
+    assert err < TOL_GRAD, err
+
+
 # -------------------------------------------------------------- design optimiser
 def test_adam_step_matches_oracle():
     r = np.random.default_rng(50)
