@@ -189,6 +189,28 @@ size_t doe_wiener_workspace_bytes(int C, int H, int W);
 int doe_adam_step(float* h, const float* grad, float* m, float* v, long long n, double lr, double beta1,
                   double beta2, double eps, int t, double h_min, double h_max, void* stream);
 
+/* Radially symmetric height map (Sec. 5, broadband imaging: radial symmetry enforced through a
+ * 16th-order polynomial), read as an even polynomial in the normalised radius:
+ *   h[i][j] = sum_{k < n_c} c[k] s^k,  s = ((i - n/2)^2 + (j - n/2)^2) / (n/2)^2 = (rho / R)^2,
+ * R = n dx / 2 the half-aperture, the axis at sample (n/2, n/2).
+ *   n      power of two, 16 .. 65536 (the side of the height array given to doe_grad: N, or
+ *          N / f with DOE_UPSAMPLE)
+ *   c      device float [n_c], 1 <= n_c <= 9 (degree 2 (n_c - 1) <= 16), metres
+ *   h      device float [n][n], overwritten
+ * Horner in double-float, rounded once to float.  Stream-ordered.  Errors: DOE_EINVAL,
+ * DOE_ECUDA. */
+int doe_radial_heights(int n, const float* c, int n_c, float* h, void* stream);
+
+/* Bytes of workspace doe_radial_grad needs (0 when n_c is out of range). */
+size_t doe_radial_workspace_bytes(int n_c);
+
+/* Transpose of doe_radial_heights: c_grad[k] = sum_{i,j} grad_h[i][j] s^k, the coefficient
+ * gradient from doe_grad's height gradient.  grad_h device float [n][n]; c_grad device float
+ * [n_c], overwritten; ws device, 8-byte aligned, >= doe_radial_workspace_bytes(n_c).  Double-
+ * float terms, FP64 partial sums combined in a fixed order (deterministic).  Errors:
+ * DOE_EINVAL, DOE_ENOWS, DOE_ECUDA. */
+int doe_radial_grad(int n, int n_c, const float* grad_h, float* c_grad, void* ws, size_t ws_bytes, void* stream);
+
 /* Integer band logic of the transfer function, computed on the host exactly as the kernels
  * use it (for bit-exact checks).  For wavelength j: kmax[j] = the largest signed frequency
  * index kept per axis (ceil(f_lim / du) - 1 capped at P/2, with

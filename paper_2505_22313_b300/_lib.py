@@ -29,7 +29,8 @@ DOE_GRAD_L2_TARGET, DOE_GRAD_VJP = 0, 1
 EXPORTS = (
     "doe_init", "doe_workspace_bytes", "doe_propagate", "doe_psf", "doe_psf_many",
     "doe_workspace_bytes_many", "doe_grad", "doe_render", "doe_render_workspace_bytes",
-    "doe_wiener", "doe_wiener_workspace_bytes", "doe_adam_step",
+    "doe_wiener", "doe_wiener_workspace_bytes", "doe_adam_step", "doe_radial_heights",
+    "doe_radial_workspace_bytes", "doe_radial_grad",
     "doe_band_limits", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
     "doe_pass_name", "doe_launch_count", "doe_psf_noalloc",
 )
@@ -89,6 +90,9 @@ def load(path: Path | None = None) -> ctypes.CDLL:
         "doe_wiener_workspace_bytes": ([I, I, I], S),
         "doe_adam_step": ([F, F, F, F, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                            ctypes.c_double, I, ctypes.c_double, ctypes.c_double, V], I),
+        "doe_radial_heights": ([I, F, I, F, V], I),
+        "doe_radial_workspace_bytes": ([I], S),
+        "doe_radial_grad": ([I, I, F, F, V, S, V], I),
         "doe_band_limits": ([G, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], I),
         "doe_debug_band_mask": ([G, I, F, V, S, V], I),
         "doe_strerror": ([I], ctypes.c_char_p),

@@ -218,6 +218,32 @@ def wiener(psf_t: torch.Tensor, y: torch.Tensor, gamma: float, out: torch.Tensor
     return out
 
 
+def radial_heights(c: torch.Tensor, n: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Radially symmetric heights [n][n] = sum_k c[k] s^k, s = (rho / R)^2 (c: float32 [n_c] on
+    the device, n_c <= 9)."""
+    n_c = c.numel()
+    cp = _dev_ptr(c, torch.float32, (n_c,), "c")
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device=c.device)
+    op = _dev_ptr(out, torch.float32, (n, n), "out")
+    L.check(L.load().doe_radial_heights(int(n), cp, n_c, op, _stream(stream)), "doe_radial_heights")
+    return out
+
+
+def radial_grad(grad_h: torch.Tensor, n_c: int, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Coefficient gradient [n_c] = sum over the grid of grad_h * s^k (transpose of radial_heights)."""
+    n = grad_h.shape[0]
+    gp = _dev_ptr(grad_h, torch.float32, (n, n), "grad_h")
+    if out is None:
+        out = torch.empty((n_c,), dtype=torch.float32, device=grad_h.device)
+    op = _dev_ptr(out, torch.float32, (n_c,), "out")
+    need = int(L.load().doe_radial_workspace_bytes(int(n_c)))
+    ws, wp, wb = _ws_args(ws, need, grad_h.device)
+    L.check(L.load().doe_radial_grad(int(n), int(n_c), gp, op, wp, wb, _stream(stream)), "doe_radial_grad")
+    return out
+
+
 def adam_step(h: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, t: int,
               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, h_min: float = 0.0,
               h_max: float = float("inf"), stream=None) -> torch.Tensor:

@@ -477,7 +477,8 @@ const char* doe_pass_name(int id) {
   static const char* names[TR_COUNT] = {"transfer_table", "pass_a_rows", "pass_b_columns", "pass_c_rows",
                                         "pass_c_adjoint_rows", "pass_b_adjoint_columns", "pass_a_adjoint_rows",
                                         "loss_reduce", "render_rows", "render_columns", "render_output",
-                                        "band_mask", "upsample_adjoint", "adam_step", "lanczos_upsample", "lanczos_adjoint"};
+                                        "band_mask", "upsample_adjoint", "adam_step", "lanczos_upsample", "lanczos_adjoint",
+                                        "radial_heights", "radial_grad"};
   return (id >= 0 && id < TR_COUNT) ? names[id] : "unknown";
 }
 

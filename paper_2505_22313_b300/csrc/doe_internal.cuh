@@ -139,20 +139,23 @@ __device__ __forceinline__ float incident_phase(const Slice& s, IncRow r, int xx
     const dfl c = {s.sc_hi, s.sc_lo};
     const dfl u = df_add(df_mul_f(c, m_hi), df_mul_f(c, m_lo));
     const dfl w = df_add({1.f, 0.f}, u);  // 1 + u
-    // sqrt(1 + u): one Newton step from the FP32 root
-    const float s0 = sqrtf(w.hi);
+    // sqrt(1 + u): one Newton step from the approximate root w rsqrt(w); the step squares the
+    // starting error (a few ulp), so approximate reciprocals suffice in the corrections
+    const float rs = rsqrtf(w.hi);
+    const float s0 = __fmul_rn(w.hi, rs);
     const dfl s0sq = two_prod(s0, s0);
     const float res = __fadd_rn(__fsub_rn(__fsub_rn(w.hi, s0sq.hi), s0sq.lo), w.lo);
-    const dfl sq = fast_two_sum(s0, __fmul_rn(res, __fdiv_rn(0.5f, s0)));
+    const dfl sq = fast_two_sum(s0, __fmul_rn(res, __fmul_rn(0.5f, rs)));
     const dfl den = df_add({1.f, 0.f}, sq);  // >= 2
-    // q = u / (1 + sqrt(1 + u)): FP32 quotient corrected by one residual step
-    const float q0 = __fdiv_rn(u.hi, den.hi);
+    // q = u / (1 + sqrt(1 + u)): approximate quotient corrected by one residual step
+    const float inv = __fdividef(1.f, den.hi);
+    const float q0 = __fmul_rn(u.hi, inv);
     const dfl rq = df_add(u, df_neg(df_mul_f(den, q0)));
-    const dfl q = fast_two_sum(q0, __fdiv_rn(rq.hi, den.hi));
+    const dfl q = fast_two_sum(q0, __fmul_rn(rq.hi, inv));
     const dfl t = df_mul({s.sk_hi, s.sk_lo}, q);  // (r - |d|) / lambda, cycles
     const float f = __fadd_rn(__fsub_rn(t.hi, rintf(t.hi)), t.lo);
     cyc = fmaf(s.ssgn, f, cyc);
-    amp = __fdiv_rn(1.f, sq.hi);  // |d| / r
+    amp = rs;  // |d| / r = 1 / sqrt(1 + u), to a few ulp
   }
   cyc = __fsub_rn(cyc, rintf(cyc));  // exact
   return fmaf(cyc, kTwoPiHi, __fmul_rn(cyc, kTwoPiLo));

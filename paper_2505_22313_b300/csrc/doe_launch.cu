@@ -1,6 +1,7 @@
 // doe_launch.cu -- the single device translation unit: twiddle tables, every instantiation of
 // the passes for L = 16 .. 16384, and their launchers.
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -384,6 +385,25 @@ cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long 
                         float beta2, float eps_hat, float h_min, float h_max, cudaStream_t st) {
   Traced tr(TR_ADAM, st);
   adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h, g, m, v, n, lr_hat, beta1, beta2, eps_hat, h_min, h_max);
+  return cudaGetLastError();
+}
+// inverse squared half-side (N/2)^-2, a power of two
+static float radial_inv_r2(int N) { return std::ldexp(1.0f, -2 * (ilog2i(N) - 1)); }
+cudaError_t launch_radial_heights(const float* c, int n_c, int N, float* h, cudaStream_t st) {
+  Traced tr(TR_RADIAL, st);
+  const long long n = (long long)N * N;
+  radial_heights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, n_c, N, radial_inv_r2(N), h);
+  return cudaGetLastError();
+}
+cudaError_t launch_radial_grad(const float* g, int n_c, int N, double* part, float* c_grad, cudaStream_t st) {
+  {
+    Traced tr(TR_RADIAL_GRAD, st);
+    radial_grad_kernel<<<kRadialBlocks, 256, 0, st>>>(g, n_c, N, radial_inv_r2(N), part);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  Traced tr(TR_RADIAL_GRAD, st);
+  radial_grad_final_kernel<<<1, 32, 0, st>>>(part, kRadialBlocks, n_c, c_grad);
   return cudaGetLastError();
 }
 cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st) {

@@ -22,13 +22,16 @@ cudaError_t launch_lanczos_up(const float* hl, float* hs, int N, const LanczosTa
 cudaError_t launch_lanczos_adjoint(const float* g, float* gl, int N, const LanczosTab& tb, cudaStream_t st);
 cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long n, float lr_hat, float beta1,
                         float beta2, float eps_hat, float h_min, float h_max, cudaStream_t st);
+cudaError_t launch_radial_heights(const float* c, int n_c, int N, float* h, cudaStream_t st);
+cudaError_t launch_radial_grad(const float* g, int n_c, int N, double* part, float* c_grad, cudaStream_t st);
 
 struct RenderArgs;
 
 // pass identifiers reported by the tracer (doe_trace_read / doe_pass_name)
 enum : int {
   TR_HTAB = 0, TR_PASS_A, TR_PASS_B, TR_PASS_C, TR_PASS_C_ADJ, TR_PASS_B_ADJ, TR_PASS_A_ADJ, TR_LOSS,
-  TR_RENDER_ROWS, TR_RENDER_COLS, TR_RENDER_OUT, TR_MASK, TR_UPSAMPLE_ADJ, TR_ADAM, TR_LANCZOS, TR_LANCZOS_ADJ, TR_COUNT
+  TR_RENDER_ROWS, TR_RENDER_COLS, TR_RENDER_OUT, TR_MASK, TR_UPSAMPLE_ADJ, TR_ADAM, TR_LANCZOS, TR_LANCZOS_ADJ,
+  TR_RADIAL, TR_RADIAL_GRAD, TR_COUNT
 };
 int trace_enable(int max_records);
 int trace_read(int max, int* pass_ids, float* ms);

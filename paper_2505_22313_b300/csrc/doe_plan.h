@@ -70,6 +70,8 @@ constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
 constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
 constexpr int kTile = 4;    // tile width of the column-tiled buffer (4 x 8 B = one 32-byte sector); columns per cluster for P <= 8192
 constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536 = 8 x 8192)
+constexpr int kMaxRadial = 9;       // coefficients of the radial height polynomial (degree 16 in rho / R)
+constexpr int kRadialBlocks = 592;  // CTAs of the radial gradient reduction (4 per SM)
 
 // One (request, wavelength) slice of a batched launch.  Everything a pass needs that is not
 // shared by the whole launch.

@@ -642,9 +642,11 @@ def test_adam_step_matches_oracle():
     assert rel_l2(ht.cpu().numpy(), ho) < 1e-6
 
 
-def test_design_loop_matches_oracle():
+@pytest.mark.parametrize("target", ["spots", "flat_top"])
+def test_design_loop_matches_oracle(target):
     # Adam + cosine schedule on the L2 gradient (64^2 DOE, 2 wavelengths, 6 steps), the GPU
-    # library against the same loop on the FP64 oracle's gradient and Adam
+    # library against the same loop on the FP64 oracle's gradient and Adam; targets: the
+    # Gaussian spot lattice and the flat-top 8 x 8 beam-splitter lattice
     from paper_2505_22313_b300 import design
 
     N, dx, z = 64, 1e-6, 2e-3
@@ -652,7 +654,7 @@ def test_design_loop_matches_oracle():
     P = 2 * N
     iters, lr0 = 6, 1.2e-8
     h0 = _h(N, 7000)
-    T = inputs.spot_target(P, N, 2, 7001)
+    T = inputs.spot_target(P, N, 2, 7001) if target == "spots" else inputs.flat_top_target(P, N, 2)
     g = Geometry.make(N, dx, z, lams)
     h, losses = design.optimize(torch.from_numpy(h0).cuda(), g, torch.from_numpy(T).cuda(), iters, lr0=lr0)
     ho, mo, vo = h0.astype(np.float64), np.zeros((N, N)), np.zeros((N, N))
@@ -665,3 +667,61 @@ def test_design_loop_matches_oracle():
     assert np.all(np.abs(lg - np.array(lo)) <= 1e-4 * np.abs(lo)), (lg, lo)
     assert lo[-1] < lo[0]  # the loop descends
     assert rel_l2(h.cpu().numpy(), ho) < 1e-3
+
+
+# -------------------------------------------------------------- radial parameterisation
+@pytest.mark.parametrize("n,n_c", [(16, 1), (256, 5), (256, 9), (4096, 9)])
+def test_radial_heights_vs_oracle(n, n_c):
+    r = np.random.default_rng(9000 + n_c)
+    c = (r.standard_normal(n_c) * 3e-7).astype(np.float32)
+    h = api.radial_heights(torch.from_numpy(c).cuda(), n).cpu().numpy()
+    ref = oracle.radial_heights(c.astype(np.float64), n)
+    # double-float Horner then one rounding: within an ulp of the exact value
+    assert np.all(np.abs(h - ref) <= 2.0**-23 * np.abs(ref) + 1e-12 * np.abs(c).sum())
+
+
+@pytest.mark.parametrize("n", [64, 2048])
+def test_radial_grad_vs_oracle(n):
+    r = np.random.default_rng(9100 + n)
+    g = r.standard_normal((n, n)).astype(np.float32)
+    gt = torch.from_numpy(g).cuda()
+    got = api.radial_grad(gt, 9).cpu().numpy()
+    ref = oracle.radial_grad(g, 9)
+    s = oracle.radial_s(n)
+    scale = np.array([(np.abs(g.astype(np.float64)) * s**k).sum() for k in range(9)])
+    # float32 rounding of each result, and FP64-level summation of the terms
+    assert np.all(np.abs(got - ref) <= 2.0**-23 * np.abs(ref) + 1e-12 * scale), (got, ref)
+    assert torch.equal(api.radial_grad(gt, 9), api.radial_grad(gt, 9))  # fixed summation order
+
+
+def test_radial_design_loop_matches_oracle():
+    # radially symmetric design (Sec. 5): Adam on 9 even-polynomial coefficients towards an
+    # on-axis focus, 64^2 DOE, 2 wavelengths, 5 steps, against the same loop on the oracle
+    from paper_2505_22313_b300 import design
+
+    N, dx, z = 64, 1e-6, 2e-3
+    lams = [500e-9, 600e-9]
+    P = 2 * N
+    iters, lr0 = 5, 3e-9
+    c0 = np.zeros(9, np.float32)
+    c0[0], c0[1] = 0.6e-6, -0.3e-6
+    T = inputs.spot_target(P, N, 2, 9201, grid=1)
+    g = Geometry.make(N, dx, z, lams)
+    c, losses = design.optimize_radial(torch.from_numpy(c0).cuda(), g, torch.from_numpy(T).cuda(), iters, lr0)
+    co, mo, vo = c0.astype(np.float64), np.zeros(9), np.zeros(9)
+    lo = []
+    inf = np.inf
+    for t in range(1, iters + 1):
+        h = oracle.radial_heights(co.astype(np.float32).astype(np.float64), N).astype(np.float32)
+        gh, loss = oracle.grad(h, dx, z, lams, T)
+        lo.append(loss)
+        gc = oracle.radial_grad(gh, 9)
+        co, mo, vo = oracle.adam_step(co, gc, mo, vo, oracle.cosine_lr(lr0, t, iters), t, h_min=-inf, h_max=inf)
+    lg = losses.cpu().numpy()
+    assert np.all(np.abs(lg - np.array(lo)) <= 1e-4 * np.abs(lo)), (lg, lo)
+    assert lo[-1] < lo[0]
+    cg = c.cpu().numpy()
+    # the piston c[0] has a zero gradient (a global phase), so Adam moves it by the sign of
+    # rounding noise: compare it only up to the steps taken
+    assert rel_l2(cg[1:], co[1:]) < 1e-3
+    assert abs(cg[0] - co[0]) <= iters * lr0
