@@ -101,7 +101,7 @@ def num_threads() -> int:
 
 # ---------------------------------------------------------------- FFT
 def fft(x, inverse: bool = False) -> np.ndarray:
-    """Unnormalised 1-D DFT (sign -1 forward, +1 inverse) with the oracle's radix-2 FFT."""
+    """Unnormalised 1-D DFT (sign -1 forward, +1 inverse) with the oracle's FFT (any length)."""
     a = np.array(x, dtype=np.complex128, copy=True)
     _load().orc_fft1d(_ptr(a), a.shape[0], +1 if inverse else -1)
     return a

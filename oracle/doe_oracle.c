@@ -18,7 +18,8 @@
  *           Wirtinger calculus (the adjoint of the chain above).
  * plus the FFT convolution of an image with the PSFs used by the imaging application
  * (Sec. 5.3, Eq. 9 context) and a Rayleigh-Sommerfeld direct sum used only to pin the
- * physics.  Everything is FP64; the FFT is an iterative radix-2 written here.
+ * physics.  Everything is FP64; the FFT (iterative radix-2 for powers of two, mixed-radix
+ * decimation in time with direct prime-length DFTs otherwise) is written here.
  *
  * Layouts: arrays are row-major [row = y][col = x]; complex arrays are interleaved
  * (re, im) doubles, i.e. C99 double complex, the same memory layout as numpy complex128.
@@ -48,12 +49,48 @@ int orc_num_threads(void) {
 
 /* ------------------------------------------------------------------------------------
  * FFT.  Unnormalised DFT with kernel exp(sign * 2 pi i j k / n): sign = -1 is the
- * forward transform, sign = +1 the (unnormalised) inverse.  Iterative radix-2:
- * bit-reversal permutation, then log2(n) butterfly levels with twiddles taken from libm
- * cos/sin at each level.  n must be a power of two.
+ * forward transform, sign = +1 the (unnormalised) inverse.  A power of two n takes the
+ * iterative radix-2 path: bit-reversal permutation, then log2(n) butterfly levels with
+ * twiddles taken from libm cos/sin at each level.  Any other n takes fft_any below.
  * ---------------------------------------------------------------------------------- */
+static long smallest_factor(long n) {
+    for (long p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+/* Mixed-radix decimation in time, for any n.  With p the smallest prime factor of n and
+ * n = p m, the p interleaved subsequences y_r[j] = x[r + p j] (r < p) are transformed
+ * recursively (length m), then X[k + m q] = sum_r exp(sign 2 pi i r (k + m q) / n) Y_r[k]
+ * for k < m, q < p.  A prime n (m = 1) is a direct DFT.  Twiddle angles are reduced
+ * exactly in integers (r (k + m q) mod n) before libm cos/sin. */
+static void fft_any(cplx *x, long n, int sign) {
+    if (n <= 1) return;
+    const long p = smallest_factor(n), m = n / p;
+    cplx *y = (cplx *)malloc((size_t)n * sizeof(cplx));
+    for (long r = 0; r < p; ++r) {
+        for (long j = 0; j < m; ++j) y[r * m + j] = x[r + p * j];
+        fft_any(y + r * m, m, sign);
+    }
+    for (long q = 0; q < p; ++q)
+        for (long k = 0; k < m; ++k) {
+            const long kk = k + m * q;
+            cplx s = 0;
+            for (long r = 0; r < p; ++r) {
+                const double ang = (double)sign * 2.0 * ORC_PI * (double)((r * kk) % n) / (double)n;
+                s += (cos(ang) + I * sin(ang)) * y[r * m + k];
+            }
+            x[kk] = s;
+        }
+    free(y);
+}
+
 void orc_fft1d(cplx *x, long n, int sign) {
     if (n <= 1) return;
+    if (!is_pow2(n)) {
+        fft_any(x, n, sign);
+        return;
+    }
     for (long i = 1, j = 0; i < n; ++i) {
         long bit = n >> 1;
         for (; j & bit; bit >>= 1) j ^= bit;
@@ -77,7 +114,7 @@ void orc_fft1d(cplx *x, long n, int sign) {
 
 /* 2-D transform of a [ny][nx] array: 1-D transforms of every row, then of every column. */
 int orc_fft2d(cplx *a, long ny, long nx, int sign) {
-    if (!is_pow2(ny) || !is_pow2(nx)) return -1;
+    if (ny < 1 || nx < 1) return -1;
 #pragma omp parallel for schedule(static)
     for (long r = 0; r < ny; ++r) orc_fft1d(a + r * nx, nx, sign);
 #pragma omp parallel
@@ -232,7 +269,7 @@ static void orc_asm_inplace(cplx *a, long P, double dx, double z, double lambda,
 /* E_dest for one wavelength: e_out is [P][P], P = pad * N. */
 int orc_propagate(long N, long pad, double dx, double z, double lambda, double n_index,
                   int bandlimit, const float *h, const cplx *e_in, cplx *e_out) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N;
     cplx *e_doe = (cplx *)malloc((size_t)N * N * sizeof(cplx));
     if (!e_doe) return -2;
@@ -265,7 +302,7 @@ int orc_psf(long N, long pad, double dx, double z, double lambda, double n_index
 int orc_psf_rows(long N, long pad, double dx, double z, double lambda, double n_index,
                  int bandlimit, const float *h, const cplx *e_in, long nrows, const long *rows,
                  double *psf_rows) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
     int64_t mev = orc_mev(lambda, dx, P);
@@ -329,7 +366,7 @@ int orc_psf_rows(long N, long pad, double dx, double z, double lambda, double n_
 int orc_grad_rows(long N, long pad, double dx, double z, double lambda, double n_index,
                   int bandlimit, const float *h, const cplx *e_in, long nrows, const long *rows,
                   const float *g_rows, long nd, const long *drows, double *grad_rows) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
     int64_t mev = orc_mev(lambda, dx, P);
@@ -428,7 +465,7 @@ int orc_grad_rows(long N, long pad, double dx, double z, double lambda, double n
 int orc_grad(long N, long pad, double dx, double z, long L, const double *lambda,
              const double *n_index, int bandlimit, const float *h, const cplx *e_in,
              const float *t_or_g, int mode, double *grad, double *loss) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     cplx *e_doe = (cplx *)malloc((size_t)N * N * sizeof(cplx));
     cplx *a = (cplx *)malloc((size_t)P * P * sizeof(cplx));
@@ -472,7 +509,7 @@ int orc_grad(long N, long pad, double dx, double z, long L, const double *lambda
 int orc_loss_l2(long N, long pad, double dx, double z, long L, const double *lambda,
                 const double *n_index, int bandlimit, const double *h, const cplx *e_in,
                 const float *target, double *loss) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N;
     cplx *e_doe = (cplx *)malloc((size_t)N * N * sizeof(cplx));
     cplx *a = (cplx *)malloc((size_t)P * P * sizeof(cplx));
@@ -513,7 +550,7 @@ int orc_fd_exact(long N, long pad, double dx, double z, long L, const double *la
                  const double *n_index, int bandlimit, const float *h, const cplx *e_in,
                  const float *target, long npix, const long *pix_y, const long *pix_x, double eps,
                  double *fd) {
-    if (!is_pow2(N) || (pad != 1 && pad != 2)) return -1;
+    if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     cplx *e_doe = (cplx *)malloc((size_t)N * N * sizeof(cplx));
     cplx *e = (cplx *)malloc((size_t)P * P * sizeof(cplx));
