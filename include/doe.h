@@ -25,11 +25,12 @@
  *    doe_init(); make that first call before capturing a stream into a CUDA graph.
  *  - Return value: DOE_OK (0) or a negative DOE_E* code; nothing is launched when a call
  *    fails validation.  No C++ exception crosses this interface.
- *  - Grid: N x N DOE samples (N a power of two, 16 <= N), padded to P = pad * N per axis with
- *    the DOE at offset (P - N) / 2; output sample (y, x) lies at the same physical position
- *    as padded input sample (y, x) (the optical axis is at (P/2, P/2)).  This build supports
- *    P <= 65536; above 16384 each row / column transform is split across a thread-block
- *    cluster of P / 8192 CTAs.
+ *  - Grid: N x N DOE samples (N even, 16 <= N), padded to P = pad * N per axis with the DOE
+ *    at offset (P - N) / 2; output sample (y, x) lies at the same physical position as padded
+ *    input sample (y, x) (the optical axis is at (P/2, P/2)).  P is either a power of two
+ *    <= 65536 (above 16384 each row / column transform is split across a thread-block
+ *    cluster of P / 8192 CTAs), or P = 2^a 3^b 5^c <= 8192 (a >= 1), e.g. Table 2's 3600 x
+ *    3600 grid, which runs on a mixed-radix FFT in shared memory (no band compaction).
  */
 #ifndef DOE_H
 #define DOE_H
@@ -78,7 +79,7 @@ extern "C" {
 
 /* Geometry of one DOE evaluation (Sec. 3.1 notation). */
 typedef struct doe_geom {
-    int32_t nx, ny;        /* DOE samples per axis; powers of two, >= 16; nx == ny in this build */
+    int32_t nx, ny;        /* DOE samples per axis; even, >= 16, P = pad * nx as in the grid note above; nx == ny */
     int32_t pad;           /* 1 or 2: padded grid P = pad * n per axis (the paper's grids are 2x) */
     double dx;             /* sampling pitch [m], square pixels, > 0 */
     double z;              /* propagation distance [m], > 0 */
@@ -110,8 +111,9 @@ size_t doe_workspace_bytes(const doe_geom* g, int op);
  *   h      device float [ny/f][nx/f]      heights in metres (Eq. 1); f = 1 unless DOE_UPSAMPLE
  *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
  *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
- * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (P > 65536 or
- * nx != ny), DOE_ENOWS (workspace), DOE_ECUDA. */
+ * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (a side P that is
+ * neither a power of two <= 65536 nor 2^a 3^b 5^c <= 8192, or nx != ny), DOE_ENOWS
+ * (workspace), DOE_ECUDA. */
 int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
                   size_t ws_bytes, void* stream);
 

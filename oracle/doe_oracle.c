@@ -68,6 +68,11 @@ static void fft_any(cplx *x, long n, int sign) {
     if (n <= 1) return;
     const long p = smallest_factor(n), m = n / p;
     cplx *y = (cplx *)malloc((size_t)n * sizeof(cplx));
+    cplx *w = (cplx *)malloc((size_t)n * sizeof(cplx)); /* w[e] = exp(sign 2 pi i e / n) */
+    for (long e = 0; e < n; ++e) {
+        const double ang = (double)sign * 2.0 * ORC_PI * (double)e / (double)n;
+        w[e] = cos(ang) + I * sin(ang);
+    }
     for (long r = 0; r < p; ++r) {
         for (long j = 0; j < m; ++j) y[r * m + j] = x[r + p * j];
         fft_any(y + r * m, m, sign);
@@ -76,12 +81,10 @@ static void fft_any(cplx *x, long n, int sign) {
         for (long k = 0; k < m; ++k) {
             const long kk = k + m * q;
             cplx s = 0;
-            for (long r = 0; r < p; ++r) {
-                const double ang = (double)sign * 2.0 * ORC_PI * (double)((r * kk) % n) / (double)n;
-                s += (cos(ang) + I * sin(ang)) * y[r * m + k];
-            }
+            for (long r = 0; r < p; ++r) s += w[(r * kk) % n] * y[r * m + k];
             x[kk] = s;
         }
+    free(w);
     free(y);
 }
 

@@ -67,6 +67,39 @@ int ensure_device() {
 }
 
 bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Radices of the mixed-radix plan of an even P = 2^a 3^b 5^c <= kMrMax that is not a power of
+// two: the 5s, then the 3s, then the power of two as 8s and 4s (a single 2 only for a = 1);
+// empty when P has another factor, is odd or is too long.
+std::vector<int> mr_plan(long P) {
+  std::vector<int> r;
+  if (P < 2 || P > kMrMax || (P & 1) || is_pow2(P)) return r;
+  long n = P;
+  for (int p : {5, 3})
+    while (n % p == 0) {
+      r.push_back(p);
+      n /= p;
+    }
+  int a = 0;
+  while (n % 2 == 0) {
+    ++a;
+    n /= 2;
+  }
+  if (n != 1 || (int)r.size() + a > kMrMaxStages) return {};
+  while (a > 0) {
+    if (a == 4 || a == 2) {
+      r.push_back(4);
+      a -= 2;
+    } else if (a >= 3) {
+      r.push_back(8);
+      a -= 3;
+    } else {
+      r.push_back(2);
+      a -= 1;
+    }
+  }
+  return r;
+}
 int ilog2(long n) { int l = 0; while ((1L << l) < n) ++l; return l; }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 void split(double x, float& hi, float& lo) {
@@ -127,7 +160,7 @@ LanczosTab lanczos_table(int N, int u) {
 
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
-  if (g->nx < 16 || g->ny < 16 || !is_pow2(g->nx) || !is_pow2(g->ny)) return DOE_EINVAL;
+  if (g->nx < 16 || g->ny < 16 || (g->nx & 1) || (g->ny & 1)) return DOE_EINVAL;
   if (g->pad != 1 && g->pad != 2) return DOE_EINVAL;
   if ((long)g->pad * g->nx < (1L << kMinLog)) return DOE_EUNSUPPORTED;
   if (!(g->dx > 0.0) || !(g->z > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->z)) return DOE_EINVAL;
@@ -138,7 +171,8 @@ int check_geom(const doe_geom* g) {
   }
   if (g->nx != g->ny) return DOE_EUNSUPPORTED;
   if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
-  if ((g->nx >> upsample_log2(g)) < 4) return DOE_EINVAL;
+  if (!is_pow2((long)g->pad * g->nx) && mr_plan((long)g->pad * g->nx).empty()) return DOE_EUNSUPPORTED;
+  if ((g->nx >> upsample_log2(g)) < 4 || (g->nx & ((1 << upsample_log2(g)) - 1))) return DOE_EINVAL;
   if (!(std::fabs(g->theta_x) < 0.5 * kPi) || !(std::fabs(g->theta_y) < 0.5 * kPi) || !std::isfinite(g->src_d))
     return DOE_EINVAL;
   return DOE_OK;
@@ -153,7 +187,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   std::memset(&s, 0, sizeof(s));
   s.uf = lanczos(g) ? 0 : upsample_log2(g);  // Lanczos: the passes read pre-interpolated heights
   s.kmax = (int)kmax;
-  if (kmax >= P / 2 || P > (1L << kMaxLog)) {  // no compaction (split rows store sub-transform order)
+  if (kmax >= P / 2 || P > (1L << kMaxLog) || !is_pow2(P)) {  // no compaction (split rows: sub-transform order; mixed radix: natural)
     s.seg_a = (int)P;
     s.w = (int)P;
   } else {
@@ -190,6 +224,7 @@ struct Layout {
   size_t loss = 0;
   size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint
   std::vector<size_t> hsim;  // per request, Lanczos-3: heights interpolated onto the simulation grid
+  size_t mrtw = 0;           // mixed radix: the [P] twiddle table
 };
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
@@ -220,6 +255,10 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_r
       L.gsim = off;
       off = align256(off + (size_t)N * N * sizeof(float));
     }
+  }
+  if (!is_pow2(P)) {
+    L.mrtw = off;
+    off = align256(off + (size_t)P * sizeof(float2));
   }
   L.hsim.assign(n_req, 0);
   for (int r = 0; r < n_req; ++r)
@@ -271,6 +310,13 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
   }
   bt.total_tiles = tiles;
   bt.max_kmax = kmx;
+  if (!is_pow2(bt.P)) {
+    const std::vector<int> pl = mr_plan(bt.P);
+    bt.mr = 1;
+    bt.mr_nst = (int)pl.size();
+    for (size_t s = 0; s < pl.size(); ++s) bt.mr_radix[s] = pl[s];
+    bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
+  }
 }
 
 int ws_ok(void* ws, size_t ws_bytes, size_t need) {
@@ -281,6 +327,7 @@ int ws_ok(void* ws, size_t ws_bytes, size_t need) {
 
 int forward_passes(Batch& bt, cudaStream_t st) {
   const int lg = ilog2(bt.P);
+  if (bt.mr && launch_mr_twiddles(bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_htab(bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_pass_a(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   bt.mode = MODE_FWD;
@@ -398,6 +445,7 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   bt.grad = uf ? reinterpret_cast<float*>(static_cast<char*>(ws) + lay.gsim) : grad_h;
   const int lg = ilog2(P);
   if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
+  if (!recompute && bt.mr && launch_mr_twiddles(bt, st) != cudaSuccess) return DOE_ECUDA;
   bt.mode = mode == DOE_GRAD_L2_TARGET ? GRAD_L2 : GRAD_VJP;
   if (launch_pass_c_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   const int gmode = bt.mode;
@@ -478,7 +526,7 @@ const char* doe_pass_name(int id) {
                                         "pass_c_adjoint_rows", "pass_b_adjoint_columns", "pass_a_adjoint_rows",
                                         "loss_reduce", "render_rows", "render_columns", "render_output",
                                         "band_mask", "upsample_adjoint", "adam_step", "lanczos_upsample", "lanczos_adjoint",
-                                        "radial_heights", "radial_grad"};
+                                        "radial_heights", "radial_grad", "mixed_radix_twiddles"};
   return (id >= 0 && id < TR_COUNT) ? names[id] : "unknown";
 }
 

@@ -8,6 +8,7 @@
 #include "doe_big.cuh"
 #include "doe_kernels.cuh"
 #include "doe_launch.h"
+#include "doe_mixed.cuh"
 #include "doe_render.cuh"
 
 namespace doe {
@@ -322,6 +323,16 @@ cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st) {
   return [&]() -> cudaError_t { DOE_DISPATCH(lw, render_out_t, ra, st); }();
 }
 
+cudaError_t prep_mr() {
+  cudaError_t e;
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
+  if ((e = prep_one(mr_rows_fwd_kernel, b, kMrT)) || (e = prep_one(mr_cols_kernel, b, kMrT)) ||
+      (e = prep_one(mr_rows_out_kernel, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel, b, kMrT)) ||
+      (e = prep_one(mr_rows_adj_a_kernel, b, kMrT)))
+    return e;
+  return cudaSuccess;
+}
+
 cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = prep_t<32>()) || (e = prep_t<64>()) || (e = prep_t<128>()) ||
@@ -329,6 +340,7 @@ cudaError_t prepare_kernels() {
       (e = prep_t<4096>()) || (e = prep_t<8192>()) || (e = prep_t<16384>()) || (e = prep_big_t<4>()) ||
       (e = prep_big_t<8>()))
     return e;
+  if ((e = prep_mr())) return e;
   return cudaSuccess;
 }
 
@@ -341,11 +353,33 @@ cudaError_t launch_htab(const Batch& bt, cudaStream_t st) {
 #define DOE_BIG_ROWS(which, trace)                                          \
   if (lg == 15) { Traced tr(trace, st); return big_rows_t<4>(which, bt, st); } \
   if (lg == 16) { Traced tr(trace, st); return big_rows_t<8>(which, bt, st); }
+// Non-power-of-two sides (bt.mr): the mixed-radix passes of doe_mixed.cuh, one CTA of kMrT
+// threads per row / column pair, the whole transform in shared memory.
+// shared memory: the twiddle table plus two transform buffers
+size_t mr_smem(const Batch& bt) { return (size_t)3 * bt.P * sizeof(float2); }
+#define DOE_MR(kern, grid)                                      \
+  do {                                                          \
+    kern<<<grid, kMrT, mr_smem(bt), st>>>(bt);                  \
+    return cudaGetLastError();                                  \
+  } while (0)
+cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st) {
+  Traced tr(TR_MR_TWIDDLES, st);
+  mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.P);
+  return cudaGetLastError();
+}
 cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
+  if (bt.mr) {
+    Traced tr(TR_PASS_A, st);
+    DOE_MR(mr_rows_fwd_kernel, dim3(bt.N, bt.S));
+  }
   DOE_BIG_ROWS(0, TR_PASS_A)
   DOE_DISPATCH(lg, pass_a_t, bt, st);
 }
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
+  if (bt.mr) {
+    Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
+    DOE_MR(mr_cols_kernel, dim3(bt.P, bt.S));
+  }
   if (lg >= 15) {  // columns longer than one CTA's transform: Q = P / 8192 sub-transforms of 8192 points
     Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
     return lg == 15 ? big_cols_t<4>(bt, st) : big_cols_t<8>(bt, st);
@@ -353,14 +387,26 @@ cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
   DOE_DISPATCH(lg, pass_b_t, bt, st);
 }
 cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) {
+  if (bt.mr) {
+    Traced tr(TR_PASS_C, st);
+    DOE_MR(mr_rows_out_kernel, dim3(bt.P, bt.S));
+  }
   DOE_BIG_ROWS(1, TR_PASS_C)
   DOE_DISPATCH(lg, pass_c_t, bt, st);
 }
 cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) {
+  if (bt.mr) {
+    Traced tr(TR_PASS_C_ADJ, st);
+    DOE_MR(mr_rows_adj_c_kernel, dim3(bt.P, bt.S));
+  }
   DOE_BIG_ROWS(2, TR_PASS_C_ADJ)
   DOE_DISPATCH(lg, pass_c_adj_t, bt, st);
 }
 cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st) {
+  if (bt.mr) {
+    Traced tr(TR_PASS_A_ADJ, st);
+    DOE_MR(mr_rows_adj_a_kernel, dim3(bt.N));
+  }
   DOE_BIG_ROWS(3, TR_PASS_A_ADJ)
   DOE_DISPATCH(lg, pass_a_adj_t, bt, st);
 }

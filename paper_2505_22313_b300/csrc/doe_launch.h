@@ -10,6 +10,7 @@ namespace doe {
 cudaError_t upload_tables(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big);
 cudaError_t prepare_kernels();
 cudaError_t launch_htab(const Batch& bt, cudaStream_t st);
+cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st);
 cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st);
@@ -31,7 +32,7 @@ struct RenderArgs;
 enum : int {
   TR_HTAB = 0, TR_PASS_A, TR_PASS_B, TR_PASS_C, TR_PASS_C_ADJ, TR_PASS_B_ADJ, TR_PASS_A_ADJ, TR_LOSS,
   TR_RENDER_ROWS, TR_RENDER_COLS, TR_RENDER_OUT, TR_MASK, TR_UPSAMPLE_ADJ, TR_ADAM, TR_LANCZOS, TR_LANCZOS_ADJ,
-  TR_RADIAL, TR_RADIAL_GRAD, TR_COUNT
+  TR_RADIAL, TR_RADIAL_GRAD, TR_MR_TWIDDLES, TR_COUNT
 };
 int trace_enable(int max_records);
 int trace_read(int max, int* pass_ids, float* ms);

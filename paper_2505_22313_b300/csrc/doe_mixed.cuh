@@ -1,0 +1,328 @@
+// doe_mixed.cuh -- grids whose side P is not a power of two (P = 2^a 3^b 5^c <= 8192, P even):
+// the same propagation, PSF and adjoint as the power-of-two passes (Eq. 1-4), on a generic
+// mixed-radix FFT held in shared memory.  Table 2's 3600 x 3600 grid is of this kind.
+//
+// FFT: Stockham autosort, one stage per radix R in {2, 3, 4, 5, 8} of the host plan.  Stage
+// with Ns = product of the earlier radices: butterfly j < P/R reads x[j + r P/R] (r < R),
+// multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
+// output r to y[(j - k) R + k + r Ns].  Twiddles w_P^m = exp(-2 pi i m / P) come from a table
+// of P entries built per call in FP64 (mr_twiddle_kernel) and copied into shared memory by
+// every CTA.  Stages go out of place between two shared buffers (one barrier per stage), one
+// butterfly in registers at a time.
+//
+// Buffers (natural row-major layout, rows of P samples): tbuf holds the row spectra of the N
+// DOE rows (forward) or of all P rows (adjoint), buf the field after the column pass.
+#pragma once
+#include "doe_kernels.cuh"
+
+namespace doe {
+
+constexpr int kMrT = 256;  // threads per CTA of every mixed-radix pass
+
+// Twiddle table w_P^m, m < P, from FP64 sincospi of the exact ratio 2 m / P.
+__global__ void __launch_bounds__(256) mr_twiddle_kernel(float2* __restrict__ tw, int P) {
+  const int m = blockIdx.x * 256 + threadIdx.x;
+  if (m >= P) return;
+  double s, c;
+  sincospi(-2.0 * (double)m / (double)P, &s, &c);
+  tw[m] = make_float2((float)c, (float)s);
+}
+
+// R-point DFTs (forward kernel exp(-2 pi i n k / R); inv: exp(+...)), written from the
+// definition with the symmetric pairs folded.
+__device__ __forceinline__ float2 mr_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mr_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// -i s a (s = +1) or +i a (s = -1): the rotation shared by every odd-order term
+__device__ __forceinline__ float2 mr_rot(float2 a, float s) { return make_float2(s * a.y, -s * a.x); }
+
+template <int R>
+__device__ __forceinline__ void mr_dft(float2 (&v)[R], bool inv);
+
+template <>
+__device__ __forceinline__ void mr_dft<2>(float2 (&v)[2], bool) {
+  const float2 a = v[0], b = v[1];
+  v[0] = mr_add(a, b);
+  v[1] = mr_sub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void mr_dft<3>(float2 (&v)[3], bool inv) {
+  const float s = inv ? -1.f : 1.f;
+  const float kS3 = 0.86602540378443864676f;  // sin(2 pi / 3)
+  const float2 t1 = mr_add(v[1], v[2]);
+  const float2 t2 = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+  const float2 d = mr_rot(mr_sub(v[1], v[2]), s);  // -i s (v1 - v2)
+  v[0] = mr_add(v[0], t1);
+  v[1] = make_float2(fmaf(kS3, d.x, t2.x), fmaf(kS3, d.y, t2.y));
+  v[2] = make_float2(fmaf(-kS3, d.x, t2.x), fmaf(-kS3, d.y, t2.y));
+}
+
+template <>
+__device__ __forceinline__ void mr_dft<4>(float2 (&v)[4], bool inv) {
+  const float s = inv ? -1.f : 1.f;
+  const float2 t0 = mr_add(v[0], v[2]), t1 = mr_sub(v[0], v[2]);
+  const float2 t2 = mr_add(v[1], v[3]), t3 = mr_rot(mr_sub(v[1], v[3]), s);
+  v[0] = mr_add(t0, t2);
+  v[2] = mr_sub(t0, t2);
+  v[1] = mr_add(t1, t3);
+  v[3] = mr_sub(t1, t3);
+}
+
+template <>
+__device__ __forceinline__ void mr_dft<5>(float2 (&v)[5], bool inv) {
+  const float s = inv ? -1.f : 1.f;
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;  // cos(2 pi / 5), cos(4 pi / 5)
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;   // sin(2 pi / 5), sin(4 pi / 5)
+  const float2 a1 = mr_add(v[1], v[4]), b1 = mr_sub(v[1], v[4]);
+  const float2 a2 = mr_add(v[2], v[3]), b2 = mr_sub(v[2], v[3]);
+  const float2 x0 = v[0];
+  // X1, X4 = x0 + c1 a1 + c2 a2 -+ i s (s1 b1 + s2 b2); X2, X3 = x0 + c2 a1 + c1 a2 -+ i s (s2 b1 - s1 b2)
+  const float2 p1 = make_float2(fmaf(c2, a2.x, fmaf(c1, a1.x, x0.x)), fmaf(c2, a2.y, fmaf(c1, a1.y, x0.y)));
+  const float2 p2 = make_float2(fmaf(c1, a2.x, fmaf(c2, a1.x, x0.x)), fmaf(c1, a2.y, fmaf(c2, a1.y, x0.y)));
+  const float2 q1 = mr_rot(make_float2(fmaf(s2, b2.x, s1 * b1.x), fmaf(s2, b2.y, s1 * b1.y)), s);
+  const float2 q2 = mr_rot(make_float2(fmaf(-s1, b2.x, s2 * b1.x), fmaf(-s1, b2.y, s2 * b1.y)), s);
+  v[0] = mr_add(x0, mr_add(a1, a2));
+  v[1] = mr_add(p1, q1);
+  v[4] = mr_sub(p1, q1);
+  v[2] = mr_add(p2, q2);
+  v[3] = mr_sub(p2, q2);
+}
+
+template <>
+__device__ __forceinline__ void mr_dft<8>(float2 (&v)[8], bool inv) {
+  // two 4-point DFTs (even and odd inputs), combined with w_8^k
+  const float s = inv ? -1.f : 1.f;
+  const float kH = 0.70710678118654752440f;  // sqrt(1/2)
+  float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  mr_dft<4>(e, inv);
+  mr_dft<4>(o, inv);
+  // w_8 = sqrt(1/2) (1 - i s), w_8^2 = -i s, w_8^3 = sqrt(1/2) (-1 - i s)
+  const float2 o1 = make_float2(kH * (o[1].x + s * o[1].y), kH * (o[1].y - s * o[1].x));
+  const float2 o2 = mr_rot(o[2], s);
+  const float2 o3 = make_float2(kH * (-o[3].x + s * o[3].y), kH * (-o[3].y - s * o[3].x));
+  v[0] = mr_add(e[0], o[0]);
+  v[4] = mr_sub(e[0], o[0]);
+  v[1] = mr_add(e[1], o1);
+  v[5] = mr_sub(e[1], o1);
+  v[2] = mr_add(e[2], o2);
+  v[6] = mr_sub(e[2], o2);
+  v[3] = mr_add(e[3], o3);
+  v[7] = mr_sub(e[3], o3);
+}
+
+// One Stockham stage of radix R: src -> dst (both P samples of shared memory), see the file
+// comment; ends with a barrier so that dst is visible.  One butterfly in registers at a time.
+template <int R>
+__device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, int Ns, const float2* tw, bool inv,
+                                         int t) {
+  const int nb = P / R, step = P / (Ns * R);
+#pragma unroll 2
+  for (int j = t; j < nb; j += kMrT) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+    const int k = j % Ns;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[r * k * step];  // r k step < P
+      if (inv) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+    mr_dft<R>(v, inv);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+
+// Unnormalised transform of the P samples at a (shared memory; b is a second buffer of P) with
+// the batch's plan and the twiddles tw (shared memory).  The caller has made a's contents
+// visible (barrier).  Returns the buffer holding the result (a or b).
+__device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t) {
+  const int P = bt.P;
+  int Ns = 1;
+  for (int s = 0; s < bt.mr_nst; ++s) {
+    const int R = bt.mr_radix[s];
+    if (R == 8) mr_stage<8>(a, b, P, Ns, tw, inv, t);
+    else if (R == 5) mr_stage<5>(a, b, P, Ns, tw, inv, t);
+    else if (R == 4) mr_stage<4>(a, b, P, Ns, tw, inv, t);
+    else if (R == 3) mr_stage<3>(a, b, P, Ns, tw, inv, t);
+    else mr_stage<2>(a, b, P, Ns, tw, inv, t);
+    Ns *= R;
+    float2* c = a;
+    a = b;
+    b = c;
+  }
+  return a;
+}
+
+// Shared memory of a mixed-radix CTA: the twiddle table, then two transform buffers (3 P
+// samples).  Copies the table in; the caller's first barrier publishes it.
+__device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t) {
+  for (int m = t; m < bt.P; m += kMrT) sm[m] = __ldg(bt.mr_tw + m);
+  return sm + bt.P;
+}
+
+// E_doe of Eq. 2 at DOE sample (i, x): transmittance, parametric incident field, E_in array.
+__device__ __forceinline__ float2 mr_doe_field(const Slice& sl, const float* hrow, int i, int x, int N, IncRow ir) {
+  const float hv = __ldg(hrow + (x >> sl.uf));
+  float2 e = sl.illum ? transmittance_inc(hv, sl, ir, x - N / 2) : transmittance(hv, sl.kp_hi, sl.kp_lo);
+  if (sl.e_in) e = cmul(e, __ldg(sl.e_in + (size_t)i * N + x));
+  return e;
+}
+
+// Band-limited transfer function at column frequency index kc, row index lr (FFT order), from
+// the slice's quarter table; conjugated for the adjoint.  H depends on kt^2 + lt^2 only, so
+// the column's values are read along a table row (contiguous in lr).
+__device__ __forceinline__ float2 mr_transfer(const Slice& sl, int kc, int lr, int P, bool conj_h) {
+  const int a = abs_signed(kc, P), b = abs_signed(lr, P);
+  if (a > sl.kmax || b > sl.kmax) return make_float2(0.f, 0.f);
+  float2 h = __ldg(sl.htab + (size_t)a * sl.hp + b);
+  if (conj_h) h.y = -h.y;
+  return h;
+}
+
+// ---- pass A (mixed radix): DOE row i of slice blockIdx.y -> its row spectrum, tbuf row i.
+__global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ float2 sm_mr[];
+  const Slice& sl = bt.s[blockIdx.y];
+  const int i = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
+  const float2* tw = sm_mr;
+  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xb = xa + P;
+  const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
+  const IncRow ir = incident_row(sl, i - N / 2);
+  for (int c = t; c < P; c += kMrT) {
+    const int x = c - off;
+    xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, hrow, i, x, N, ir) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  float2* dst = sl.tbuf + (size_t)i * P;
+  for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
+}
+
+// ---- pass B / B* (mixed radix): one column kc per CTA.  Forward: the N row spectra (tbuf rows
+// 0..N-1) placed at rows off..off+N-1, FFT, x H, IFFT, all P rows to buf.  Adjoint
+// (bt.mode == MODE_ADJ): all P rows of tbuf, FFT, x conj(H), IFFT, rows off..off+N-1 back to
+// tbuf rows 0..N-1 (in place: the CTA owns its column).  Neighbouring CTAs read the other
+// samples of each 32-byte sector, which they find in L2.
+__global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ float2 sm_mr[];
+  const Slice& sl = bt.s[blockIdx.y];
+  const int kc = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
+  const bool adj = bt.mode == MODE_ADJ;
+  const float2* tw = sm_mr;
+  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xb = xa + P;
+  for (int l = t; l < P; l += kMrT) {
+    const int r = adj ? l : l - off;
+    xa[l] = (unsigned)r < (unsigned)(adj ? P : N) ? __ldcs(sl.tbuf + (size_t)r * P + kc) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  float2* z = y == xa ? xb : xa;
+  for (int l = t; l < P; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, P, adj));
+  __syncthreads();
+  y = mr_fft(y, z, bt, tw, true, t);
+  if (!adj) {
+    for (int l = t; l < P; l += kMrT) __stcs(sl.buf + (size_t)l * P + kc, y[l]);
+  } else {
+    for (int r = t; r < N; r += kMrT) __stcs(sl.tbuf + (size_t)r * P + kc, y[r + off]);
+  }
+}
+
+// ---- pass C (mixed radix): output row y: IFFT, 1/P^2, then |E|^2 (OUT_PSF) or E.
+__global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ float2 sm_mr[];
+  const Slice& sl = bt.s[blockIdx.y];
+  const int row = blockIdx.x, t = threadIdx.x, P = bt.P;
+  const float2* tw = sm_mr;
+  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xb = xa + P;
+  const float2* src = sl.buf + (size_t)row * P;
+  for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+  __syncthreads();
+  const float2* y = mr_fft(xa, xb, bt, tw, true, t);
+  const float s = bt.inv_p2;
+  if (bt.mode == OUT_PSF) {
+    float* dst = static_cast<float*>(sl.out) + (size_t)row * P;
+    for (int c = t; c < P; c += kMrT) {
+      const float2 e = cscale(y[c], s);
+      __stcs(dst + c, fmaf(e.x, e.x, e.y * e.y));
+    }
+  } else {
+    float2* dst = static_cast<float2*>(sl.out) + (size_t)row * P;
+    for (int c = t; c < P; c += kMrT) __stcs(dst + c, cscale(y[c], s));
+  }
+}
+
+// ---- pass C' (mixed radix): output row y: E = IFFT / P^2, g = 2 (I - T) E (L2, with the row's
+// loss partial) or (dL/dI) E (VJP), forward FFT of g into tbuf row y.
+__global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ float2 sm_mr[];
+  __shared__ double red[32];
+  const Slice& sl = bt.s[blockIdx.y];
+  const int row = blockIdx.x, t = threadIdx.x, P = bt.P;
+  const float2* tw = sm_mr;
+  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xb = xa + P;
+  const float2* src = sl.buf + (size_t)row * P;
+  for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+  __syncthreads();
+  float2* y = mr_fft(xa, xb, bt, tw, true, t);
+  const float s = bt.inv_p2;
+  const float* trow = sl.tgt + (size_t)row * P;
+  float acc = 0.f;
+  for (int c = t; c < P; c += kMrT) {
+    const float2 e = cscale(y[c], s);
+    const float tt = __ldcs(trow + c);
+    float w;
+    if (bt.mode == GRAD_L2) {
+      const float d = fmaf(e.x, e.x, e.y * e.y) - tt;
+      acc = fmaf(d, d, acc);
+      w = 2.f * d;
+    } else {
+      w = tt;
+    }
+    y[c] = cscale(e, w);
+  }
+  __syncthreads();
+  y = mr_fft(y, y == xa ? xb : xa, bt, tw, false, t);
+  float2* dst = sl.tbuf + (size_t)row * P;
+  for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
+  const double tot = block_sum<kMrT>((double)acc, red);
+  if (t == 0 && sl.loss_part) sl.loss_part[row] = tot;
+}
+
+// ---- pass A* (mixed radix): DOE row i, summed over the slices in order: g_doe = IFFT(tbuf
+// row i) / P^2 on the DOE columns, dL/dh += -2 k' Im(conj(g_doe) E_doe).  Each thread owns its
+// DOE columns, so the running sum lives in the gradient row itself.
+__global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ float2 sm_mr[];
+  const int i = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
+  const float2* tw = sm_mr;
+  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xb = xa + P;
+  float* grow = bt.grad + (size_t)i * N;
+  for (int j = 0; j < bt.S; ++j) {
+    const Slice& sl = bt.s[j];
+    const float2* src = sl.tbuf + (size_t)i * P;
+    for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+    __syncthreads();
+    const float2* y = mr_fft(xa, xb, bt, tw, true, t);
+    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
+    const IncRow ir = incident_row(sl, i - N / 2);
+    const float k2 = -2.f * sl.kp_hi;
+    for (int x = t; x < N; x += kMrT) {
+      const float2 e = mr_doe_field(sl, hrow, i, x, N, ir);
+      const float2 g = cscale(y[off + x], bt.inv_p2);
+      const float prev = j ? grow[x] : 0.f;
+      grow[x] = fmaf(k2, fmaf(g.x, e.y, -g.y * e.x), prev);
+    }
+    __syncthreads();  // xa / xb are reused by the next slice
+  }
+}
+
+}  // namespace doe

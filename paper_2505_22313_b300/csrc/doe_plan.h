@@ -70,6 +70,8 @@ constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
 constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
 constexpr int kTile = 4;    // tile width of the column-tiled buffer (4 x 8 B = one 32-byte sector); columns per cluster for P <= 8192
 constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536 = 8 x 8192)
+constexpr int kMrMax = 8192;        // longest mixed-radix (non-power-of-two) transform, one CTA
+constexpr int kMrMaxStages = 16;    // radix stages of a mixed-radix plan
 constexpr int kMaxRadial = 9;       // coefficients of the radial height polynomial (degree 16 in rho / R)
 constexpr int kRadialBlocks = 592;  // CTAs of the radial gradient reduction (4 per SM)
 
@@ -126,6 +128,10 @@ struct Batch {
   int max_kmax;      // largest kmax over the slices (table builder grid)
   int qf;            // sub-transforms per row: P / 16384 for P > 16384, else 1
   int illum;         // some slice has a parametric incident field (selects the DOE-row kernels)
+  int mr;            // P is not a power of two: the mixed-radix passes run
+  int mr_nst;        // mixed-radix plan: stages and their radices (2, 3, 4, 5 or 8)
+  int mr_radix[kMrMaxStages];
+  const float2* mr_tw;  // [P] twiddles exp(-2 pi i m / P) in the workspace
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
   Slice s[kMaxSlices];

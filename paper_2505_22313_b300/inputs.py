@@ -53,12 +53,13 @@ def heights(N: int, seed: int, hmax: float = HMAX, sigma: float = 2.0, radius: i
     out = np.empty((N, N), np.float32)
     B = min(N, 256)
     for r0 in range(0, N, B):
-        idx = np.arange(r0 - radius, r0 + B + radius) % N
+        b = min(B, N - r0)  # the last block is shorter when B does not divide N
+        idx = np.arange(r0 - radius, r0 + b + radius) % N
         blk = _smooth_rows_periodic(raw[idx].astype(np.float64), w)
         from scipy.ndimage import correlate1d
 
-        acc = correlate1d(blk, w, axis=0, mode="constant")[radius:radius + B]
-        out[r0:r0 + B] = acc.astype(np.float32)
+        acc = correlate1d(blk, w, axis=0, mode="constant")[radius:radius + b]
+        out[r0:r0 + b] = acc.astype(np.float32)
     mn = float(out.min())
     mx = float(out.max())
     scale = hmax / (mx - mn)

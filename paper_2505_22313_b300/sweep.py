@@ -1,6 +1,6 @@
 """Per-configuration timing of the library's passes (PSF and gradient).
 
-    python -m paper_2505_22313_b300.sweep [--configs small,rgb,gradient,large_area,wiener] [--reps K]
+    python -m paper_2505_22313_b300.sweep [--configs small,rgb,gradient,large_area,wiener,design_table2_3600] [--reps K]
 
 Each configuration runs the PSF (and, where listed, the L2 gradient against the spot-array
 target with recomputed fields) K times after warm-up, timed with CUDA events on the current
@@ -24,6 +24,9 @@ CONFIGS = {
     "large_area": (32768, 1e-6, 100e-3, [550e-9], True),
     # the RGB geometry designed on a 1024^2 layout at 4 um, nearest-upsampled 4x in pass A
     "rgb_layout4": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 4),
+    # Table 2's 3600 x 3600 grid: a 3.6 mm DOE at 2 um, 520.6 nm, hologram plane at 10 mm
+    # (mixed-radix transforms)
+    "table2_3600": (1800, 2e-6, 10e-3, [520.6e-9], True),
     # the RGB geometry lit by a tilted wave converging to 200 mm (evaluated in the DOE-row passes)
     "rgb_tilted_converging": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 1,
                               dict(theta_x=0.01, theta_y=-0.005, src_d=-0.2)),
@@ -157,7 +160,8 @@ def main():
         if name == "wiener":
             row = run_wiener(args.reps)
         elif name.startswith("design"):
-            row = run_design(args.reps)
+            # "design" times the gradient workload; "design_<config>" any configuration
+            row = run_design(args.reps, name[len("design_"):] if name.startswith("design_") else "gradient")
         else:
             row = run(name, args.reps, grad=not args.no_grad)
         print(json.dumps(row), flush=True)

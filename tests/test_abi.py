@@ -72,8 +72,9 @@ def _geom(**kw):
 
 @pytest.mark.parametrize(
     "g",
-    [_geom(N=48), _geom(N=8), _geom(dx=0.0), _geom(z=-1.0), _geom(lambdas=[0.0]), _geom(n_index=0.5),
-     _geom(lambdas=np.full(65, 5e-7))],
+    [_geom(N=49), _geom(N=8), _geom(N=42), _geom(N=4200), _geom(N=5000), _geom(N=134),
+     _geom(dx=0.0), _geom(z=-1.0), _geom(lambdas=[0.0]), _geom(n_index=0.5), _geom(lambdas=np.full(65, 5e-7)),
+     _geom(N=180, upsample=8)],
 )
 def test_invalid_geometry_rejected(lib, g):
     c = g.c()
@@ -118,3 +119,14 @@ def test_null_pointers_and_bad_mode(lib):
 def test_strerror(lib):
     for code in (0, -1, -2, -3, -4, -5, -99):
         assert lib.doe_strerror(code)
+
+
+@pytest.mark.parametrize("N,pad", [(48, 2), (180, 2), (1800, 2), (3600, 1), (4000, 2), (4050, 2), (360, 1)])
+def test_mixed_radix_sizes_accepted(lib, N, pad):
+    # even N with P = pad N = 2^a 3^b 5^c <= 8192 (Table 2's 3600 grid among them)
+    c = _geom(N=N, pad=pad).c()
+    P = pad * N
+    need = lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_PSF)
+    assert need >= P * P * 8 + N * P * 8  # natural-layout field buffers, no band compaction
+    cg = _geom(N=N, pad=pad, lambdas=[450e-9, 650e-9]).c()
+    assert lib.doe_workspace_bytes(ctypes.byref(cg), L.DOE_OP_GRAD) > 2 * need - 2 * N * P * 8

@@ -725,3 +725,81 @@ def test_radial_design_loop_matches_oracle():
     # rounding noise: compare it only up to the steps taken
     assert rel_l2(cg[1:], co[1:]) < 1e-3
     assert abs(cg[0] - co[0]) <= iters * lr0
+
+
+# -------------------------------------------------------------- non-power-of-two grids
+@pytest.mark.parametrize("N,pad", [(24, 2), (90, 2), (180, 2), (360, 1), (1500, 2)])
+def test_mixed_radix_propagate_vs_oracle(N, pad):
+    # P = 48, 180, 360, 360, 3000: radix 2, 3, 4, 5, 8 stages
+    dx, z, lam = 1e-6, 2e-3, 550e-9
+    h = _h(N, 9500 + N)
+    g = Geometry.make(N, dx, z, [lam], pad=pad)
+    E = api.propagate(torch.from_numpy(h).cuda(), g).cpu().numpy()[0]
+    ref = oracle.propagate(h, dx, z, lam, pad=pad)
+    assert rel_l2(E, ref) < TOL_PSF, rel_l2(E, ref)
+
+
+@pytest.mark.parametrize("N,pad,bandlimit", [(180, 2, True), (360, 1, True), (180, 2, False)])
+def test_mixed_radix_psf_and_grad_vs_oracle(N, pad, bandlimit):
+    dx, z = 0.5e-6, 2e-3
+    lams = [450e-9, 550e-9, 650e-9]
+    P = pad * N
+    h = _h(N, 9600 + N)
+    T = inputs.spot_target(P, N, 3, 9700 + N)
+    g = Geometry.make(N, dx, z, lams, pad=pad, bandlimit=bandlimit)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    ref = oracle.psf(h, dx, z, lams, pad=pad, bandlimit=bandlimit)
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    gref, lref = oracle.grad(h, dx, z, lams, T, pad=pad, bandlimit=bandlimit)
+    for recompute in (True, False):
+        ws = None
+        if not recompute:
+            ws = api.workspace(api.workspace_bytes(g, 3))
+            api.psf(ht, g, ws=ws)
+        gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda(), recompute=recompute, ws=ws)
+        err = rel_l2(gr.cpu().numpy(), gref)
+        assert err < TOL_GRAD, err
+        assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_mixed_radix_table2_grid_3600():
+    # Table 2's first grid: a 3.6 mm DOE at 2 um (1800^2), padded to 3600 x 3600, 520.6 nm
+    # laser (Sec. 4's toy example), hologram plane at 10 mm: PSF and L2 gradient vs the oracle
+    N, dx, z, lam = 1800, 2e-6, 10e-3, 520.6e-9
+    P = 2 * N
+    h = _h(N, 9800)
+    T = inputs.flat_top_target(P, N, 1)
+    g = Geometry.make(N, dx, z, [lam])
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    assert rel_l2(I, oracle.psf(h, dx, z, [lam])) < TOL_PSF
+    gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
+    gref, lref = oracle.grad(h, dx, z, [lam], T)
+    assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_mixed_radix_with_upsampling_illumination_and_batching():
+    # 45^2 layout, 4x nearest-upsampled onto a 180^2 DOE, 360^2 grid, tilted converging wave;
+    # Lanczos-3 variant; and three requests of one grid in one batched launch
+    N, f, dx, z = 180, 4, 0.5e-6, 2e-3
+    lams = [500e-9, 620e-9]
+    kw = dict(theta_x=0.05, src_d=-3e-3)
+    hl = _h(N // f, 9900)
+    T = inputs.spot_target(2 * N, N, 2, 9901)
+    for lanczos in (False, True):
+        hs = oracle.upsample_lanczos3(hl, f) if lanczos else oracle.upsample_nearest(hl, f)
+        g = Geometry.make(N, dx, z, lams, upsample=f, lanczos=lanczos, **kw)
+        I = api.psf(torch.from_numpy(hl).cuda(), g).cpu().numpy()
+        gr, loss = api.grad(torch.from_numpy(hl).cuda(), g, torch.from_numpy(T).cuda())
+        Iref, gref, lref = _illum_oracle(hs, N, dx, z, lams, kw, T)
+        assert rel_l2(I, Iref) < TOL_PSF, rel_l2(I, Iref)
+        lg = oracle.layout_grad_lanczos3(gref, f) if lanczos else oracle.layout_grad(gref, f)
+        assert rel_l2(gr.cpu().numpy(), lg) < TOL_GRAD
+        assert abs(loss.item() - lref) <= 1e-5 * lref
+    hs3 = [torch.from_numpy(_h(N, 9910 + k)).cuda() for k in range(3)]
+    gs = [Geometry.make(N, dx, z, [500e-9]), Geometry.make(N, dx, 3e-3, [600e-9, 700e-9]),
+          Geometry.make(N, dx, z, [450e-9], theta_y=0.02)]
+    for h, gg, m in zip(hs3, gs, api.psf_many(hs3, gs)):
+        assert torch.equal(m, api.psf(h, gg))
