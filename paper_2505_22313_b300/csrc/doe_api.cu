@@ -68,13 +68,12 @@ int ensure_device() {
 
 bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Radices of the mixed-radix plan of an even P = 2^a 3^b 5^c <= kMrMax that is not a power of
-// two: the 5s, then the 3s, then the power of two as 8s and 4s (a single 2 only for a = 1);
-// empty when P has another factor, is odd or is too long.
-std::vector<int> mr_plan(long P) {
+// Radices of the mixed-radix plan of a length M = 2^a 3^b 5^c <= kMrMax (M >= 2): the 5s, then
+// the 3s, then the power of two as 8s and 4s (a single 2 only for a = 1); empty for any other M.
+std::vector<int> mr_radices(long M) {
   std::vector<int> r;
-  if (P < 2 || P > kMrMax || (P & 1) || is_pow2(P)) return r;
-  long n = P;
+  if (M < 2 || M > kMrMax) return r;
+  long n = M;
   for (int p : {5, 3})
     while (n % p == 0) {
       r.push_back(p);
@@ -100,6 +99,21 @@ std::vector<int> mr_plan(long P) {
   }
   return r;
 }
+
+// Split of a non-power-of-two side P into Q CTAs of M = P / Q points: Q = 1 up to kMrMax
+// (P even), else the first of Q = 8, 5, 4, 3, 2 that divides P with a supported M <= kMrMax.
+// {0, 0} when P is unsupported.
+struct MrSplit {
+  int Q, M;
+};
+MrSplit mr_split(long P) {
+  if (P < 2 || (P & 1) || is_pow2(P) || P > (1L << kBigLog)) return {0, 0};
+  if (P <= kMrMax) return mr_radices(P).empty() ? MrSplit{0, 0} : MrSplit{1, (int)P};
+  for (int q : {8, 5, 4, 3, 2})
+    if (P % q == 0 && P / q <= kMrMax && !mr_radices(P / q).empty()) return {q, (int)(P / q)};
+  return {0, 0};
+}
+
 int ilog2(long n) { int l = 0; while ((1L << l) < n) ++l; return l; }
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 void split(double x, float& hi, float& lo) {
@@ -171,7 +185,7 @@ int check_geom(const doe_geom* g) {
   }
   if (g->nx != g->ny) return DOE_EUNSUPPORTED;
   if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
-  if (!is_pow2((long)g->pad * g->nx) && mr_plan((long)g->pad * g->nx).empty()) return DOE_EUNSUPPORTED;
+  if (!is_pow2((long)g->pad * g->nx) && mr_split((long)g->pad * g->nx).Q == 0) return DOE_EUNSUPPORTED;
   if ((g->nx >> upsample_log2(g)) < 4 || (g->nx & ((1 << upsample_log2(g)) - 1))) return DOE_EINVAL;
   if (!(std::fabs(g->theta_x) < 0.5 * kPi) || !(std::fabs(g->theta_y) < 0.5 * kPi) || !std::isfinite(g->src_d))
     return DOE_EINVAL;
@@ -224,7 +238,8 @@ struct Layout {
   size_t loss = 0;
   size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint
   std::vector<size_t> hsim;  // per request, Lanczos-3: heights interpolated onto the simulation grid
-  size_t mrtw = 0;           // mixed radix: the [P] twiddle table
+  size_t mrtw = 0;           // mixed radix: the [M] twiddle table of the per-CTA transform
+  size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
 };
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
@@ -257,8 +272,13 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_r
     }
   }
   if (!is_pow2(P)) {
+    const MrSplit sp = mr_split(P);
     L.mrtw = off;
-    off = align256(off + (size_t)P * sizeof(float2));
+    off = align256(off + (size_t)sp.M * sizeof(float2));
+    if (sp.Q > 1) {
+      L.mrtwP = off;
+      off = align256(off + (size_t)P * sizeof(float2));
+    }
   }
   L.hsim.assign(n_req, 0);
   for (int r = 0; r < n_req; ++r)
@@ -311,11 +331,16 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
   bt.total_tiles = tiles;
   bt.max_kmax = kmx;
   if (!is_pow2(bt.P)) {
-    const std::vector<int> pl = mr_plan(bt.P);
+    const MrSplit sp = mr_split(bt.P);
+    const std::vector<int> pl = mr_radices(sp.M);
     bt.mr = 1;
+    bt.mr_Q = sp.Q;
+    bt.mr_M = sp.M;
+    bt.qf = sp.Q;  // split rows write one loss partial per CTA
     bt.mr_nst = (int)pl.size();
     for (size_t s = 0; s < pl.size(); ++s) bt.mr_radix[s] = pl[s];
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
+    if (sp.Q > 1) bt.mr_twP = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP);
   }
 }
 

@@ -9,6 +9,7 @@
 #include "doe_kernels.cuh"
 #include "doe_launch.h"
 #include "doe_mixed.cuh"
+#include "doe_mixed_big.cuh"
 #include "doe_render.cuh"
 
 namespace doe {
@@ -323,12 +324,25 @@ cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st) {
   return [&]() -> cudaError_t { DOE_DISPATCH(lw, render_out_t, ra, st); }();
 }
 
+template <int Q>
+cudaError_t prep_mrq_t() {
+  cudaError_t e;
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);
+  if ((e = prep_one(mrq_rows_fwd_kernel<Q>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_out_kernel<Q>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_adj_a_kernel<Q>, b, kMrT)))
+    return e;
+  return cudaSuccess;
+}
 cudaError_t prep_mr() {
   cudaError_t e;
   constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
   if ((e = prep_one(mr_rows_fwd_kernel, b, kMrT)) || (e = prep_one(mr_cols_kernel, b, kMrT)) ||
       (e = prep_one(mr_rows_out_kernel, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel, b, kMrT)) ||
       (e = prep_one(mr_rows_adj_a_kernel, b, kMrT)))
+    return e;
+  if ((e = prep_mrq_t<2>()) || (e = prep_mrq_t<3>()) || (e = prep_mrq_t<4>()) || (e = prep_mrq_t<5>()) ||
+      (e = prep_mrq_t<8>()))
     return e;
   return cudaSuccess;
 }
@@ -363,13 +377,46 @@ size_t mr_smem(const Batch& bt) { return (size_t)3 * bt.P * sizeof(float2); }
     return cudaGetLastError();                                  \
   } while (0)
 cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st) {
+  {
+    Traced tr(TR_MR_TWIDDLES, st);
+    mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || bt.mr_Q == 1) return e;
+  }
   Traced tr(TR_MR_TWIDDLES, st);
-  mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.P);
+  mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_twP), bt.P);
   return cudaGetLastError();
 }
+// Split sides (bt.mr_Q > 1): cluster launches of doe_mixed_big.cuh.  which: 0 rows forward (A),
+// 1 columns (B / B*), 2 rows out (C), 3 rows adjoint (C'), 4 DOE-row adjoint (A*).
+template <int Q>
+cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
+  const void* fn = which == 0   ? (const void*)mrq_rows_fwd_kernel<Q>
+                   : which == 1 ? (const void*)mrq_cols_kernel<Q>
+                   : which == 2 ? (const void*)mrq_rows_out_kernel<Q>
+                   : which == 3 ? (const void*)mrq_rows_adj_c_kernel<Q>
+                                : (const void*)mrq_rows_adj_a_kernel<Q>;
+  const int lines = (which == 0 || which == 4) ? bt.N : bt.P;
+  void* args[] = {const_cast<Batch*>(&bt)};
+  return launch_cluster(fn, dim3(lines * Q, which == 4 ? 1 : bt.S), Q, (size_t)3 * bt.mr_M * sizeof(float2), st,
+                        args, kMrT);
+}
+cudaError_t mrq_dispatch(int which, const Batch& bt, cudaStream_t st) {
+  switch (bt.mr_Q) {
+    case 2: return mrq_launch<2>(which, bt, st);
+    case 3: return mrq_launch<3>(which, bt, st);
+    case 4: return mrq_launch<4>(which, bt, st);
+    case 5: return mrq_launch<5>(which, bt, st);
+    case 8: return mrq_launch<8>(which, bt, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#define DOE_MRQ(which)                                      \
+  if (bt.mr_Q > 1) return mrq_dispatch(which, bt, st)
 cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
   if (bt.mr) {
     Traced tr(TR_PASS_A, st);
+    DOE_MRQ(0);
     DOE_MR(mr_rows_fwd_kernel, dim3(bt.N, bt.S));
   }
   DOE_BIG_ROWS(0, TR_PASS_A)
@@ -378,6 +425,7 @@ cudaError_t launch_pass_a(int lg, const Batch& bt, cudaStream_t st) {
 cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
   if (bt.mr) {
     Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
+    DOE_MRQ(1);
     DOE_MR(mr_cols_kernel, dim3(bt.P, bt.S));
   }
   if (lg >= 15) {  // columns longer than one CTA's transform: Q = P / 8192 sub-transforms of 8192 points
@@ -389,6 +437,7 @@ cudaError_t launch_pass_b(int lg, const Batch& bt, cudaStream_t st) {
 cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) {
   if (bt.mr) {
     Traced tr(TR_PASS_C, st);
+    DOE_MRQ(2);
     DOE_MR(mr_rows_out_kernel, dim3(bt.P, bt.S));
   }
   DOE_BIG_ROWS(1, TR_PASS_C)
@@ -397,6 +446,7 @@ cudaError_t launch_pass_c(int lg, const Batch& bt, cudaStream_t st) {
 cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) {
   if (bt.mr) {
     Traced tr(TR_PASS_C_ADJ, st);
+    DOE_MRQ(3);
     DOE_MR(mr_rows_adj_c_kernel, dim3(bt.P, bt.S));
   }
   DOE_BIG_ROWS(2, TR_PASS_C_ADJ)
@@ -405,6 +455,7 @@ cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st) {
 cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st) {
   if (bt.mr) {
     Traced tr(TR_PASS_A_ADJ, st);
+    DOE_MRQ(4);
     DOE_MR(mr_rows_adj_a_kernel, dim3(bt.N));
   }
   DOE_BIG_ROWS(3, TR_PASS_A_ADJ)

@@ -140,7 +140,7 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
 // the batch's plan and the twiddles tw (shared memory).  The caller has made a's contents
 // visible (barrier).  Returns the buffer holding the result (a or b).
 __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t) {
-  const int P = bt.P;
+  const int P = bt.mr_M;  // the transform length: P, or the chunk length M of a split transform
   int Ns = 1;
   for (int s = 0; s < bt.mr_nst; ++s) {
     const int R = bt.mr_radix[s];
@@ -157,11 +157,12 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
   return a;
 }
 
-// Shared memory of a mixed-radix CTA: the twiddle table, then two transform buffers (3 P
-// samples).  Copies the table in; the caller's first barrier publishes it.
+// Shared memory of a mixed-radix CTA: the twiddle table, then two transform buffers (3 M
+// samples, M = bt.mr_M the length each CTA transforms).  Copies the table in; the caller's
+// first barrier publishes it.
 __device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t) {
-  for (int m = t; m < bt.P; m += kMrT) sm[m] = __ldg(bt.mr_tw + m);
-  return sm + bt.P;
+  for (int m = t; m < bt.mr_M; m += kMrT) sm[m] = __ldg(bt.mr_tw + m);
+  return sm + bt.mr_M;
 }
 
 // E_doe of Eq. 2 at DOE sample (i, x): transmittance, parametric incident field, E_in array.

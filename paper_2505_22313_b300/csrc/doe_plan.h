@@ -129,9 +129,11 @@ struct Batch {
   int qf;            // sub-transforms per row: P / 16384 for P > 16384, else 1
   int illum;         // some slice has a parametric incident field (selects the DOE-row kernels)
   int mr;            // P is not a power of two: the mixed-radix passes run
-  int mr_nst;        // mixed-radix plan: stages and their radices (2, 3, 4, 5 or 8)
+  int mr_Q, mr_M;    // P = Q M: Q CTAs (a cluster) per row / column, each transforming M points (Q = 1: M = P)
+  int mr_nst;        // mixed-radix plan of M: stages and their radices (2, 3, 4, 5 or 8)
   int mr_radix[kMrMaxStages];
-  const float2* mr_tw;  // [P] twiddles exp(-2 pi i m / P) in the workspace
+  const float2* mr_tw;   // [M] twiddles exp(-2 pi i m / M) in the workspace
+  const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
   Slice s[kMaxSlices];

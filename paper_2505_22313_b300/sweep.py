@@ -27,6 +27,12 @@ CONFIGS = {
     # Table 2's 3600 x 3600 grid: a 3.6 mm DOE at 2 um, 520.6 nm, hologram plane at 10 mm
     # (mixed-radix transforms)
     "table2_3600": (1800, 2e-6, 10e-3, [520.6e-9], True),
+    # Table 2's CHD / beam-shaping grid: the 1800^2 design at 2 um upsampled 8x onto 14400^2 at
+    # 0.25 um, padded to 28800 x 28800 (clusters of 8 CTAs of 3600 points)
+    "table2_28800": (14400, 0.25e-6, 10e-3, [520.6e-9], True, 8),
+    # Table 2's broadband-imaging grid: a 10 mm DOE at 0.5 um (20000^2) padded to 40000 x 40000,
+    # six wavelengths over 400-700 nm (clusters of 8 CTAs of 5000 points); ~200 GB for the gradient
+    "table2_40000x6": (20000, 0.5e-6, 50e-3, [400e-9, 460e-9, 520e-9, 580e-9, 640e-9, 700e-9], True),
     # the RGB geometry lit by a tilted wave converging to 200 mm (evaluated in the DOE-row passes)
     "rgb_tilted_converging": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 1,
                               dict(theta_x=0.01, theta_y=-0.005, src_d=-0.2)),
@@ -125,9 +131,11 @@ def run_design(reps: int, name: str = "gradient") -> dict:
     from .api import Geometry
 
     N, dx, z, lams, _, *rest = CONFIGS[name]
+    f = rest[0] if rest else 1
+    illum = rest[1] if len(rest) > 1 else {}
     P = 2 * N
-    g = Geometry.make(N, dx, z, lams)
-    h0 = inputs.heights_device(N, 1000 + N, "cuda")
+    g = Geometry.make(N, dx, z, lams, upsample=f, **illum)
+    h0 = inputs.heights_device(N // f, 1000 + N, "cuda")
     T = torch.from_numpy(inputs.spot_target(P, N, g.L, 2000 + N)).cuda()
     design.optimize(h0, g, T, 2)
     torch.cuda.synchronize()

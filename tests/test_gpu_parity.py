@@ -803,3 +803,69 @@ def test_mixed_radix_with_upsampling_illumination_and_batching():
           Geometry.make(N, dx, z, [450e-9], theta_y=0.02)]
     for h, gg, m in zip(hs3, gs, api.psf_many(hs3, gs)):
         assert torch.equal(m, api.psf(h, gg))
+
+
+# P = Q M above one CTA: Q CTAs of a cluster per row / column (four-step split)
+@pytest.mark.parametrize("N,pad", [(4500, 2), (4374, 2)])  # P = 9000 (Q 8, M 1125), 8748 (Q 4, M 2187)
+def test_split_mixed_radix_psf_and_grad_vs_oracle(N, pad):
+    dx, z, lam = 1e-6, 5e-3, 550e-9
+    P = pad * N
+    h = _h(N, 9950 + N)
+    T = inputs.spot_target(P, N, 1, 9960 + N)
+    g = Geometry.make(N, dx, z, [lam], pad=pad)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    assert rel_l2(I, oracle.psf(h, dx, z, [lam], pad=pad)) < TOL_PSF
+    del I
+    gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
+    gref, lref = oracle.grad(h, dx, z, [lam], T, pad=pad)
+    assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+@pytest.mark.parametrize("N,pad,kw", [(6750, 2, {}), (13122, 1, dict(theta_x=0.02, src_d=-0.3))])
+def test_split_mixed_radix_rows_vs_oracle(N, pad, kw):
+    # P = 13500 (Q 5, M 2700), 13122 (pad 1, Q 3, M 4374; tilted converging illumination):
+    # sampled PSF rows and the row-subset gradient against the oracle
+    dx, z, lam = 1e-6, 20e-3, 550e-9
+    P = pad * N
+    h = _h(N, 9970 + N)
+    e = oracle.incident(N, dx, lam, kw.get("theta_x", 0.0), 0.0, kw.get("src_d", 0.0)) if kw else None
+    g = Geometry.make(N, dx, z, [lam], pad=pad, **kw)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g)
+    rows = np.array([0, P // 3, P // 2 - 1, P // 2, P // 2 + 7, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    del I
+    assert rel_l2(Ig, oracle.psf_rows(h, dx, z, lam, rows, pad=pad, e_in=e)) < TOL_PSF
+    r = np.random.default_rng(9980 + N)
+    grows = np.unique(np.concatenate([[P // 2], r.integers(0, P, 5)]))
+    g_rows = r.standard_normal((grows.size, P)).astype(np.float32)
+    G = torch.zeros((1, P, P), dtype=torch.float32, device="cuda")
+    G[0, torch.from_numpy(grows).cuda()] = torch.from_numpy(g_rows).cuda()
+    gr, _ = api.grad(ht, g, G, mode="vjp")
+    drows = np.unique(np.concatenate([[0, N // 2, N - 1], r.integers(0, N, 3)]))
+    got = gr[torch.from_numpy(drows).cuda()].cpu().numpy()
+    del G, gr
+    torch.cuda.empty_cache()
+    ref = oracle.grad_rows(h, dx, z, lam, grows, g_rows, drows, pad=pad, e_in=e)
+    assert rel_l2(got, ref) < TOL_GRAD
+
+
+def test_table2_grid_28800_rows_vs_oracle():
+    # Table 2's CHD / beam-shaping grid: a 3.6 mm DOE simulated at 0.25 um (14400^2, the 1800^2
+    # design at 2 um upsampled 8x), padded to 28800 x 28800 (8 CTAs of 3600 points per
+    # transform), 520.6 nm, 10 mm: sampled PSF rows and energy against the oracle
+    N, f, dx, z, lam = 14400, 8, 0.25e-6, 10e-3, 520.6e-9
+    P = 2 * N
+    hl = _h(N // f, 9990)
+    g = Geometry.make(N, dx, z, [lam], upsample=f)
+    I = api.psf(torch.from_numpy(hl).cuda(), g)
+    tot = I.double().sum().item()
+    rows = np.array([0, P // 4, P // 2 - 1, P // 2, P // 2 + 1, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    del I
+    torch.cuda.empty_cache()
+    ref = oracle.psf_rows(oracle.upsample_nearest(hl, f), dx, z, lam, rows)
+    assert rel_l2(Ig, ref) < TOL_PSF
+    assert 0.5 * N * N < tot <= N * N * (1 + 1e-5)  # Parseval over the band
