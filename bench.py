@@ -20,7 +20,6 @@ import json
 import math
 import os
 import statistics
-import subprocess
 import sys
 import time
 from pathlib import Path
@@ -124,54 +123,126 @@ def _traffic(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
-class _Clocks:
-    """nvidia-smi sampler running during the timed region."""
+class _Nvml:
+    """Read-only NVML queries: pynvml when importable, else the driver's libnvidia-ml through
+    ctypes (same public entry points)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    CLOCK_SM = 1  # NVML_CLOCK_SM
+
+    def __init__(self):
+        try:
+            import pynvml as nv
+
+            nv.nvmlInit()
+            self.nv, self.lib = nv, None
+        except ImportError:
+            import ctypes
+
+            self.nv, self.lib, self.ct = None, ctypes.CDLL("libnvidia-ml.so.1"), ctypes
+            if self.lib.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+
+    def handle(self, bus: str | None, index: int):
+        if self.nv:
+            try:
+                return self.nv.nvmlDeviceGetHandleByPciBusId(bus) if bus else self.nv.nvmlDeviceGetHandleByIndex(index)
+            except Exception:
+                return self.nv.nvmlDeviceGetHandleByIndex(index)
+        h = self.ct.c_void_p()
+        if not bus or self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), self.ct.byref(h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(index), self.ct.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        return h
+
+    def _uint(self, fn, h, *args):
+        v = self.ct.c_uint()
+        if getattr(self.lib, fn)(h, *args, self.ct.byref(v)) != 0:
+            raise RuntimeError(fn)
+        return v.value
+
+    def sm_clock(self, h):
+        return self.nv.nvmlDeviceGetClockInfo(h, self.CLOCK_SM) if self.nv else self._uint("nvmlDeviceGetClockInfo", h, self.CLOCK_SM)
+
+    def sm_max(self, h):
+        return self.nv.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM) if self.nv else self._uint("nvmlDeviceGetMaxClockInfo", h, self.CLOCK_SM)
+
+    def reasons(self, h):
+        if self.nv:
+            get = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            return get(h)
+        v = self.ct.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(h, self.ct.byref(v)) != 0:
+            raise RuntimeError("clock event reasons")
+        return v.value
+
+
+class _Clocks:
+    """SM clock and clock-event reasons of the device, sampled during the timed region through
+    NVML (read-only queries): one sample on entry, one every 5 ms from a thread, one on exit, so
+    that a region of a few tens of milliseconds still has several samples."""
+
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
 
     def __init__(self, dev: int):
         self.dev = dev
-        self.p = None
+        self.h = None
+        self.samples = []
+        self.max_mhz = None
+        self.error = None
+
+    def _sample(self):
+        self.samples.append((self.nvml.sm_clock(self.h), self.nvml.reasons(self.h)))
+
+    def _run(self):
+        while not self.stop.wait(0.005):
+            try:
+                self._sample()
+            except Exception:
+                return
 
     def __enter__(self):
+        import threading
+
+        import torch
+
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
-                                      stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
+            self.nvml = _Nvml()
+            pr = torch.cuda.get_device_properties(self.dev)
+            try:  # the CUDA device by its PCI address (NVML and CUDA may order devices differently)
+                bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            except AttributeError:
+                bus = None
+            self.h = self.nvml.handle(bus, self.dev)
+            self.max_mhz = self.nvml.sm_max(self.h)
+            self._sample()
+            self.stop = threading.Event()
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        except Exception as e:  # no NVML: the line reports no samples and why
+            self.h = None
+            self.error = f"{type(e).__name__}: {e}"
         return self
 
     def __exit__(self, *a):
-        self.out = ""
-        if self.p:
-            self.p.terminate()
-            try:
-                self.out, _ = self.p.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.p.kill()
-                self.out = ""
+        if self.h is None:
+            return
+        self.stop.set()
+        self.t.join(timeout=1.0)
+        try:
+            self._sample()
+        except Exception:
+            pass
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.out or "").strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "error": self.error}
+        reasons = sorted({n for _, r in self.samples for n, bit in self.REASONS if r & bit})
+        return {"sm_mhz": statistics.median(sm for sm, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "NVML, every 5 ms"}
 
 
 def _oracle_sample(h, lams, img1, psf_gpu=None, j_cmp=0):

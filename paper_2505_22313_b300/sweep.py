@@ -27,6 +27,9 @@ CONFIGS = {
     # Table 2's 3600 x 3600 grid: a 3.6 mm DOE at 2 um, 520.6 nm, hologram plane at 10 mm
     # (mixed-radix transforms)
     "table2_3600": (1800, 2e-6, 10e-3, [520.6e-9], True),
+    # a split mixed-radix grid small enough to profile: 4500^2 DOE padded to 9000 x 9000
+    # (clusters of 8 CTAs of 1125 points)
+    "split_9000": (4500, 1e-6, 5e-3, [550e-9], False),
     # Table 2's CHD / beam-shaping grid: the 1800^2 design at 2 um upsampled 8x onto 14400^2 at
     # 0.25 um, padded to 28800 x 28800 (clusters of 8 CTAs of 3600 points)
     "table2_28800": (14400, 0.25e-6, 10e-3, [520.6e-9], True, 8),
