@@ -29,8 +29,10 @@
  *    at offset (P - N) / 2; output sample (y, x) lies at the same physical position as padded
  *    input sample (y, x) (the optical axis is at (P/2, P/2)).  P is either a power of two
  *    <= 65536 (above 16384 each row / column transform is split across a thread-block
- *    cluster of P / 8192 CTAs), or P = 2^a 3^b 5^c <= 8192 (a >= 1), e.g. Table 2's 3600 x
- *    3600 grid, which runs on a mixed-radix FFT in shared memory (no band compaction).
+ *    cluster of P / 8192 CTAs), or an even P whose prime factors are 2, 3, 5 or primes up to
+ *    127 (Table 2's 3600, 28800 and 40000 grids; the 67 of its large-area grid): a mixed-radix
+ *    FFT in shared memory (no band compaction), one CTA per transform up to P = 8192, above
+ *    that a cluster of Q in {2, 3, 4, 5, 8} CTAs of P / Q <= 8192 points each (P <= 65536).
  */
 #ifndef DOE_H
 #define DOE_H
@@ -111,9 +113,8 @@ size_t doe_workspace_bytes(const doe_geom* g, int op);
  *   h      device float [ny/f][nx/f]      heights in metres (Eq. 1); f = 1 unless DOE_UPSAMPLE
  *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
  *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
- * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (a side P that is
- * neither a power of two <= 65536 nor 2^a 3^b 5^c <= 8192, or nx != ny), DOE_ENOWS
- * (workspace), DOE_ECUDA. */
+ * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (a side P outside the
+ * grid note above, or nx != ny), DOE_ENOWS (workspace), DOE_ECUDA. */
 int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
                   size_t ws_bytes, void* stream);
 

@@ -68,12 +68,22 @@ int ensure_device() {
 
 bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Radices of the mixed-radix plan of a length M = 2^a 3^b 5^c <= kMrMax (M >= 2): the 5s, then
-// the 3s, then the power of two as 8s and 4s (a single 2 only for a = 1); empty for any other M.
+// Radices of the mixed-radix plan of a length 2 <= M <= kMrMax: its prime factors above 5 (up to
+// kMrMaxPrime, one direct-DFT stage each), the 5s, the 3s, then the power of two as 8s and 4s
+// (a single 2 only for a = 1); empty for any other M.
 std::vector<int> mr_radices(long M) {
   std::vector<int> r;
   if (M < 2 || M > kMrMax) return r;
   long n = M;
+  for (int p = 7; p <= kMrMaxPrime; p += 2) {
+    bool prime = true;
+    for (int d = 3; d * d <= p; d += 2)
+      if (p % d == 0) prime = false;
+    while (prime && n % p == 0) {
+      r.push_back(p);
+      n /= p;
+    }
+  }
   for (int p : {5, 3})
     while (n % p == 0) {
       r.push_back(p);

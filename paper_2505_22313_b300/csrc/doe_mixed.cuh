@@ -1,8 +1,10 @@
-// doe_mixed.cuh -- grids whose side P is not a power of two (P = 2^a 3^b 5^c <= 8192, P even):
+// doe_mixed.cuh -- grids whose side P is not a power of two (P <= 8192 even, with factors 2, 3, 5
+// and primes up to 127, e.g. the 67 of Table 2's large-area grid):
 // the same propagation, PSF and adjoint as the power-of-two passes (Eq. 1-4), on a generic
 // mixed-radix FFT held in shared memory.  Table 2's 3600 x 3600 grid is of this kind.
 //
-// FFT: Stockham autosort, one stage per radix R in {2, 3, 4, 5, 8} of the host plan.  Stage
+// FFT: Stockham autosort, one stage per radix R in {2, 3, 4, 5, 8} of the host plan, plus a
+// direct-DFT stage for each larger prime factor.  Stage
 // with Ns = product of the earlier radices: butterfly j < P/R reads x[j + r P/R] (r < R),
 // multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
 // output r to y[(j - k) R + k + r Ns].  Twiddles w_P^m = exp(-2 pi i m / P) come from a table
@@ -136,6 +138,32 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
   __syncthreads();
 }
 
+// One stage of a prime radix R > 5 (Table 2's large-area grid carries 67): one thread per
+// output (butterfly j, output r), a direct R-point DFT fused with the stage twiddle:
+//   dst[(j - k) R + k + r Ns] = sum_m src[j + m P/R] w_P^(m e),  e = k P/(Ns R) + r P/R
+// (w_P^(m k P/(Ns R)) w_R^(m r) = w_P^(m e)); the exponent m e is kept reduced mod P.
+__device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, int P, int Ns, int R,
+                                               const float2* tw, bool inv, int t) {
+  const int nb = P / R, step = P / (Ns * R);
+  for (int o = t; o < P; o += kMrT) {
+    const int j = o / R, r = o - j * R, k = j % Ns;
+    const int e = k * step + r * nb;  // < P
+    float2 acc = make_float2(0.f, 0.f);
+    int idx = 0;
+    for (int m = 0; m < R; ++m) {
+      float2 w = tw[idx];
+      if (inv) w.y = -w.y;
+      const float2 v = src[j + m * nb];
+      acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
+      acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+      idx += e;
+      if (idx >= P) idx -= P;
+    }
+    dst[(j - k) * R + k + r * Ns] = acc;
+  }
+  __syncthreads();
+}
+
 // Unnormalised transform of the P samples at a (shared memory; b is a second buffer of P) with
 // the batch's plan and the twiddles tw (shared memory).  The caller has made a's contents
 // visible (barrier).  Returns the buffer holding the result (a or b).
@@ -148,7 +176,8 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
     else if (R == 5) mr_stage<5>(a, b, P, Ns, tw, inv, t);
     else if (R == 4) mr_stage<4>(a, b, P, Ns, tw, inv, t);
     else if (R == 3) mr_stage<3>(a, b, P, Ns, tw, inv, t);
-    else mr_stage<2>(a, b, P, Ns, tw, inv, t);
+    else if (R == 2) mr_stage<2>(a, b, P, Ns, tw, inv, t);
+    else mr_stage_prime(a, b, P, Ns, R, tw, inv, t);
     Ns *= R;
     float2* c = a;
     a = b;

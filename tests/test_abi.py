@@ -72,7 +72,7 @@ def _geom(**kw):
 
 @pytest.mark.parametrize(
     "g",
-    [_geom(N=49), _geom(N=8), _geom(N=42), _geom(N=4200), _geom(N=36000), _geom(N=14000), _geom(N=134),
+    [_geom(N=49), _geom(N=8), _geom(N=278, pad=1), _geom(N=4106), _geom(N=36000), _geom(N=4192), _geom(N=262, pad=1),
      _geom(dx=0.0), _geom(z=-1.0), _geom(lambdas=[0.0]), _geom(n_index=0.5), _geom(lambdas=np.full(65, 5e-7)),
      _geom(N=180, upsample=8)],
 )
@@ -122,7 +122,7 @@ def test_strerror(lib):
 
 
 @pytest.mark.parametrize("N,pad", [(48, 2), (180, 2), (1800, 2), (3600, 1), (4000, 2), (4050, 2), (360, 1),
-                                   (4500, 2), (14400, 2), (20000, 2), (13122, 1)])
+                                   (4500, 2), (14400, 2), (20000, 2), (13122, 1), (670, 2), (8040, 2)])
 def test_mixed_radix_sizes_accepted(lib, N, pad):
     # even N with P = pad N = 2^a 3^b 5^c: one CTA per transform up to 8192, a cluster of Q CTAs
     # above (Table 2's 3600, 28800 and 40000 grids among them)

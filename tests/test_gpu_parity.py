@@ -869,3 +869,47 @@ def test_table2_grid_28800_rows_vs_oracle():
     ref = oracle.psf_rows(oracle.upsample_nearest(hl, f), dx, z, lam, rows)
     assert rel_l2(Ig, ref) < TOL_PSF
     assert 0.5 * N * N < tot <= N * N * (1 + 1e-5)  # Parseval over the band
+
+
+# prime factor 67 (Table 2's large-area grid 128640 x 85760 = 2^7 3 5 67 x 2^8 5 67): a
+# direct-DFT stage inside the mixed-radix plan
+@pytest.mark.parametrize("N,pad", [(670, 2), (1340, 1)])  # P = 1340 = 2^2 5 67
+def test_prime_67_psf_and_grad_vs_oracle(N, pad):
+    dx, z = 1e-6, 3e-3
+    lams = [500e-9, 650e-9]
+    P = pad * N
+    h = _h(N, 9400 + N)
+    T = inputs.spot_target(P, N, 2, 9410 + N)
+    g = Geometry.make(N, dx, z, lams, pad=pad)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    assert rel_l2(I, oracle.psf(h, dx, z, lams, pad=pad)) < TOL_PSF
+    gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
+    gref, lref = oracle.grad(h, dx, z, lams, T, pad=pad)
+    assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
+    assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def test_prime_67_split_rows_vs_oracle():
+    # P = 16080 = 8 x 2010 (2010 = 2 3 5 67): cluster split with a radix-67 stage per chunk
+    N, dx, z, lam = 8040, 1e-6, 20e-3, 550e-9
+    P = 2 * N
+    h = _h(N, 9420)
+    g = Geometry.make(N, dx, z, [lam])
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g)
+    rows = np.array([0, P // 3, P // 2 - 1, P // 2, P - 1])
+    Ig = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    del I
+    assert rel_l2(Ig, oracle.psf_rows(h, dx, z, lam, rows)) < TOL_PSF
+    r = np.random.default_rng(9421)
+    grows = np.unique(np.concatenate([[P // 2], r.integers(0, P, 4)]))
+    g_rows = r.standard_normal((grows.size, P)).astype(np.float32)
+    G = torch.zeros((1, P, P), dtype=torch.float32, device="cuda")
+    G[0, torch.from_numpy(grows).cuda()] = torch.from_numpy(g_rows).cuda()
+    gr, _ = api.grad(ht, g, G, mode="vjp")
+    drows = np.array([0, N // 2, N - 1])
+    got = gr[torch.from_numpy(drows).cuda()].cpu().numpy()
+    del G, gr
+    torch.cuda.empty_cache()
+    assert rel_l2(got, oracle.grad_rows(h, dx, z, lam, grows, g_rows, drows)) < TOL_GRAD
