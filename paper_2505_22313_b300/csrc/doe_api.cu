@@ -69,8 +69,10 @@ int ensure_device() {
 bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Radices of the mixed-radix plan of a length 2 <= M <= kMrMax: its prime factors above 5 (up to
-// kMrMaxPrime, one direct-DFT stage each), the 5s, the 3s, then the power of two as 8s and 4s
-// (a single 2 only for a = 1); empty for any other M.
+// kMrMaxPrime, one direct-DFT stage each), then the 5s and 3s in pairs (25, 9; a lone 5 and 3 as
+// 15), then the power of two as 16s, with 8, 4 or 2 for the rest; empty for any other M.  Below
+// 2048 points a composite stage has too few butterflies for a CTA's threads (1125 / 25 = 45), so
+// short transforms keep the single radices (5, 3, then 8s and 4s).
 std::vector<int> mr_radices(long M) {
   std::vector<int> r;
   if (M < 2 || M > kMrMax) return r;
@@ -84,29 +86,28 @@ std::vector<int> mr_radices(long M) {
       n /= p;
     }
   }
-  for (int p : {5, 3})
-    while (n % p == 0) {
-      r.push_back(p);
-      n /= p;
+  int c5 = 0, c3 = 0, a = 0;
+  for (; n % 5 == 0; n /= 5) ++c5;
+  for (; n % 3 == 0; n /= 3) ++c3;
+  for (; n % 2 == 0; n /= 2) ++a;
+  if (n != 1) return {};
+  if (M >= 2048) {
+    for (; c5 >= 2; c5 -= 2) r.push_back(25);
+    for (; c3 >= 2; c3 -= 2) r.push_back(9);
+    if (c5 && c3) {
+      r.push_back(15);
+      c5 = c3 = 0;
     }
-  int a = 0;
-  while (n % 2 == 0) {
-    ++a;
-    n /= 2;
+    for (; a >= 4; a -= 4) r.push_back(16);
   }
-  if (n != 1 || (int)r.size() + a > kMrMaxStages) return {};
-  while (a > 0) {
-    if (a == 4 || a == 2) {
-      r.push_back(4);
-      a -= 2;
-    } else if (a >= 3) {
-      r.push_back(8);
-      a -= 3;
-    } else {
-      r.push_back(2);
-      a -= 1;
-    }
+  for (; c5 > 0; --c5) r.push_back(5);
+  for (; c3 > 0; --c3) r.push_back(3);
+  while (a > 0) {  // 8s, with 4 4 for a remainder of 4 and a single 2 only for a = 1
+    const int e = (a == 4 || a == 2) ? 2 : (a >= 3 ? 3 : 1);
+    r.push_back(1 << e);
+    a -= e;
   }
+  if ((int)r.size() > kMrMaxStages) return {};
   return r;
 }
 
@@ -348,7 +349,10 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
     bt.mr_M = sp.M;
     bt.qf = sp.Q;  // split rows write one loss partial per CTA
     bt.mr_nst = (int)pl.size();
-    for (size_t s = 0; s < pl.size(); ++s) bt.mr_radix[s] = pl[s];
+    for (size_t s = 0; s < pl.size(); ++s) {
+      bt.mr_radix[s] = pl[s];
+      if (pl[s] == 9 || pl[s] == 15 || pl[s] == 16 || pl[s] == 25) bt.mr_cmp = 1;
+    }
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
     if (sp.Q > 1) bt.mr_twP = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP);
   }

@@ -324,26 +324,32 @@ cudaError_t launch_render(const RenderArgs& ra, cudaStream_t st) {
   return [&]() -> cudaError_t { DOE_DISPATCH(lw, render_out_t, ra, st); }();
 }
 
-template <int Q>
+template <int Q, bool CMP>
 cudaError_t prep_mrq_t() {
   cudaError_t e;
   constexpr int b = 3 * kMrMax * (int)sizeof(float2);
-  if ((e = prep_one(mrq_rows_fwd_kernel<Q>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q>, b, kMrT)) ||
-      (e = prep_one(mrq_rows_out_kernel<Q>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q>, b, kMrT)) ||
-      (e = prep_one(mrq_rows_adj_a_kernel<Q>, b, kMrT)))
+  if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, CMP>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_out_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q, CMP>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_adj_a_kernel<Q, CMP>, b, kMrT)))
+    return e;
+  return cudaSuccess;
+}
+template <bool CMP>
+cudaError_t prep_mr_t() {
+  cudaError_t e;
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
+  if ((e = prep_one(mr_rows_fwd_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_cols_kernel<CMP>, b, kMrT)) ||
+      (e = prep_one(mr_rows_out_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel<CMP>, b, kMrT)) ||
+      (e = prep_one(mr_rows_adj_a_kernel<CMP>, b, kMrT)))
+    return e;
+  if ((e = prep_mrq_t<2, CMP>()) || (e = prep_mrq_t<3, CMP>()) || (e = prep_mrq_t<4, CMP>()) ||
+      (e = prep_mrq_t<5, CMP>()) || (e = prep_mrq_t<8, CMP>()))
     return e;
   return cudaSuccess;
 }
 cudaError_t prep_mr() {
   cudaError_t e;
-  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
-  if ((e = prep_one(mr_rows_fwd_kernel, b, kMrT)) || (e = prep_one(mr_cols_kernel, b, kMrT)) ||
-      (e = prep_one(mr_rows_out_kernel, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel, b, kMrT)) ||
-      (e = prep_one(mr_rows_adj_a_kernel, b, kMrT)))
-    return e;
-  if ((e = prep_mrq_t<2>()) || (e = prep_mrq_t<3>()) || (e = prep_mrq_t<4>()) || (e = prep_mrq_t<5>()) ||
-      (e = prep_mrq_t<8>()))
-    return e;
+  if ((e = prep_mr_t<false>()) || (e = prep_mr_t<true>())) return e;
   return cudaSuccess;
 }
 
@@ -373,7 +379,10 @@ cudaError_t launch_htab(const Batch& bt, cudaStream_t st) {
 size_t mr_smem(const Batch& bt) { return (size_t)3 * bt.P * sizeof(float2); }
 #define DOE_MR(kern, grid)                                      \
   do {                                                          \
-    kern<<<grid, kMrT, mr_smem(bt), st>>>(bt);                  \
+    if (bt.mr_cmp)                                              \
+      kern<true><<<grid, kMrT, mr_smem(bt), st>>>(bt);          \
+    else                                                        \
+      kern<false><<<grid, kMrT, mr_smem(bt), st>>>(bt);         \
     return cudaGetLastError();                                  \
   } while (0)
 cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st) {
@@ -389,13 +398,17 @@ cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st) {
 }
 // Split sides (bt.mr_Q > 1): cluster launches of doe_mixed_big.cuh.  which: 0 rows forward (A),
 // 1 columns (B / B*), 2 rows out (C), 3 rows adjoint (C'), 4 DOE-row adjoint (A*).
+template <int Q, bool CMP>
+const void* mrq_fn(int which) {
+  return which == 0   ? (const void*)mrq_rows_fwd_kernel<Q, CMP>
+         : which == 1 ? (const void*)mrq_cols_kernel<Q, CMP>
+         : which == 2 ? (const void*)mrq_rows_out_kernel<Q, CMP>
+         : which == 3 ? (const void*)mrq_rows_adj_c_kernel<Q, CMP>
+                      : (const void*)mrq_rows_adj_a_kernel<Q, CMP>;
+}
 template <int Q>
 cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
-  const void* fn = which == 0   ? (const void*)mrq_rows_fwd_kernel<Q>
-                   : which == 1 ? (const void*)mrq_cols_kernel<Q>
-                   : which == 2 ? (const void*)mrq_rows_out_kernel<Q>
-                   : which == 3 ? (const void*)mrq_rows_adj_c_kernel<Q>
-                                : (const void*)mrq_rows_adj_a_kernel<Q>;
+  const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which) : mrq_fn<Q, false>(which);
   const int lines = (which == 0 || which == 4) ? bt.N : bt.P;
   void* args[] = {const_cast<Batch*>(&bt)};
   return launch_cluster(fn, dim3(lines * Q, which == 4 ? 1 : bt.S), Q, (size_t)3 * bt.mr_M * sizeof(float2), st,

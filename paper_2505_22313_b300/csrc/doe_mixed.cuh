@@ -3,8 +3,8 @@
 // the same propagation, PSF and adjoint as the power-of-two passes (Eq. 1-4), on a generic
 // mixed-radix FFT held in shared memory.  Table 2's 3600 x 3600 grid is of this kind.
 //
-// FFT: Stockham autosort, one stage per radix R in {2, 3, 4, 5, 8} of the host plan, plus a
-// direct-DFT stage for each larger prime factor.  Stage
+// FFT: Stockham autosort, one stage per radix of the host plan: 2, 3, 4, 5, 8, the composites
+// 9, 15, 16, 25 (split in registers), and a direct-DFT stage for each larger prime factor.  Stage
 // with Ns = product of the earlier radices: butterfly j < P/R reads x[j + r P/R] (r < R),
 // multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
 // output r to y[(j - k) R + k + r Ns].  Twiddles w_P^m = exp(-2 pi i m / P) come from a table
@@ -138,6 +138,56 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
   __syncthreads();
 }
 
+// One Stockham stage of a composite radix R = R1 R2 (16 = 4 x 4, 25 = 5 x 5, 9 = 3 x 3, 15 = 3 x 5):
+// the R-point DFT of each butterfly is split in registers (n = n1 + R1 n2, k = k2 + R2 k1):
+//   X[k2 + R2 k1] = sum_n1 w_R1^(n1 k1) [ w_R^(n1 k2) sum_n2 v[n1 + R1 n2] w_R2^(n2 k2) ],
+// which halves the shared-memory passes (and barriers) of a plan.  w_R^e = w_P^(e P/R).
+template <int R1, int R2>
+__device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P, int Ns, const float2* tw, bool inv,
+                                          int t) {
+  constexpr int R = R1 * R2;
+  const int nb = P / R, step = P / (Ns * R);
+  for (int j = t; j < nb; j += kMrT) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+    const int k = j % Ns;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[r * k * step];  // r k step < P
+      if (inv) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      float2 a[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) a[n2] = v[n1 + R1 * n2];
+      mr_dft<R2>(a, inv);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        if (n1 && k2) {
+          float2 w = tw[n1 * k2 * nb];  // w_R^(n1 k2); n1 k2 nb < P
+          if (inv) w.y = -w.y;
+          a[k2] = cmul(a[k2], w);
+        }
+        v[n1 + R1 * k2] = a[k2];
+      }
+    }
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      float2 b[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) b[n1] = v[n1 + R1 * k2];
+      mr_dft<R1>(b, inv);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) dst[base + (k2 + R2 * k1) * Ns] = b[k1];
+    }
+  }
+  __syncthreads();
+}
+
 // One stage of a prime radix R > 5 (Table 2's large-area grid carries 67): one thread per
 // output (butterfly j, output r), a direct R-point DFT fused with the stage twiddle:
 //   dst[(j - k) R + k + r Ns] = sum_m src[j + m P/R] w_P^(m e),  e = k P/(Ns R) + r P/R
@@ -167,12 +217,20 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
 // Unnormalised transform of the P samples at a (shared memory; b is a second buffer of P) with
 // the batch's plan and the twiddles tw (shared memory).  The caller has made a's contents
 // visible (barrier).  Returns the buffer holding the result (a or b).
+// CMP: the plan has composite stages (9, 15, 16, 25); kernels are compiled both ways because
+// those stages raise the register count (about 125 against 66), which costs occupancy to the
+// short transforms that do not use them.
+template <bool CMP>
 __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t) {
   const int P = bt.mr_M;  // the transform length: P, or the chunk length M of a split transform
   int Ns = 1;
   for (int s = 0; s < bt.mr_nst; ++s) {
     const int R = bt.mr_radix[s];
-    if (R == 8) mr_stage<8>(a, b, P, Ns, tw, inv, t);
+    if (CMP && R == 25) mr_stage2<5, 5>(a, b, P, Ns, tw, inv, t);
+    else if (CMP && R == 16) mr_stage2<4, 4>(a, b, P, Ns, tw, inv, t);
+    else if (CMP && R == 9) mr_stage2<3, 3>(a, b, P, Ns, tw, inv, t);
+    else if (CMP && R == 15) mr_stage2<3, 5>(a, b, P, Ns, tw, inv, t);
+    else if (R == 8) mr_stage<8>(a, b, P, Ns, tw, inv, t);
     else if (R == 5) mr_stage<5>(a, b, P, Ns, tw, inv, t);
     else if (R == 4) mr_stage<4>(a, b, P, Ns, tw, inv, t);
     else if (R == 3) mr_stage<3>(a, b, P, Ns, tw, inv, t);
@@ -214,6 +272,7 @@ __device__ __forceinline__ float2 mr_transfer(const Slice& sl, int kc, int lr, i
 }
 
 // ---- pass A (mixed radix): DOE row i of slice blockIdx.y -> its row spectrum, tbuf row i.
+template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
@@ -228,7 +287,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
     xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, hrow, i, x, N, ir) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)i * P;
   for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
 }
@@ -238,6 +297,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
 // (bt.mode == MODE_ADJ): all P rows of tbuf, FFT, x conj(H), IFFT, rows off..off+N-1 back to
 // tbuf rows 0..N-1 (in place: the CTA owns its column).  Neighbouring CTAs read the other
 // samples of each 32-byte sector, which they find in L2.
+template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
@@ -251,11 +311,11 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
     xa[l] = (unsigned)r < (unsigned)(adj ? P : N) ? __ldcs(sl.tbuf + (size_t)r * P + kc) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   float2* z = y == xa ? xb : xa;
   for (int l = t; l < P; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, P, adj));
   __syncthreads();
-  y = mr_fft(y, z, bt, tw, true, t);
+  y = mr_fft<CMP>(y, z, bt, tw, true, t);
   if (!adj) {
     for (int l = t; l < P; l += kMrT) __stcs(sl.buf + (size_t)l * P + kc, y[l]);
   } else {
@@ -264,6 +324,7 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
 }
 
 // ---- pass C (mixed radix): output row y: IFFT, 1/P^2, then |E|^2 (OUT_PSF) or E.
+template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
@@ -274,7 +335,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
   const float2* src = sl.buf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
   __syncthreads();
-  const float2* y = mr_fft(xa, xb, bt, tw, true, t);
+  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   const float s = bt.inv_p2;
   if (bt.mode == OUT_PSF) {
     float* dst = static_cast<float*>(sl.out) + (size_t)row * P;
@@ -290,6 +351,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
 
 // ---- pass C' (mixed radix): output row y: E = IFFT / P^2, g = 2 (I - T) E (L2, with the row's
 // loss partial) or (dL/dI) E (VJP), forward FFT of g into tbuf row y.
+template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   __shared__ double red[32];
@@ -301,7 +363,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
   const float2* src = sl.buf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
   __syncthreads();
-  float2* y = mr_fft(xa, xb, bt, tw, true, t);
+  float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   const float s = bt.inv_p2;
   const float* trow = sl.tgt + (size_t)row * P;
   float acc = 0.f;
@@ -319,7 +381,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
     y[c] = cscale(e, w);
   }
   __syncthreads();
-  y = mr_fft(y, y == xa ? xb : xa, bt, tw, false, t);
+  y = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
   const double tot = block_sum<kMrT>((double)acc, red);
@@ -329,6 +391,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
 // ---- pass A* (mixed radix): DOE row i, summed over the slices in order: g_doe = IFFT(tbuf
 // row i) / P^2 on the DOE columns, dL/dh += -2 k' Im(conj(g_doe) E_doe).  Each thread owns its
 // DOE columns, so the running sum lives in the gradient row itself.
+template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const int i = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
@@ -341,7 +404,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_consta
     const float2* src = sl.tbuf + (size_t)i * P;
     for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
     __syncthreads();
-    const float2* y = mr_fft(xa, xb, bt, tw, true, t);
+    const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
     const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const IncRow ir = incident_row(sl, i - N / 2);
     const float k2 = -2.f * sl.kp_hi;

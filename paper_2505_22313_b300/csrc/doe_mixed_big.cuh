@@ -51,7 +51,7 @@ __device__ __forceinline__ void mrq_map(cg::cluster_group& cl, float2* local, fl
 }
 
 // ---- pass A (split): DOE row i -> its row spectrum in chunk order, tbuf row i.
-template <int Q>
+template <int Q, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   cg::cluster_group cl = cg::this_cluster();
@@ -77,13 +77,13 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
   cl.sync();  // chunk k1 is complete in xa (and the twiddle table visible)
-  const float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)i * bt.P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT) __stcs(dst + c, y[c]);
 }
 
 // ---- pass C (split): output row: chunk IFFTs, inverse Q-point step, 1/P^2, |E|^2 or E.
-template <int Q>
+template <int Q, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   cg::cluster_group cl = cg::this_cluster();
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
   __syncthreads();
-  float2* z = mr_fft(xa, xb, bt, tw, true, t);
+  float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   float2* rem[Q];
   mrq_map<Q>(cl, z, rem);
   cl.sync();  // every chunk is transformed
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
 
 // ---- pass C' (split): output row: E (inverse as in pass C), g = 2 (I - T) E (L2, loss partial per
 // CTA) or (dL/dI) E, forward transform of g into tbuf row (chunk order).
-template <int Q>
+template <int Q, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   __shared__ double red[32];
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
   __syncthreads();
-  float2* z = mr_fft(xa, xb, bt, tw, true, t);
+  float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   float2* w = z == xa ? xb : xa;  // the same buffer in every CTA (same plan)
   float2* remz[Q];
   float2* remw[Q];
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
     mrq_scatter_fwd<Q>(v, n2, bt, remw);
   }
   cl.sync();  // w holds chunk k1 of the forward step in every CTA; reads of z are done
-  const float2* y = mr_fft(w, z, bt, tw, false, t);
+  const float2* y = mr_fft<CMP>(w, z, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT) __stcs(dst + c, y[c]);
   const double tot = block_sum<kMrT>((double)acc, red);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
 
 // ---- pass A* (split): DOE row i summed over the slices: inverse of tbuf row i (chunk order),
 // 1/P^2, dL/dh += -2 k' Im(conj(g_doe) E_doe) on the DOE columns this thread owns.
-template <int Q>
+template <int Q, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   cg::cluster_group cl = cg::this_cluster();
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
     const float2* src = sl.tbuf + (size_t)i * P + (size_t)k1 * M;
     for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
     __syncthreads();
-    float2* z = mr_fft(xa, xb, bt, tw, true, t);
+    float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
     float2* rem[Q];
     mrq_map<Q>(cl, z, rem);
     cl.sync();  // every chunk of this slice is transformed
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
 // Forward: padded rows M n1 + n2 from the DOE rows of tbuf (rows off..off+N-1), forward
 // transform, x H, inverse, all P rows to buf.  Adjoint: all P rows of tbuf, x conj(H), rows
 // off..off+N-1 back to tbuf rows 0..N-1 (the cluster owns the column).
-template <int Q>
+template <int Q, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   cg::cluster_group cl = cg::this_cluster();
@@ -242,11 +242,11 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
   cl.sync();  // chunk k1 of the column is complete in xa
-  float2* y = mr_fft(xa, xb, bt, tw, false, t);
+  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   const int kc = mrq_freq(c, Q, M);
   for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, adj));
   __syncthreads();
-  float2* z = mr_fft(y, y == xa ? xb : xa, bt, tw, true, t);
+  float2* z = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, true, t);
   float2* remz[Q];
   mrq_map<Q>(cl, z, remz);
   cl.sync();  // every chunk is back in the row domain

@@ -131,7 +131,8 @@ struct Batch {
   int illum;         // some slice has a parametric incident field (selects the DOE-row kernels)
   int mr;            // P is not a power of two: the mixed-radix passes run
   int mr_Q, mr_M;    // P = Q M: Q CTAs (a cluster) per row / column, each transforming M points (Q = 1: M = P)
-  int mr_nst;        // mixed-radix plan of M: stages and their radices (2, 3, 4, 5 or 8)
+  int mr_cmp;        // the plan has composite stages (9, 15, 16, 25): selects the kernel build
+  int mr_nst;        // mixed-radix plan of M: stages and their radices (2..8, 9, 15, 16, 25, primes)
   int mr_radix[kMrMaxStages];
   const float2* mr_tw;   // [M] twiddles exp(-2 pi i m / M) in the workspace
   const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
