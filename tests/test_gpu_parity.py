@@ -806,19 +806,21 @@ def test_mixed_radix_with_upsampling_illumination_and_batching():
 
 
 # P = Q M above one CTA: Q CTAs of a cluster per row / column (four-step split)
-@pytest.mark.parametrize("N,pad", [(4500, 2), (4374, 2)])  # P = 9000 (Q 8, M 1125), 8748 (Q 4, M 2187)
-def test_split_mixed_radix_psf_and_grad_vs_oracle(N, pad):
-    dx, z, lam = 1e-6, 5e-3, 550e-9
+# P = 9000 (Q 8, M 1125), 8748 (Q 4, M 2187; two wavelengths: several slices per launch, loss
+# partials of every CTA of every slice)
+@pytest.mark.parametrize("N,pad,lams", [(4500, 2, [550e-9]), (4374, 2, [500e-9, 620e-9])])
+def test_split_mixed_radix_psf_and_grad_vs_oracle(N, pad, lams):
+    dx, z = 1e-6, 5e-3
     P = pad * N
     h = _h(N, 9950 + N)
-    T = inputs.spot_target(P, N, 1, 9960 + N)
-    g = Geometry.make(N, dx, z, [lam], pad=pad)
+    T = inputs.spot_target(P, N, len(lams), 9960 + N)
+    g = Geometry.make(N, dx, z, lams, pad=pad)
     ht = torch.from_numpy(h).cuda()
     I = api.psf(ht, g).cpu().numpy()
-    assert rel_l2(I, oracle.psf(h, dx, z, [lam], pad=pad)) < TOL_PSF
+    assert rel_l2(I, oracle.psf(h, dx, z, lams, pad=pad)) < TOL_PSF
     del I
     gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
-    gref, lref = oracle.grad(h, dx, z, [lam], T, pad=pad)
+    gref, lref = oracle.grad(h, dx, z, lams, T, pad=pad)
     assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
     assert abs(loss.item() - lref) <= 1e-5 * lref
 
