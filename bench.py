@@ -494,7 +494,8 @@ def run_reference(args):
     srt = sorted(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": len(times),
-        "steps_requested": args.steps, "warmup": 0, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+        "steps_requested": args.steps, "warmup": 0, "warmup_requested": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config({"parallelism": "host cores"}),
         "latency_ms": {"p50": 1e3 * srt[len(srt) // 2], "p99": 1e3 * srt[-1]},
