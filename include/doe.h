@@ -62,7 +62,7 @@ extern "C" {
 #define DOE_UPSAMPLE_SHIFT 4
 #define DOE_UPSAMPLE(u) (((uint32_t)(u) & 3u) << DOE_UPSAMPLE_SHIFT)
 /* With DOE_UPSAMPLE(u), u >= 1: Lanczos-3 interpolation instead of nearest (the smooth kernel
- * the paper compares against, Sec. 4):
+ * the paper compares against, Sec. 3.2):
  *   h_sim[i][x] = sum_{m,n} w(i, m) w(x, n) h[m][n],
  *   w(x, n) = K(u_x - n) / sum_n' K(u_x - n'),  u_x = (x + 1/2) / f - 1/2 (cell centres),
  *   K(t) = sinc(t) sinc(t / 3) for |t| < 3, else 0,  cells clamped to the layout at its edges;
@@ -180,7 +180,7 @@ int doe_wiener(int C, int H, int W, const float* psf, int Py, int Px, const floa
 size_t doe_wiener_workspace_bytes(int C, int H, int W);
 
 /* One step of the design optimiser: Adam (Kingma & Ba 2015; the optimiser of the paper's
- * designs, Sec. 4 and 5) on the heights with the gradient of doe_grad, then projection onto
+ * designs, Sec. 3.2 and 5) on the heights with the gradient of doe_grad, then projection onto
  * the fabricable range [h_min, h_max]:
  *   m = beta1 m + (1 - beta1) g;  v = beta2 v + (1 - beta2) g^2;
  *   h = clamp(h - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps), h_min, h_max)
@@ -192,7 +192,7 @@ size_t doe_wiener_workspace_bytes(int C, int H, int W);
 int doe_adam_step(float* h, const float* grad, float* m, float* v, long long n, double lr, double beta1,
                   double beta2, double eps, int t, double h_min, double h_max, void* stream);
 
-/* Radially symmetric height map (Sec. 5, broadband imaging: radial symmetry enforced through a
+/* Radially symmetric height map (Sec. 5.4, broadband imaging: radial symmetry enforced through a
  * 16th-order polynomial), read as an even polynomial in the normalised radius:
  *   h[i][j] = sum_{k < n_c} c[k] s^k,  s = ((i - n/2)^2 + (j - n/2)^2) / (n/2)^2 = (rho / R)^2,
  * R = n dx / 2 the half-aperture, the axis at sample (n/2, n/2).

@@ -218,7 +218,7 @@ def radial_s(N: int) -> np.ndarray:
 
 
 def radial_heights(c, N: int) -> np.ndarray:
-    """Radially symmetric height map of Sec. 5's broadband design (radial symmetry through a
+    """Radially symmetric height map of Sec. 5.4's broadband design (radial symmetry through a
     16th-order polynomial), read as an even polynomial in rho / R:
     h = sum_k c[k] s^k, s = (rho / R)^2, k = 0 .. len(c) - 1 <= 8 (degree <= 16).  FP64."""
     c = np.asarray(c, np.float64)
@@ -235,7 +235,7 @@ def radial_grad(g, n_c: int) -> np.ndarray:
 
 # ---------------------------------------------------------------- design optimiser
 def adam_step(h, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, h_min=0.0, h_max=np.inf):
-    """One Adam step (Kingma & Ba 2015, the optimiser of the paper's designs, Sec. 4) in FP64,
+    """One Adam step (Kingma & Ba 2015, the optimiser of the paper's designs, Sec. 3.2) in FP64,
     then projection onto [h_min, h_max]; returns (h, m, v)."""
     g = np.asarray(g, np.float64)
     m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
@@ -247,15 +247,15 @@ def adam_step(h, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, h_min=0.0, h_
 
 
 def cosine_lr(lr0, t, iters):
-    """Cosine decay of the learning rate to zero over iters steps (Sec. 4's schedule), t = 1.."""
+    """Cosine decay of the learning rate to zero over iters steps (Sec. 3.2's schedule), t = 1.."""
     return 0.5 * lr0 * (1.0 + np.cos(np.pi * (t - 1) / iters))
 
 
 # ---------------------------------------------------------------- super-resolved design input
 def upsample_nearest(h_layout, f: int) -> np.ndarray:
     """Heights on the simulation grid from a layout at f times its pitch by nearest (zero-order)
-    upsampling, the interpolation the paper's conventional large-area designs use (Sec. 4, toy
-    example; Sec. 5: 8x and 4x nearest upsampling): h[i][x] = h_layout[i // f][x // f]."""
+    upsampling, the interpolation the paper's conventional large-area designs use (Sec. 3.2, toy
+    example; Sec. 5.2: 8x and 4x nearest upsampling): h[i][x] = h_layout[i // f][x // f]."""
     return np.repeat(np.repeat(np.asarray(h_layout, np.float32), f, axis=0), f, axis=1)
 
 
@@ -269,7 +269,7 @@ def layout_grad(g_sim, f: int) -> np.ndarray:
 
 def lanczos3_matrix(n_layout: int, f: int) -> np.ndarray:
     """[n_layout f][n_layout] FP64 interpolation matrix of Lanczos-3 upsampling by f, the
-    smooth kernel the paper compares nearest upsampling against (Sec. 4, toy example), read
+    smooth kernel the paper compares nearest upsampling against (Sec. 3.2, toy example), read
     as: sample x at layout coordinate u = (x + 1/2) / f - 1/2 (cell centres), weights
     K(u - n) = sinc(u - n) sinc((u - n) / 3) for |u - n| < 3 normalised to sum 1, cells
     clamped to the layout at its edges."""

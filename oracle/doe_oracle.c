@@ -17,7 +17,7 @@
  *   Eq. 4   gradient of sum_lambda L(I_lambda) with respect to h, derived by hand with
  *           Wirtinger calculus (the adjoint of the chain above).
  * plus the FFT convolution of an image with the PSFs used by the imaging application
- * (Sec. 5.3, Eq. 9 context) and a Rayleigh-Sommerfeld direct sum used only to pin the
+ * (Sec. 5.4, Eq. 9 context) and a Rayleigh-Sommerfeld direct sum used only to pin the
  * physics.  Everything is FP64; the FFT (iterative radix-2 for powers of two, mixed-radix
  * decimation in time with direct prime-length DFTs otherwise) is written here.
  *
@@ -603,7 +603,7 @@ int orc_fd_exact(long N, long pad, double dx, double z, long L, const double *la
 
 /* ------------------------------------------------------------------------------------
  * Image formation by PSF convolution (the imaging application's convolution model,
- * Sec. 5.3 around Eq. 9).  Channel c uses PSF c:
+ * Sec. 5.4 around Eq. 9).  Channel c uses PSF c:
  *   k_c[u][v] = psf_c[P/2 - H/2 + u][P/2 - W/2 + v],  u < H, v < W  (crop at the axis)
  *   k_c /= sum(k_c)
  *   out_c[y][x] = sum_{u,v} img_c[y + H/2 - u][x + W/2 - v] k_c[u][v]   (zero outside)

@@ -1,9 +1,9 @@
 // doe_design.cu -- design-loop tools around doe_grad.
 //  * doe_adam_step: one step of Adam (Kingma & Ba 2015, the optimiser the paper uses for its
-//    designs, Sec. 4's toy example and the applications of Sec. 5) on the height map,
+//    designs, Sec. 3.2's toy example and the applications of Sec. 5) on the height map,
 //    followed by a projection onto the fabricable height range [h_min, h_max].  Elementwise,
 //    one thread per height sample, FP32 state.
-//  * doe_radial_heights / doe_radial_grad: the radially symmetric parameterisation of Sec. 5's
+//  * doe_radial_heights / doe_radial_grad: the radially symmetric parameterisation of Sec. 5.4's
 //    broadband design (an even polynomial of degree 16 in the normalised radius) and its
 //    transpose, which maps doe_grad's height gradient to the coefficients.
 #include <cuda_runtime.h>

@@ -1,4 +1,4 @@
-"""Design loop: the recipe of the paper's toy example (Sec. 4) on this library's adjoint.
+"""Design loop: the recipe of the paper's toy example (Sec. 3.2) on this library's adjoint.
 
 Adam on the height map (doe_adam_step), gradients from doe_grad against a target intensity
 (the L2 loss of Eq. 4 stands in for the supplement's task losses), the learning rate decayed
@@ -9,7 +9,7 @@ and keeps the per-step losses on the device until the end.
     from paper_2505_22313_b300 import design, api
     h, losses = design.optimize(h0, geom, target, iters=3000)
 
-The broadband design of Sec. 5 keeps the phase radially symmetric through a polynomial in the
+The broadband design of Sec. 5.4 keeps the phase radially symmetric through a polynomial in the
 radius; ``optimize_radial`` runs the same loop on the coefficients of that polynomial
 (doe_radial_heights, then doe_grad, then doe_radial_grad, then Adam on the coefficients).
 """

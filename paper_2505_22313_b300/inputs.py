@@ -15,10 +15,10 @@ Recipes (seeds: heights 1000 + c, images and targets 2000 + c, request stream 30
   image    C x H x W float32: iid U[0, 1), then 64 filled disks painted over it, each with
            radius U[8, 128] px, a uniform random centre, and one U[0, 1) value per channel.
   target   8 x 8 lattice of Gaussian spots per wavelength (the beam-splitter task of
-           Sec. 5.2): pitch P/32, sigma 8 px, each centre jittered by U[-P/256, P/256] in
+           Sec. 5.3): pitch P/32, sigma 8 px, each centre jittered by U[-P/256, P/256] in
            both axes, lattice centred at (P/2, P/2), scaled so that each wavelength's
            target sums to N^2 (the energy of a unit-amplitude N x N aperture).
-  flat-top 8 x 8 regular lattice of equal-intensity discs (Sec. 5.2's flat-top spot array),
+  flat-top 8 x 8 regular lattice of equal-intensity discs (Sec. 5.3's flat-top spot array),
            pitch P/32, radius pitch/4, centred at (P/2, P/2), summing to N^2.
   requests Poisson arrivals at a given rate; side N uniform in {1024, ..., 16384};
            1..31 wavelengths uniform in [400, 700] nm; z uniform in [10, 100] mm;

@@ -695,7 +695,7 @@ def test_radial_grad_vs_oracle(n):
 
 
 def test_radial_design_loop_matches_oracle():
-    # radially symmetric design (Sec. 5): Adam on 9 even-polynomial coefficients towards an
+    # radially symmetric design (Sec. 5.4): Adam on 9 even-polynomial coefficients towards an
     # on-axis focus, 64^2 DOE, 2 wavelengths, 5 steps, against the same loop on the oracle
     from paper_2505_22313_b300 import design
 
@@ -765,7 +765,7 @@ def test_mixed_radix_psf_and_grad_vs_oracle(N, pad, bandlimit):
 
 def test_mixed_radix_table2_grid_3600():
     # Table 2's first grid: a 3.6 mm DOE at 2 um (1800^2), padded to 3600 x 3600, 520.6 nm
-    # laser (Sec. 4's toy example), hologram plane at 10 mm: PSF and L2 gradient vs the oracle
+    # laser (Sec. 3.2's toy example), hologram plane at 10 mm: PSF and L2 gradient vs the oracle
     N, dx, z, lam = 1800, 2e-6, 10e-3, 520.6e-9
     P = 2 * N
     h = _h(N, 9800)
