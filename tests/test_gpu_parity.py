@@ -915,3 +915,20 @@ def test_prime_67_split_rows_vs_oracle():
     del G, gr
     torch.cuda.empty_cache()
     assert rel_l2(got, oracle.grad_rows(h, dx, z, lam, grows, g_rows, drows)) < TOL_GRAD
+
+
+def test_split_mixed_radix_propagate_and_batching():
+    # complex destination field on a split grid (P = 8748: Q 4 x 2187) against the oracle, and
+    # two requests of that grid in one batched launch equal to their separate calls
+    N, dx, z, lam = 4374, 1e-6, 5e-3, 550e-9
+    h = _h(N, 9990 + 1)
+    g = Geometry.make(N, dx, z, [lam])
+    ht = torch.from_numpy(h).cuda()
+    E = api.propagate(ht, g).cpu().numpy()[0]
+    assert rel_l2(E, oracle.propagate(h, dx, z, lam)) < TOL_PSF
+    del E
+    h2 = torch.from_numpy(_h(N, 9990 + 2)).cuda()
+    g2 = Geometry.make(N, dx, 8e-3, [480e-9, 640e-9], theta_x=0.01)
+    many = api.psf_many([ht, h2], [g, g2])
+    assert torch.equal(many[0], api.psf(ht, g))
+    assert torch.equal(many[1], api.psf(h2, g2))
