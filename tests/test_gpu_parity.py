@@ -102,8 +102,10 @@ def test_psf_large_rows_vs_oracle(N, lams):
 
 
 def test_band_mask_bit_exact():
+    # power-of-two grids and mixed-radix ones (P = 360, 3600: the same integer band logic)
     for N, dx, z, lams in [(32, 0.25e-6, 5e-6, [400e-9, 700e-9]), (256, 2e-6, 20e-3, [550e-9]),
-                           (512, 1e-6, 50e-3, [450e-9, 650e-9])]:
+                           (512, 1e-6, 50e-3, [450e-9, 650e-9]), (180, 1e-6, 2e-3, [500e-9]),
+                           (1800, 2e-6, 10e-3, [520.6e-9])]:
         g = Geometry.make(N, dx, z, lams)
         for j, lam in enumerate(lams):
             m = api.debug_band_mask(g, j).cpu().numpy()
@@ -823,6 +825,11 @@ def test_split_mixed_radix_psf_and_grad_vs_oracle(N, pad, lams):
     gref, lref = oracle.grad(h, dx, z, lams, T, pad=pad)
     assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
     assert abs(loss.item() - lref) <= 1e-5 * lref
+    # the gradient from the fields a PSF call left in a gradient-sized workspace is the same
+    ws = api.workspace(api.workspace_bytes(g, 3))
+    api.psf(ht, g, ws=ws)
+    g2, l2 = api.grad(ht, g, torch.from_numpy(T).cuda(), recompute=False, ws=ws)
+    assert torch.equal(g2, gr) and torch.equal(l2, loss)
 
 
 @pytest.mark.parametrize("N,pad,kw", [(6750, 2, {}), (13122, 1, dict(theta_x=0.02, src_d=-0.3))])
