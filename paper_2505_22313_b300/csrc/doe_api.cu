@@ -249,6 +249,7 @@ struct Layout {
   size_t loss = 0;
   size_t gsim = 0;  // gradient on the simulation grid before the upsampling adjoint
   std::vector<size_t> hsim;  // per request, Lanczos-3: heights interpolated onto the simulation grid
+  size_t ltmp = 0;           // Lanczos-3: the [N / f][N] buffer of the separable passes
   size_t mrtw = 0;           // mixed radix: the [M] twiddle table of the per-CTA transform
   size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
 };
@@ -290,6 +291,13 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_r
       L.mrtwP = off;
       off = align256(off + (size_t)P * sizeof(float2));
     }
+  }
+  long nl_max = 0;  // Lanczos-3: [N / f][N] buffer of the separable interpolation (and its adjoint)
+  for (int r = 0; r < n_req; ++r)
+    if (lanczos(&geoms[r]) && (N >> upsample_log2(&geoms[r])) > nl_max) nl_max = N >> upsample_log2(&geoms[r]);
+  if (nl_max) {
+    L.ltmp = off;
+    off = align256(off + (size_t)N * nl_max * sizeof(float));
   }
   L.hsim.assign(n_req, 0);
   for (int r = 0; r < n_req; ++r)
@@ -395,7 +403,8 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
   for (int r = 0; r < n_req; ++r)
     if (lanczos(&geoms[r])) {
       float* hs = reinterpret_cast<float*>(static_cast<char*>(ws) + lay.hsim[r]);
-      if (launch_lanczos_up(h[r], hs, N, lanczos_table(N, upsample_log2(&geoms[r])), st) != cudaSuccess)
+      float* tmp = reinterpret_cast<float*>(static_cast<char*>(ws) + lay.ltmp);
+      if (launch_lanczos_up(h[r], tmp, hs, N, lanczos_table(N, upsample_log2(&geoms[r])), st) != cudaSuccess)
         return DOE_ECUDA;
       hr[r] = hs;
     }
@@ -473,7 +482,8 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   const bool lz = lanczos(g);
   const float* hsim = lz ? reinterpret_cast<const float*>(static_cast<char*>(ws) + lay.hsim[0]) : nullptr;
   // the adjoint row pass reads the heights too, so the interpolation runs with stored fields as well
-  if (lz && launch_lanczos_up(h, const_cast<float*>(hsim), N, lanczos_table(N, upsample_log2(g)), st) != cudaSuccess)
+  if (lz && launch_lanczos_up(h, reinterpret_cast<float*>(static_cast<char*>(ws) + lay.ltmp), const_cast<float*>(hsim),
+                             N, lanczos_table(N, upsample_log2(g)), st) != cudaSuccess)
     return DOE_ECUDA;
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j].h = lz ? hsim : h;
@@ -492,7 +502,8 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   if (launch_pass_b(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_pass_a_adj(lg, bt, st) != cudaSuccess) return DOE_ECUDA;
   if (lz) {
-    if (launch_lanczos_adjoint(bt.grad, grad_h, N, lanczos_table(N, uf), st) != cudaSuccess) return DOE_ECUDA;
+    float* tmp = reinterpret_cast<float*>(static_cast<char*>(ws) + lay.ltmp);
+    if (launch_lanczos_adjoint(bt.grad, tmp, grad_h, N, lanczos_table(N, uf), st) != cudaSuccess) return DOE_ECUDA;
   } else if (uf && launch_upsample_adjoint(bt.grad, grad_h, N, uf, st) != cudaSuccess) {
     return DOE_ECUDA;
   }

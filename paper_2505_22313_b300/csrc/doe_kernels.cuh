@@ -486,23 +486,30 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ h, const 
 }
 
 // Lanczos-3 interpolation of the (nl x nl) height layout onto the N x N simulation grid,
-// separable with the tap table tb; one thread per simulation sample.
-__global__ void __launch_bounds__(256) lanczos_up_kernel(const float* __restrict__ hl, float* __restrict__ hs, int N,
-                                                        const __grid_constant__ LanczosTab tb) {
+// separable with the tap table tb, in two passes through an [nl][N] buffer (the row sums of
+// each layout row, then the column sums; the same order of operations as the 2-D sum taken
+// row by row).  One thread per output element.
+__global__ void __launch_bounds__(256) lanczos_up_rows_kernel(const float* __restrict__ hl, float* __restrict__ tmp,
+                                                             int N, const __grid_constant__ LanczosTab tb) {
+  const long long e = blockIdx.x * 256LL + threadIdx.x;
+  if (e >= (long long)tb.nl * N) return;
+  const int m = (int)(e / N), x = (int)(e % N);
+  const int f = tb.f, nl = tb.nl, rx = x & (f - 1), mx = x / f + tb.off[rx];
+  const float* row = hl + (size_t)m * nl;
+  float s = 0.f;
+#pragma unroll
+  for (int dx = 0; dx < 6; ++dx) s = fmaf(tb.w[rx][dx], __ldg(row + min(max(mx + dx, 0), nl - 1)), s);
+  tmp[e] = s;
+}
+__global__ void __launch_bounds__(256) lanczos_up_cols_kernel(const float* __restrict__ tmp, float* __restrict__ hs,
+                                                             int N, const __grid_constant__ LanczosTab tb) {
   const long long idx = blockIdx.x * 256LL + threadIdx.x;
   if (idx >= (long long)N * N) return;
   const int i = (int)(idx / N), x = (int)(idx % N);
-  const int f = tb.f, nl = tb.nl, ri = i & (f - 1), rx = x & (f - 1);
-  const int my = i / f + tb.off[ri], mx = x / f + tb.off[rx];
+  const int f = tb.f, nl = tb.nl, ri = i & (f - 1), my = i / f + tb.off[ri];
   float acc = 0.f;
 #pragma unroll
-  for (int dy = 0; dy < 6; ++dy) {
-    const float* row = hl + (size_t)min(max(my + dy, 0), nl - 1) * nl;
-    float s = 0.f;
-#pragma unroll
-    for (int dx = 0; dx < 6; ++dx) s = fmaf(tb.w[rx][dx], __ldg(row + min(max(mx + dx, 0), nl - 1)), s);
-    acc = fmaf(tb.w[ri][dy], s, acc);
-  }
+  for (int dy = 0; dy < 6; ++dy) acc = fmaf(tb.w[ri][dy], __ldg(tmp + (size_t)min(max(my + dy, 0), nl - 1) * N + x), acc);
   hs[idx] = acc;
 }
 
@@ -516,26 +523,30 @@ __device__ __forceinline__ float lanczos_coef(const LanczosTab& tb, int i, int m
   return c;
 }
 
-// Adjoint of lanczos_up_kernel: the layout gradient of cell (m, n) gathers the simulation-grid
-// gradient over the samples whose taps reach it (rows and columns [f (m - 3), f (m + 4)) cover
-// them, edge clamping included), in a fixed order.  One thread per layout cell.
-__global__ void __launch_bounds__(256) lanczos_adjoint_kernel(const float* __restrict__ g, float* __restrict__ gl,
-                                                             int N, const __grid_constant__ LanczosTab tb) {
+// Adjoint of lanczos_up_kernel, separable like the interpolation (gl = W^T g W), in two
+// fixed-order passes through a [N][nl] buffer: rows first, tmp[i][n] = sum_x w(x, n) g[i][x],
+// then columns, gl[m][n] = sum_i w(i, m) tmp[i][n]; the samples whose taps reach cell n are
+// x in [f (n - 3), f (n + 4)) (edge clamping included).  One thread per output element.
+__global__ void __launch_bounds__(256) lanczos_adjoint_rows_kernel(const float* __restrict__ g, float* __restrict__ tmp,
+                                                                  int N, const __grid_constant__ LanczosTab tb) {
+  const long long e = blockIdx.x * 256LL + threadIdx.x;
+  if (e >= (long long)N * tb.nl) return;
+  const int i = (int)(e / tb.nl), n = (int)(e % tb.nl), f = tb.f;
+  const int x0 = max(0, f * (n - 3)), x1 = min(N, f * (n + 4));
+  const float* gr = g + (size_t)i * N;
+  float s = 0.f;
+  for (int x = x0; x < x1; ++x) s = fmaf(lanczos_coef(tb, x, n), __ldg(gr + x), s);
+  tmp[e] = s;
+}
+__global__ void __launch_bounds__(256) lanczos_adjoint_cols_kernel(const float* __restrict__ tmp, float* __restrict__ gl,
+                                                                  int N, const __grid_constant__ LanczosTab tb) {
   const long long cell = blockIdx.x * 256LL + threadIdx.x;
   if (cell >= (long long)tb.nl * tb.nl) return;
   const int m = (int)(cell / tb.nl), n = (int)(cell % tb.nl), f = tb.f;
   const int i0 = max(0, f * (m - 3)), i1 = min(N, f * (m + 4));
-  const int x0 = max(0, f * (n - 3)), x1 = min(N, f * (n + 4));
-  float acc = 0.f;
-  for (int i = i0; i < i1; ++i) {
-    const float cy = lanczos_coef(tb, i, m);
-    if (cy == 0.f) continue;
-    const float* gr = g + (size_t)i * N;
-    float s = 0.f;
-    for (int x = x0; x < x1; ++x) s = fmaf(lanczos_coef(tb, x, n), gr[x], s);
-    acc = fmaf(cy, s, acc);
-  }
-  gl[cell] = acc;
+  float s = 0.f;
+  for (int i = i0; i < i1; ++i) s = fmaf(lanczos_coef(tb, i, m), __ldg(tmp + (size_t)i * tb.nl + n), s);
+  gl[cell] = s;
 }
 
 // ------------------------------------------------------------------ radial parameterisation

@@ -479,16 +479,31 @@ cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st) {
   loss_reduce_kernel<<<1, 1024, 0, st>>>(bt, loss);
   return cudaGetLastError();
 }
-cudaError_t launch_lanczos_up(const float* hl, float* hs, int N, const LanczosTab& tb, cudaStream_t st) {
+cudaError_t launch_lanczos_up(const float* hl, float* tmp, float* hs, int N, const LanczosTab& tb, cudaStream_t st) {
+  {
+    Traced tr(TR_LANCZOS, st);
+    const long long n = (long long)tb.nl * N;
+    lanczos_up_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hl, tmp, N, tb);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   Traced tr(TR_LANCZOS, st);
   const long long n = (long long)N * N;
-  lanczos_up_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hl, hs, N, tb);
+  lanczos_up_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp, hs, N, tb);
   return cudaGetLastError();
 }
-cudaError_t launch_lanczos_adjoint(const float* g, float* gl, int N, const LanczosTab& tb, cudaStream_t st) {
+cudaError_t launch_lanczos_adjoint(const float* g, float* tmp, float* gl, int N, const LanczosTab& tb,
+                                   cudaStream_t st) {
+  {
+    Traced tr(TR_LANCZOS_ADJ, st);
+    const long long n = (long long)N * tb.nl;
+    lanczos_adjoint_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, tmp, N, tb);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   Traced tr(TR_LANCZOS_ADJ, st);
   const long long n = (long long)tb.nl * tb.nl;
-  lanczos_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, gl, N, tb);
+  lanczos_adjoint_cols_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp, gl, N, tb);
   return cudaGetLastError();
 }
 cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long n, float lr_hat, float beta1,

@@ -19,8 +19,9 @@ cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st);
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st);
 cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st);
-cudaError_t launch_lanczos_up(const float* hl, float* hs, int N, const LanczosTab& tb, cudaStream_t st);
-cudaError_t launch_lanczos_adjoint(const float* g, float* gl, int N, const LanczosTab& tb, cudaStream_t st);
+cudaError_t launch_lanczos_up(const float* hl, float* tmp, float* hs, int N, const LanczosTab& tb, cudaStream_t st);
+cudaError_t launch_lanczos_adjoint(const float* g, float* tmp, float* gl, int N, const LanczosTab& tb,
+                                   cudaStream_t st);
 cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long n, float lr_hat, float beta1,
                         float beta2, float eps_hat, float h_min, float h_max, cudaStream_t st);
 cudaError_t launch_radial_heights(const float* c, int n_c, int N, float* h, cudaStream_t st);

@@ -24,6 +24,8 @@ CONFIGS = {
     "large_area": (32768, 1e-6, 100e-3, [550e-9], True),
     # the RGB geometry designed on a 1024^2 layout at 4 um, nearest-upsampled 4x in pass A
     "rgb_layout4": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 4),
+    # the same layout interpolated with Lanczos-3 instead (a pre-pass and its transpose)
+    "rgb_layout4_lanczos": (4096, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9], True, 4, dict(lanczos=True)),
     # Table 2's 3600 x 3600 grid: a 3.6 mm DOE at 2 um, 520.6 nm, hologram plane at 10 mm
     # (mixed-radix transforms)
     "table2_3600": (1800, 2e-6, 10e-3, [520.6e-9], True),
@@ -157,6 +159,39 @@ def run_design(reps: int, name: str = "gradient") -> dict:
             "loss_first_last": [float(losses[0]), float(losses[-1])]}
 
 
+def run_design_radial(reps: int, name: str = "rgb") -> dict:
+    """Radially symmetric design iterations (doe_radial_heights, doe_grad, doe_radial_grad, Adam
+    on 9 coefficients) per second on a configuration."""
+    import torch
+
+    from . import api, design, inputs
+    from .api import Geometry
+
+    N, dx, z, lams, *_ = CONFIGS[name]
+    P = 2 * N
+    g = Geometry.make(N, dx, z, lams)
+    c0 = torch.zeros(9, device="cuda")
+    c0[0], c0[1] = 0.6e-6, -0.3e-6
+    T = torch.from_numpy(inputs.spot_target(P, N, g.L, 2000 + N, grid=1)).cuda()
+    design.optimize_radial(c0, g, T, 2, 3e-9)
+    torch.cuda.synchronize()
+    api.trace_enable(reps * 16 + 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, losses = design.optimize_radial(c0, g, T, reps, 3e-9)
+    e1.record()
+    torch.cuda.synchronize()
+    recs = api.trace_read()
+    api.trace_enable(0)
+    per: dict[str, list[float]] = {}
+    for n, ms in recs:
+        per.setdefault(n, []).append(ms)
+    ms = e0.elapsed_time(e1) / reps
+    return {"config": f"design_radial_{name}", "iteration_ms": round(ms, 3),
+            "passes_ms": {k: round(sorted(v)[len(v) // 2], 4) for k, v in per.items()},
+            "loss_first_last": [float(losses[0]), float(losses[-1])]}
+
+
 def main():
     from . import api
 
@@ -170,6 +205,9 @@ def main():
         name = name.strip()
         if name == "wiener":
             row = run_wiener(args.reps)
+        elif name.startswith("radial"):
+            # "radial" times the radially symmetric design loop on the RGB geometry; "radial_<config>"
+            row = run_design_radial(args.reps, name[len("radial_"):] if name.startswith("radial_") else "rgb")
         elif name.startswith("design"):
             # "design" times the gradient workload; "design_<config>" any configuration
             row = run_design(args.reps, name[len("design_"):] if name.startswith("design_") else "gradient")
