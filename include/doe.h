@@ -67,7 +67,8 @@ extern "C" {
  *   w(x, n) = K(u_x - n) / sum_n' K(u_x - n'),  u_x = (x + 1/2) / f - 1/2 (cell centres),
  *   K(t) = sinc(t) sinc(t / 3) for |t| < 3, else 0,  cells clamped to the layout at its edges;
  * gradients are returned on the layout through the transpose.  The interpolation is a pre-pass
- * into the workspace (N^2 floats per Lanczos request, counted by doe_workspace_bytes*). */
+ * into the workspace (N^2 floats per Lanczos request plus one shared (N/f) x N buffer of the
+ * separable passes, counted by doe_workspace_bytes*). */
 #define DOE_UPSAMPLE_LANCZOS3 0x40u
 
 /* ---- operations, for doe_workspace_bytes ---- */
