@@ -197,7 +197,7 @@ int doe_adam_step(float* h, const float* grad, float* m, float* v, long long n, 
  * 16th-order polynomial), read as an even polynomial in the normalised radius:
  *   h[i][j] = sum_{k < n_c} c[k] s^k,  s = ((i - n/2)^2 + (j - n/2)^2) / (n/2)^2 = (rho / R)^2,
  * R = n dx / 2 the half-aperture, the axis at sample (n/2, n/2).
- *   n      power of two, 16 .. 65536 (the side of the height array given to doe_grad: N, or
+ *   n      even, 16 .. 65536 (the side of the height array given to doe_grad: N, or
  *          N / f with DOE_UPSAMPLE)
  *   c      device float [n_c], 1 <= n_c <= 9 (degree 2 (n_c - 1) <= 16), metres
  *   h      device float [n][n], overwritten

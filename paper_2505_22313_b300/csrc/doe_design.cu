@@ -30,7 +30,7 @@ extern "C" int doe_adam_step(float* h, const float* grad, float* m, float* v, lo
 }
 
 static bool radial_size_ok(int n, int n_c) {
-  return n >= 16 && n <= 65536 && (n & (n - 1)) == 0 && n_c >= 1 && n_c <= doe::kMaxRadial;
+  return n >= 16 && n <= 65536 && (n & 1) == 0 && n_c >= 1 && n_c <= doe::kMaxRadial;
 }
 
 extern "C" int doe_radial_heights(int n, const float* c, int n_c, float* h, void* stream) {

@@ -551,20 +551,21 @@ __global__ void __launch_bounds__(256) lanczos_adjoint_cols_kernel(const float* 
 
 // ------------------------------------------------------------------ radial parameterisation
 // Squared normalised radius s = ((i - N/2)^2 + (x - N/2)^2) / (N/2)^2 of sample idx = i N + x,
-// as an exact float pair: the integer numerator is split into two exactly representable parts
-// and inv_r2 = (N/2)^-2 is a power of two.
-__device__ __forceinline__ dfl radial_s(long long idx, int N, float inv_r2) {
+// as a float pair: the integer numerator is split into two exactly representable parts and
+// multiplied by (N/2)^-2 = inv_hi + inv_lo (FP64 on the host; a power of two when N is).
+__device__ __forceinline__ dfl radial_s(long long idx, int N, float inv_hi, float inv_lo) {
   const int i = (int)(idx / N) - N / 2, x = (int)(idx % N) - N / 2;
   const unsigned int m = (unsigned int)(i * i) + (unsigned int)(x * x);  // <= 2^31
-  return two_sum(__fmul_rn((float)(m & 0xFFFFF000u), inv_r2), __fmul_rn((float)(m & 0x00000FFFu), inv_r2));
+  const dfl inv = {inv_hi, inv_lo};
+  return df_add(df_mul_f(inv, (float)(m & 0xFFFFF000u)), df_mul_f(inv, (float)(m & 0x00000FFFu)));
 }
 
 // Radially symmetric heights h = sum_k c[k] s^k (Horner in double-float, rounded once).
 __global__ void __launch_bounds__(256) radial_heights_kernel(const float* __restrict__ c, int n_c, int N,
-                                                            float inv_r2, float* __restrict__ h) {
+                                                            float inv_hi, float inv_lo, float* __restrict__ h) {
   const long long idx = blockIdx.x * 256LL + threadIdx.x;
   if (idx >= (long long)N * N) return;
-  const dfl s = radial_s(idx, N, inv_r2);
+  const dfl s = radial_s(idx, N, inv_hi, inv_lo);
   dfl acc = {__ldg(c + n_c - 1), 0.f};
   for (int k = n_c - 2; k >= 0; --k) acc = df_add(df_mul(acc, s), {__ldg(c + k), 0.f});
   h[idx] = __fadd_rn(acc.hi, acc.lo);
@@ -573,15 +574,15 @@ __global__ void __launch_bounds__(256) radial_heights_kernel(const float* __rest
 // Transpose of radial_heights_kernel, first stage: CTA b writes part[b][k] = the sum of
 // g s^k over its grid-stride share of the samples (double-float terms and per-thread sums,
 // then a fixed-order FP64 block sum).
-__global__ void __launch_bounds__(256) radial_grad_kernel(const float* __restrict__ g, int n_c, int N, float inv_r2,
-                                                         double* __restrict__ part) {
+__global__ void __launch_bounds__(256) radial_grad_kernel(const float* __restrict__ g, int n_c, int N, float inv_hi,
+                                                         float inv_lo, double* __restrict__ part) {
   __shared__ double red[32];
   dfl acc[kMaxRadial];
 #pragma unroll
   for (int k = 0; k < kMaxRadial; ++k) acc[k] = {0.f, 0.f};
   const long long n = (long long)N * N, step = (long long)gridDim.x * 256;
   for (long long idx = blockIdx.x * 256LL + threadIdx.x; idx < n; idx += step) {
-    const dfl s = radial_s(idx, N, inv_r2);
+    const dfl s = radial_s(idx, N, inv_hi, inv_lo);
     dfl p = {__ldcs(g + idx), 0.f};  // g s^k
 #pragma unroll
     for (int k = 0; k < kMaxRadial; ++k)

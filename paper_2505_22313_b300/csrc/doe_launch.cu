@@ -512,18 +512,26 @@ cudaError_t launch_adam(float* h, const float* g, float* m, float* v, long long 
   adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h, g, m, v, n, lr_hat, beta1, beta2, eps_hat, h_min, h_max);
   return cudaGetLastError();
 }
-// inverse squared half-side (N/2)^-2, a power of two
-static float radial_inv_r2(int N) { return std::ldexp(1.0f, -2 * (ilog2i(N) - 1)); }
+// inverse squared half-side (N/2)^-2 in FP64, split into a float pair
+static void radial_inv_r2(int N, float& hi, float& lo) {
+  const double v = 1.0 / ((0.5 * N) * (0.5 * N));
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
 cudaError_t launch_radial_heights(const float* c, int n_c, int N, float* h, cudaStream_t st) {
   Traced tr(TR_RADIAL, st);
   const long long n = (long long)N * N;
-  radial_heights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, n_c, N, radial_inv_r2(N), h);
+  float hi, lo;
+  radial_inv_r2(N, hi, lo);
+  radial_heights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, n_c, N, hi, lo, h);
   return cudaGetLastError();
 }
 cudaError_t launch_radial_grad(const float* g, int n_c, int N, double* part, float* c_grad, cudaStream_t st) {
   {
     Traced tr(TR_RADIAL_GRAD, st);
-    radial_grad_kernel<<<kRadialBlocks, 256, 0, st>>>(g, n_c, N, radial_inv_r2(N), part);
+    float hi, lo;
+    radial_inv_r2(N, hi, lo);
+    radial_grad_kernel<<<kRadialBlocks, 256, 0, st>>>(g, n_c, N, hi, lo, part);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -672,7 +672,7 @@ def test_design_loop_matches_oracle(target):
 
 
 # -------------------------------------------------------------- radial parameterisation
-@pytest.mark.parametrize("n,n_c", [(16, 1), (256, 5), (256, 9), (4096, 9)])
+@pytest.mark.parametrize("n,n_c", [(16, 1), (256, 5), (256, 9), (4096, 9), (1800, 9), (20000, 9)])
 def test_radial_heights_vs_oracle(n, n_c):
     r = np.random.default_rng(9000 + n_c)
     c = (r.standard_normal(n_c) * 3e-7).astype(np.float32)
@@ -682,7 +682,7 @@ def test_radial_heights_vs_oracle(n, n_c):
     assert np.all(np.abs(h - ref) <= 2.0**-23 * np.abs(ref) + 1e-12 * np.abs(c).sum())
 
 
-@pytest.mark.parametrize("n", [64, 2048])
+@pytest.mark.parametrize("n", [64, 2048, 1800])
 def test_radial_grad_vs_oracle(n):
     r = np.random.default_rng(9100 + n)
     g = r.standard_normal((n, n)).astype(np.float32)
