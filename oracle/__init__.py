@@ -2,8 +2,11 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package.  The product library never does, and this package imports nothing
-from it: the two share no code.  The arithmetic lives in ``doe_oracle.c`` (plain C, FP64,
-its own radix-2 FFT); this module only compiles it and marshals numpy arrays.
+from it: the two share no code.  The propagation, PSF, gradient and render arithmetic lives in
+``doe_oracle.c`` (plain C, FP64, its own FFT for any length); this module compiles it, marshals
+numpy arrays, and writes out in FP64 numpy the smaller definitions (incident fields,
+upsampling, the radial parameterisation, Adam) and the rectangular-grid propagation (numpy's
+FFT as the library transform).
 
 Every function follows Wei et al., "Large-Area Fabrication-Aware Computational Diffractive
 Optics" (TOG 2025), Sec. 3.1:
@@ -187,6 +190,79 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
         "psf_rows",
     )
     return out
+
+
+# ---------------------------------------------------------------- rectangular grids
+# Sides Py x Px (Table 2's 128640 x 85760 large-area grid is not square).  numpy's FFT serves as
+# the library transform; everything else is written out here.  Reading of Sec. 3.1 for Py != Px:
+# each axis keeps its own frequency step (dux = 1 / (Px dx), duy = 1 / (Py dx)) and its own
+# band limit (the square rule per axis: kmax_x = ceil(flim_x / dux) - 1 capped at Px / 2 with
+# flim_x = 1 / (lambda sqrt((2 dux z)^2 + 1)), likewise in y); a sample propagates iff
+# lambda^2 (fx^2 + fy^2) < 1, evaluated in FP64.
+def _kmax_axis(lam: float, dx: float, P: int, z: float, bandlimit: bool) -> int:
+    if not bandlimit:
+        return P // 2
+    du = 1.0 / (P * dx)
+    flim = 1.0 / (lam * np.sqrt((2.0 * du * z) ** 2 + 1.0))
+    return int(min(max(np.ceil(flim / du) - 1, 0), P // 2))
+
+
+def transfer_rect(Py: int, Px: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
+    """[Py][Px] complex128 band-limited transfer function, FFT order, Nyquist at -P/2."""
+    kx = np.fft.fftfreq(Px, 1.0 / Px)
+    ky = np.fft.fftfreq(Py, 1.0 / Py)
+    fx = kx / (Px * dx)
+    fy = ky / (Py * dx)
+    q = lam * lam * (fx[None, :] ** 2 + fy[:, None] ** 2)
+    band = (np.abs(kx)[None, :] <= _kmax_axis(lam, dx, Px, z, bandlimit)) & \
+           (np.abs(ky)[:, None] <= _kmax_axis(lam, dx, Py, z, bandlimit)) & (q < 1.0)
+    H = np.zeros((Py, Px), np.complex128)
+    H[band] = np.exp(2j * np.pi * z * np.sqrt(1.0 / (lam * lam) - (fx[None, :] ** 2 + fy[:, None] ** 2)[band]))
+    return H
+
+
+def _doe_field_rect(h, lam, n_index, e_in):
+    h = np.asarray(h)
+    h64 = h if h.dtype == np.float64 else h.astype(np.float32).astype(np.float64)  # float64 kept as is (FD)
+    e = np.exp(1j * 2 * np.pi * (n_index - 1.0) * h64 / lam)
+    return e if e_in is None else e * np.asarray(e_in, np.complex128)
+
+
+def propagate_rect(h, dx, z, lam, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """E_dest [pad Ny][pad Nx] for heights [Ny][Nx] (Eq. 1-3), DOE at offset ((P - N) / 2) per axis."""
+    Ny, Nx = np.asarray(h).shape
+    Py, Px = pad * Ny, pad * Nx
+    E = np.zeros((Py, Px), np.complex128)
+    E[(Py - Ny) // 2:(Py - Ny) // 2 + Ny, (Px - Nx) // 2:(Px - Nx) // 2 + Nx] = _doe_field_rect(h, lam, n_index, e_in)
+    return np.fft.ifft2(np.fft.fft2(E) * transfer_rect(Py, Px, dx, z, lam, bandlimit))
+
+
+def psf_rect(h, dx, z, lams, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
+    """FP64 PSFs [L][Py][Px] on a rectangular grid."""
+    return np.stack([np.abs(propagate_rect(h, dx, z, lam, n_index, pad, e_in, bandlimit)) ** 2
+                     for lam in np.atleast_1d(lams)])
+
+
+def grad_rect(h, dx, z, lams, target, n_index=1.46, pad=2, e_in=None, bandlimit=True):
+    """(dL/dh [Ny][Nx], L) for L = sum_lambda sum (I - T)^2 on a rectangular grid: g_out = 2 (I - T) E,
+    g_pad = IFFT2(conj(H) FFT2(g_out)), dL/dh = sum_lambda -2 k' Im(conj(g_doe) E_doe)."""
+    Ny, Nx = np.asarray(h).shape
+    Py, Px = pad * Ny, pad * Nx
+    oy, ox = (Py - Ny) // 2, (Px - Nx) // 2
+    g = np.zeros((Ny, Nx))
+    loss = 0.0
+    for j, lam in enumerate(np.atleast_1d(lams)):
+        H = transfer_rect(Py, Px, dx, z, lam, bandlimit)
+        ed = _doe_field_rect(h, lam, n_index, e_in)
+        E = np.zeros((Py, Px), np.complex128)
+        E[oy:oy + Ny, ox:ox + Nx] = ed
+        Eo = np.fft.ifft2(np.fft.fft2(E) * H)
+        d = np.abs(Eo) ** 2 - np.asarray(target[j], np.float64)
+        loss += float((d * d).sum())
+        gp = np.fft.ifft2(np.conj(H) * np.fft.fft2(2.0 * d * Eo))[oy:oy + Ny, ox:ox + Nx]
+        kp = 2 * np.pi * (n_index - 1.0) / lam
+        g += -2.0 * kp * np.imag(np.conj(gp) * ed)
+    return g, loss
 
 
 # ---------------------------------------------------------------- incident fields

@@ -134,6 +134,76 @@ def test_gaussian_beam_paraxial():
     assert rel_l2(e, ref) < 5e-6  # measured 8.2e-7; non-paraxial terms ~1e-6
 
 
+# ------------------------------------------------------------------ rectangular grids
+def test_rect_oracle_reduces_to_the_square_one():
+    # numpy FFT and the FP64 transfer rule here against the C oracle (its own FFT and H)
+    for N, pad, dx, z, lam, bl in ((64, 2, 1e-6, 2e-3, 550e-9, True), (90, 2, 0.5e-6, 1e-3, 450e-9, True),
+                                   (48, 1, 1e-6, 5e-3, 650e-9, False)):
+        h = inputs.heights(N, 30 + N)
+        a = oracle.propagate_rect(h, dx, z, lam, pad=pad, bandlimit=bl)
+        b = oracle.propagate(h, dx, z, lam, pad=pad, bandlimit=bl)
+        assert rel_l2(a, b) < 1e-11  # FP64 rounding of two FFT algorithms (measured <= 1.9e-12)
+        assert np.array_equal(oracle.transfer_rect(pad * N, pad * N, dx, z, lam, bl) != 0,
+                              oracle.band_mask(pad * N, dx, z, lam, bl).astype(bool))
+
+
+def test_rect_tilted_flat_plate_closed_form():
+    # pad 1, flat plate, a plane wave on exact spectral lines of a 48 x 80 grid: ASM multiplies it
+    # by H(mx / (Px dx), my / (Py dx)) with each axis's own step
+    Ny, Nx, dx, lam, z, c = 48, 80, 1e-6, 550e-9, 200e-6, 0.3e-6
+    for mx, my in ((5, -3), (-12, 7)):
+        sx, sy = mx * lam / (Nx * dx), my * lam / (Ny * dx)
+        yy = (np.arange(Ny) - Ny // 2)[:, None] * dx
+        xx = (np.arange(Nx) - Nx // 2)[None, :] * dx
+        e_in = np.exp(2j * np.pi * (xx * sx + yy * sy) / lam)
+        e = oracle.propagate_rect(np.full((Ny, Nx), c, np.float32), dx, z, lam, pad=1, e_in=e_in)
+        fx, fy = mx / (Nx * dx), my / (Ny * dx)
+        ph = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z * np.sqrt(1 / lam**2 - fx**2 - fy**2)
+        assert np.abs(e - np.exp(1j * ph) * e_in).max() < 1e-9
+
+
+def test_rect_band_limit_per_axis_and_parseval():
+    Ny, Nx, dx, z, lam = 96, 64, 1e-6, 5e-3, 550e-9
+    Py, Px = 2 * Ny, 2 * Nx
+    H = oracle.transfer_rect(Py, Px, dx, z, lam)
+    kx = np.abs(np.fft.fftfreq(Px, 1.0 / Px))
+    ky = np.abs(np.fft.fftfreq(Py, 1.0 / Py))
+    # the band's extent along each axis is that axis's square-grid kmax (C oracle)
+    assert kx[(H != 0).any(axis=0)].max() == oracle.kmax(lam, dx, Px, z)
+    assert ky[(H != 0).any(axis=1)].max() == oracle.kmax(lam, dx, Py, z)
+    h = inputs.heights(96, 33)[:, :64]
+    e = oracle.propagate_rect(h, dx, z, lam)
+    Ep = np.zeros((Py, Px), np.complex128)
+    Ep[Ny // 2:Ny // 2 + Ny, Nx // 2:Nx // 2 + Nx] = np.exp(1j * 2 * np.pi * 0.46 * h.astype(np.float64) / lam)
+    U = np.fft.fft2(Ep)
+    lhs = (np.abs(e) ** 2).sum()
+    rhs = (np.abs(U[H != 0]) ** 2).sum() / (Px * Py)
+    assert abs(lhs - rhs) / rhs < 1e-12 and lhs <= Nx * Ny * (1 + 1e-12)
+
+
+def test_rect_gradient_matches_central_differences():
+    Ny, Nx, dx, z = 6, 4, 2e-6, 1e-3
+    lams = [450e-9, 650e-9]
+    h = inputs.heights(8, 34)[:Ny, :Nx]
+    T = rng.random((2, 2 * Ny, 2 * Nx)) * 0.5
+    g, loss = oracle.grad_rect(h, dx, z, lams, T)
+    h64 = h.astype(np.float64)
+
+    def lossf(hh):  # FP64 heights are used as they are
+        return sum(float(((np.abs(oracle.propagate_rect(hh, dx, z, lam)) ** 2 - T[j]) ** 2).sum())
+                   for j, lam in enumerate(lams))
+
+    eps = 1e-11
+    fd = np.zeros((Ny, Nx))
+    for i in range(Ny):
+        for j in range(Nx):
+            hp = h64.copy(); hp[i, j] += eps
+            hm = h64.copy(); hm[i, j] -= eps
+            fd[i, j] = (lossf(hp) - lossf(hm)) / (2 * eps)
+    assert abs(lossf(h64) - loss) <= 1e-12 * loss
+    assert rel_l2(g, fd) < 1e-5
+
+
 # ------------------------------------------------------------------ incident fields
 def test_incident_tilt_is_one_spectral_line():
     # sin(theta) = m lambda / (N dx) puts the tilted plane wave on DFT bin m of each axis, with
