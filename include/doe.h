@@ -235,7 +235,8 @@ int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_
  * library, held by every GPU that loads the library until the process exits; the call
  * allocates nothing.  h, e_in, psf and the errors are as for doe_psf, plus DOE_ESCRATCH when
  * doe_workspace_bytes(g, DOE_OP_PSF) exceeds DOE_NOALLOC_SCRATCH_BYTES.  The first call on a
- * device looks up the array's device address (make it before any stream capture).  All calls
+ * device, and the first after that device's context was re-created (cudaDeviceReset), looks
+ * up the array's device address (make it before any stream capture).  All calls
  * share the one array: calls whose work overlaps on the GPU (different streams, or other
  * host threads) race on it and must be serialised by the caller. */
 #define DOE_NOALLOC_SCRATCH_BYTES (32u << 20)

@@ -21,7 +21,8 @@ COMPARE_LIB = PKG / "libdoe_cufft.so"  # cuFFT comparison chain, loaded only by 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
-SOURCES = ["doe_api.cu", "doe_launch.cu", "doe_render.cu", "doe_noalloc.cu", "doe_design.cu"]
+SOURCES = ["doe_pass_mr.cu", "doe_pass_pow2_large.cu", "doe_pass_big.cu", "doe_pass_pow2_small.cu",
+           "doe_pass_render.cu", "doe_launch.cu", "doe_api.cu", "doe_render.cu", "doe_noalloc.cu", "doe_design.cu"]
 
 
 def _deps() -> list[Path]:
@@ -44,9 +45,13 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if not force and not _stale_all(deps):
         return LIB
     BUILD.mkdir(exist_ok=True)
+    headers = [d for d in deps if d.suffix != ".cu"]
 
     def compile_one(src: str) -> Path:
         obj = BUILD / (Path(src).stem + ".o")
+        # an object is rebuilt when its own source or any header is newer than it
+        if not force and not verbose and not _stale(obj, [CSRC / src, *headers]):
+            return obj
         cmd = [NVCC, *FLAGS, *ARCH, "-c", str(CSRC / src), "-o", str(obj)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -59,12 +64,15 @@ def build(force: bool = False, verbose: bool = False) -> Path:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
-    cmd = [NVCC, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    if force or _stale(LIB, objs):
+        tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
+        cmd = [NVCC, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
+    else:
+        os.utime(LIB)
     _build_compare(verbose)
     return LIB
 

@@ -36,10 +36,22 @@ namespace doe {
 __device__ __forceinline__ int swz(int c) { return c ^ ((c >> 4) & 7); }
 __device__ __forceinline__ int phys(int e) { return (swz(e >> 1) << 1) | (e & 1); }
 
-// Tables live in static device memory, filled once per device at library set-up.  This header
-// is included by exactly one translation unit (doe_launch.cu), which owns these definitions.
-__device__ __align__(16) float2 g_tw[kTwTotal];
-__device__ __align__(16) float2 g_tw_big[1 << kBigLog];  // W_65536^n, n < 65536
+// Tables live in static device memory, filled once per device at library set-up.  Every
+// translation unit that includes this header holds its own copy (internal linkage, so the
+// kernel TUs compile separately without device linking) and registers an uploader for it;
+// the set-up fills every registered copy.
+static __device__ __align__(16) float2 g_tw[kTwTotal];
+static __device__ __align__(16) float2 g_tw_big[1 << kBigLog];  // W_65536^n, n < 65536
+
+using TableUpload = cudaError_t (*)(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big);
+int register_table_upload(TableUpload fn);  // defined once, in doe_launch.cu
+static cudaError_t upload_tables_of_this_unit(const float2* stage_tw, size_t n_stage, const float2* big_tw,
+                                              size_t n_big) {
+  cudaError_t e = cudaMemcpyToSymbol(g_tw, stage_tw, n_stage * sizeof(float2));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_tw_big, big_tw, n_big * sizeof(float2));
+}
+[[maybe_unused]] static const int g_tables_registered = register_table_upload(upload_tables_of_this_unit);
 
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

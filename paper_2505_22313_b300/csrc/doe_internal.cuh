@@ -202,4 +202,35 @@ __device__ __forceinline__ size_t tiled_at(int row, int pos, int R, int TC) {
   return ((size_t)(pos / TC) * R + row) * TC + (pos % TC);
 }
 
+// Deterministic block sum of one double per thread (result valid in thread 0).
+template <int NT>
+__device__ __forceinline__ double block_sum(double x, double* red) {
+  if constexpr (NT < 32) {  // partial warp: no full-mask shuffles
+    red[threadIdx.x] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < NT; ++i) s += red[i];
+      x = s;
+    }
+    return x;
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if constexpr (NT > 32) {
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      __syncthreads();
+      if (lane == 0) red[w] = x;
+      __syncthreads();
+      x = 0.0;
+      if (w == 0) {
+        x = lane < NT / 32 ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      }
+    }
+    return x;
+  }
+}
+
 }  // namespace doe

@@ -1,0 +1,108 @@
+// doe_pass_mr.cu -- grids whose side is not a power of two: the mixed-radix passes of
+// doe_mixed.cuh (one CTA of kMrT threads per row / column, the whole transform in shared
+// memory) and their cluster splits of doe_mixed_big.cuh.
+#include "doe_launch_impl.h"
+#include "doe_mixed.cuh"
+#include "doe_mixed_big.cuh"
+
+namespace doe {
+namespace {
+
+template <int Q, bool CMP>
+cudaError_t prep_mrq_t() {
+  cudaError_t e;
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);
+  if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, CMP>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_out_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q, CMP>, b, kMrT)) ||
+      (e = prep_one(mrq_rows_adj_a_kernel<Q, CMP>, b, kMrT)))
+    return e;
+  return cudaSuccess;
+}
+template <bool CMP>
+cudaError_t prep_mr_t() {
+  cudaError_t e;
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
+  if ((e = prep_one(mr_rows_fwd_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_cols_kernel<CMP>, b, kMrT)) ||
+      (e = prep_one(mr_rows_out_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel<CMP>, b, kMrT)) ||
+      (e = prep_one(mr_rows_adj_a_kernel<CMP>, b, kMrT)))
+    return e;
+  if ((e = prep_mrq_t<2, CMP>()) || (e = prep_mrq_t<3, CMP>()) || (e = prep_mrq_t<4, CMP>()) ||
+      (e = prep_mrq_t<5, CMP>()) || (e = prep_mrq_t<8, CMP>()))
+    return e;
+  return cudaSuccess;
+}
+
+// shared memory: the twiddle table plus two transform buffers
+size_t mr_smem(const Batch& bt) { return (size_t)3 * bt.P * sizeof(float2); }
+
+// one CTA per row / column (P <= kMrMax)
+template <bool CMP>
+cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
+  const size_t sm = mr_smem(bt);
+  switch (which) {
+    case PASS_A: mr_rows_fwd_kernel<CMP><<<dim3(bt.N, bt.S), kMrT, sm, st>>>(bt); break;
+    case PASS_B: mr_cols_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
+    case PASS_C: mr_rows_out_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
+    case PASS_C_ADJ: mr_rows_adj_c_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
+    case PASS_A_ADJ: mr_rows_adj_a_kernel<CMP><<<dim3(bt.N), kMrT, sm, st>>>(bt); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// split sides (bt.mr_Q > 1): cluster launches
+template <int Q, bool CMP>
+const void* mrq_fn(int which) {
+  return which == PASS_A   ? (const void*)mrq_rows_fwd_kernel<Q, CMP>
+         : which == PASS_B ? (const void*)mrq_cols_kernel<Q, CMP>
+         : which == PASS_C ? (const void*)mrq_rows_out_kernel<Q, CMP>
+         : which == PASS_C_ADJ ? (const void*)mrq_rows_adj_c_kernel<Q, CMP>
+                               : (const void*)mrq_rows_adj_a_kernel<Q, CMP>;
+}
+template <int Q>
+cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
+  const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which) : mrq_fn<Q, false>(which);
+  const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.N : bt.P;
+  void* args[] = {const_cast<Batch*>(&bt)};
+  return launch_cluster(fn, dim3(lines * Q, which == PASS_A_ADJ ? 1 : bt.S), Q, (size_t)3 * bt.mr_M * sizeof(float2),
+                        st, args, kMrT);
+}
+
+}  // namespace
+
+cudaError_t mr_pass(int which, const Batch& bt, cudaStream_t st) {
+  const int tr = which == PASS_A ? TR_PASS_A
+               : which == PASS_B ? (bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B)
+               : which == PASS_C ? TR_PASS_C
+               : which == PASS_C_ADJ ? TR_PASS_C_ADJ : TR_PASS_A_ADJ;
+  Traced t(tr, st);
+  switch (bt.mr_Q) {
+    case 1: return bt.mr_cmp ? mr_one_t<true>(which, bt, st) : mr_one_t<false>(which, bt, st);
+    case 2: return mrq_launch<2>(which, bt, st);
+    case 3: return mrq_launch<3>(which, bt, st);
+    case 4: return mrq_launch<4>(which, bt, st);
+    case 5: return mrq_launch<5>(which, bt, st);
+    case 8: return mrq_launch<8>(which, bt, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t mr_twiddles(const Batch& bt, cudaStream_t st) {
+  {
+    Traced tr(TR_MR_TWIDDLES, st);
+    mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || bt.mr_Q == 1) return e;
+  }
+  Traced tr(TR_MR_TWIDDLES, st);
+  mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_twP), bt.P);
+  return cudaGetLastError();
+}
+
+cudaError_t mr_prepare() {
+  cudaError_t e;
+  if ((e = prep_mr_t<false>()) || (e = prep_mr_t<true>())) return e;
+  return cudaSuccess;
+}
+
+}  // namespace doe

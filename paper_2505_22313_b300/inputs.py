@@ -106,14 +106,14 @@ def image(C: int, H: int, W: int, seed: int, n_disks: int = 64) -> np.ndarray:
     return img
 
 
-def spot_target(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: float = 8.0) -> np.ndarray:
-    """[L][P][P] float32 Gaussian spot-array targets, each summing to N^2."""
+def _spot_tiles(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: float = 8.0):
+    """The non-zero tiles of spot_target: (wavelength, y0, x0, float32 tile) in drawing order."""
     rng = np.random.default_rng(seed)
-    T = np.zeros((n_lambda, P, P), np.float32)
     pitch = P / 32.0
     jit = P / 256.0
     rad = int(np.ceil(5 * sigma))
     offs = (np.arange(grid) - (grid - 1) / 2.0) * pitch + P / 2.0
+    out = []
     for j in range(n_lambda):
         spots = []
         for cy0 in offs:
@@ -129,11 +129,29 @@ def spot_target(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: 
             ys = np.arange(y0, y1)[:, None]
             xs = np.arange(x0, x1)[None, :]
             g = np.exp(-((ys - cy) ** 2 + (xs - cx) ** 2) / (2 * sigma * sigma))
-            tiles.append((y0, y1, x0, x1, g))
+            tiles.append((y0, x0, g))
             total += g.sum()
         scale = float(N) * float(N) / total
-        for y0, y1, x0, x1, g in tiles:
-            T[j, y0:y1, x0:x1] += (g * scale).astype(np.float32)
+        out += [(j, y0, x0, (g * scale).astype(np.float32)) for y0, x0, g in tiles]
+    return out
+
+
+def spot_target(P: int, N: int, n_lambda: int, seed: int, grid: int = 8, sigma: float = 8.0) -> np.ndarray:
+    """[L][P][P] float32 Gaussian spot-array targets, each summing to N^2."""
+    T = np.zeros((n_lambda, P, P), np.float32)
+    for j, y0, x0, g in _spot_tiles(P, N, n_lambda, seed, grid, sigma):
+        T[j, y0:y0 + g.shape[0], x0:x0 + g.shape[1]] += g
+    return T
+
+
+def spot_target_device(P: int, N: int, n_lambda: int, seed: int, device, grid: int = 8, sigma: float = 8.0):
+    """spot_target assembled directly in device memory (the same values; for grids whose
+    target is too large to stage on the host)."""
+    import torch
+
+    T = torch.zeros((n_lambda, P, P), dtype=torch.float32, device=device)
+    for j, y0, x0, g in _spot_tiles(P, N, n_lambda, seed, grid, sigma):
+        T[j, y0:y0 + g.shape[0], x0:x0 + g.shape[1]] += torch.from_numpy(g).to(device)
     return T
 
 

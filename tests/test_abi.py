@@ -31,6 +31,16 @@ def test_exports_every_declared_symbol(lib):
     assert declared <= set(L.EXPORTS) | {"doe_render_workspace_bytes"}
 
 
+def test_binding_constants_match_header():
+    # the Python binding's error codes and sizes are the header's #define values
+    hdr = open(os.path.join(ROOT, "include", "doe.h")).read()
+    defs = dict(re.findall(r"^#define\s+(DOE_\w+)\s+(.+?)\s*(?:/\*.*)?$", hdr, re.M))
+    m = re.fullmatch(r"\((\d+)u?\s*<<\s*(\d+)\)", defs["DOE_NOALLOC_SCRATCH_BYTES"])
+    assert m and L.DOE_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+    for name in ("DOE_OK", "DOE_EINVAL", "DOE_EUNSUPPORTED", "DOE_ENOWS", "DOE_ECUDA", "DOE_ETIMEDOUT", "DOE_ESCRATCH"):
+        assert getattr(L, name) == int(defs[name].strip("()")), name
+
+
 CASES = [
     (256, 2, 2e-6, 20e-3, [550e-9]),
     (4096, 2, 1e-6, 50e-3, [450e-9, 550e-9, 650e-9]),

@@ -57,3 +57,67 @@ def test_one_at_a_time_baseline_same_results():
     assert st.summary()["completed"] == len(trace)
     for r in trace:
         assert torch.equal(res[r.rid], _alone(r))
+
+
+# -------------------------------------------------------------- serving workload vs the oracle
+# Requests shaped like the serving workload: sides N in {1024, ..., 16384} (grids 2048^2 to
+# 32768^2), 1..31 wavelengths in [400, 700] nm, z in [10, 100] mm, 1 um pitch, Poisson arrivals
+# at 200 requests/s, so that all of them are admitted and in flight together.  Wavelength counts
+# of the large sides are capped so that every PSF of the trace fits on the device at once
+# (4096: up to 12, 8192: up to 4, 16384: up to 2).
+TOL_PSF = 1e-5
+_C5_SIDES = [16384, 1024, 4096, 2048, 8192, 1024, 2048, 4096, 1024, 2048]
+_C5_LMAX = {1024: 31, 2048: 31, 4096: 12, 8192: 4, 16384: 2}
+
+
+def _c5_trace(seed=3005):
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for i, N in enumerate(_C5_SIDES):
+        t += rng.exponential(1.0 / 200.0)
+        L = int(rng.integers(1, _C5_LMAX[N] + 1))
+        out.append(Req(rid=i, arrival_s=t, N=N, lambdas=rng.uniform(400e-9, 700e-9, L),
+                       z=float(rng.uniform(10e-3, 100e-3)), seed=100000 + i))
+    return out
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm((np.asarray(a, np.float64) - b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def test_serving_mix_vs_oracle():
+    """Each request's PSFs, computed in the continuous-batching mix (shared launches of
+    several requests, three streams, admission under a budget that holds several large
+    requests at once), against the FP64 oracle: in full for grids up to 8192^2 (two seeded
+    wavelengths per request), on seeded rows for 16384^2 and 32768^2 (one seeded wavelength,
+    the oracle's row-subset mode), relative L2 <= 1e-5 per wavelength.  Beside it, the mix
+    equals the same request computed alone, bit for bit."""
+    import oracle
+
+    trace = _c5_trace()
+    budget = 48 << 30
+    lau = CudaLauncher(n_streams=3, ws_bytes=20 << 30, keep_results=True)
+    st = Scheduler(lau, budget, unit_lambdas=8).run(trace)
+    torch.cuda.synchronize()
+    assert st.summary()["completed"] == len(trace)
+    assert st.launches < sum(-(-r.L // 8) for r in trace)  # some launches were shared
+    rng = np.random.default_rng(42)
+    for r in trace:
+        mix = lau.results[r.rid]
+        assert torch.equal(mix, _alone(r)), r.rid
+        h = heights_device(r.N, r.seed, "cuda").cpu().numpy()  # the heights the launcher used
+        if r.P <= 8192:
+            js = sorted(set(rng.choice(r.L, size=min(2, r.L), replace=False).tolist()))
+            for j in js:
+                ref = oracle.psf(h, r.dx, r.z, [float(r.lambdas[j])], n_index=r.n_index)[0]
+                err = _rel_l2(mix[j].cpu().numpy(), ref)
+                assert err <= TOL_PSF, (r.rid, r.N, j, err)
+        else:
+            j = int(rng.integers(0, r.L))
+            rows = np.unique(np.concatenate([[0, r.P // 2 - 1, r.P // 2, r.P - 1], rng.integers(0, r.P, 4)]))
+            ref = oracle.psf_rows(h, r.dx, r.z, float(r.lambdas[j]), rows, n_index=r.n_index)
+            got = mix[j][torch.from_numpy(rows).cuda()].cpu().numpy()
+            err = _rel_l2(got, ref)
+            assert err <= TOL_PSF, (r.rid, r.N, j, err)
+        del mix
+        lau.results.pop(r.rid)

@@ -475,6 +475,24 @@ def test_adam_first_step_scale_invariance_and_descent():
     assert hc[0] == 0.0 and abs(hc[1] - 1.2) < 1e-12
 
 
+@pytest.mark.parametrize("iters", [3000, 7, 2])
+def test_cosine_schedule_pins(iters):
+    # Sec. 3.2: the learning rate starts at lr0 and decays to zero over `iters` iterations along
+    # a half cosine.  Steps are numbered t = 1 .. iters, so step 1 uses lr0, the midpoint
+    # t = iters / 2 + 1 uses lr0 / 2, and the step after the last one would use exactly 0; the
+    # last step itself uses lr0 sin^2(pi / (2 iters)) (half-angle identity).
+    lr0 = 1e-2
+    assert oracle.cosine_lr(lr0, 1, iters) == lr0
+    if iters % 2 == 0:
+        assert abs(oracle.cosine_lr(lr0, iters // 2 + 1, iters) - 0.5 * lr0) <= 1e-15
+    assert abs(oracle.cosine_lr(lr0, iters + 1, iters)) <= 1e-18
+    assert abs(oracle.cosine_lr(lr0, iters, iters) - lr0 * np.sin(np.pi / (2 * iters)) ** 2) <= 1e-15
+    lrs = [oracle.cosine_lr(lr0, t, iters) for t in range(1, iters + 2)]
+    assert all(a > b for a, b in zip(lrs, lrs[1:]))  # strictly decreasing to zero
+    # symmetric about the midpoint: lr(t) + lr(iters + 2 - t) = lr0
+    assert max(abs(lrs[k] + lrs[iters - k] - lr0) for k in range(iters + 1)) <= 1e-15
+
+
 def test_lanczos3_upsampling_properties():
     r = np.random.default_rng(42)
     # f = 1 is the identity (the kernel vanishes at non-zero integers and is 1 at 0)
