@@ -254,6 +254,18 @@ int doe_trace_read(int max, int* pass_ids, float* ms);
 const char* doe_pass_name(int id);
 long long doe_launch_count(void);
 
+/* Fault word of the kernels on the current device.  Kernels never trap: a bounded wait on an
+ * asynchronous copy that runs out (DOE_FAULT_WAIT_TIMEOUT), or, in a library built with
+ * DOE_DEBUG, an index found outside its buffer (DOE_FAULT_BOUNDS, the access is skipped),
+ * sets a bit and the kernel runs to its end, so its results are then undefined.
+ * doe_fault_status() synchronises the device, writes the OR of every kernel's bits since the
+ * last call into *word (host memory) and clears them; DOE_ECUDA if the device cannot be read.
+ * doe_debug_build() is 1 in a DOE_DEBUG build, else 0.  Not part of the paper: diagnostics. */
+#define DOE_FAULT_WAIT_TIMEOUT 0x1u
+#define DOE_FAULT_BOUNDS 0x2u
+int doe_fault_status(uint32_t* word);
+int doe_debug_build(void);
+
 /* Human-readable text for a status code. */
 const char* doe_strerror(int code);
 

@@ -20,6 +20,8 @@ DOE_ETIMEDOUT = -5
 DOE_ESCRATCH = -6
 DOE_NOALLOC_SCRATCH_BYTES = 32 << 20
 DOE_BANDLIMIT = 0x1
+DOE_FAULT_WAIT_TIMEOUT = 0x1
+DOE_FAULT_BOUNDS = 0x2
 DOE_UPSAMPLE_SHIFT = 4  # flags bits 4-5: log2 of the upsampling factor of the heights
 DOE_UPSAMPLE_LANCZOS3 = 0x40  # Lanczos-3 instead of nearest upsampling
 DOE_OP_PROPAGATE, DOE_OP_PSF, DOE_OP_GRAD = 1, 2, 3
@@ -32,7 +34,7 @@ EXPORTS = (
     "doe_wiener", "doe_wiener_workspace_bytes", "doe_adam_step", "doe_radial_heights",
     "doe_radial_workspace_bytes", "doe_radial_grad",
     "doe_band_limits", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
-    "doe_pass_name", "doe_launch_count", "doe_psf_noalloc",
+    "doe_pass_name", "doe_launch_count", "doe_psf_noalloc", "doe_fault_status", "doe_debug_build",
 )
 
 
@@ -101,6 +103,8 @@ def load(path: Path | None = None) -> ctypes.CDLL:
         "doe_pass_name": ([I], ctypes.c_char_p),
         "doe_launch_count": ([], ctypes.c_longlong),
         "doe_psf_noalloc": ([G, F, F, F, V], I),
+        "doe_fault_status": ([ctypes.POINTER(ctypes.c_uint32)], I),
+        "doe_debug_build": ([], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -317,6 +317,18 @@ def trace_read(max_records: int = 1 << 16) -> list[tuple[str, float]]:
     return [(lib.doe_pass_name(ids[i]).decode(), float(ms[i])) for i in range(n)]
 
 
+def fault_status() -> int:
+    """OR of the kernels' fault bits (DOE_FAULT_*) since the last call, then cleared; 0 when
+    every bounded wait completed and (in a DOE_DEBUG build) every index was in bounds."""
+    w = ctypes.c_uint32(0)
+    L.check(L.load().doe_fault_status(ctypes.byref(w)), "doe_fault_status")
+    return int(w.value)
+
+
+def debug_build() -> bool:
+    return bool(L.load().doe_debug_build())
+
+
 def launch_count() -> int:
     """Number of kernels libdoe has launched in this process."""
     return int(L.load().doe_launch_count())

@@ -47,8 +47,11 @@ const std::vector<float2>& host_stage_tables() {
 const std::vector<float2>& host_big_table() {
   static std::vector<float2> tw;
   if (tw.empty()) {
-    tw.resize(1u << kBigLog);
-    for (long n = 0; n < (1L << kBigLog); ++n) tw[n] = twiddle(n, 1L << kBigLog);
+    tw.resize(kBigTab);  // W_65536^lo, then W_65536^(256 hi), lo, hi < 256
+    for (long n = 0; n < 256; ++n) {
+      tw[n] = twiddle(n, 1L << kBigLog);
+      tw[256 + n] = twiddle(256 * n, 1L << kBigLog);
+    }
   }
   return tw;
 }
@@ -220,7 +223,12 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
     s.w = s.seg_a + (int)((kmax + 1) & ~1L);  // + kmax rounded up to even
   }
   s.wp = (s.w + kTile - 1) / kTile * kTile;
-  s.hp = (int)kmax + 1;
+  s.hp = (int)((kmax + 2) & ~1L);  // kmax + 1 rounded up to even
+  if (is_pow2(P) && P > (1L << kMaxLog)) {  // split grids: rows grouped by residue mod Q = P / 8192
+    s.hqs = ilog2(P / 8192);
+    s.hq = (int)(kmax >> s.hqs) + 1;
+    s.hp = s.hq << s.hqs;
+  }
   s.mev = band_mev(lam, g->dx, P);
   const double ld = lam * du;
   split(ld * ld, s.c_hi, s.c_lo);
@@ -581,6 +589,23 @@ const char* doe_pass_name(int id) {
 }
 
 long long doe_launch_count(void) { return launch_count(); }
+
+int doe_fault_status(uint32_t* word) {
+  if (!word) return DOE_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DOE_ECUDA;
+  unsigned int w = 0;
+  if (read_faults(&w) != cudaSuccess) return DOE_ECUDA;
+  *word = w;
+  return DOE_OK;
+}
+
+int doe_debug_build(void) {
+#ifdef DOE_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 const char* doe_strerror(int code) {
   switch (code) {

@@ -28,8 +28,8 @@ constexpr int kBigL = 8192;  // sub-transform length of split rows / columns
 // L1-resident) and one complex product, instead of a scattered read of a 512 KB table.
 template <int P>
 __device__ __forceinline__ float2 wbig(int m) {
-  const int n = m * ((1 << kBigLog) / P);
-  return cmul(__ldg(g_tw_big + ((n >> 8) << 8)), __ldg(g_tw_big + (n & 255)));
+  const int n = (m * ((1 << kBigLog) / P)) & ((1 << kBigLog) - 1);
+  return cmul(__ldg(g_tw_big + 256 + (n >> 8)), __ldg(g_tw_big + (n & 255)));
 }
 template <bool INV>
 __device__ __forceinline__ float2 tw_apply(float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); }
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
   float4* rsm[Q];
 #pragma unroll
   for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
-  cl.sync();  // every CTA of the cluster has started before its shared memory is written
+  cluster_sync_relaxed();  // every CTA of the cluster has started before its shared memory is written
 #pragma unroll
   for (int it = 0; it < SH / (2 * T); ++it) {  // compile-time count: loads of all items in flight together
     const int n2 = s * SH + 2 * t + it * 2 * T;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
         __stcs(reinterpret_cast<float4*>(static_cast<float2*>(sl.out) + o), make_float4(a.x, a.y, b.x, b.y));
     }
   }
-  cl.sync();  // peers have finished reading this CTA's shared memory
+  cluster_sync_relaxed();  // peers have finished reading this CTA's shared memory
 }
 
 // ------------------------------------------------------------------ columns (pass B / B*)
@@ -209,11 +209,16 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   const int kcol = big_pos_to_k(pos0 + c, Q);
   const bool live = pos0 + c < sl.w && abs_signed(kcol, P) <= sl.kmax;
   if (live) {
-    // this column's transfer-function row (up to 256 KB, read at a stride of Q entries after
-    // the forward transform): the column's Q CTAs bring its lines into L2 now
-    const char* hb = reinterpret_cast<const char*>(sl.htab + (size_t)abs_signed(kcol, P) * sl.hp);
-    for (int o = 128 * (s * T + t); o < (sl.kmax + 1) * (int)sizeof(float2); o += 128 * T * Q)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(hb + o));
+    // the two residue classes of this column's transfer-function row that sub-transform s
+    // reads after its forward transform (frequencies s + Q k2 below P/2 and their mirrors
+    // above): this CTA brings their lines into L2 now
+    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, P) * sl.hp;
+    const char* h0 = reinterpret_cast<const char*>(hrow + (size_t)s * sl.hq);
+    const char* h1 = reinterpret_cast<const char*>(hrow + (size_t)((Q - s) % Q) * sl.hq);
+    for (int o = 128 * t; o < sl.hq * (int)sizeof(float2); o += 128 * T) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(h0 + o));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(h1 + o));
+    }
   }
   const bool adj = bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   float2* rsm[CL];
 #pragma unroll
   for (int k = 0; k < CL; ++k) rsm[k] = cl.map_shared_rank(sm, k);
-  cl.sync();
+  cluster_sync_relaxed();
   // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2; each
   // thread takes the adjacent pair (y2, y2 + 1) so its shared-memory writes are 16 bytes
 #pragma unroll
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
         const int a = abs_signed(s + Q * G::idx(t, b, r), P);
         float2& x = v[b * G::R + r];
         if (live && a <= sl.kmax) {
-          const float2 hv = hrow[a];
+          const float2 hv = hrow[htab_col(sl, a)];  // consecutive threads: consecutive entries
           x = adj ? cmulc(x, hv) : cmul(x, hv);
         } else {
           x = make_float2(0.f, 0.f);
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
         }
       }
   }
-  cl.sync();
+  cluster_sync_relaxed();
 }
 
 // ------------------------------------------------------------------ rows, adjoint (pass C')

@@ -41,7 +41,9 @@ __device__ __forceinline__ int phys(int e) { return (swz(e >> 1) << 1) | (e & 1)
 // kernel TUs compile separately without device linking) and registers an uploader for it;
 // the set-up fills every registered copy.
 static __device__ __align__(16) float2 g_tw[kTwTotal];
-static __device__ __align__(16) float2 g_tw_big[1 << kBigLog];  // W_65536^n, n < 65536
+// W_65536^n = W_65536^(256 hi) W_65536^lo for n = 256 hi + lo: entries [0, 256) hold
+// W_65536^lo, entries [256, 512) W_65536^(256 hi) (4 KB, L1-resident)
+static __device__ __align__(16) float2 g_tw_big[kBigTab];
 
 using TableUpload = cudaError_t (*)(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big);
 int register_table_upload(TableUpload fn);  // defined once, in doe_launch.cu
@@ -52,6 +54,22 @@ static cudaError_t upload_tables_of_this_unit(const float2* stage_tw, size_t n_s
   return cudaMemcpyToSymbol(g_tw_big, big_tw, n_big * sizeof(float2));
 }
 [[maybe_unused]] static const int g_tables_registered = register_table_upload(upload_tables_of_this_unit);
+
+// Fault word of this translation unit's kernels (bits DOE_FAULT_*): a bounded wait that ran
+// out, or (in the bounds-checked build) an index outside its buffer.  Kernels set bits and
+// carry on without the faulting access; doe_fault_status() reads and clears every unit's word.
+static __device__ unsigned int g_fault_word;
+using FaultRead = cudaError_t (*)(unsigned int* word);
+int register_fault_reader(FaultRead fn);  // defined once, in doe_launch.cu
+static cudaError_t read_fault_of_this_unit(unsigned int* word) {
+  const unsigned int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_fault_word, sizeof(unsigned int));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_fault_word, &zero, sizeof(unsigned int));
+}
+[[maybe_unused]] static const int g_fault_registered = register_fault_reader(read_fault_of_this_unit);
+enum : unsigned int { FAULT_WAIT_TIMEOUT = 1u, FAULT_BOUNDS = 2u };
+__device__ __forceinline__ void raise_fault(unsigned int bits) { atomicOr(&g_fault_word, bits); }
 
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

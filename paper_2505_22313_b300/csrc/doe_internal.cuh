@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "doe_async.cuh"
 #include "doe_fft.cuh"
 #include "doe_plan.h"
 
@@ -177,6 +178,22 @@ __device__ __forceinline__ float2 heights_pair(const float* hrow, int x, int uf)
   if (uf == 0) return __ldcs(reinterpret_cast<const float2*>(hrow + x));
   const float h = __ldcs(hrow + (x >> uf));
   return make_float2(h, h);
+}
+
+// Cluster barrier without memory ordering, for a point where no CTA publishes data: the
+// arriving CTA's reads of its peers' shared memory have all been consumed (their values are
+// already used by its later instructions), and the barrier only keeps a peer from reusing or
+// releasing that memory early.  Unlike the default (release / acquire) barrier it does not
+// wait for the CTA's outstanding global stores.
+__device__ __forceinline__ void cluster_sync_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
+// Position of entry a (= |lt|) in a row of the transfer-function table.  Split grids group a
+// row by residue mod Q (the cluster size of their column pass): entry a at (a mod Q) hq + a / Q,
+// so CTA s of a column cluster, which needs the frequencies s + Q k2, reads a contiguous run.
+__device__ __forceinline__ int htab_col(const Slice& s, int a) {
+  return s.hqs ? (a & ((1 << s.hqs) - 1)) * s.hq + (a >> s.hqs) : a;
 }
 
 // Stored (band-compacted) spectrum rows.  With the band limit active a row keeps the two

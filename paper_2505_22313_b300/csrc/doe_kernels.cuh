@@ -61,6 +61,17 @@ __device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const floa
     }
 }
 
+// With 2x zero padding the DOE fills the middle half [L/4, 3L/4) of a forward transform's
+// input.  First-stage register r of every thread holds input j + r L/R0 with j < L/R0, so for a
+// first radix R0 >= 4 it lies inside the DOE exactly when R0/4 <= r < 3 R0/4: a compile-time
+// pattern, so the first butterflies of the transform fold the zero inputs away.
+template <int L>
+__host__ __device__ constexpr bool pad2_foldable() { return First<L, false>::R >= 4; }
+template <int L>
+__device__ __forceinline__ constexpr bool pad2_live(int r) {
+  return r >= First<L, false>::R / 4 && r < 3 * First<L, false>::R / 4;
+}
+
 // ------------------------------------------------------------------ pass A: DOE rows
 // 16-byte asynchronous copies of a height row into shared memory (cp.async, L2 only).
 __device__ __forceinline__ void stage_heights(float* dst, const float* src, int n, int t, int nt) {
@@ -77,7 +88,8 @@ __device__ __forceinline__ void wait_staged() { asm volatile("cp.async.wait_all;
 // exchange buffer (N <= L / 2, i.e. pad 2) the next item's heights are copied into shared
 // memory while the current row is transformed; otherwise they are read from global memory.
 // ILLUM: some slice has a parametric incident field (evaluated per sample with the phase).
-template <int L, bool ILLUM>
+// PAD2: 2x padding (N = L / 2) with the compile-time input pattern of pad2_live.
+template <int L, bool ILLUM, bool PAD2>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __grid_constant__ Batch bt) {
   using F = First<L, false>;
   constexpr int T = L / 32;
@@ -107,7 +119,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
       for (int r = 0; r < F::R; ++r) {
         const int x = F::idx(t, b, r) - off;  // even
         hv[b / 2][r] = make_float2(0.f, 0.f);
-        if ((unsigned)x < (unsigned)N) {
+        if (PAD2 ? pad2_live<L>(r) : (unsigned)x < (unsigned)N) {
           if (!staged) hv[b / 2][r] = heights_pair(hrow, x, uf);
           else if (uf == 0) hv[b / 2][r] = *reinterpret_cast<const float2*>(hs + x);
           else hv[b / 2][r] = make_float2(hs[x >> uf], hs[x >> uf]);
@@ -127,7 +139,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
       for (int r = 0; r < F::R; ++r) {
         const int x = F::idx(t, b, r) - off;
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-        if ((unsigned)x < (unsigned)N) {
+        if (PAD2 ? pad2_live<L>(r) : (unsigned)x < (unsigned)N) {
           if (ILLUM && sl.illum) {
             a = transmittance_inc(hv[b / 2][r].x, sl, ir, x - N / 2);
             c = transmittance_inc(hv[b / 2][r].y, sl, ir, x + 1 - N / 2);
@@ -155,7 +167,9 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
 // (the cluster's CTAs together consume whole 32-byte sectors).  Output: after the transforms
 // each CTA gathers a quarter of the output rows of all four columns from the cluster's shared
 // memory (distributed shared memory) and writes them as 32-byte row segments.
-template <int L>
+// PAD2F: the forward pass at 2x padding (N = L / 2), with the compile-time input pattern of
+// pad2_live.
+template <int L, bool PAD2F>
 __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __grid_constant__ Batch bt) {
   using G = Last<L, false>;  // forward's last stage = inverse's first stage (radix 16)
   using H = Last<L, true>;
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
   const Slice& sl = bt.s[si];
   const int pos0 = (tile_g - sl.tile_begin) * kTile;
   const int mypos = pos0 + q;
-  const bool adj = bt.mode == MODE_ADJ;
+  const bool adj = !PAD2F && bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;
   const int nin = adj ? L : N, yin0 = adj ? 0 : off;     // input rows (padded coordinates)
   const int nout = adj ? N : L, yout0 = adj ? off : 0;   // output rows (padded coordinates)
@@ -203,9 +217,11 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
       for (int r = 0; r < F::R; ++r) {
         const int y = F::idx(t, b, r) - yin0;
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-        if (live && (unsigned)y < (unsigned)nin) {
-          a = __ldcs(col + (size_t)y * kTile);
-          c = __ldcs(col + (size_t)(y + 1) * kTile);
+        if (PAD2F ? pad2_live<L>(r) : (unsigned)y < (unsigned)nin) {
+          if (live) {
+            a = __ldcs(col + (size_t)y * kTile);
+            c = __ldcs(col + (size_t)(y + 1) * kTile);
+          }
         }
         v[b * F::R + r] = a;
         v[(b + 1) * F::R + r] = c;
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
       }
     }
   }
-  cl.sync();
+  cluster_sync_relaxed();  // the peers have read this CTA's shared memory before it exits
 }
 
 // ------------------------------------------------------------------ pass C: output rows

@@ -85,6 +85,27 @@ cudaError_t upload_tables(const float2* stage_tw, size_t n_stage, const float2* 
   return cudaSuccess;
 }
 
+namespace {
+std::vector<FaultRead>& fault_registry() {
+  static std::vector<FaultRead> r;
+  return r;
+}
+}  // namespace
+int register_fault_reader(FaultRead fn) {
+  fault_registry().push_back(fn);
+  return (int)fault_registry().size();
+}
+cudaError_t read_faults(unsigned int* word) {
+  *word = 0;
+  for (FaultRead fn : fault_registry()) {
+    unsigned int w = 0;
+    const cudaError_t e = fn(&w);
+    if (e != cudaSuccess) return e;
+    *word |= w;
+  }
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ kernel set-up, launches
 cudaError_t prep_kernel(const void* kern, int smem, int threads) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

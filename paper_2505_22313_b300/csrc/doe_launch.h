@@ -8,6 +8,7 @@
 
 namespace doe {
 cudaError_t upload_tables(const float2* stage_tw, size_t n_stage, const float2* big_tw, size_t n_big);
+cudaError_t read_faults(unsigned int* word);  // ORs and clears the fault words of every kernel unit
 cudaError_t prepare_kernels();
 cudaError_t launch_htab(const Batch& bt, cudaStream_t st);
 cudaError_t launch_mr_twiddles(const Batch& bt, cudaStream_t st);

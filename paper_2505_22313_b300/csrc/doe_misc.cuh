@@ -7,7 +7,7 @@
 namespace doe {
 
 // ------------------------------------------------------------------ transfer-function table
-// Grid (max_kmax + 1, S); row b = |kt|, entries a = |lt|.  Integer band logic: the table
+// Grid (max_kmax + 1, S); row b = |kt|, entries a = |lt| (at htab_col).  Integer band logic: the table
 // covers |kt|, |lt| <= kmax; a sample is zero iff kt^2 + lt^2 >= mev (evanescent).
 __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch bt) {
   const Slice& sl = bt.s[blockIdx.y];
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch
   float2* row = sl.htab + (size_t)b * sl.hp;
   for (int a = threadIdx.x; a <= sl.kmax; a += blockDim.x) {
     const long long m = (long long)b * b + (long long)a * a;
-    row[a] = (m < sl.mev) ? transfer_value((unsigned int)m, sl) : make_float2(0.f, 0.f);
+    row[htab_col(sl, a)] = (m < sl.mev) ? transfer_value((unsigned int)m, sl) : make_float2(0.f, 0.f);
   }
 }
 
@@ -199,7 +199,7 @@ __global__ void band_mask_kernel(const __grid_constant__ Batch bt, uint8_t* mask
     const int b = abs_signed(k, P);
     uint8_t mv = 0;
     if (a <= sl.kmax && b <= sl.kmax) {
-      const float2 hv = sl.htab[(size_t)b * sl.hp + a];
+      const float2 hv = sl.htab[(size_t)b * sl.hp + htab_col(sl, a)];
       mv = (hv.x != 0.f || hv.y != 0.f) ? 1 : 0;
     }
     mask[(size_t)l * P + k] = mv;

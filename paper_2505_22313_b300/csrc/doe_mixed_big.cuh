@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
   const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
   const IncRow ir = incident_row(sl, i - N / 2);
   const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
-  cl.sync();  // every CTA of the cluster runs before its shared memory is written
+  cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
   for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
     float2 v[Q];
 #pragma unroll
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
       else __stcs(static_cast<float2*>(sl.out) + at, e);
     }
   }
-  cl.sync();  // the peers' reads of this CTA's chunk are done before it exits
+  cluster_sync_relaxed();  // the peers' reads of this CTA's chunk are done before it exits
 }
 
 // ---- pass C' (split): output row: E (inverse as in pass C), g = 2 (I - T) E (L2, loss partial per
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
   float2* rem[Q];
   mrq_map<Q>(cl, xa, rem);
   const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
-  cl.sync();  // every CTA of the cluster runs before its shared memory is written
+  cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
   for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
     float2 v[Q];
 #pragma unroll

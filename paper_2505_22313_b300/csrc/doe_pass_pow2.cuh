@@ -7,6 +7,10 @@
 namespace doe {
 namespace {
 
+// Transforms long enough to matter whose first radix lets the 2x-padding zeros fold away.
+template <int L>
+constexpr bool kPad2Fold = L >= 1024 && pad2_foldable<L>();
+
 // pass A: exchange buffer plus the staged height row (at most L / 2 floats)
 template <int L>
 constexpr int pass_a_smem() { return (int)(smem_bytes<L>() + (size_t)(L / 2) * sizeof(float)); }
@@ -16,10 +20,15 @@ cudaError_t prep_pow2_t() {
   cudaError_t e;
   const int sb = (int)smem_bytes<L>();
   const int nt = threads<L>();
-  if ((e = prep_one(pass_a_kernel<L, false>, pass_a_smem<L>(), nt)) ||
-      (e = prep_one(pass_a_kernel<L, true>, pass_a_smem<L>(), nt)))
+  if ((e = prep_one(pass_a_kernel<L, false, false>, pass_a_smem<L>(), nt)) ||
+      (e = prep_one(pass_a_kernel<L, true, false>, pass_a_smem<L>(), nt)))
     return e;
-  if ((e = prep_one(pass_b_kernel<L>, sb, nt))) return e;
+  if ((e = prep_one(pass_b_kernel<L, false>, sb, nt))) return e;
+  if constexpr (kPad2Fold<L>)
+    if ((e = prep_one(pass_a_kernel<L, false, true>, pass_a_smem<L>(), nt)) ||
+        (e = prep_one(pass_a_kernel<L, true, true>, pass_a_smem<L>(), nt)) ||
+        (e = prep_one(pass_b_kernel<L, true>, sb, nt)))
+      return e;
   if ((e = prep_one(pass_c_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_kernel<L>, sb, nt))) return e;
   if ((e = prep_one(pass_a_adj_kernel<L, false>, sb, nt)) || (e = prep_one(pass_a_adj_kernel<L, true>, sb, nt)))
@@ -27,13 +36,13 @@ cudaError_t prep_pow2_t() {
   return cudaSuccess;
 }
 
-template <int L, bool ILLUM>
+template <int L, bool ILLUM, bool PAD2>
 cudaError_t pass_a_run(const Batch& bt, cudaStream_t st) {
   // persistent: about as many CTAs as are resident at once, each looping over (slice, row) items
   static const int resident = [] {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_a_kernel<L, ILLUM>, threads<L>(),
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_a_kernel<L, ILLUM, PAD2>, threads<L>(),
                                                       pass_a_smem<L>()))
       return 0;
     return sms * per_sm;
@@ -41,7 +50,7 @@ cudaError_t pass_a_run(const Batch& bt, cudaStream_t st) {
   const long items = (long)bt.S * bt.N;
   const int grid = (int)(resident > 0 && resident < items ? resident : items);
   const size_t smem = smem_bytes<L>() + (2 * bt.N <= L ? (size_t)bt.N * sizeof(float) : 0);
-  pass_a_kernel<L, ILLUM><<<dim3(grid), threads<L>(), smem, st>>>(bt);
+  pass_a_kernel<L, ILLUM, PAD2><<<dim3(grid), threads<L>(), smem, st>>>(bt);
   return cudaGetLastError();
 }
 
@@ -50,13 +59,17 @@ cudaError_t pow2_run(int which, const Batch& bt, cudaStream_t st) {
   switch (which) {
     case PASS_A: {
       Traced tr(TR_PASS_A, st);
-      return bt.illum ? pass_a_run<L, true>(bt, st) : pass_a_run<L, false>(bt, st);
+      if constexpr (kPad2Fold<L>)
+        if (2 * bt.N == L) return bt.illum ? pass_a_run<L, true, true>(bt, st) : pass_a_run<L, false, true>(bt, st);
+      return bt.illum ? pass_a_run<L, true, false>(bt, st) : pass_a_run<L, false, false>(bt, st);
     }
     case PASS_B: {
       Traced tr(bt.mode == MODE_ADJ ? TR_PASS_B_ADJ : TR_PASS_B, st);
       void* args[] = {const_cast<Batch*>(&bt)};
-      return launch_cluster((const void*)pass_b_kernel<L>, dim3(bt.total_tiles * kTile), kTile, smem_bytes<L>(), st,
-                            args, threads<L>());
+      const void* fn = (const void*)pass_b_kernel<L, false>;
+      if constexpr (kPad2Fold<L>)
+        if (bt.mode != MODE_ADJ && 2 * bt.N == L) fn = (const void*)pass_b_kernel<L, true>;
+      return launch_cluster(fn, dim3(bt.total_tiles * kTile), kTile, smem_bytes<L>(), st, args, threads<L>());
     }
     case PASS_C: {
       Traced tr(TR_PASS_C, st);

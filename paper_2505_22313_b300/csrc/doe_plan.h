@@ -9,7 +9,8 @@ namespace doe {
 
 constexpr int kMinLog = 5;   // L = 32
 constexpr int kMaxLog = 14;  // L = 16384 (one CTA)
-constexpr int kBigLog = 16;  // 65536-point table for the cross-CTA (four-step) twiddles
+constexpr int kBigLog = 16;  // longest transform: 65536 points, split across a cluster
+constexpr int kBigTab = 512;  // cross-CTA (four-step) twiddle tables: W_65536^lo and W_65536^(256 hi)
 
 __host__ __device__ constexpr int plan_r0(int lg) { return (lg % 4 == 0) ? 16 : (1 << (lg % 4)); }
 // 8192 points use the three-stage plan 16 x 32 x 16 (two exchanges); other lengths radix-16
@@ -96,7 +97,9 @@ struct Slice {
   int seg_a;             // length of the stored non-negative-frequency segment (even)
   int w;                 // stored columns: P if the band limit is inactive, else seg_a + even(kmax)
   int wp;                // row pitch of buf (w rounded up to kTile)
-  int hp;                // row pitch of htab (kmax + 1)
+  int hp;                // row pitch of htab: kmax + 1 rounded up to even, or hq << hqs
+  int hqs;               // split grids: row entries grouped by residue mod 2^hqs (0: natural order)
+  int hq;                // split grids: entries per residue class of a row
   int tile_begin;        // first global column-tile index of this slice (column pass)
   int uf;                // log2 of the nearest-upsampling factor of the heights (0: none)
   int illum;             // parametric incident field: ILLUM_TILT | ILLUM_SPHERE (0: none)

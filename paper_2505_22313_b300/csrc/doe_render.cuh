@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
       }
     }
   }
-  cl.sync();  // peers have finished reading this CTA's shared memory
+  cluster_sync_relaxed();  // peers have finished reading this CTA's shared memory
 }
 
 // R3: one CTA per (pair of output rows, channel); transform length L = 2W.
