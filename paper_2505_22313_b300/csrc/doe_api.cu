@@ -155,8 +155,8 @@ long long band_mev(double lam, double dx, long P) {
 }
 
 // Columns per column-pass tile: 4, except for rows split into Q = P / 8192 sub-transforms,
-// where a cluster holds 8 / Q columns (P = 32768: 2, P = 65536: 1).
-int col_tile(long P) { return P == 65536 ? 1 : (P == 32768 ? 2 : kTile); }
+// where a cluster of 2 Q CTAs holds 2 columns.
+int col_tile(long P) { return (P == 65536 || P == 32768) ? 2 : kTile; }
 
 int upsample_log2(const doe_geom* g) { return (int)((g->flags >> DOE_UPSAMPLE_SHIFT) & 3u); }
 // Lanczos-3 interpolation of the layout (a pre-pass) instead of nearest (fused into pass A)

@@ -36,8 +36,10 @@ __device__ __forceinline__ float2 tw_apply(float2 a, float2 w) { return INV ? cm
 
 // frequency index of stored column position pos when rows are stored in sub-transform order
 __device__ __forceinline__ int big_pos_to_k(int pos, int Q) { return (pos % kBigL) * Q + pos / kBigL; }
-// column tile of split grids: 8 / Q columns (one cluster = tile columns x Q sub-transforms)
-__host__ __device__ constexpr int big_tile(int Q) { return Q >= 8 ? 1 : 8 / Q; }
+// column tile of split grids: two adjacent stored columns per cluster (one cluster = 2 Q CTAs:
+// 8 at P = 32768, 16 at P = 65536, the non-portable cluster size), so that the output rows
+// are written as 16-byte pairs and the input read 16 bytes per row
+__host__ __device__ constexpr int big_tile(int) { return 2; }
 
 // ------------------------------------------------------------------ rows, forward (pass A)
 template <int Q, bool ILLUM>
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
 
 // ------------------------------------------------------------------ columns (pass B / B*)
 // Cluster of TC x Q CTAs (TC = big_tile(Q) adjacent stored columns x Q sub-transforms, at
-// most 8); rank = c Q + s.
+// most 16); rank = c Q + s.
 // Rows are stored in sub-transform order (the row passes above).
 template <int Q>
 __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
@@ -224,9 +226,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   const int N = bt.N, off = bt.off;
   const int nin = adj ? P : N, yin0 = adj ? 0 : off;
   const int nout = adj ? N : P, yout0 = adj ? off : 0;
-  float2* rsm[CL];
-#pragma unroll
-  for (int k = 0; k < CL; ++k) rsm[k] = cl.map_shared_rank(sm, k);
+  // peers' shared memory, mapped where it is used (an array of 2 Q pointers would hold 4 Q registers)
+  auto rsm = [&](int k) { return cl.map_shared_rank(sm, k); };
   cluster_sync_relaxed();
   // decimation-in-frequency split of the TC columns over the row chunks y = y1 L + y2; each
   // thread takes the adjacent pair (y2, y2 + 1) so its shared-memory writes are 16 bytes
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
 #pragma unroll
       for (int sp = 0; sp < Q; ++sp) {
         const float2 a = cmul(col[0][cc][sp], wbig<P>(y2 * sp)), d = cmul(col[1][cc][sp], wbig<P>((y2 + 1) * sp));
-        reinterpret_cast<float4*>(rsm[cc * Q + sp])[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        reinterpret_cast<float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
     }
   }
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
     for (int cc = 0; cc < TC; ++cc) {
 #pragma unroll
       for (int sp = 0; sp < Q; ++sp) {
-        const float4 q4 = reinterpret_cast<const float4*>(rsm[cc * Q + sp])[swz(y2 >> 1)];
+        const float4 q4 = reinterpret_cast<const float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)];
         out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * y2));
         out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (y2 + 1)));
       }

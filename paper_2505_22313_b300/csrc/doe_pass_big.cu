@@ -37,6 +37,8 @@ cudaError_t prep_big_t() {
   if ((e = prep_one(pass_a_big_kernel<Q, false>, sb, nt)) || (e = prep_one(pass_a_big_kernel<Q, true>, sb, nt)))
     return e;
   if ((e = prep_one(pass_b_big_kernel<Q>, sb, nt))) return e;
+  if constexpr (big_tile(Q) * Q > 8)  // 16-CTA clusters: the non-portable size
+    if ((e = cudaFuncSetAttribute(pass_b_big_kernel<Q>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
   if ((e = prep_one(pass_c_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_c_adj_big_kernel<Q>, sb, nt))) return e;
   if ((e = prep_one(pass_a_adj_big_kernel<Q, false>, sb, nt)) ||
