@@ -55,6 +55,12 @@ extern "C" {
 
 /* ---- geometry flags ---- */
 #define DOE_BANDLIMIT 0x1u /* apply the band limit of the transfer function (default on) */
+/* With DOE_BANDLIMIT: a circular band, fx^2 + fy^2 < f_lim^2, instead of the separable square
+ * |fx|, |fy| < f_lim.  The paper cites the band-limited angular spectrum method (Sec. 3.1, next
+ * to Eq. 3) without fixing the window's shape; the disc is the rotation-invariant reading.  In
+ * integers: (kt, lt) is kept iff kt^2 + lt^2 < ceil((f_lim / du)^2) (the disc lies inside the
+ * square of kmax). */
+#define DOE_BANDLIMIT_CIRCULAR 0x2u
 /* Super-resolved design input: the heights h are a layout of (ny / f) x (nx / f) cells at
  * pitch f dx, nearest-upsampled by f = 2^u (u = 0..3) onto the dx simulation grid inside the
  * first pass (h_sim[i][x] = h[i / f][x / f]); gradients are returned on the layout (the sum
@@ -219,8 +225,9 @@ int doe_radial_grad(int n, int n_c, const float* grad_h, float* c_grad, void* ws
  * use it (for bit-exact checks).  For wavelength j: kmax[j] = the largest signed frequency
  * index kept per axis (ceil(f_lim / du) - 1 capped at P/2, with
  * f_lim = 1 / (lambda sqrt((2 du z)^2 + 1)), du = 1 / (P dx), Matsushima & Shimobaba 2009
- * as cited next to Eq. 3), and m_ev[j] = ceil(1 / (lambda du)^2): a sample (kt, lt) with
- * |kt|, |lt| <= kmax propagates iff kt^2 + lt^2 < m_ev.  Host arrays of n_lambda entries. */
+ * as cited next to Eq. 3), and m_ev[j] = ceil(1 / (lambda du)^2), or with
+ * DOE_BANDLIMIT_CIRCULAR min(that, ceil((f_lim / du)^2)): a sample (kt, lt) with
+ * |kt|, |lt| <= kmax is kept iff kt^2 + lt^2 < m_ev.  Host arrays of n_lambda entries. */
 int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev);
 
 /* Debug: writes the band mask the kernels apply for wavelength j (1 = H != 0) as device

@@ -60,6 +60,7 @@ def _load():
         "orc_dft1d": ([P, P, L, Ii], None),
         "orc_kmax": ([D, D, L, D, Ii], L),
         "orc_mev": ([D, D, L], ctypes.c_int64),
+        "orc_mlim": ([D, D, L, D, Ii], ctypes.c_int64),
         "orc_transfer": ([P, L, D, D, D, Ii], None),
         "orc_band_mask": ([P, L, D, D, D, Ii], None),
         "orc_propagate": ([L, L, D, D, D, D, Ii, P, P, P], Ii),
@@ -91,6 +92,16 @@ def _c128(a):
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _bl(bandlimit) -> int:
+    """Band-limit mode of the C oracle: 0 none, 1 the separable square (the default reading),
+    2 the circular disc (bandlimit="circular")."""
+    if isinstance(bandlimit, str):
+        if bandlimit != "circular":
+            raise ValueError(f"unknown band limit {bandlimit!r}")
+        return 2
+    return int(bool(bandlimit))
 
 
 def _check(rc: int, what: str):
@@ -126,22 +137,28 @@ def dft(x, inverse: bool = False) -> np.ndarray:
 
 # ---------------------------------------------------------------- band limit / H
 def kmax(lam: float, dx: float, P: int, z: float, bandlimit: bool = True) -> int:
-    return int(_load().orc_kmax(lam, dx, P, z, int(bandlimit)))
+    return int(_load().orc_kmax(lam, dx, P, z, _bl(bandlimit)))
 
 
 def m_ev(lam: float, dx: float, P: int) -> int:
     return int(_load().orc_mev(lam, dx, P))
 
 
+def m_lim(lam: float, dx: float, P: int, z: float, bandlimit=True) -> int:
+    """The bound of m = kt^2 + lt^2 the transfer function applies: the evanescent m_ev, and
+    for the circular band limit min(m_ev, ceil((f_lim / du)^2))."""
+    return int(_load().orc_mlim(lam, dx, P, z, _bl(bandlimit)))
+
+
 def transfer(P: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
     H = np.empty((P, P), np.complex128)
-    _load().orc_transfer(_ptr(H), P, dx, z, lam, int(bandlimit))
+    _load().orc_transfer(_ptr(H), P, dx, z, lam, _bl(bandlimit))
     return H
 
 
 def band_mask(P: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
     m = np.empty((P, P), np.uint8)
-    _load().orc_band_mask(_ptr(m), P, dx, z, lam, int(bandlimit))
+    _load().orc_band_mask(_ptr(m), P, dx, z, lam, _bl(bandlimit))
     return m
 
 
@@ -154,7 +171,7 @@ def propagate(h, dx, z, lam, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> 
     out = np.empty((P, P), np.complex128)
     e_in = _c128(e_in)
     _check(
-        _load().orc_propagate(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), _ptr(out)),
+        _load().orc_propagate(N, pad, dx, z, lam, n_index, _bl(bandlimit), _ptr(h), _ptr(e_in), _ptr(out)),
         "propagate",
     )
     return out
@@ -171,7 +188,7 @@ def psf(h, dx, z, lams, n_index=None, pad=2, e_in=None, bandlimit=True) -> np.nd
     e_in = _c128(e_in)
     for j, lam in enumerate(lams):
         _check(
-            _load().orc_psf(N, pad, dx, z, float(lam), float(nidx[j]), int(bandlimit), _ptr(h), _ptr(e_in), _ptr(out[j])),
+            _load().orc_psf(N, pad, dx, z, float(lam), float(nidx[j]), _bl(bandlimit), _ptr(h), _ptr(e_in), _ptr(out[j])),
             "psf",
         )
     return out
@@ -186,7 +203,7 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
     out = np.empty((rows.size, P), np.float64)
     e_in = _c128(e_in)
     _check(
-        _load().orc_psf_rows(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows), _ptr(out)),
+        _load().orc_psf_rows(N, pad, dx, z, lam, n_index, _bl(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows), _ptr(out)),
         "psf_rows",
     )
     return out
@@ -200,6 +217,8 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
 # flim_x = 1 / (lambda sqrt((2 dux z)^2 + 1)), likewise in y); a sample propagates iff
 # lambda^2 (fx^2 + fy^2) < 1, evaluated in FP64.
 def _kmax_axis(lam: float, dx: float, P: int, z: float, bandlimit: bool) -> int:
+    if isinstance(bandlimit, str):
+        raise ValueError("rectangular grids take the separable band limit only")
     if not bandlimit:
         return P // 2
     du = 1.0 / (P * dx)
@@ -391,7 +410,7 @@ def grad_rows(h, dx, z, lam, rows, g_rows, drows, n_index=1.46, pad=2, e_in=None
     out = np.empty((drows.size, N), np.float64)
     e_in = _c128(e_in)
     _check(
-        _load().orc_grad_rows(N, pad, dx, z, lam, n_index, int(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows),
+        _load().orc_grad_rows(N, pad, dx, z, lam, n_index, _bl(bandlimit), _ptr(h), _ptr(e_in), rows.size, _ptr(rows),
                               _ptr(g_rows), drows.size, _ptr(drows), _ptr(out)),
         "grad_rows",
     )
@@ -411,7 +430,7 @@ def grad(h, dx, z, lams, t_or_g, n_index=None, pad=2, e_in=None, mode="l2", band
     loss = ctypes.c_double(0.0)
     e_in = _c128(e_in)
     _check(
-        _load().orc_grad(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h), _ptr(e_in),
+        _load().orc_grad(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), _bl(bandlimit), _ptr(h), _ptr(e_in),
                          _ptr(t), 0 if mode == "l2" else 1, _ptr(g), ctypes.byref(loss)),
         "grad",
     )
@@ -428,7 +447,7 @@ def loss_l2(h64, dx, z, lams, target, n_index=None, pad=2, e_in=None, bandlimit=
     out = ctypes.c_double(0.0)
     e_in = _c128(e_in)
     _check(
-        _load().orc_loss_l2(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h64), _ptr(e_in), _ptr(t), ctypes.byref(out)),
+        _load().orc_loss_l2(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), _bl(bandlimit), _ptr(h64), _ptr(e_in), _ptr(t), ctypes.byref(out)),
         "loss",
     )
     return float(out.value)
@@ -448,7 +467,7 @@ def fd_exact(h, dx, z, lams, target, pix_y, pix_x, eps, n_index=None, pad=2, e_i
     out = np.empty(py.size, np.float64)
     e_in = _c128(e_in)
     _check(
-        _load().orc_fd_exact(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), int(bandlimit), _ptr(h), _ptr(e_in),
+        _load().orc_fd_exact(N, pad, dx, z, lams.size, _ptr(lams), _ptr(nidx), _bl(bandlimit), _ptr(h), _ptr(e_in),
                              _ptr(t), py.size, _ptr(py), _ptr(px), eps, _ptr(out)),
         "fd_exact",
     )

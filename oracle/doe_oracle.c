@@ -184,6 +184,24 @@ int64_t orc_mev(double lambda, double dx, long P) {
     return (int64_t)ceil(x);
 }
 
+/* Circular band limit (bandlimit == 2): the disc fx^2 + fy^2 < f_lim^2 instead of the square
+ * |fx|, |fy| < f_lim (the paper cites the band-limited ASM without fixing the window's shape;
+ * the disc is the rotation-invariant reading).  With m = kt^2 + lt^2 that is m < (f_lim/du)^2,
+ * i.e. m < m_circ = ceil((f_lim/du)^2) evaluated once in FP64.  The disc lies inside the
+ * square of kmax, so the square bounds still hold.  Returns the bound of m that the transfer
+ * function applies: m_ev, or min(m_ev, m_circ) for the disc. */
+int64_t orc_mlim(double lambda, double dx, long P, double z, int bandlimit) {
+    int64_t mev = orc_mev(lambda, dx, P);
+    if (bandlimit != 2) return mev;
+    double du = 1.0 / ((double)P * dx);
+    double t = 2.0 * du * z;
+    double flim = 1.0 / (lambda * sqrt(t * t + 1.0));
+    double r = flim / du;
+    double x = r * r;
+    int64_t mc = x > 9.0e18 ? INT64_MAX : (int64_t)ceil(x);
+    return mc < mev ? mc : mev;
+}
+
 /* H at integer frequency indices (kt, lt):
  *   exp(+i 2 pi z sqrt(1/lambda^2 - fx^2 - fy^2))  inside the band and propagating,
  *   0 otherwise.  The e^{+i} sign matches Eq. 2's e^{+i Phi} (Goodman's convention). */
@@ -201,7 +219,7 @@ static cplx orc_transfer_value(long kt, long lt, long kmax, int64_t mev, double 
 /* Full [P][P] transfer function in FFT order, H[l][k]. */
 void orc_transfer(cplx *H, long P, double dx, double z, double lambda, int bandlimit) {
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
-    int64_t mev = orc_mev(lambda, dx, P);
+    int64_t mev = orc_mlim(lambda, dx, P, z, bandlimit);
     double du = 1.0 / ((double)P * dx);
 #pragma omp parallel for schedule(static)
     for (long l = 0; l < P; ++l)
@@ -213,7 +231,7 @@ void orc_transfer(cplx *H, long P, double dx, double z, double lambda, int bandl
 /* Band mask, 1 where H != 0 by the integer rules above ([P][P] bytes). */
 void orc_band_mask(uint8_t *mask, long P, double dx, double z, double lambda, int bandlimit) {
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
-    int64_t mev = orc_mev(lambda, dx, P);
+    int64_t mev = orc_mlim(lambda, dx, P, z, bandlimit);
     for (long l = 0; l < P; ++l)
         for (long k = 0; k < P; ++k) {
             long kt = orc_signed_index(k, P), lt = orc_signed_index(l, P);
@@ -253,7 +271,7 @@ static void orc_pad(cplx *pad, long P, const cplx *src, long N) {
 static void orc_asm_inplace(cplx *a, long P, double dx, double z, double lambda, int bandlimit,
                             int conj_h) {
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
-    int64_t mev = orc_mev(lambda, dx, P);
+    int64_t mev = orc_mlim(lambda, dx, P, z, bandlimit);
     double du = 1.0 / ((double)P * dx);
     orc_fft2d(a, P, P, -1);
 #pragma omp parallel for schedule(static)
@@ -308,7 +326,7 @@ int orc_psf_rows(long N, long pad, double dx, double z, double lambda, double n_
     if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
-    int64_t mev = orc_mev(lambda, dx, P);
+    int64_t mev = orc_mlim(lambda, dx, P, z, bandlimit);
     double du = 1.0 / ((double)P * dx);
     double kp = orc_kprime(lambda, n_index);
     cplx *a = (cplx *)malloc((size_t)N * P * sizeof(cplx));
@@ -372,7 +390,7 @@ int orc_grad_rows(long N, long pad, double dx, double z, double lambda, double n
     if (N < 2 || (N & 1) || (pad != 1 && pad != 2)) return -1;
     long P = pad * N, off = (P - N) / 2;
     long kmax = orc_kmax(lambda, dx, P, z, bandlimit);
-    int64_t mev = orc_mev(lambda, dx, P);
+    int64_t mev = orc_mlim(lambda, dx, P, z, bandlimit);
     double du = 1.0 / ((double)P * dx);
     double kp = orc_kprime(lambda, n_index);
     double s = 1.0 / ((double)P * (double)P);

@@ -20,6 +20,7 @@ DOE_ETIMEDOUT = -5
 DOE_ESCRATCH = -6
 DOE_NOALLOC_SCRATCH_BYTES = 32 << 20
 DOE_BANDLIMIT = 0x1
+DOE_BANDLIMIT_CIRCULAR = 0x2
 DOE_FAULT_WAIT_TIMEOUT = 0x1
 DOE_FAULT_BOUNDS = 0x2
 DOE_UPSAMPLE_SHIFT = 4  # flags bits 4-5: log2 of the upsampling factor of the heights

@@ -28,7 +28,7 @@ class Geometry:
     lambdas: np.ndarray
     n_index: np.ndarray
     pad: int = 2
-    bandlimit: bool = True
+    bandlimit: bool | str = True  # True: separable square band; "circular": the disc; False: none
     upsample: int = 1
     lanczos: bool = False  # Lanczos-3 instead of nearest upsampling of the layout
     theta_x: float = 0.0   # incident plane-wave tilt [rad]
@@ -42,7 +42,10 @@ class Geometry:
         nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
         if upsample not in (1, 2, 4, 8):
             raise ValueError("upsample must be 1, 2, 4 or 8")
-        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bool(bandlimit), int(upsample), bool(lanczos),
+        if isinstance(bandlimit, str) and bandlimit != "circular":
+            raise ValueError("bandlimit must be True, False or 'circular'")
+        bl = bandlimit if isinstance(bandlimit, str) else bool(bandlimit)
+        return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bl, int(upsample), bool(lanczos),
                         float(theta_x), float(theta_y), float(src_d))
 
     @property
@@ -67,7 +70,8 @@ class Geometry:
         g.n_lambda = self.L
         g.lambda_ = self.lambdas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         g.n_index = self.n_index.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        g.flags = ((L.DOE_BANDLIMIT if self.bandlimit else 0) | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
+        g.flags = ((L.DOE_BANDLIMIT if self.bandlimit else 0) | (L.DOE_BANDLIMIT_CIRCULAR if self.bandlimit == "circular" else 0)
+                   | ((self.upsample.bit_length() - 1) << L.DOE_UPSAMPLE_SHIFT)
                    | (L.DOE_UPSAMPLE_LANCZOS3 if self.lanczos else 0))
         g.theta_x, g.theta_y, g.src_d = self.theta_x, self.theta_y, self.src_d
         return g

@@ -146,6 +146,20 @@ long band_kmax(double lam, double dx, long P, double z, bool bandlimit) {
   if (k < 0) k = 0;
   return k;
 }
+// The bound of kt^2 + lt^2 the transfer function applies: the evanescent cut, and with the
+// circular band limit also the disc m < ceil((f_lim / du)^2).
+long long band_mev(double lam, double dx, long P);
+long long band_mlim(const doe_geom* g, double lam, long P) {
+  const long long mev = band_mev(lam, g->dx, P);
+  if (!(g->flags & DOE_BANDLIMIT) || !(g->flags & DOE_BANDLIMIT_CIRCULAR)) return mev;
+  const double du = 1.0 / ((double)P * g->dx);
+  const double t = 2.0 * du * g->z;
+  const double flim = 1.0 / (lam * std::sqrt(t * t + 1.0));
+  const double r = flim / du;
+  const double x = r * r;
+  const long long mc = x > 9.0e18 ? LLONG_MAX : (long long)std::ceil(x);
+  return mc < mev ? mc : mev;
+}
 long long band_mev(double lam, double dx, long P) {
   const double du = 1.0 / ((double)P * dx);
   const double ld = lam * du;
@@ -229,7 +243,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
     s.hq = (int)(kmax >> s.hqs) + 1;
     s.hp = s.hq << s.hqs;
   }
-  s.mev = band_mev(lam, g->dx, P);
+  s.mev = band_mlim(g, lam, P);
   const double ld = lam * du;
   split(ld * ld, s.c_hi, s.c_lo);
   const double phi0 = 2.0 * kPi * g->z / lam;
@@ -529,7 +543,7 @@ int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev) {
   const long P = (long)g->pad * g->nx;
   for (int j = 0; j < g->n_lambda; ++j) {
     kmax[j] = (int32_t)band_kmax(g->lambda[j], g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
-    m_ev[j] = (int64_t)band_mev(g->lambda[j], g->dx, P);
+    m_ev[j] = (int64_t)band_mlim(g, g->lambda[j], P);
   }
   return DOE_OK;
 }

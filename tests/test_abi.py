@@ -72,6 +72,10 @@ def test_band_limits_random_geometries(lib):
         k, m = band_limits(g)
         assert int(k[0]) == oracle.kmax(lam, dx, 2 * N, z)
         assert int(m[0]) == oracle.m_ev(lam, dx, 2 * N)
+        # circular band: the same kmax, the bound of kt^2 + lt^2 including the disc
+        kc, mc = band_limits(Geometry.make(N, dx, z, [lam], bandlimit="circular"))
+        assert int(kc[0]) == int(k[0])
+        assert int(mc[0]) == oracle.m_lim(lam, dx, 2 * N, z, "circular")
 
 
 def _geom(**kw):

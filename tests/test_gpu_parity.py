@@ -939,3 +939,51 @@ def test_split_mixed_radix_propagate_and_batching():
     many = api.psf_many([ht, h2], [g, g2])
     assert torch.equal(many[0], api.psf(ht, g))
     assert torch.equal(many[1], api.psf(h2, g2))
+
+
+# -------------------------------------------------------------- circular band limit
+def test_circular_band_mask_bit_exact():
+    # the disc kt^2 + lt^2 < ceil((f_lim / du)^2): integer logic, equal to the oracle's mask
+    for N, dx, z, lams in [(32, 0.25e-6, 5e-6, [400e-9, 700e-9]), (256, 2e-6, 20e-3, [550e-9]),
+                           (180, 1e-6, 2e-3, [500e-9]), (16384, 1e-6, 50e-3, [550e-9])]:
+        g = Geometry.make(N, dx, z, lams, bandlimit="circular")
+        for j, lam in enumerate(lams):
+            m = api.debug_band_mask(g, j).cpu().numpy()
+            ref = oracle.band_mask(2 * N, dx, z, lam, bandlimit="circular")
+            assert np.array_equal(m, ref), (N, j)
+
+
+@pytest.mark.parametrize("N,pad", [(256, 2), (180, 2), (128, 1)])
+def test_circular_band_psf_and_grad_vs_oracle(N, pad):
+    dx, z = 2e-6, 20e-3 * N / 256
+    lams = [450e-9, 550e-9, 650e-9]
+    P = pad * N
+    h = _h(N, 1301)
+    T = inputs.spot_target(P, N, 3, 2301)
+    g = Geometry.make(N, dx, z, lams, pad=pad, bandlimit="circular")
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    ref = oracle.psf(h, dx, z, lams, pad=pad, bandlimit="circular")
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
+    rg, rloss = oracle.grad(h, dx, z, lams, T, pad=pad, bandlimit="circular")
+    assert rel_l2(gr.cpu().numpy(), rg) < TOL_GRAD
+    assert abs(loss.item() - rloss) <= 1e-5 * rloss
+    # the disc removes energy the square band keeps
+    assert I.sum() < api.psf(ht, Geometry.make(N, dx, z, lams, pad=pad)).cpu().numpy().sum()
+
+
+def test_circular_band_split_grid_rows_vs_oracle():
+    # 16384^2 DOE on the 32768^2 split grid at 50 mm: the square band is inactive there
+    # (kmax = P / 2) while the disc still cuts the corners of the spectrum
+    N, dx, z, lam = 16384, 1e-6, 50e-3, 550e-9
+    P = 2 * N
+    assert oracle.kmax(lam, dx, P, z) == P // 2
+    assert oracle.m_lim(lam, dx, P, z, "circular") < 2 * (P // 2) ** 2
+    h = _h(N, 1305)
+    g = Geometry.make(N, dx, z, [lam], bandlimit="circular")
+    I = api.psf(torch.from_numpy(h).cuda(), g)
+    rows = np.array([0, P // 4, P // 2, P // 2 + 5, P - 1])
+    got = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
+    ref = oracle.psf_rows(h, dx, z, lam, rows, bandlimit="circular")
+    assert rel_l2(got, ref) < TOL_PSF, rel_l2(got, ref)

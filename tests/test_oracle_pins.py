@@ -105,6 +105,70 @@ def test_band_mask_integer_rules():
     assert (~prop).any()  # the case really exercises the evanescent cut
 
 
+# ------------------------------------------------------------------ circular band limit
+def _flim(lam, du, z):
+    return 1.0 / (lam * np.sqrt((2 * du * z) ** 2 + 1))
+
+
+@pytest.mark.parametrize("P,dx,z,lam", [(64, 0.25e-6, 5e-6, 700e-9), (512, 2e-6, 20e-3, 550e-9),
+                                        (256, 1e-6, 2e-3, 450e-9), (96, 1e-6, 1e-3, 633e-9)])
+def test_circular_band_mask_rules(P, dx, z, lam):
+    # the disc fx^2 + fy^2 < f_lim^2 (and the evanescent cut), written out in floating point
+    # here, against the oracle's integer rule m < ceil((f_lim / du)^2); the disc is inside the
+    # square band and symmetric under swapping the axes
+    m = oracle.band_mask(P, dx, z, lam, bandlimit="circular").astype(bool)
+    sq = oracle.band_mask(P, dx, z, lam).astype(bool)
+    du = 1.0 / (P * dx)
+    kt = np.where(np.arange(P) < P // 2, np.arange(P), np.arange(P) - P).astype(np.float64)
+    fx, fy = kt[None, :] * du, kt[:, None] * du
+    disc = fx * fx + fy * fy < _flim(lam, du, z) ** 2
+    prop = lam**2 * (fx * fx + fy * fy) < 1.0
+    assert np.array_equal(m, disc & prop)
+    assert np.array_equal(m & sq, m) and (sq & ~m).any()  # strictly inside the square
+    assert np.array_equal(m, m.T)
+    assert oracle.m_lim(lam, dx, P, z, "circular") <= oracle.m_ev(lam, dx, P)
+
+
+def test_circular_band_plane_waves_closed_form():
+    # pad = 1, flat plate lit by a plane wave on an exact spectral line (kx, ky): inside the disc
+    # ASM multiplies it by H(fx, fy); outside the disc but inside the square the circular band
+    # removes it entirely, while the square band keeps it
+    N, dx, lam, z, c = 64, 1e-6, 550e-9, 200e-6, 0.3e-6
+    du = 1.0 / (N * dx)
+    r = _flim(lam, du, z) / du  # disc radius in bins (18.4)
+    k = oracle.kmax(lam, dx, N, z)
+    inside, outside = (int(0.5 * r), -int(0.4 * r)), (k, -k)  # the square's corner lies outside the disc
+    assert inside[0] ** 2 + inside[1] ** 2 < r * r < outside[0] ** 2 + outside[1] ** 2
+    h = np.full((N, N), c, np.float32)
+    for (mx, my), kept in ((inside, True), (outside, False)):
+        e_in = oracle.incident(N, dx, lam, np.arcsin(mx * lam / (N * dx)), np.arcsin(my * lam / (N * dx)))
+        ph = 2 * np.pi * 0.46 * float(np.float32(c)) / lam + 2 * np.pi * z * np.sqrt(1 / lam**2 - (mx * du) ** 2 - (my * du) ** 2)
+        ref = np.exp(1j * ph) * e_in
+        e_c = oracle.propagate(h, dx, z, lam, n_index=1.46, pad=1, e_in=e_in, bandlimit="circular")
+        e_s = oracle.propagate(h, dx, z, lam, n_index=1.46, pad=1, e_in=e_in)
+        assert np.abs(e_s - ref).max() < 1e-9
+        assert np.abs(e_c - (ref if kept else 0.0)).max() < 1e-9
+
+
+@pytest.mark.parametrize("N", [128, 90])
+def test_parseval_over_circular_band(N):
+    dx, z, lam = 1e-6, 5e-3, 550e-9
+    P = 2 * N
+    h = inputs.heights(N, 12)
+    e = oracle.propagate(h, dx, z, lam, bandlimit="circular")
+    epad = np.zeros((P, P), np.complex128)
+    epad[N // 2:N // 2 + N, N // 2:N // 2 + N] = np.exp(1j * 2 * np.pi * 0.46 * h.astype(np.float64) / lam)
+    U = np.fft.fft2(epad)
+    du = 1.0 / (P * dx)
+    kt = np.fft.fftfreq(P, 1.0 / P)
+    disc = (kt[None, :] * du) ** 2 + (kt[:, None] * du) ** 2 < _flim(lam, du, z) ** 2
+    lhs = (np.abs(e) ** 2).sum()
+    rhs = (np.abs(U[disc]) ** 2).sum() / P**2
+    assert abs(lhs - rhs) / rhs < 1e-12
+    # the disc keeps less energy than the square band of the same f_lim
+    assert lhs < (np.abs(oracle.propagate(h, dx, z, lam)) ** 2).sum()
+
+
 # ------------------------------------------------------------------ closed forms
 @pytest.mark.parametrize("P,z,lam", [(16, 20e-3, 550e-9), (64, 0.1, 550e-9), (256, 50e-3, 450e-9), (1024, 0.1, 650e-9),
                                      (48, 20e-3, 550e-9), (720, 50e-3, 450e-9)])
