@@ -10,6 +10,7 @@ from pathlib import Path
 
 _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libdoe.so"
+DEBUG_LIB_PATH = _PKG / "libdoe_debug.so"  # every kernel index bounds-checked (DOE_DEBUG build)
 
 DOE_OK = 0
 DOE_EINVAL = -1
@@ -67,12 +68,19 @@ _lib = None
 
 
 def load(path: Path | None = None) -> ctypes.CDLL:
+    """The library (libdoe.so), loaded once per process."""
     global _lib
     if _lib is not None:
         return _lib
-    p = Path(path) if path else LIB_PATH
+    _lib = open_library(Path(path) if path else LIB_PATH)
+    return _lib
+
+
+def open_library(p: Path) -> ctypes.CDLL:
+    """A separate handle on a build of the library (libdoe.so or the bounds-checked
+    libdoe_debug.so) with the C signatures set."""
     if not p.exists():
-        raise RuntimeError(f"libdoe.so not built ({p}); run `python -m paper_2505_22313_b300.build`")
+        raise RuntimeError(f"{p.name} not built ({p}); run `python -m paper_2505_22313_b300.build`")
     lib = ctypes.CDLL(str(p))
     V = ctypes.c_void_p
     I = ctypes.c_int
@@ -111,7 +119,6 @@ def load(path: Path | None = None) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    _lib = lib
     return lib
 
 

@@ -274,6 +274,7 @@ struct Layout {
   size_t ltmp = 0;           // Lanczos-3: the [N / f][N] buffer of the separable passes
   size_t mrtw = 0;           // mixed radix: the [M] twiddle table of the per-CTA transform
   size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
+  long tbuf_rows = 0;        // rows of the column-tiled buffers (N forward, P with the adjoint)
 };
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
@@ -293,6 +294,7 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_r
     off = align256(off + (size_t)(s.kmax + 1) * s.hp * sizeof(float2));
   }
   const long R = op == DOE_OP_GRAD ? P : N;
+  L.tbuf_rows = R;
   for (const auto& s : sl) {
     L.tbuf.push_back(off);
     off = align256(off + (size_t)R * s.wp * sizeof(float2));
@@ -364,6 +366,10 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
     bt.s[j].htab = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.htab[j]);
     bt.s[j].tbuf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.tbuf[j]);
     if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P * kMaxQf;
+    bt.s[j].n_buf = (long long)bt.P * sl[j].wp;
+    bt.s[j].n_tbuf = (long long)lay.tbuf_rows * sl[j].wp;
+    bt.s[j].n_htab = (long long)(sl[j].kmax + 1) * sl[j].hp;
+    if (lay.loss) bt.s[j].n_loss = (long long)bt.P * kMaxQf;
     bt.s[j].tile_begin = tiles;
     tiles += sl[j].wp / col_tile(bt.P);
     if (sl[j].kmax > kmx) kmx = sl[j].kmax;
@@ -439,6 +445,10 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
     bt.s[j].e_in = e_in ? reinterpret_cast<const float2*>(e_in[r]) : nullptr;
     const size_t esz = out_kind == OUT_PSF ? sizeof(float) : sizeof(float2);
     bt.s[j].out = static_cast<char*>(out[r]) + (size_t)jr * P * P * esz;
+    const long nl = lanczos(&geoms[r]) ? N : (N >> upsample_log2(&geoms[r]));
+    bt.s[j].n_h = (long long)nl * nl;
+    bt.s[j].n_ein = e_in && e_in[r] ? (long long)N * N : 0;
+    bt.s[j].n_out = (long long)P * P;
   }
   if ((rc = forward_passes(bt, st)) != DOE_OK) return rc;
   bt.mode = out_kind;
@@ -507,13 +517,18 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   if (lz && launch_lanczos_up(h, reinterpret_cast<float*>(static_cast<char*>(ws) + lay.ltmp), const_cast<float*>(hsim),
                              N, lanczos_table(N, upsample_log2(g)), st) != cudaSuccess)
     return DOE_ECUDA;
+  const int uf = upsample_log2(g);
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j].h = lz ? hsim : h;
     bt.s[j].e_in = reinterpret_cast<const float2*>(e_in);
     bt.s[j].tgt = t_or_dldi + (size_t)j * P * P;
+    const long nl = lz ? N : (N >> uf);
+    bt.s[j].n_h = (long long)nl * nl;
+    bt.s[j].n_ein = e_in ? (long long)N * N : 0;
+    bt.s[j].n_tgt = (long long)P * P;
   }
-  const int uf = upsample_log2(g);
   bt.grad = uf ? reinterpret_cast<float*>(static_cast<char*>(ws) + lay.gsim) : grad_h;
+  bt.n_grad = (long long)N * N;
   const int lg = ilog2(P);
   if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
   if (!recompute && bt.mr && launch_mr_twiddles(bt, st) != cudaSuccess) return DOE_ECUDA;

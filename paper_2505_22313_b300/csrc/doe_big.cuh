@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
   const int i = blockIdx.x / Q;
   const Slice& sl = bt.s[blockIdx.y];
   const int t = threadIdx.x, N = bt.N, off = bt.off;
-  const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
-  const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+  const bool erow = sl.e_in != nullptr;
   IncRow ir = {0.f, 0u};
   if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
   float4* rsm[Q];
@@ -69,7 +68,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
       const int x = n1 * L + n2 - off;  // even
       xa[n1] = xb[n1] = make_float2(0.f, 0.f);
       if ((unsigned)x < (unsigned)N) {
-        const float2 hv = heights_pair(hrow, x, sl.uf);
+        const float2 hv = heights_pair(sl, N, i, x);
         if (ILLUM && sl.illum) {
           xa[n1] = transmittance_inc(hv.x, sl, ir, x - N / 2);
           xb[n1] = transmittance_inc(hv.y, sl, ir, x + 1 - N / 2);
@@ -78,7 +77,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
           xb[n1] = sl.uf ? xa[n1] : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
         }
         if (erow) {
-          const float4 ev = __ldcs(erow + (x >> 1));
+          const float4 ev = ein_pair(sl, N, i, x);
           xa[n1] = cmul(xa[n1], make_float2(ev.x, ev.y));
           xb[n1] = cmul(xb[n1], make_float2(ev.z, ev.w));
         }
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const float2 a = cmul(xa[q], wbig<P>(n2 * q)), b = cmul(xb[q], wbig<P>((n2 + 1) * q));
-      rsm[q][swz(n2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
+      if (DOE_IN(swz(n2 >> 1), L / 2)) rsm[q][swz(n2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
     }
   }
   cl.sync();
@@ -103,24 +102,27 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_big_kern
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);
-      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, kTile)), make_float4(a.x, a.y, c.x, c.y));
+      if (DOE_IN(tiled_at(i, pos, N, kTile) + 1, sl.n_tbuf))
+        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(i, pos, N, kTile)), make_float4(a.x, a.y, c.x, c.y));
     }
 }
 
 // Inverse sub-transform s of a stored row (positions s L .. s L + L - 1), result written to
 // this CTA's shared memory in natural order.
 template <int Q>
-__device__ __forceinline__ void big_row_inverse_to_smem(const float2* row, int s, int t, float2* sm) {
+__device__ __forceinline__ void big_row_inverse_to_smem(const Slice& sl, int y, int s, int t, float2* sm) {
   constexpr int L = kBigL;
   using F = First<L, true>;
   using H = Last<L, true>;
-  const float4* src = reinterpret_cast<const float4*>(row + (size_t)s * L);
+  const size_t r0 = (size_t)y * sl.wp + (size_t)s * L;
+  const float4* src = reinterpret_cast<const float4*>(sl.buf + r0);
   float2 v[32];
 #pragma unroll
   for (int b = 0; b < F::B; b += 2)
 #pragma unroll
     for (int r = 0; r < F::R; ++r) {
-      const float4 q = __ldcs(src + (F::idx(t, b, r) >> 1));
+      const float4 q = DOE_IN(r0 + F::idx(t, b, r) + 1, sl.n_buf) ? __ldcs(src + (F::idx(t, b, r) >> 1))
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
       v[b * F::R + r] = make_float2(q.x, q.y);
       v[(b + 1) * F::R + r] = make_float2(q.z, q.w);
     }
@@ -132,7 +134,7 @@ __device__ __forceinline__ void big_row_inverse_to_smem(const float2* row, int s
 #pragma unroll
     for (int r = 0; r < H::R; ++r) {
       const float2 a = v[b * H::R + r], c = v[(b + 1) * H::R + r];
-      s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
+      if (DOE_IN(swz(H::idx(t, b, r) >> 1), L / 2)) s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
     }
 }
 
@@ -143,7 +145,7 @@ __device__ __forceinline__ void big_combine(float4* const (&rsm)[Q], int x2, flo
   constexpr int P = kBigL * Q;
 #pragma unroll
   for (int sp = 0; sp < Q; ++sp) {
-    const float4 q4 = rsm[sp][swz(x2 >> 1)];
+    const float4 q4 = DOE_IN(swz(x2 >> 1), kBigL / 2) ? rsm[sp][swz(x2 >> 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
     oa[sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * x2));
     ob[sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (x2 + 1)));
   }
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
   float4* rsm[Q];
 #pragma unroll
   for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
-  big_row_inverse_to_smem<Q>(sl.buf + (size_t)y * sl.wp, s, t, sm);
+  big_row_inverse_to_smem<Q>(sl, y, s, t, sm);
   cl.sync();
   const float sc = bt.inv_p2;
 #pragma unroll
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
     for (int q = 0; q < Q; ++q) {
       const float2 a = cscale(oa[q], sc), b = cscale(ob[q], sc);
       const size_t o = (size_t)y * P + (size_t)q * L + x2;
+      if (!DOE_IN(o + 1, sl.n_out)) continue;
       if (bt.mode == OUT_PSF)
         __stcs(reinterpret_cast<float2*>(static_cast<float*>(sl.out) + o),
                make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(b.x, b.x, b.y * b.y)));
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
         const int y = y1 * L + y2 + u;
         if ((unsigned)(y - yin0) < (unsigned)nin) {
           const float2* src = sl.tbuf + tiled_at(y - yin0, pos0, nin, kTile);
+          if (!DOE_IN(tiled_at(y - yin0, pos0, nin, kTile) + TC - 1, sl.n_tbuf)) src = sl.tbuf;  // skip: read entry 0
           if constexpr (TC >= 2) {
 #pragma unroll
             for (int f = 0; f < TC / 2; ++f) {
@@ -266,7 +270,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
 #pragma unroll
       for (int sp = 0; sp < Q; ++sp) {
         const float2 a = cmul(col[0][cc][sp], wbig<P>(y2 * sp)), d = cmul(col[1][cc][sp], wbig<P>((y2 + 1) * sp));
-        reinterpret_cast<float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        if (DOE_IN(swz(y2 >> 1), L / 2))
+          reinterpret_cast<float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
     }
   }
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
       for (int r = 0; r < G::R; ++r) {
         const int a = abs_signed(s + Q * G::idx(t, b, r), P);
         float2& x = v[b * G::R + r];
-        if (live && a <= sl.kmax) {
+        if (live && a <= sl.kmax && DOE_IN((size_t)abs_signed(kcol, P) * sl.hp + htab_col(sl, a), sl.n_htab)) {
           const float2 hv = hrow[htab_col(sl, a)];  // consecutive threads: consecutive entries
           x = adj ? cmulc(x, hv) : cmul(x, hv);
         } else {
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
 #pragma unroll
       for (int r = 0; r < Hh::R; ++r) {
         const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
-        s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        if (DOE_IN(swz(Hh::idx(t, b, r) >> 1), L / 2)) s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
   cl.sync();
@@ -312,7 +317,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
     for (int cc = 0; cc < TC; ++cc) {
 #pragma unroll
       for (int sp = 0; sp < Q; ++sp) {
-        const float4 q4 = reinterpret_cast<const float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)];
+        const float4 q4 = DOE_IN(swz(y2 >> 1), L / 2) ? reinterpret_cast<const float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)]
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
         out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * y2));
         out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (y2 + 1)));
       }
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
 #pragma unroll
       for (int y1 = 0; y1 < Q; ++y1) {
         const int y = y1 * L + y2 + u;
-        if ((unsigned)(y - yout0) < (unsigned)nout) {
+        if ((unsigned)(y - yout0) < (unsigned)nout && DOE_IN((size_t)(y - yout0) * sl.wp + pos0 + TC - 1, sl.n_buf)) {
           if constexpr (TC >= 2) {
             float4* dst = reinterpret_cast<float4*>(sl.buf + (size_t)(y - yout0) * sl.wp + pos0);
 #pragma unroll
@@ -352,11 +358,10 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
   const int y = blockIdx.x / Q;
   const Slice& sl = bt.s[blockIdx.y];
   const int t = threadIdx.x;
-  float2* row = sl.buf + (size_t)y * sl.wp;
   float4* rsm[Q];
 #pragma unroll
   for (int c = 0; c < Q; ++c) rsm[c] = reinterpret_cast<float4*>(cl.map_shared_rank(sm, c));
-  big_row_inverse_to_smem<Q>(row, s, t, sm);
+  big_row_inverse_to_smem<Q>(sl, y, s, t, sm);
   cl.sync();
   float2 ga[IT][Q], gb[IT][Q];
 #pragma unroll
@@ -370,7 +375,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
     const int x2 = s * SH + 2 * t + it * 2 * T;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const float2 tv = __ldcs(reinterpret_cast<const float2*>(trow + (size_t)q * L + x2));
+      const float2 tv = DOE_IN((size_t)y * P + (size_t)q * L + x2 + 1, sl.n_tgt)
+                            ? __ldcs(reinterpret_cast<const float2*>(trow + (size_t)q * L + x2)) : make_float2(0.f, 0.f);
       const float2 ea = cscale(ga[it][q], sc), eb = cscale(gb[it][q], sc);
       float wa, wb;
       if (bt.mode == GRAD_L2) {
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
 #pragma unroll
     for (int sp = 0; sp < Q; ++sp) {
       const float2 a = cmul(ga[it][sp], wbig<P>(x2 * sp)), b = cmul(gb[it][sp], wbig<P>((x2 + 1) * sp));
-      rsm[sp][swz(x2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
+      if (DOE_IN(swz(x2 >> 1), L / 2)) rsm[sp][swz(x2 >> 1)] = make_float4(a.x, a.y, b.x, b.y);
     }
   }
   cl.sync();
@@ -404,10 +410,11 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_adj_big_
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
       const int pos = s * L + G::idx(t, b, r);  // J1 row y of the column-tiled buffer (P rows)
-      __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, kTile)), make_float4(a.x, a.y, c.x, c.y));
+      if (DOE_IN(tiled_at(y, pos, P, kTile) + 1, sl.n_tbuf))
+        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(y, pos, P, kTile)), make_float4(a.x, a.y, c.x, c.y));
     }
   const double tot = block_sum<T>((double)acc, red);
-  if (t == 0 && sl.loss_part) sl.loss_part[(size_t)y * Q + s] = tot;
+  if (t == 0 && sl.loss_part && DOE_IN((size_t)y * Q + s, sl.n_loss)) sl.loss_part[(size_t)y * Q + s] = tot;
 }
 
 // ------------------------------------------------------------------ DOE rows, adjoint (pass A*)
@@ -430,10 +437,9 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
   for (int j = 0; j < bt.S; ++j) {
     const Slice& sl = bt.s[j];
     if (j > 0) cl.sync();  // peers finished reading the previous slice's sub-transforms
-    big_row_inverse_to_smem<Q>(sl.buf + (size_t)i * sl.wp, s, t, sm);
+    big_row_inverse_to_smem<Q>(sl, i, s, t, sm);
     cl.sync();
-    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
-    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+    const bool erow = sl.e_in != nullptr;
     const float k2 = -2.f * sl.kp_hi;
     IncRow ir = {0.f, 0u};
     if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
       for (int q = 0; q < Q; ++q) {
         const int x = q * L + x2 - off;  // even
         if ((unsigned)x < (unsigned)N) {
-          const float2 hv = heights_pair(hrow, x, sl.uf);
+          const float2 hv = heights_pair(sl, N, i, x);
           float2 e0, e1;
           if (ILLUM && sl.illum) {
             e0 = transmittance_inc(hv.x, sl, ir, x - N / 2);
@@ -456,7 +462,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
             e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
           }
           if (erow) {
-            const float4 ev = __ldcs(erow + (x >> 1));
+            const float4 ev = ein_pair(sl, N, i, x);
             e0 = cmul(e0, make_float2(ev.x, ev.y));
             e1 = cmul(e1, make_float2(ev.z, ev.w));
           }
@@ -475,7 +481,8 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_a_adj_big_
     for (int q = 0; q < Q; ++q) {
       const int x = q * L + x2 - off;
       if ((unsigned)x < (unsigned)N)
-        *reinterpret_cast<float2*>(bt.grad + (size_t)i * N + x) = make_float2(acc[it][q][0], acc[it][q][1]);
+        if (DOE_IN((size_t)i * N + x + 1, bt.n_grad))
+          *reinterpret_cast<float2*>(bt.grad + (size_t)i * N + x) = make_float2(acc[it][q][0], acc[it][q][1]);
     }
   }
 }

@@ -71,6 +71,20 @@ static cudaError_t read_fault_of_this_unit(unsigned int* word) {
 enum : unsigned int { FAULT_WAIT_TIMEOUT = 1u, FAULT_BOUNDS = 2u };
 __device__ __forceinline__ void raise_fault(unsigned int bits) { atomicOr(&g_fault_word, bits); }
 
+// Bounds checks of the DOE_DEBUG build: DOE_IN(i, n) is true when 0 <= i < n; otherwise it sets
+// FAULT_BOUNDS and is false, and the access it guards is skipped (a load then yields zero).  In
+// the release build it is the constant true and the checks compile away.
+#ifdef DOE_DEBUG
+__device__ __forceinline__ bool doe_in(long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  raise_fault(FAULT_BOUNDS);
+  return false;
+}
+#define DOE_IN(i, n) ::doe::doe_in((long long)(i), (long long)(n))
+#else
+#define DOE_IN(i, n) true
+#endif
+
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -249,7 +263,9 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[E], int t) {
       const float4* tw = reinterpret_cast<const float4*>(g_tw + tw_offset(X::LOG, INV && !tw_shared_dirs(X::LOG), S));
 #pragma unroll
       for (int r = 0; r < R; r += 2) {
-        const float4 w = __ldg(tw + tw_quad(R, X::NS, k, r));
+        const long q = tw_quad(R, X::NS, k, r);
+        const float4 w = DOE_IN(2 * (tw_offset(X::LOG, INV && !tw_shared_dirs(X::LOG), S) + 2 * q) + 3, 2 * kTwTotal)
+                             ? __ldg(tw + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (r > 0) v[b * R + r] = ctw<INV>(v[b * R + r], make_float2(w.x, w.y));
         v[b * R + r + 1] = ctw<INV>(v[b * R + r + 1], make_float2(w.z, w.w));
       }
@@ -275,8 +291,8 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
 #pragma unroll
     for (int q = 0; q < R / 2; ++q) {
       const int ch = (c0 & ~7) + 16 * q + ((c0 & 7) ^ (((c0 >> 4) + q) & 7));
-      sm[(ch << 1) | odd] = v[2 * q];
-      sm[((ch + 8) << 1) | odd] = v[2 * q + 1];
+      if (DOE_IN((ch << 1) | odd, L)) sm[(ch << 1) | odd] = v[2 * q];
+      if (DOE_IN(((ch + 8) << 1) | odd, L)) sm[((ch + 8) << 1) | odd] = v[2 * q + 1];
     }
   } else if constexpr (!X::PAIRED && NS > 1) {
     // one butterfly per thread: its outputs base + r Ns are not adjacent, 8-byte accesses
@@ -284,7 +300,8 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
     const int k = jj & (NS - 1);
     const int base = (jj - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[phys(base + r * NS)] = v[r];
+    for (int r = 0; r < R; ++r)
+      if (DOE_IN(phys(base + r * NS), L)) sm[phys(base + r * NS)] = v[r];
   } else if constexpr (NS == 1) {
     // butterfly j's outputs are the contiguous elements j R + r: chunks c0 + d, d < R / 2, all
     // inside one 16-chunk row of the swizzle (c0 = j R / 2), so the swizzle term is fixed
@@ -293,7 +310,8 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
       const int c0 = X::j(t, b) * (R / 2), x = (c0 >> 4) & 7;
 #pragma unroll
       for (int r = 0; r < R; r += 2)
-        s4[(c0 + r / 2) ^ x] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
+        if (DOE_IN((c0 + r / 2) ^ x, L / 2))
+          s4[(c0 + r / 2) ^ x] = make_float4(v[b * R + r].x, v[b * R + r].y, v[b * R + r + 1].x, v[b * R + r + 1].y);
     }
   } else {
     // the pair (j, j + 1) writes adjacent elements base + r Ns, base + 1 + r Ns: chunks c0 + C r,
@@ -312,7 +330,8 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[E], int t, float2*
         else if constexpr (C % 16 == 0) ch = (c0 ^ ((x0 + (C / 16) * r) & 7)) + C * r;
         else if constexpr (C == 8) ch = (c0 & ~7) + 8 * r + ((c0 & 7) ^ ((x0 + (r >> 1)) & 7));
         else ch = swz(c0 + C * r);
-        s4[ch] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
+        if (DOE_IN(ch, L / 2))
+          s4[ch] = make_float4(v[b * R + r].x, v[b * R + r].y, v[(b + 1) * R + r].x, v[(b + 1) * R + r].y);
       }
     }
   }
@@ -330,14 +349,18 @@ __device__ __forceinline__ void stage_load(float2 (&v)[E], int t, const float2* 
   if constexpr (!X::PAIRED) {
     const int p0 = phys(X::j(t, 0));
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[kFlat ? p0 + r * (L / R) : phys(X::j(t, 0) + r * (L / R))];
+    for (int r = 0; r < R; ++r) {
+      const int e = kFlat ? p0 + r * (L / R) : phys(X::j(t, 0) + r * (L / R));
+      v[r] = DOE_IN(e, L) ? sm[e] : make_float2(0.f, 0.f);
+    }
   } else {
 #pragma unroll
     for (int b = 0; b < X::B; b += 2) {
       const int c0 = X::j(t, b) >> 1, q0 = swz(c0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float4 q = s4[kFlat ? q0 + r * (L / R / 2) : swz(c0 + r * (L / R / 2))];
+        const int ch = kFlat ? q0 + r * (L / R / 2) : swz(c0 + r * (L / R / 2));
+        const float4 q = DOE_IN(ch, L / 2) ? s4[ch] : make_float4(0.f, 0.f, 0.f, 0.f);
         v[b * R + r] = make_float2(q.x, q.y);
         v[(b + 1) * R + r] = make_float2(q.z, q.w);
       }

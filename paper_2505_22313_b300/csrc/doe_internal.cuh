@@ -171,13 +171,20 @@ __device__ __forceinline__ float2 transmittance_inc(float hv, const Slice& s, In
   return make_float2(amp * cs, amp * sn);
 }
 
-// Heights of the adjacent simulation samples (x, x + 1), x even, of the DOE row whose layout
-// row starts at hrow: without upsampling one 8-byte load; with nearest upsampling by 2^uf
-// (uf >= 1) both samples lie in the same layout cell x >> uf.
-__device__ __forceinline__ float2 heights_pair(const float* hrow, int x, int uf) {
-  if (uf == 0) return __ldcs(reinterpret_cast<const float2*>(hrow + x));
-  const float h = __ldcs(hrow + (x >> uf));
+// Heights of the adjacent simulation samples (x, x + 1), x even, of DOE row i: without
+// upsampling one 8-byte load; with nearest upsampling by 2^uf (uf >= 1) both samples lie in the
+// same layout cell x >> uf.
+__device__ __forceinline__ float2 heights_pair(const Slice& s, int N, int i, int x) {
+  const size_t o = (size_t)(i >> s.uf) * (N >> s.uf) + (x >> s.uf);  // layout cell of DOE row i
+  if (s.uf == 0)
+    return DOE_IN(o + 1, s.n_h) ? __ldcs(reinterpret_cast<const float2*>(s.h + o)) : make_float2(0.f, 0.f);
+  const float h = DOE_IN(o, s.n_h) ? __ldcs(s.h + o) : 0.f;
   return make_float2(h, h);
+}
+// Incident field array values at DOE samples (x, x + 1) of row i (x even): one 16-byte load.
+__device__ __forceinline__ float4 ein_pair(const Slice& s, int N, int i, int x) {
+  const size_t o = (size_t)i * N + x;
+  return DOE_IN(o + 1, s.n_ein) ? __ldcs(reinterpret_cast<const float4*>(s.e_in + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Cluster barrier without memory ordering, for a point where no CTA publishes data: the

@@ -39,23 +39,26 @@ __device__ __forceinline__ void store_band_row(const float2 (&v)[32], int t, int
         float2 a = v[b * G::R + r], c = v[(b + 1) * G::R + r];
         if (abs_signed(k, L) > sl.kmax) a = make_float2(0.f, 0.f);
         if (abs_signed(k + 1, L) > sl.kmax) c = make_float2(0.f, 0.f);
-        __stcs(reinterpret_cast<float4*>(sl.tbuf + tiled_at(row, pos, R, kTile)), make_float4(a.x, a.y, c.x, c.y));
+        const size_t o = tiled_at(row, pos, R, kTile);
+        if (DOE_IN(o + 1, sl.n_tbuf)) __stcs(reinterpret_cast<float4*>(sl.tbuf + o), make_float4(a.x, a.y, c.x, c.y));
       }
     }
 }
 
-// Loads a stored band row into the first-stage registers of a row IFFT (16-byte pairs).
+// Loads stored band row `row` of the slice's field buffer into the first-stage registers of a
+// row IFFT (16-byte pairs).
 template <int L>
-__device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, const float2* src, const Slice& sl) {
+__device__ __forceinline__ void load_band_row(float2 (&v)[32], int t, int row, const Slice& sl) {
   using F = First<L, true>;
-  const float4* s4 = reinterpret_cast<const float4*>(src);
+  const size_t r0 = (size_t)row * sl.wp;
+  const float4* s4 = reinterpret_cast<const float4*>(sl.buf + r0);
 #pragma unroll
   for (int b = 0; b < F::B; b += 2)
 #pragma unroll
     for (int r = 0; r < F::R; ++r) {
       const int pos = band_pos(F::idx(t, b, r), L, sl.seg_a, sl.w);
       float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (pos >= 0) q = __ldcs(s4 + (pos >> 1));
+      if (pos >= 0 && DOE_IN(r0 + pos + 1, sl.n_buf)) q = __ldcs(s4 + (pos >> 1));
       v[b * F::R + r] = make_float2(q.x, q.y);
       v[(b + 1) * F::R + r] = make_float2(q.z, q.w);
     }
@@ -73,11 +76,14 @@ __device__ __forceinline__ constexpr bool pad2_live(int r) {
 }
 
 // ------------------------------------------------------------------ pass A: DOE rows
-// 16-byte asynchronous copies of a height row into shared memory (cp.async, L2 only).
-__device__ __forceinline__ void stage_heights(float* dst, const float* src, int n, int t, int nt) {
+// 16-byte asynchronous copies of the n heights at element o of the slice's layout into shared
+// memory (cp.async, L2 only).
+__device__ __forceinline__ void stage_heights(float* dst, const Slice& sl, size_t o, int n, int t, int nt) {
   const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+  const float* src = sl.h + o;
   for (int k = t; k < n / 4; k += nt)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * k), "l"(src + 4 * k) : "memory");
+    if (DOE_IN(o + 4 * k + 3, sl.n_h))
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * k), "l"(src + 4 * k) : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 __device__ __forceinline__ void wait_staged() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -100,14 +106,13 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
   const bool staged = 2 * N <= L;
   const int items = bt.S * N, k0 = blockIdx.x, dk = gridDim.x;
   // height layout row of DOE row i: row i >> uf of the (N >> uf)-wide layout
-  auto layout_row = [&](int kk) { const Slice& q = bt.s[kk / N]; return q.h + (size_t)((kk % N) >> q.uf) * (N >> q.uf); };
+  auto layout_off = [&](int kk) { const Slice& q = bt.s[kk / N]; return (size_t)((kk % N) >> q.uf) * (N >> q.uf); };
   auto layout_n = [&](int kk) { return N >> bt.s[kk / N].uf; };
-  if (staged && k0 < items) stage_heights(hs, layout_row(k0), layout_n(k0), t, T);
+  if (staged && k0 < items) stage_heights(hs, bt.s[k0 / N], layout_off(k0), layout_n(k0), t, T);
   for (int k = k0; k < items; k += dk) {
     const Slice& sl = bt.s[k / N];
     const int i = k % N, uf = sl.uf;
-    const float* hrow = layout_row(k);
-    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+    const bool erow = sl.e_in != nullptr;
     float2 hv[F::B / 2][F::R];
     if (staged) {
       wait_staged();
@@ -120,15 +125,15 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
         const int x = F::idx(t, b, r) - off;  // even
         hv[b / 2][r] = make_float2(0.f, 0.f);
         if (PAD2 ? pad2_live<L>(r) : (unsigned)x < (unsigned)N) {
-          if (!staged) hv[b / 2][r] = heights_pair(hrow, x, uf);
-          else if (uf == 0) hv[b / 2][r] = *reinterpret_cast<const float2*>(hs + x);
-          else hv[b / 2][r] = make_float2(hs[x >> uf], hs[x >> uf]);
+          if (!staged) hv[b / 2][r] = heights_pair(sl, N, i, x);
+          else if (uf == 0) hv[b / 2][r] = DOE_IN(x + 1, N) ? *reinterpret_cast<const float2*>(hs + x) : make_float2(0.f, 0.f);
+          else hv[b / 2][r] = DOE_IN(x >> uf, N >> uf) ? make_float2(hs[x >> uf], hs[x >> uf]) : make_float2(0.f, 0.f);
         }
       }
     if (staged) {
       __syncthreads();  // every thread has read hs
       const int kn = k + dk;
-      if (kn < items) stage_heights(hs, layout_row(kn), layout_n(kn), t, T);
+      if (kn < items) stage_heights(hs, bt.s[kn / N], layout_off(kn), layout_n(kn), t, T);
     }
     float2 v[32];
     IncRow ir = {0.f, 0u};
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_kernel(const __g
             c = uf ? a : transmittance(hv[b / 2][r].y, sl.kp_hi, sl.kp_lo);  // one layout cell
           }
           if (erow) {
-            const float4 ev = __ldcs(erow + (x >> 1));
+            const float4 ev = ein_pair(sl, N, i, x);
             a = cmul(a, make_float2(ev.x, ev.y));
             c = cmul(c, make_float2(ev.z, ev.w));
           }
@@ -210,7 +215,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
   {
     using F = First<L, false>;
     static_assert(F::PAIRED, "first stage holds adjacent pairs");
-    const float2* col = sl.tbuf + tiled_at(0, mypos, nin, kTile);
+    const size_t c0 = tiled_at(0, mypos, nin, kTile);
+    const float2* col = sl.tbuf + c0;
 #pragma unroll
     for (int b = 0; b < F::B; b += 2)
 #pragma unroll
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
         const int y = F::idx(t, b, r) - yin0;
         float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
         if (PAD2F ? pad2_live<L>(r) : (unsigned)y < (unsigned)nin) {
-          if (live) {
+          if (live && DOE_IN(c0 + (size_t)(y + 1) * kTile, sl.n_tbuf)) {
             a = __ldcs(col + (size_t)y * kTile);
             c = __ldcs(col + (size_t)(y + 1) * kTile);
           }
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
       for (int r = 0; r < G::R; ++r) {
         const int a = abs_signed(G::idx(t, b, r), L);
         float2& x = v[b * G::R + r];
-        if (live && a <= sl.kmax) {
+        if (live && a <= sl.kmax && DOE_IN((size_t)abs_signed(kcol, L) * sl.hp + a, sl.n_htab)) {
           const float2 hv = hrow[a];
           x = adj ? cmulc(x, hv) : cmul(x, hv);
         } else {
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
 #pragma unroll
       for (int r = 0; r < H::R; ++r) {
         const float2 a = v[b * H::R + r], c = v[(b + 1) * H::R + r];
-        s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
+        if (DOE_IN(swz(H::idx(t, b, r) >> 1), L / 2)) s4[swz(H::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, c.x, c.y);
       }
   }
   cl.sync();  // all four columns are in shared memory (and every CTA of the cluster has started)
@@ -268,8 +274,11 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
       const int idx = t + it * T, f = idx & 1;  // f = t & 1 whenever T is even
       if (idx < lim) {
         const int ch = swz((yout0 + rbeg + 2 * (idx / F4)) >> 1);
-        a[it] = (f ? rsm[2] : rsm[0])[ch];  // rows rr, rr + 1 of column 2f
-        b[it] = (f ? rsm[3] : rsm[1])[ch];  // of column 2f + 1
+        a[it] = b[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (DOE_IN(ch, L / 2)) {
+          a[it] = (f ? rsm[2] : rsm[0])[ch];  // rows rr, rr + 1 of column 2f
+          b[it] = (f ? rsm[3] : rsm[1])[ch];  // of column 2f + 1
+        }
       }
     }
 #pragma unroll
@@ -277,9 +286,12 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_b_kernel(const __g
       const int idx = t + it * T, f = idx & 1;
       if (idx < lim) {
         const int rr = rbeg + 2 * (idx / F4);
-        float2* dst = sl.buf + (size_t)rr * sl.wp + pos0 + 2 * f;
-        __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
-        __stcs(reinterpret_cast<float4*>(dst + sl.wp), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+        const size_t o = (size_t)rr * sl.wp + pos0 + 2 * f;
+        float2* dst = sl.buf + o;
+        if (DOE_IN(o + sl.wp + 1, sl.n_buf)) {
+          __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
+          __stcs(reinterpret_cast<float4*>(dst + sl.wp), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
+        }
       }
     }
   }
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_kernel(const __g
   const int y = blockIdx.x;
   const int t = threadIdx.x;
   float2 v[32];
-  load_band_row<L>(v, t, sl.buf + (size_t)y * sl.wp, sl);
+  load_band_row<L>(v, t, y, sl);
   fft_run<L, 32, true>(v, t, sm);
   const float s = bt.inv_p2;
   if (bt.mode == OUT_PSF) {
@@ -305,7 +317,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_kernel(const __g
 #pragma unroll
       for (int r = 0; r < H::R; ++r) {
         const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
-        __stcs(dst + (H::idx(t, b, r) >> 1), make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(c.x, c.x, c.y * c.y)));
+        if (DOE_IN((size_t)y * L + H::idx(t, b, r) + 1, sl.n_out))
+          __stcs(dst + (H::idx(t, b, r) >> 1), make_float2(fmaf(a.x, a.x, a.y * a.y), fmaf(c.x, c.x, c.y * c.y)));
       }
   } else {
     float4* dst = reinterpret_cast<float4*>(static_cast<float2*>(sl.out) + (size_t)y * L);
@@ -314,7 +327,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_kernel(const __g
 #pragma unroll
       for (int r = 0; r < H::R; ++r) {
         const float2 a = cscale(v[b * H::R + r], s), c = cscale(v[(b + 1) * H::R + r], s);
-        __stcs(dst + (H::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
+        if (DOE_IN((size_t)y * L + H::idx(t, b, r) + 1, sl.n_out))
+          __stcs(dst + (H::idx(t, b, r) >> 1), make_float4(a.x, a.y, c.x, c.y));
       }
   }
 }
@@ -329,9 +343,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const
   const Slice& sl = bt.s[blockIdx.y];
   const int y = blockIdx.x;
   const int t = threadIdx.x;
-  float2* row = sl.buf + (size_t)y * sl.wp;
   float2 v[32];
-  load_band_row<L>(v, t, row, sl);
+  load_band_row<L>(v, t, y, sl);
   fft_run<L, 32, true>(v, t, sm);
   const float s = bt.inv_p2;
   const float2* trow = reinterpret_cast<const float2*>(sl.tgt + (size_t)y * L);
@@ -340,7 +353,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const
   for (int b = 0; b < H::B; b += 2)
 #pragma unroll
     for (int r = 0; r < H::R; ++r) {
-      const float2 tv = __ldcs(trow + (H::idx(t, b, r) >> 1));
+      const float2 tv = DOE_IN((size_t)y * L + H::idx(t, b, r) + 1, sl.n_tgt) ? __ldcs(trow + (H::idx(t, b, r) >> 1))
+                                                                              : make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const float2 e = cscale(v[(b + u) * H::R + r], s);
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_c_adj_kernel(const
   fft_run<L, 32, false>(v, t, sm);
   store_band_row<L>(v, t, y, L, sl);  // J1 row y of the column-tiled buffer (P rows)
   const double tot = block_sum<L / 32>((double)acc, red);
-  if (t == 0 && sl.loss_part) sl.loss_part[y] = tot;
+  if (t == 0 && sl.loss_part && DOE_IN(y, sl.n_loss)) sl.loss_part[y] = tot;
 }
 
 // ------------------------------------------------------------------ pass A*: DOE-row adjoint
@@ -377,10 +391,9 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
   for (int j = 0; j < bt.S; ++j) {
     const Slice& sl = bt.s[j];
     float2 v[32];
-    load_band_row<L>(v, t, sl.buf + (size_t)i * sl.wp, sl);
+    load_band_row<L>(v, t, i, sl);
     fft_run<L, 32, true>(v, t, sm);
-    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
-    const float4* erow = sl.e_in ? reinterpret_cast<const float4*>(sl.e_in + (size_t)i * N) : nullptr;
+    const bool erow = sl.e_in != nullptr;
     const float k2 = -2.f * sl.kp_hi;
     IncRow ir = {0.f, 0u};
     if constexpr (ILLUM) ir = incident_row(sl, i - N / 2);
@@ -390,7 +403,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
       for (int r = 0; r < H::R; ++r) {
         const int x = H::idx(t, b, r) - off;  // even
         if ((unsigned)x < (unsigned)N) {
-          const float2 hv = heights_pair(hrow, x, sl.uf);
+          const float2 hv = heights_pair(sl, N, i, x);
           float2 e0, e1;
           if (ILLUM && sl.illum) {
             e0 = transmittance_inc(hv.x, sl, ir, x - N / 2);
@@ -400,7 +413,7 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
             e1 = sl.uf ? e0 : transmittance(hv.y, sl.kp_hi, sl.kp_lo);
           }
           if (erow) {
-            const float4 ev = erow[x >> 1];
+            const float4 ev = ein_pair(sl, N, i, x);
             e0 = cmul(e0, make_float2(ev.x, ev.y));
             e1 = cmul(e1, make_float2(ev.z, ev.w));
           }
@@ -417,7 +430,8 @@ __global__ void __launch_bounds__(L / 32, min_blocks(L)) pass_a_adj_kernel(const
 #pragma unroll
     for (int r = 0; r < H::R; ++r) {
       const int x = H::idx(t, b, r) - off;
-      if ((unsigned)x < (unsigned)N) grow[x >> 1] = make_float2(acc[b * H::R + r], acc[(b + 1) * H::R + r]);
+      if ((unsigned)x < (unsigned)N && DOE_IN((size_t)i * N + x + 1, bt.n_grad))
+        grow[x >> 1] = make_float2(acc[b * H::R + r], acc[(b + 1) * H::R + r]);
     }
 }
 

@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch
   float2* row = sl.htab + (size_t)b * sl.hp;
   for (int a = threadIdx.x; a <= sl.kmax; a += blockDim.x) {
     const long long m = (long long)b * b + (long long)a * a;
-    row[htab_col(sl, a)] = (m < sl.mev) ? transfer_value((unsigned int)m, sl) : make_float2(0.f, 0.f);
+    if (DOE_IN((size_t)b * sl.hp + htab_col(sl, a), sl.n_htab))
+      row[htab_col(sl, a)] = (m < sl.mev) ? transfer_value((unsigned int)m, sl) : make_float2(0.f, 0.f);
   }
 }
 
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant
   double acc = 0.0;
   const int n = bt.P * bt.qf;  // per-row (and, for split rows, per-CTA) partials
   for (int j = 0; j < bt.S; ++j)
-    for (int y = threadIdx.x; y < n; y += 1024) acc += bt.s[j].loss_part[y];
+    for (int y = threadIdx.x; y < n; y += 1024)
+      if (DOE_IN(y, bt.s[j].n_loss)) acc += bt.s[j].loss_part[y];
   const double tot = block_sum<1024>(acc, red);
   if (threadIdx.x == 0) *loss = bt.mode == GRAD_L2 ? tot : 0.0;
 }
@@ -199,7 +201,8 @@ __global__ void band_mask_kernel(const __grid_constant__ Batch bt, uint8_t* mask
     const int b = abs_signed(k, P);
     uint8_t mv = 0;
     if (a <= sl.kmax && b <= sl.kmax) {
-      const float2 hv = sl.htab[(size_t)b * sl.hp + htab_col(sl, a)];
+      const float2 hv = DOE_IN((size_t)b * sl.hp + htab_col(sl, a), sl.n_htab) ? sl.htab[(size_t)b * sl.hp + htab_col(sl, a)]
+                                                                           : make_float2(0.f, 0.f);
       mv = (hv.x != 0.f || hv.y != 0.f) ? 1 : 0;
     }
     mask[(size_t)l * P + k] = mv;

@@ -122,18 +122,19 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
   for (int j = t; j < nb; j += kMrT) {
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = DOE_IN(j + r * nb, P) ? src[j + r * nb] : make_float2(0.f, 0.f);
     const int k = j % Ns;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      float2 w = tw[r * k * step];  // r k step < P
+      float2 w = DOE_IN(r * k * step, P) ? tw[r * k * step] : make_float2(0.f, 0.f);  // r k step < P
       if (inv) w.y = -w.y;
       v[r] = cmul(v[r], w);
     }
     mr_dft<R>(v, inv);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r)
+      if (DOE_IN(base + r * Ns, P)) dst[base + r * Ns] = v[r];
   }
   __syncthreads();
 }
@@ -150,11 +151,11 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
   for (int j = t; j < nb; j += kMrT) {
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = DOE_IN(j + r * nb, P) ? src[j + r * nb] : make_float2(0.f, 0.f);
     const int k = j % Ns;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      float2 w = tw[r * k * step];  // r k step < P
+      float2 w = DOE_IN(r * k * step, P) ? tw[r * k * step] : make_float2(0.f, 0.f);  // r k step < P
       if (inv) w.y = -w.y;
       v[r] = cmul(v[r], w);
     }
@@ -167,7 +168,7 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) {
         if (n1 && k2) {
-          float2 w = tw[n1 * k2 * nb];  // w_R^(n1 k2); n1 k2 nb < P
+          float2 w = DOE_IN(n1 * k2 * nb, P) ? tw[n1 * k2 * nb] : make_float2(0.f, 0.f);  // w_R^(n1 k2); n1 k2 nb < P
           if (inv) w.y = -w.y;
           a[k2] = cmul(a[k2], w);
         }
@@ -182,7 +183,8 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
       for (int n1 = 0; n1 < R1; ++n1) b[n1] = v[n1 + R1 * k2];
       mr_dft<R1>(b, inv);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) dst[base + (k2 + R2 * k1) * Ns] = b[k1];
+      for (int k1 = 0; k1 < R1; ++k1)
+        if (DOE_IN(base + (k2 + R2 * k1) * Ns, P)) dst[base + (k2 + R2 * k1) * Ns] = b[k1];
     }
   }
   __syncthreads();
@@ -201,15 +203,15 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
     float2 acc = make_float2(0.f, 0.f);
     int idx = 0;
     for (int m = 0; m < R; ++m) {
-      float2 w = tw[idx];
+      float2 w = DOE_IN(idx, P) ? tw[idx] : make_float2(0.f, 0.f);
       if (inv) w.y = -w.y;
-      const float2 v = src[j + m * nb];
+      const float2 v = DOE_IN(j + m * nb, P) ? src[j + m * nb] : make_float2(0.f, 0.f);
       acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
       acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
       idx += e;
       if (idx >= P) idx -= P;
     }
-    dst[(j - k) * R + k + r * Ns] = acc;
+    if (DOE_IN((j - k) * R + k + r * Ns, P)) dst[(j - k) * R + k + r * Ns] = acc;
   }
   __syncthreads();
 }
@@ -253,10 +255,11 @@ __device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, in
 }
 
 // E_doe of Eq. 2 at DOE sample (i, x): transmittance, parametric incident field, E_in array.
-__device__ __forceinline__ float2 mr_doe_field(const Slice& sl, const float* hrow, int i, int x, int N, IncRow ir) {
-  const float hv = __ldg(hrow + (x >> sl.uf));
+__device__ __forceinline__ float2 mr_doe_field(const Slice& sl, int i, int x, int N, IncRow ir) {
+  const size_t o = (size_t)(i >> sl.uf) * (N >> sl.uf) + (x >> sl.uf);  // layout cell of DOE row i
+  const float hv = DOE_IN(o, sl.n_h) ? __ldg(sl.h + o) : 0.f;
   float2 e = sl.illum ? transmittance_inc(hv, sl, ir, x - N / 2) : transmittance(hv, sl.kp_hi, sl.kp_lo);
-  if (sl.e_in) e = cmul(e, __ldg(sl.e_in + (size_t)i * N + x));
+  if (sl.e_in && DOE_IN((size_t)i * N + x, sl.n_ein)) e = cmul(e, __ldg(sl.e_in + (size_t)i * N + x));
   return e;
 }
 
@@ -266,6 +269,7 @@ __device__ __forceinline__ float2 mr_doe_field(const Slice& sl, const float* hro
 __device__ __forceinline__ float2 mr_transfer(const Slice& sl, int kc, int lr, int P, bool conj_h) {
   const int a = abs_signed(kc, P), b = abs_signed(lr, P);
   if (a > sl.kmax || b > sl.kmax) return make_float2(0.f, 0.f);
+  if (!DOE_IN((size_t)a * sl.hp + b, sl.n_htab)) return make_float2(0.f, 0.f);
   float2 h = __ldg(sl.htab + (size_t)a * sl.hp + b);
   if (conj_h) h.y = -h.y;
   return h;
@@ -280,16 +284,16 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
   const float2* tw = sm_mr;
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + P;
-  const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
   const IncRow ir = incident_row(sl, i - N / 2);
   for (int c = t; c < P; c += kMrT) {
     const int x = c - off;
-    xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, hrow, i, x, N, ir) : make_float2(0.f, 0.f);
+    xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, i, x, N, ir) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)i * P;
-  for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
+  for (int c = t; c < P; c += kMrT)
+    if (DOE_IN((size_t)i * P + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
 }
 
 // ---- pass B / B* (mixed radix): one column kc per CTA.  Forward: the N row spectra (tbuf rows
@@ -308,7 +312,8 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
   float2* xb = xa + P;
   for (int l = t; l < P; l += kMrT) {
     const int r = adj ? l : l - off;
-    xa[l] = (unsigned)r < (unsigned)(adj ? P : N) ? __ldcs(sl.tbuf + (size_t)r * P + kc) : make_float2(0.f, 0.f);
+    xa[l] = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + kc, sl.n_tbuf)
+                ? __ldcs(sl.tbuf + (size_t)r * P + kc) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
@@ -317,9 +322,11 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
   __syncthreads();
   y = mr_fft<CMP>(y, z, bt, tw, true, t);
   if (!adj) {
-    for (int l = t; l < P; l += kMrT) __stcs(sl.buf + (size_t)l * P + kc, y[l]);
+    for (int l = t; l < P; l += kMrT)
+      if (DOE_IN((size_t)l * P + kc, sl.n_buf)) __stcs(sl.buf + (size_t)l * P + kc, y[l]);
   } else {
-    for (int r = t; r < N; r += kMrT) __stcs(sl.tbuf + (size_t)r * P + kc, y[r + off]);
+    for (int r = t; r < N; r += kMrT)
+      if (DOE_IN((size_t)r * P + kc, sl.n_tbuf)) __stcs(sl.tbuf + (size_t)r * P + kc, y[r + off]);
   }
 }
 
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + P;
   const float2* src = sl.buf + (size_t)row * P;
-  for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+  for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)row * P + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
   const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   const float s = bt.inv_p2;
@@ -341,11 +348,12 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
     float* dst = static_cast<float*>(sl.out) + (size_t)row * P;
     for (int c = t; c < P; c += kMrT) {
       const float2 e = cscale(y[c], s);
-      __stcs(dst + c, fmaf(e.x, e.x, e.y * e.y));
+      if (DOE_IN((size_t)row * P + c, sl.n_out)) __stcs(dst + c, fmaf(e.x, e.x, e.y * e.y));
     }
   } else {
     float2* dst = static_cast<float2*>(sl.out) + (size_t)row * P;
-    for (int c = t; c < P; c += kMrT) __stcs(dst + c, cscale(y[c], s));
+    for (int c = t; c < P; c += kMrT)
+      if (DOE_IN((size_t)row * P + c, sl.n_out)) __stcs(dst + c, cscale(y[c], s));
   }
 }
 
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + P;
   const float2* src = sl.buf + (size_t)row * P;
-  for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+  for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)row * P + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   const float s = bt.inv_p2;
@@ -369,7 +377,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
   float acc = 0.f;
   for (int c = t; c < P; c += kMrT) {
     const float2 e = cscale(y[c], s);
-    const float tt = __ldcs(trow + c);
+    const float tt = DOE_IN((size_t)row * P + c, sl.n_tgt) ? __ldcs(trow + c) : 0.f;
     float w;
     if (bt.mode == GRAD_L2) {
       const float d = fmaf(e.x, e.x, e.y * e.y) - tt;
@@ -383,9 +391,10 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
   __syncthreads();
   y = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)row * P;
-  for (int c = t; c < P; c += kMrT) __stcs(dst + c, y[c]);
+  for (int c = t; c < P; c += kMrT)
+    if (DOE_IN((size_t)row * P + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
   const double tot = block_sum<kMrT>((double)acc, red);
-  if (t == 0 && sl.loss_part) sl.loss_part[row] = tot;
+  if (t == 0 && sl.loss_part && DOE_IN(row, sl.n_loss)) sl.loss_part[row] = tot;
 }
 
 // ---- pass A* (mixed radix): DOE row i, summed over the slices in order: g_doe = IFFT(tbuf
@@ -402,14 +411,14 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_consta
   for (int j = 0; j < bt.S; ++j) {
     const Slice& sl = bt.s[j];
     const float2* src = sl.tbuf + (size_t)i * P;
-    for (int c = t; c < P; c += kMrT) xa[c] = __ldcs(src + c);
+    for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)i * P + c, sl.n_tbuf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
     __syncthreads();
     const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
-    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const IncRow ir = incident_row(sl, i - N / 2);
     const float k2 = -2.f * sl.kp_hi;
     for (int x = t; x < N; x += kMrT) {
-      const float2 e = mr_doe_field(sl, hrow, i, x, N, ir);
+      if (!DOE_IN((size_t)i * N + x, bt.n_grad)) continue;
+      const float2 e = mr_doe_field(sl, i, x, N, ir);
       const float2 g = cscale(y[off + x], bt.inv_p2);
       const float prev = j ? grow[x] : 0.f;
       grow[x] = fmaf(k2, fmaf(g.x, e.y, -g.y * e.x), prev);

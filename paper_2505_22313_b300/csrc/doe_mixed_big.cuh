@@ -21,7 +21,7 @@ __device__ __forceinline__ int mrq_freq(int p, int Q, int M) { return p / M + Q 
 
 // w_P^(n2 k1) (n2 k1 < P), conjugated for the inverse
 __device__ __forceinline__ float2 mrq_tw(const Batch& bt, int n2, int k1, bool inv) {
-  float2 w = __ldg(bt.mr_twP + n2 * k1);
+  float2 w = DOE_IN(n2 * k1, bt.P) ? __ldg(bt.mr_twP + n2 * k1) : make_float2(0.f, 0.f);
   if (inv) w.y = -w.y;
   return w;
 }
@@ -32,14 +32,15 @@ template <int Q>
 __device__ __forceinline__ void mrq_scatter_fwd(float2 (&v)[Q], int n2, const Batch& bt, float2* const (&dst)[Q]) {
   mr_dft<Q>(v, false);
 #pragma unroll
-  for (int k1 = 0; k1 < Q; ++k1) dst[k1][n2] = cmul(v[k1], mrq_tw(bt, n2, k1, false));
+  for (int k1 = 0; k1 < Q; ++k1)
+    if (DOE_IN(n2, bt.mr_M)) dst[k1][n2] = cmul(v[k1], mrq_tw(bt, n2, k1, false));
 }
 // Inverse Q-point step for n2: z_k1[n2] from CTA k1, times w_P^(-n2 k1), IDFT over k1:
 // v[n1] = x[M n1 + n2] (unnormalised).
 template <int Q>
 __device__ __forceinline__ void mrq_gather_inv(float2 (&v)[Q], int n2, const Batch& bt, float2* const (&src)[Q]) {
 #pragma unroll
-  for (int k1 = 0; k1 < Q; ++k1) v[k1] = cmul(src[k1][n2], mrq_tw(bt, n2, k1, true));
+  for (int k1 = 0; k1 < Q; ++k1) v[k1] = DOE_IN(n2, bt.mr_M) ? cmul(src[k1][n2], mrq_tw(bt, n2, k1, true)) : make_float2(0.f, 0.f);
   mr_dft<Q>(v, true);
 }
 
@@ -63,7 +64,6 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
   float2* xb = xa + M;
   float2* rem[Q];
   mrq_map<Q>(cl, xa, rem);
-  const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
   const IncRow ir = incident_row(sl, i - N / 2);
   const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
   cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
@@ -72,14 +72,15 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const int x = M * n1 + n2 - off;
-      v[n1] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, hrow, i, x, N, ir) : make_float2(0.f, 0.f);
+      v[n1] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, i, x, N, ir) : make_float2(0.f, 0.f);
     }
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
   cl.sync();  // chunk k1 is complete in xa (and the twiddle table visible)
   const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)i * bt.P + (size_t)k1 * M;
-  for (int c = t; c < M; c += kMrT) __stcs(dst + c, y[c]);
+  for (int c = t; c < M; c += kMrT)
+    if (DOE_IN((size_t)i * bt.P + (size_t)k1 * M + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
 }
 
 // ---- pass C (split): output row: chunk IFFTs, inverse Q-point step, 1/P^2, |E|^2 or E.
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + M;
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
-  for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
+  for (int c = t; c < M; c += kMrT)
+    xa[c] = DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   float2* rem[Q];
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
     for (int n1 = 0; n1 < Q; ++n1) {
       const float2 e = cscale(v[n1], s);
       const size_t at = (size_t)row * P + M * n1 + n2;
+      if (!DOE_IN(at, sl.n_out)) continue;
       if (bt.mode == OUT_PSF) __stcs(static_cast<float*>(sl.out) + at, fmaf(e.x, e.x, e.y * e.y));
       else __stcs(static_cast<float2*>(sl.out) + at, e);
     }
@@ -130,7 +133,8 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + M;
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
-  for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
+  for (int c = t; c < M; c += kMrT)
+    xa[c] = DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
   float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
   float2* w = z == xa ? xb : xa;  // the same buffer in every CTA (same plan)
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const float2 e = cscale(v[n1], s);
-      const float tt = __ldcs(trow + M * n1 + n2);
+      const float tt = DOE_IN((size_t)row * P + M * n1 + n2, sl.n_tgt) ? __ldcs(trow + M * n1 + n2) : 0.f;
       float g;
       if (bt.mode == GRAD_L2) {
         const float d = fmaf(e.x, e.x, e.y * e.y) - tt;
@@ -165,9 +169,10 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
   cl.sync();  // w holds chunk k1 of the forward step in every CTA; reads of z are done
   const float2* y = mr_fft<CMP>(w, z, bt, tw, false, t);
   float2* dst = sl.tbuf + (size_t)row * P + (size_t)k1 * M;
-  for (int c = t; c < M; c += kMrT) __stcs(dst + c, y[c]);
+  for (int c = t; c < M; c += kMrT)
+    if (DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
   const double tot = block_sum<kMrT>((double)acc, red);
-  if (t == 0 && sl.loss_part) sl.loss_part[(size_t)row * Q + k1] = tot;
+  if (t == 0 && sl.loss_part && DOE_IN((size_t)row * Q + k1, sl.n_loss)) sl.loss_part[(size_t)row * Q + k1] = tot;
 }
 
 // ---- pass A* (split): DOE row i summed over the slices: inverse of tbuf row i (chunk order),
@@ -186,13 +191,13 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
   for (int j = 0; j < bt.S; ++j) {
     const Slice& sl = bt.s[j];
     const float2* src = sl.tbuf + (size_t)i * P + (size_t)k1 * M;
-    for (int c = t; c < M; c += kMrT) xa[c] = __ldcs(src + c);
+    for (int c = t; c < M; c += kMrT)
+      xa[c] = DOE_IN((size_t)i * P + (size_t)k1 * M + c, sl.n_tbuf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
     __syncthreads();
     float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
     float2* rem[Q];
     mrq_map<Q>(cl, z, rem);
     cl.sync();  // every chunk of this slice is transformed
-    const float* hrow = sl.h + (size_t)(i >> sl.uf) * (N >> sl.uf);
     const IncRow ir = incident_row(sl, i - N / 2);
     const float k2 = -2.f * sl.kp_hi;
     for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
@@ -201,8 +206,8 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
 #pragma unroll
       for (int n1 = 0; n1 < Q; ++n1) {
         const int x = M * n1 + n2 - off;
-        if ((unsigned)x < (unsigned)N) {
-          const float2 e = mr_doe_field(sl, hrow, i, x, N, ir);
+        if ((unsigned)x < (unsigned)N && DOE_IN((size_t)i * N + x, bt.n_grad)) {
+          const float2 e = mr_doe_field(sl, i, x, N, ir);
           const float2 g = cscale(v[n1], bt.inv_p2);
           const float prev = j ? grow[x] : 0.f;
           grow[x] = fmaf(k2, fmaf(g.x, e.y, -g.y * e.x), prev);
@@ -237,7 +242,8 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const int r = M * n1 + n2 - (adj ? 0 : off);
-      v[n1] = (unsigned)r < (unsigned)(adj ? P : N) ? __ldcs(sl.tbuf + (size_t)r * P + c) : make_float2(0.f, 0.f);
+      v[n1] = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + c, sl.n_tbuf)
+                  ? __ldcs(sl.tbuf + (size_t)r * P + c) : make_float2(0.f, 0.f);
     }
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
@@ -256,8 +262,11 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const int r = M * n1 + n2;
-      if (!adj) __stcs(sl.buf + (size_t)r * P + c, v[n1]);
-      else if ((unsigned)(r - off) < (unsigned)N) __stcs(sl.tbuf + (size_t)(r - off) * P + c, v[n1]);
+      if (!adj) {
+        if (DOE_IN((size_t)r * P + c, sl.n_buf)) __stcs(sl.buf + (size_t)r * P + c, v[n1]);
+      } else if ((unsigned)(r - off) < (unsigned)N && DOE_IN((size_t)(r - off) * P + c, sl.n_tbuf)) {
+        __stcs(sl.tbuf + (size_t)(r - off) * P + c, v[n1]);
+      }
     }
   }
   cl.sync();  // the peers' reads of this CTA's chunk are done before it exits

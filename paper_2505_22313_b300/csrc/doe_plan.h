@@ -108,6 +108,9 @@ struct Slice {
   float sc_hi, sc_lo;    // spherical wave: (dx / d)^2
   float sk_hi, sk_lo;    // spherical wave: |d| / lambda
   float ssgn;            // spherical wave: +1 diverging (d > 0), -1 converging
+  // extents of the slice's buffers in elements (float2, or float for h / tgt / out as a PSF),
+  // for the bounds checks of the DOE_DEBUG build
+  long long n_buf, n_tbuf, n_htab, n_h, n_ein, n_tgt, n_out, n_loss;
 };
 enum : int { ILLUM_TILT = 1, ILLUM_SPHERE = 2 };
 
@@ -141,6 +144,7 @@ struct Batch {
   const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
+  long long n_grad;  // its extent (bounds checks of the DOE_DEBUG build)
   Slice s[kMaxSlices];
 };
 

@@ -66,7 +66,7 @@ int run(int mode, int C, int H, int W, const float* psf, int Py, int Px, const f
   const RLayout lay = render_layout(C, H, nk);
   if (!ws || ws_bytes < lay.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) return DOE_ENOWS;
   if ((rc = render_ensure_device()) != DOE_OK) return rc;
-  doe::RenderArgs ra;
+  doe::RenderArgs ra = {};
   ra.mode = mode;
   ra.gamma = (float)gamma;
   ra.C = C;
@@ -84,6 +84,10 @@ int run(int mode, int C, int H, int W, const float* psf, int Py, int Px, const f
   ra.sb = reinterpret_cast<float2*>(base + lay.sb);
   ra.sc = reinterpret_cast<float2*>(base + lay.sc);
   ra.ksum = reinterpret_cast<double*>(base + lay.ks);
+  ra.n_psf = (long long)C * Py * Px;
+  ra.n_img = ra.n_out = (long long)C * H * W;
+  ra.n_s = (long long)C * H * lay.wpr;
+  ra.n_ksum = (long long)C * H;
   if (doe::launch_render(ra, static_cast<cudaStream_t>(stream)) != cudaSuccess) return DOE_ECUDA;
   return DOE_OK;
 }

@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
     for (int r = 0; r < F::R; ++r) {
       const int n = F::idx(t, b, r);  // even
       float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
-      if (n < W) {
+      if (n < W && DOE_IN(((size_t)c * H + u) * W + n + 1, ra.n_img) &&
+          DOE_IN(((size_t)c * ra.Py + (ra.Py / 2 - H / 2 + u)) * ra.Px + (ra.Px / 2 - W / 2) + n + 1, ra.n_psf)) {
         const float2 iv = __ldcs(reinterpret_cast<const float2*>(irow + n));
         const float2 kv = __ldcs(reinterpret_cast<const float2*>(krow + n));
         a = make_float2(iv.x, kv.x);
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
 #pragma unroll
     for (int r = 0; r < G::R; ++r) {
       const float2 a = v[b * G::R + r], d = v[(b + 1) * G::R + r];
-      s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+      if (DOE_IN(swz(G::idx(t, b, r) >> 1), L / 2)) s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
     }
   __syncthreads();
   float2* sa = ra.sa + (size_t)c * H * ra.wpr;
@@ -75,18 +76,20 @@ __global__ void __launch_bounds__(L / 32) render_rows_kernel(const __grid_consta
     const float2 zm = sm[phys((L - k) & (L - 1))];
     // X_img = (Z[k] + conj Z[-k]) / 2, X_k = (Z[k] - conj Z[-k]) / (2i)
     const size_t o = tiled_at(u, k, H, kTile);
+    if (!DOE_IN((size_t)c * H * ra.wpr + o, ra.n_s)) continue;
     sa[o] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     sb[o] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
   const double tot = block_sum<T>(ks, red);
-  if (t == 0) ra.ksum[(size_t)c * H + u] = tot;
+  if (t == 0 && DOE_IN((size_t)c * H + u, ra.n_ksum)) ra.ksum[(size_t)c * H + u] = tot;
 }
 
 // Loads column `col` of a column-tiled buffer (n rows, 4-wide tiles) into the first-stage
 // registers of a length-L forward transform; rows n..L-1 are zero padding.  A register pair
 // (rows e, e + 1; e even, n even) is two 8-byte loads 32 bytes apart.
 template <int L>
-__device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const float2* col, int n, bool live) {
+__device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const float2* col, int n, bool live,
+                                               size_t col_off, long long extent) {
   using F = First<L, false>;
   static_assert(F::PAIRED, "first stage holds adjacent pairs");
 #pragma unroll
@@ -95,7 +98,7 @@ __device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const flo
     for (int r = 0; r < F::R; ++r) {
       const int y = F::idx(t, b, r);
       float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
-      if (live && y < n) {
+      if (live && y < n && DOE_IN(col_off + (size_t)(y + 1) * kTile, extent)) {
         a = __ldcs(col + (size_t)y * kTile);
         d = __ldcs(col + (size_t)(y + 1) * kTile);
       }
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
   float2* baseC = ra.sc + (size_t)c * H * ra.wpr;
   float2 v[32];
   // spectrum of the image column, kept in sma at its own register positions
-  load_tiled_col<L>(v, t, colA, H, live);
+  load_tiled_col<L>(v, t, colA, H, live, (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile), ra.n_s);
   fft_run<L, 32, false>(v, t, sma);
   __syncthreads();
   {
@@ -156,12 +159,12 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
 #pragma unroll
       for (int r = 0; r < G::R; ++r) {
         const float2 a = v[b * G::R + r], d = v[(b + 1) * G::R + r];
-        s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        if (DOE_IN(swz(G::idx(t, b, r) >> 1), L / 2)) s4[swz(G::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
   // spectrum of the kernel column, times the image spectrum (same thread, same positions), or
   // the Wiener filter sign conj(K) ks Y / (|K|^2 + gamma ks^2) with K unnormalised
-  load_tiled_col<L>(v, t, colB, H, live);
+  load_tiled_col<L>(v, t, colB, H, live, (size_t)c * H * ra.wpr + tiled_at(0, mypos, H, kTile), ra.n_s);
   fft_run<L, 32, false>(v, t, smb);
   {
     const float4* s4 = reinterpret_cast<const float4*>(sma);
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
       for (int b = 0; b < G::B; b += 2)
 #pragma unroll
         for (int r = 0; r < G::R; ++r) {
-          const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
+          const float4 a = DOE_IN(swz(G::idx(t, b, r) >> 1), L / 2) ? s4[swz(G::idx(t, b, r) >> 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
           v[b * G::R + r] = cmul(v[b * G::R + r], make_float2(a.x, a.y));
           v[(b + 1) * G::R + r] = cmul(v[(b + 1) * G::R + r], make_float2(a.z, a.w));
         }
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
       for (int b = 0; b < G::B; b += 2)
 #pragma unroll
         for (int r = 0; r < G::R; ++r) {
-          const float4 a = s4[swz(G::idx(t, b, r) >> 1)];
+          const float4 a = DOE_IN(swz(G::idx(t, b, r) >> 1), L / 2) ? s4[swz(G::idx(t, b, r) >> 1)] : make_float4(0.f, 0.f, 0.f, 0.f);
           float2& k0 = v[b * G::R + r];        // row l = idx (even)
           float2& k1 = v[(b + 1) * G::R + r];  // row l + 1: opposite sign
           const float f0 = s0 / fmaf(k0.x, k0.x, fmaf(k0.y, k0.y, g2));
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
 #pragma unroll
       for (int r = 0; r < Hh::R; ++r) {
         const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
-        s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        if (DOE_IN(swz(Hh::idx(t, b, r) >> 1), L / 2)) s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
   const float4* rsb[kTile];
@@ -222,14 +225,18 @@ __global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_co
         const int idx = t + (c0 + it) * T, f = idx & 1;
         if (idx < lim) {
           const int ch = swz((r0 + rbeg + 2 * (idx / F4)) >> 1);
-          a[it] = (f ? rsb[2] : rsb[0])[ch];  // rows rr, rr + 1 of column 2f
-          b[it] = (f ? rsb[3] : rsb[1])[ch];  // of column 2f + 1
+          a[it] = b[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (DOE_IN(ch, L / 2)) {
+            a[it] = (f ? rsb[2] : rsb[0])[ch];  // rows rr, rr + 1 of column 2f
+            b[it] = (f ? rsb[3] : rsb[1])[ch];  // of column 2f + 1
+          }
         }
       }
 #pragma unroll
       for (int it = 0; it < CH; ++it) {
         const int idx = t + (c0 + it) * T, f = idx & 1;
-        if (idx < lim) {
+        if (idx < lim &&
+            DOE_IN((size_t)c * H * ra.wpr + (size_t)(rbeg + 2 * (idx / F4) + 1) * ra.wpr + pos0 + 2 * f + 1, ra.n_s)) {
           float2* dst = baseC + (size_t)(rbeg + 2 * (idx / F4)) * ra.wpr + pos0 + 2 * f;
           __stcs(reinterpret_cast<float4*>(dst), make_float4(a[it].x, a[it].y, b[it].x, b[it].y));
           __stcs(reinterpret_cast<float4*>(dst + ra.wpr), make_float4(a[it].z, a[it].w, b[it].z, b[it].w));
@@ -271,7 +278,9 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
     for (int r = 0; r < F::R; ++r) {
       const int k = F::idx(t, b, r);
       float2 a, d;  // X0[k], X1[k] with Hermitian extension above L / 2
-      if (k <= L / 2) {
+      if (!DOE_IN(((size_t)c * H + y + 1) * ra.wpr + (k <= L / 2 ? k : L - k), ra.n_s)) {
+        a = d = make_float2(0.f, 0.f);
+      } else if (k <= L / 2) {
         a = x0[k];
         d = x1[k];
       } else {
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(L / 32) render_out_kernel(const __grid_constan
 #pragma unroll
     for (int r = 0; r < Hh::R; ++r) {
       const int n = Hh::idx(t, b, r) - (L - W) / 2;  // even; window offset W/2 (render) or 0
-      if ((unsigned)n < (unsigned)W) {
+      if ((unsigned)n < (unsigned)W && DOE_IN(((size_t)c * H + y + 1) * W + n + 1, ra.n_out)) {
         const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
         __stcs(reinterpret_cast<float2*>(o0 + n), make_float2(a.x * scale, d.x * scale));
         __stcs(reinterpret_cast<float2*>(o1 + n), make_float2(a.y * scale, d.y * scale));

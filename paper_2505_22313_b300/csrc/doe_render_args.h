@@ -19,5 +19,8 @@ struct RenderArgs {
   int mode;             // RENDER_LINEAR or RENDER_WIENER
   float gamma;          // Wiener regulariser (RENDER_WIENER)
   int nk;               // stored row-spectrum columns: row transform length / 2 + 1
+  // extents in elements, for the bounds checks of the DOE_DEBUG build: psf, img and out, one
+  // spectrum buffer (sa, sb or sc: C H wpr) and ksum
+  long long n_psf, n_img, n_out, n_s, n_ksum;
 };
 }  // namespace doe
