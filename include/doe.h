@@ -33,6 +33,15 @@
  *    127 (Table 2's 3600, 28800 and 40000 grids; the 67 of its large-area grid): a mixed-radix
  *    FFT in shared memory (no band compaction), one CTA per transform up to P = 8192, above
  *    that a cluster of Q in {2, 3, 4, 5, 8} CTAs of P / Q <= 8192 points each (P <= 65536).
+ *  - Rectangular grids (Table 2's large-area grid is not square): nx x ny DOE samples padded
+ *    to Px = pad nx by Py = pad ny, arrays [Py][Px] / [ny][nx].  Each axis keeps its own
+ *    frequency step (1 / (Px dx), 1 / (Py dx)) and band limit (the square rule per axis); a
+ *    sample propagates iff lambda^2 (fx^2 + fy^2) < 1, in integers kt^2 B^2 + lt^2 A^2 <
+ *    ceil((Px Py dx / (g lambda))^2) with g = gcd(Px, Py), A = Px / g, B = Py / g.  Supported
+ *    when both Px and Py are at most 8192 with the factors above (powers of two included; the
+ *    mixed-radix passes run one CTA per transform), with the separable band, no upsampling and
+ *    no parametric incident field (an e_in array is supported).  Other rectangles return
+ *    DOE_EUNSUPPORTED.
  */
 #ifndef DOE_H
 #define DOE_H
@@ -88,7 +97,7 @@ extern "C" {
 
 /* Geometry of one DOE evaluation (Sec. 3.1 notation). */
 typedef struct doe_geom {
-    int32_t nx, ny;        /* DOE samples per axis; even, >= 16, P = pad * nx as in the grid note above; nx == ny */
+    int32_t nx, ny;        /* DOE samples per axis; even, >= 16; ny != nx as in the rectangular-grid note above */
     int32_t pad;           /* 1 or 2: padded grid P = pad * n per axis (the paper's grids are 2x) */
     double dx;             /* sampling pitch [m], square pixels, > 0 */
     double z;              /* propagation distance [m], > 0 */
@@ -121,7 +130,8 @@ size_t doe_workspace_bytes(const doe_geom* g, int op);
  *   e_in   device complex [ny][nx] or NULL incident field E_in (Eq. 2); NULL = unit plane wave
  *   e_out  device complex [n_lambda][P][P] written: E_dest on the padded grid
  * Errors: DOE_EINVAL (bad geometry / NULL h or e_out), DOE_EUNSUPPORTED (a side P outside the
- * grid note above, or nx != ny), DOE_ENOWS (workspace), DOE_ECUDA. */
+ * grid notes above), DOE_ENOWS (workspace), DOE_ECUDA.  On a rectangular grid every [P][P] of
+ * this header reads [Py][Px]. */
 int doe_propagate(const doe_geom* g, const float* h, const float* e_in, float* e_out, void* ws,
                   size_t ws_bytes, void* stream);
 
@@ -229,6 +239,9 @@ int doe_radial_grad(int n, int n_c, const float* grad_h, float* c_grad, void* ws
  * DOE_BANDLIMIT_CIRCULAR min(that, ceil((f_lim / du)^2)): a sample (kt, lt) with
  * |kt|, |lt| <= kmax is kept iff kt^2 + lt^2 < m_ev.  Host arrays of n_lambda entries. */
 int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev);
+/* Rectangular grids: kmax_x from Px, kmax_y from Py, and m_ev the bound of kt^2 B^2 + lt^2 A^2
+ * of the rectangular-grid note (on square grids kmax_y = kmax_x and m_ev as above). */
+int doe_band_limits_xy(const doe_geom* g, int32_t* kmax_x, int32_t* kmax_y, int64_t* m_ev);
 
 /* Debug: writes the band mask the kernels apply for wavelength j (1 = H != 0) as device
  * uint8 [P][P] in FFT order, read back from the transfer table the kernels use. */

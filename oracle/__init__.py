@@ -5,8 +5,8 @@ import this package.  The product library never does, and this package imports n
 from it: the two share no code.  The propagation, PSF, gradient and render arithmetic lives in
 ``doe_oracle.c`` (plain C, FP64, its own FFT for any length); this module compiles it, marshals
 numpy arrays, and writes out in FP64 numpy the smaller definitions (incident fields,
-upsampling, the radial parameterisation, Adam) and the rectangular-grid propagation (numpy's
-FFT as the library transform).
+upsampling, the radial parameterisation, Adam) and the rectangular-grid propagation (on the
+C oracle's 2-D FFT, which takes ny != nx).
 
 Every function follows Wei et al., "Large-Area Fabrication-Aware Computational Diffractive
 Optics" (TOG 2025), Sec. 3.1:
@@ -210,12 +210,13 @@ def psf_rows(h, dx, z, lam, rows, n_index=1.46, pad=2, e_in=None, bandlimit=True
 
 
 # ---------------------------------------------------------------- rectangular grids
-# Sides Py x Px (Table 2's 128640 x 85760 large-area grid is not square).  numpy's FFT serves as
-# the library transform; everything else is written out here.  Reading of Sec. 3.1 for Py != Px:
-# each axis keeps its own frequency step (dux = 1 / (Px dx), duy = 1 / (Py dx)) and its own
-# band limit (the square rule per axis: kmax_x = ceil(flim_x / dux) - 1 capped at Px / 2 with
-# flim_x = 1 / (lambda sqrt((2 dux z)^2 + 1)), likewise in y); a sample propagates iff
-# lambda^2 (fx^2 + fy^2) < 1, evaluated in FP64.
+# Sides Py x Px (Table 2's 128640 x 85760 large-area grid is not square), transformed with the
+# oracle's own FFT.  Reading of Sec. 3.1 for Py != Px: each axis keeps its own frequency step
+# (dux = 1 / (Px dx), duy = 1 / (Py dx)) and its own band limit (the square rule per axis:
+# kmax_x = ceil(flim_x / dux) - 1 capped at Px / 2 with flim_x = 1 / (lambda sqrt((2 dux z)^2
+# + 1)), likewise in y); a sample propagates iff lambda^2 (fx^2 + fy^2) < 1.  With g = gcd(Px,
+# Py), A = Px / g, B = Py / g that is the integer rule kx^2 B^2 + ky^2 A^2 < M_ev,
+# M_ev = ceil((Px Py dx / (g lambda))^2) evaluated once in FP64 (exact integers on the left).
 def _kmax_axis(lam: float, dx: float, P: int, z: float, bandlimit: bool) -> int:
     if isinstance(bandlimit, str):
         raise ValueError("rectangular grids take the separable band limit only")
@@ -226,18 +227,47 @@ def _kmax_axis(lam: float, dx: float, P: int, z: float, bandlimit: bool) -> int:
     return int(min(max(np.ceil(flim / du) - 1, 0), P // 2))
 
 
+def mev_rect(Py: int, Px: int, dx: float, lam: float) -> tuple[int, int, int]:
+    """(A^2, B^2, M_ev) of the rectangular evanescent rule kx^2 B^2 + ky^2 A^2 < M_ev."""
+    g = int(np.gcd(Px, Py))
+    a, b = Px // g, Py // g
+    x = float(Px) * float(Py) * dx / (float(g) * lam)
+    return a * a, b * b, int(np.ceil(x * x))
+
+
+def kmax_rect(Py: int, Px: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> tuple[int, int]:
+    """(kmax_x, kmax_y) of a rectangular grid."""
+    return _kmax_axis(lam, dx, Px, z, bandlimit), _kmax_axis(lam, dx, Py, z, bandlimit)
+
+
+def band_mask_rect(Py: int, Px: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
+    """[Py][Px] uint8 band mask (1 = H != 0) of a rectangular grid, FFT order."""
+    kx = np.where(np.arange(Px) < Px // 2, np.arange(Px), np.arange(Px) - Px).astype(np.int64)
+    ky = np.where(np.arange(Py) < Py // 2, np.arange(Py), np.arange(Py) - Py).astype(np.int64)
+    a2, b2, mev = mev_rect(Py, Px, dx, lam)
+    kxm, kym = kmax_rect(Py, Px, dx, z, lam, bandlimit)
+    m = kx[None, :] ** 2 * b2 + ky[:, None] ** 2 * a2
+    return ((np.abs(kx)[None, :] <= kxm) & (np.abs(ky)[:, None] <= kym) & (m < mev)).astype(np.uint8)
+
+
 def transfer_rect(Py: int, Px: int, dx: float, z: float, lam: float, bandlimit: bool = True) -> np.ndarray:
     """[Py][Px] complex128 band-limited transfer function, FFT order, Nyquist at -P/2."""
-    kx = np.fft.fftfreq(Px, 1.0 / Px)
-    ky = np.fft.fftfreq(Py, 1.0 / Py)
+    kx = np.where(np.arange(Px) < Px // 2, np.arange(Px), np.arange(Px) - Px).astype(np.float64)
+    ky = np.where(np.arange(Py) < Py // 2, np.arange(Py), np.arange(Py) - Py).astype(np.float64)
     fx = kx / (Px * dx)
     fy = ky / (Py * dx)
-    q = lam * lam * (fx[None, :] ** 2 + fy[:, None] ** 2)
-    band = (np.abs(kx)[None, :] <= _kmax_axis(lam, dx, Px, z, bandlimit)) & \
-           (np.abs(ky)[:, None] <= _kmax_axis(lam, dx, Py, z, bandlimit)) & (q < 1.0)
+    band = band_mask_rect(Py, Px, dx, z, lam, bandlimit).astype(bool)
     H = np.zeros((Py, Px), np.complex128)
     H[band] = np.exp(2j * np.pi * z * np.sqrt(1.0 / (lam * lam) - (fx[None, :] ** 2 + fy[:, None] ** 2)[band]))
     return H
+
+
+def _fft2r(a):
+    return fft2(a)
+
+
+def _ifft2r(a):
+    return fft2(a, inverse=True) / (a.shape[0] * a.shape[1])
 
 
 def _doe_field_rect(h, lam, n_index, e_in):
@@ -253,7 +283,7 @@ def propagate_rect(h, dx, z, lam, n_index=1.46, pad=2, e_in=None, bandlimit=True
     Py, Px = pad * Ny, pad * Nx
     E = np.zeros((Py, Px), np.complex128)
     E[(Py - Ny) // 2:(Py - Ny) // 2 + Ny, (Px - Nx) // 2:(Px - Nx) // 2 + Nx] = _doe_field_rect(h, lam, n_index, e_in)
-    return np.fft.ifft2(np.fft.fft2(E) * transfer_rect(Py, Px, dx, z, lam, bandlimit))
+    return _ifft2r(_fft2r(E) * transfer_rect(Py, Px, dx, z, lam, bandlimit))
 
 
 def psf_rect(h, dx, z, lams, n_index=1.46, pad=2, e_in=None, bandlimit=True) -> np.ndarray:
@@ -275,10 +305,10 @@ def grad_rect(h, dx, z, lams, target, n_index=1.46, pad=2, e_in=None, bandlimit=
         ed = _doe_field_rect(h, lam, n_index, e_in)
         E = np.zeros((Py, Px), np.complex128)
         E[oy:oy + Ny, ox:ox + Nx] = ed
-        Eo = np.fft.ifft2(np.fft.fft2(E) * H)
+        Eo = _ifft2r(_fft2r(E) * H)
         d = np.abs(Eo) ** 2 - np.asarray(target[j], np.float64)
         loss += float((d * d).sum())
-        gp = np.fft.ifft2(np.conj(H) * np.fft.fft2(2.0 * d * Eo))[oy:oy + Ny, ox:ox + Nx]
+        gp = _ifft2r(np.conj(H) * _fft2r(2.0 * d * Eo))[oy:oy + Ny, ox:ox + Nx]
         kp = 2 * np.pi * (n_index - 1.0) / lam
         g += -2.0 * kp * np.imag(np.conj(gp) * ed)
     return g, loss

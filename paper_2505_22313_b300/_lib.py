@@ -35,7 +35,7 @@ EXPORTS = (
     "doe_workspace_bytes_many", "doe_grad", "doe_render", "doe_render_workspace_bytes",
     "doe_wiener", "doe_wiener_workspace_bytes", "doe_adam_step", "doe_radial_heights",
     "doe_radial_workspace_bytes", "doe_radial_grad",
-    "doe_band_limits", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
+    "doe_band_limits", "doe_band_limits_xy", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
     "doe_pass_name", "doe_launch_count", "doe_psf_noalloc", "doe_fault_status", "doe_debug_build",
 )
 
@@ -105,6 +105,8 @@ def open_library(p: Path) -> ctypes.CDLL:
         "doe_radial_workspace_bytes": ([I], S),
         "doe_radial_grad": ([I, I, F, F, V, S, V], I),
         "doe_band_limits": ([G, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], I),
+        "doe_band_limits_xy": ([G, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int64)], I),
         "doe_debug_band_mask": ([G, I, F, V, S, V], I),
         "doe_strerror": ([I], ctypes.c_char_p),
         "doe_trace_enable": ([I], I),

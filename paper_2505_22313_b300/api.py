@@ -34,10 +34,12 @@ class Geometry:
     theta_x: float = 0.0   # incident plane-wave tilt [rad]
     theta_y: float = 0.0
     src_d: float = 0.0     # spherical incident wave: source |d| before (> 0) / focus behind (< 0) [m]
+    ny: int = 0            # rows of a rectangular DOE (0: square, N rows)
 
     @staticmethod
     def make(N, dx, z, lambdas, n_index=1.46, pad=2, bandlimit=True, upsample=1, lanczos=False,
-             theta_x=0.0, theta_y=0.0, src_d=0.0) -> "Geometry":
+             theta_x=0.0, theta_y=0.0, src_d=0.0, Ny=None) -> "Geometry":
+        """N: the DOE's columns (x side); Ny: its rows (default N: a square DOE)."""
         lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, np.float64)))
         nid = np.ascontiguousarray(np.broadcast_to(np.asarray(n_index, np.float64), lam.shape).copy())
         if upsample not in (1, 2, 4, 8):
@@ -46,7 +48,22 @@ class Geometry:
             raise ValueError("bandlimit must be True, False or 'circular'")
         bl = bandlimit if isinstance(bandlimit, str) else bool(bandlimit)
         return Geometry(int(N), float(dx), float(z), lam, nid, int(pad), bl, int(upsample), bool(lanczos),
-                        float(theta_x), float(theta_y), float(src_d))
+                        float(theta_x), float(theta_y), float(src_d), int(Ny) if Ny is not None else 0)
+
+    @property
+    def Ny(self) -> int:
+        """Rows of the DOE (y side)."""
+        return self.ny or self.N
+
+    @property
+    def Py(self) -> int:
+        """Rows of the padded grid."""
+        return self.pad * self.Ny
+
+    @property
+    def NLy(self) -> int:
+        """Rows of the height layout."""
+        return self.Ny // self.upsample
 
     @property
     def NL(self) -> int:
@@ -55,6 +72,7 @@ class Geometry:
 
     @property
     def P(self) -> int:
+        """Columns of the padded grid (its side on square grids)."""
         return self.pad * self.N
 
     @property
@@ -63,7 +81,8 @@ class Geometry:
 
     def c(self) -> L.Geom:
         g = L.Geom()
-        g.nx = g.ny = self.N
+        g.nx = self.N
+        g.ny = self.Ny
         g.pad = self.pad
         g.dx = self.dx
         g.z = self.z
@@ -120,13 +139,12 @@ def init() -> None:
 
 def psf(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: torch.Tensor | None = None,
         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """PSFs I_lambda = |E_dest|^2 on the padded grid: float32 [L, P, P]."""
-    N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
-    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
+    """PSFs I_lambda = |E_dest|^2 on the padded grid: float32 [L, Py, Px]."""
+    hp = _dev_ptr(h, torch.float32, (geom.NLy, geom.NL), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (geom.Ny, geom.N), "e_in")
     if out is None:
-        out = torch.empty((geom.L, P, P), dtype=torch.float32, device=h.device)
-    op = _dev_ptr(out, torch.float32, (geom.L, P, P), "out")
+        out = torch.empty((geom.L, geom.Py, geom.P), dtype=torch.float32, device=h.device)
+    op = _dev_ptr(out, torch.float32, (geom.L, geom.Py, geom.P), "out")
     g = geom.c()
     need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PSF))
     ws, wp, wb = _ws_args(ws, need, h.device)
@@ -136,13 +154,12 @@ def psf(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: 
 
 def propagate(h: torch.Tensor, geom: Geometry, e_in: torch.Tensor | None = None, out: torch.Tensor | None = None,
               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Destination fields E_dest (Eq. 3): complex64 [L, P, P]."""
-    N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
-    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
+    """Destination fields E_dest (Eq. 3): complex64 [L, Py, Px]."""
+    hp = _dev_ptr(h, torch.float32, (geom.NLy, geom.NL), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (geom.Ny, geom.N), "e_in")
     if out is None:
-        out = torch.empty((geom.L, P, P), dtype=torch.complex64, device=h.device)
-    op = _dev_ptr(out, torch.complex64, (geom.L, P, P), "out")
+        out = torch.empty((geom.L, geom.Py, geom.P), dtype=torch.complex64, device=h.device)
+    op = _dev_ptr(out, torch.complex64, (geom.L, geom.Py, geom.P), "out")
     g = geom.c()
     need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PROPAGATE))
     ws, wp, wb = _ws_args(ws, need, h.device)
@@ -155,10 +172,10 @@ def psf_many(hs, geoms, e_ins=None, outs=None, ws: torch.Tensor | None = None, s
     n = len(geoms)
     gs = (L.Geom * n)(*[g.c() for g in geoms])
     if outs is None:
-        outs = [torch.empty((g.L, g.P, g.P), dtype=torch.float32, device=hs[0].device) for g in geoms]
-    hp = (ctypes.c_void_p * n)(*[_dev_ptr(h, torch.float32, (g.NL, g.NL), "h").value for h, g in zip(hs, geoms)])
+        outs = [torch.empty((g.L, g.Py, g.P), dtype=torch.float32, device=hs[0].device) for g in geoms]
+    hp = (ctypes.c_void_p * n)(*[_dev_ptr(h, torch.float32, (g.NLy, g.NL), "h").value for h, g in zip(hs, geoms)])
     ep = (ctypes.c_void_p * n)(*[(e.data_ptr() if e is not None else None) for e in (e_ins or [None] * n)])
-    op = (ctypes.c_void_p * n)(*[_dev_ptr(o, torch.float32, (g.L, g.P, g.P), "out").value for o, g in zip(outs, geoms)])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o, torch.float32, (g.L, g.Py, g.P), "out").value for o, g in zip(outs, geoms)])
     need = int(L.load().doe_workspace_bytes_many(n, gs, L.DOE_OP_PSF))
     ws, wp, wb = _ws_args(ws, need, hs[0].device)
     L.check(L.load().doe_psf_many(n, gs, hp, ep, op, wp, wb, _stream(stream)), "doe_psf_many")
@@ -168,15 +185,14 @@ def psf_many(hs, geoms, e_ins=None, outs=None, ws: torch.Tensor | None = None, s
 def grad(h: torch.Tensor, geom: Geometry, t_or_dldi: torch.Tensor, mode: str = "l2",
          e_in: torch.Tensor | None = None, recompute: bool = True, out: torch.Tensor | None = None,
          loss: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
-    """(dL/dh float32 [N, N], loss float64 [1]) for L = sum (I - T)^2 (mode 'l2') or the
+    """(dL/dh float32 [Ny, N], loss float64 [1]) for L = sum (I - T)^2 (mode 'l2') or the
     vector-Jacobian product with dL/dI (mode 'vjp'; loss is then 0)."""
-    N, P = geom.N, geom.P
-    hp = _dev_ptr(h, torch.float32, (geom.NL, geom.NL), "h")
-    ep = _dev_ptr(e_in, torch.complex64, (N, N), "e_in")
-    tp = _dev_ptr(t_or_dldi, torch.float32, (geom.L, P, P), "t_or_dldi")
+    hp = _dev_ptr(h, torch.float32, (geom.NLy, geom.NL), "h")
+    ep = _dev_ptr(e_in, torch.complex64, (geom.Ny, geom.N), "e_in")
+    tp = _dev_ptr(t_or_dldi, torch.float32, (geom.L, geom.Py, geom.P), "t_or_dldi")
     if out is None:
-        out = torch.empty((geom.NL, geom.NL), dtype=torch.float32, device=h.device)
-    gp = _dev_ptr(out, torch.float32, (geom.NL, geom.NL), "grad")
+        out = torch.empty((geom.NLy, geom.NL), dtype=torch.float32, device=h.device)
+    gp = _dev_ptr(out, torch.float32, (geom.NLy, geom.NL), "grad")
     if loss is None:
         loss = torch.empty((1,), dtype=torch.float64, device=h.device)
     lp = _dev_ptr(loss, torch.float64, (1,), "loss")
@@ -270,9 +286,22 @@ def band_limits(geom: Geometry):
     return k, m
 
 
+def band_limits_xy(geom: Geometry):
+    """(kmax_x [L] int32, kmax_y [L] int32, m_ev [L] int64): the per-axis band logic (equal to
+    band_limits' kmax on both axes of a square grid)."""
+    kx = np.zeros(geom.L, np.int32)
+    ky = np.zeros(geom.L, np.int32)
+    m = np.zeros(geom.L, np.int64)
+    g = geom.c()
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    L.check(L.load().doe_band_limits_xy(ctypes.byref(g), kx.ctypes.data_as(i32), ky.ctypes.data_as(i32),
+                                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "doe_band_limits_xy")
+    return kx, ky, m
+
+
 def debug_band_mask(geom: Geometry, j: int, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    P = geom.P
-    mask = torch.empty((P, P), dtype=torch.uint8, device="cuda")
+    """The band mask (1 where H is kept) of wavelength j on the padded grid: uint8 [Py, Px]."""
+    mask = torch.empty((geom.Py, geom.P), dtype=torch.uint8, device="cuda")
     g = geom.c()
     need = int(L.load().doe_workspace_bytes(ctypes.byref(g), L.DOE_OP_PSF))
     ws, wp, wb = _ws_args(ws, need, "cuda")
@@ -282,7 +311,7 @@ def debug_band_mask(geom: Geometry, j: int, ws: torch.Tensor | None = None, stre
 
 
 class PSF(torch.autograd.Function):
-    """Differentiable h -> PSF [L, P, P].  Backward runs the library's adjoint kernels
+    """Differentiable h -> PSF [L, Py, Px].  Backward runs the library's adjoint kernels
     (conjugate transfer function) with recomputation: no field is stored between passes."""
 
     @staticmethod

@@ -200,36 +200,62 @@ LanczosTab lanczos_table(int N, int u) {
   return tb;
 }
 
+bool rect(const doe_geom* g) { return g->nx != g->ny; }
+
+// Rectangular grids (nx != ny) run on the one-CTA mixed-radix passes, which take any supported
+// length up to kMrMax on either axis (powers of two included).
+bool rect_supported(const doe_geom* g) {
+  const long px = (long)g->pad * g->nx, py = (long)g->pad * g->ny;
+  return px <= kMrMax && py <= kMrMax && !mr_radices(px).empty() && !mr_radices(py).empty() &&
+         upsample_log2(g) == 0 && !(g->flags & DOE_BANDLIMIT_CIRCULAR) && g->theta_x == 0.0 && g->theta_y == 0.0 &&
+         g->src_d == 0.0;
+}
+
 int check_geom(const doe_geom* g) {
   if (!g) return DOE_EINVAL;
   if (g->nx < 16 || g->ny < 16 || (g->nx & 1) || (g->ny & 1)) return DOE_EINVAL;
   if (g->pad != 1 && g->pad != 2) return DOE_EINVAL;
-  if ((long)g->pad * g->nx < (1L << kMinLog)) return DOE_EUNSUPPORTED;
+  if ((long)g->pad * g->nx < (1L << kMinLog) || (long)g->pad * g->ny < (1L << kMinLog)) return DOE_EUNSUPPORTED;
   if (!(g->dx > 0.0) || !(g->z > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->z)) return DOE_EINVAL;
   if (g->n_lambda < 1 || g->n_lambda > kMaxSlices || !g->lambda || !g->n_index) return DOE_EINVAL;
   for (int j = 0; j < g->n_lambda; ++j) {
     if (!(g->lambda[j] > 0.0) || !std::isfinite(g->lambda[j])) return DOE_EINVAL;
     if (!(g->n_index[j] >= 1.0) || !std::isfinite(g->n_index[j])) return DOE_EINVAL;
   }
-  if (g->nx != g->ny) return DOE_EUNSUPPORTED;
+  if (rect(g) && !rect_supported(g)) return DOE_EUNSUPPORTED;
   if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
-  if (!is_pow2((long)g->pad * g->nx) && mr_split((long)g->pad * g->nx).Q == 0) return DOE_EUNSUPPORTED;
-  if ((g->nx >> upsample_log2(g)) < 4 || (g->nx & ((1 << upsample_log2(g)) - 1))) return DOE_EINVAL;
+  if (!rect(g) && !is_pow2((long)g->pad * g->nx) && mr_split((long)g->pad * g->nx).Q == 0) return DOE_EUNSUPPORTED;
+  const int u = upsample_log2(g);
+  if ((g->nx >> u) < 4 || (g->ny >> u) < 4 || (g->nx & ((1 << u) - 1)) || (g->ny & ((1 << u) - 1))) return DOE_EINVAL;
   if (!(std::fabs(g->theta_x) < 0.5 * kPi) || !(std::fabs(g->theta_y) < 0.5 * kPi) || !std::isfinite(g->src_d))
     return DOE_EINVAL;
   return DOE_OK;
 }
 
+// Rectangular evanescent rule: with g = gcd(Px, Py), A = Px / g, B = Py / g a sample (kt, lt)
+// propagates iff kt^2 B^2 + lt^2 A^2 < ceil((Px Py dx / (g lambda))^2) (the same FP64
+// expression the oracle writes out).
+long gcdl(long a, long b) { return b ? gcdl(b, a % b) : a; }
+long long rect_mev(long Px, long Py, double dx, double lam) {
+  const long gg = gcdl(Px, Py);
+  const double x = (double)Px * (double)Py * dx / ((double)gg * lam);
+  const double x2 = x * x;
+  return x2 > 9.0e18 ? LLONG_MAX : (long long)std::ceil(x2);
+}
+
 // Fills the per-slice constants of wavelength j of g.
 void fill_slice(Slice& s, const doe_geom* g, int j) {
   const long P = (long)g->pad * g->nx;
+  const long Py = (long)g->pad * g->ny;
   const double lam = g->lambda[j];
   const double du = 1.0 / ((double)P * g->dx);
   const long kmax = band_kmax(lam, g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   std::memset(&s, 0, sizeof(s));
   s.uf = lanczos(g) ? 0 : upsample_log2(g);  // Lanczos: the passes read pre-interpolated heights
   s.kmax = (int)kmax;
-  if (kmax >= P / 2 || P > (1L << kMaxLog) || !is_pow2(P)) {  // no compaction (split rows: sub-transform order; mixed radix: natural)
+  s.kmax_y = (int)kmax;
+  s.sqa = s.sqb = 1;
+  if (kmax >= P / 2 || P > (1L << kMaxLog) || !is_pow2(P) || rect(g)) {  // no compaction (split rows: sub-transform order; mixed radix: natural)
     s.seg_a = (int)P;
     s.w = (int)P;
   } else {
@@ -246,6 +272,16 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   s.mev = band_mlim(g, lam, P);
   const double ld = lam * du;
   split(ld * ld, s.c_hi, s.c_lo);
+  if (rect(g)) {  // per-axis band limits; q = c (kt^2 B^2 + lt^2 A^2)
+    const long gg = gcdl(P, Py);
+    s.kmax_y = (int)band_kmax(lam, g->dx, Py, g->z, (g->flags & DOE_BANDLIMIT) != 0);
+    s.hp = (int)((s.kmax_y + 2) & ~1L);
+    s.sqa = (long long)(P / gg) * (P / gg);
+    s.sqb = (long long)(Py / gg) * (Py / gg);
+    s.mev = rect_mev(P, Py, g->dx, lam);
+    const double cq = lam * (double)gg / ((double)P * (double)Py * g->dx);
+    split(cq * cq, s.c_hi, s.c_lo);
+  }
   const double phi0 = 2.0 * kPi * g->z / lam;
   split(phi0, s.phi0_hi, s.phi0_lo);
   split(std::fmod(phi0, 2.0 * kPi), s.th0_hi, s.th0_lo);
@@ -274,26 +310,37 @@ struct Layout {
   size_t ltmp = 0;           // Lanczos-3: the [N / f][N] buffer of the separable passes
   size_t mrtw = 0;           // mixed radix: the [M] twiddle table of the per-CTA transform
   size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
-  long tbuf_rows = 0;        // rows of the column-tiled buffers (N forward, P with the adjoint)
+  size_t mrtw_y = 0;         // rectangular grids: the [Py] twiddle table of the column transform
+  long tbuf_rows = 0;        // rows of the column-tiled buffers (Ny forward, Py with the adjoint)
 };
+
+// Sides of a request's grid: the DOE (Nx x Ny) and its padded grid (Px x Py).
+struct Grid {
+  long Nx, Ny, Px, Py;
+};
+Grid grid_of(const doe_geom* g) {
+  return {g->nx, g->ny, (long)g->pad * g->nx, (long)g->pad * g->ny};
+}
 
 // Workspace: per slice a natural-layout [P][wp] complex field buffer, then per slice a transfer
 // table, then per slice a column-tiled buffer (N rows for the forward path, P rows when the
 // adjoint also runs), then (gradient) the per-row loss partials.  The field buffers and tables
 // sit at the same offsets in the PSF and gradient layouts, so a gradient-sized workspace used
 // by doe_psf keeps the fields and tables doe_grad(recompute=0) needs.
-Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_req, const doe_geom* geoms) {
+Layout make_layout(const std::vector<Slice>& sl, int op, int n_req, const doe_geom* geoms) {
+  const Grid gr = grid_of(&geoms[0]);
+  const long P = gr.Px, N = gr.Nx, Py = gr.Py, Ny = gr.Ny;
   Layout L;
   size_t off = 0;
   for (const auto& s : sl) {
     L.buf.push_back(off);
-    off = align256(off + (size_t)P * s.wp * sizeof(float2));
+    off = align256(off + (size_t)Py * s.wp * sizeof(float2));
   }
   for (const auto& s : sl) {
     L.htab.push_back(off);
     off = align256(off + (size_t)(s.kmax + 1) * s.hp * sizeof(float2));
   }
-  const long R = op == DOE_OP_GRAD ? P : N;
+  const long R = op == DOE_OP_GRAD ? Py : Ny;
   L.tbuf_rows = R;
   for (const auto& s : sl) {
     L.tbuf.push_back(off);
@@ -301,13 +348,18 @@ Layout make_layout(const std::vector<Slice>& sl, long P, long N, int op, int n_r
   }
   if (op == DOE_OP_GRAD) {
     L.loss = off;
-    off = align256(off + sl.size() * (size_t)P * kMaxQf * sizeof(double));
+    off = align256(off + sl.size() * (size_t)(P > Py ? P : Py) * kMaxQf * sizeof(double));
     if (upsample_log2(&geoms[0]) > 0) {
       L.gsim = off;
       off = align256(off + (size_t)N * N * sizeof(float));
     }
   }
-  if (!is_pow2(P)) {
+  if (Py != P) {  // rectangular grid: twiddle tables of the row and of the column transform
+    L.mrtw = off;
+    off = align256(off + (size_t)P * sizeof(float2));
+    L.mrtw_y = off;
+    off = align256(off + (size_t)Py * sizeof(float2));
+  } else if (!is_pow2(P)) {
     const MrSplit sp = mr_split(P);
     L.mrtw = off;
     off = align256(off + (size_t)sp.M * sizeof(float2));
@@ -338,7 +390,7 @@ int collect_slices(int n_req, const doe_geom* geoms, std::vector<Slice>& sl, std
   for (int r = 0; r < n_req; ++r) {
     const int rc = check_geom(&geoms[r]);
     if (rc != DOE_OK) return rc;
-    if (geoms[r].nx != geoms[0].nx || geoms[r].pad != geoms[0].pad) return DOE_EINVAL;
+    if (geoms[r].nx != geoms[0].nx || geoms[r].ny != geoms[0].ny || geoms[r].pad != geoms[0].pad) return DOE_EINVAL;
   }
   for (int r = 0; r < n_req; ++r)
     for (int j = 0; j < geoms[r].n_lambda; ++j) {
@@ -351,25 +403,43 @@ int collect_slices(int n_req, const doe_geom* geoms, std::vector<Slice>& sl, std
   return DOE_OK;
 }
 
-void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* ws, const Layout& lay) {
+// The mixed-radix plan of a transform of length M into (nst, radix[]); true if it has composite
+// stages (9, 15, 16, 25).
+bool set_plan(long M, int& nst, int* radix) {
+  const std::vector<int> pl = mr_radices(M);
+  bool cmp = false;
+  nst = (int)pl.size();
+  for (size_t s = 0; s < pl.size(); ++s) {
+    radix[s] = pl[s];
+    if (pl[s] == 9 || pl[s] == 15 || pl[s] == 16 || pl[s] == 25) cmp = true;
+  }
+  return cmp;
+}
+
+void init_batch(Batch& bt, const std::vector<Slice>& sl, const doe_geom* g0, void* ws, const Layout& lay) {
+  const Grid gr = grid_of(g0);
   std::memset(&bt, 0, sizeof(bt));
   bt.S = (int)sl.size();
-  bt.N = N;
-  bt.P = pad * N;
-  bt.off = (bt.P - N) / 2;
-  bt.inv_p2 = (float)(1.0 / ((double)bt.P * (double)bt.P));
+  bt.N = (int)gr.Nx;
+  bt.P = (int)gr.Px;
+  bt.off = (bt.P - bt.N) / 2;
+  bt.Ny = (int)gr.Ny;
+  bt.Py = (int)gr.Py;
+  bt.offy = (bt.Py - bt.Ny) / 2;
+  bt.inv_p2 = (float)(1.0 / ((double)bt.P * (double)bt.Py));
   bt.qf = bt.P > (1 << kMaxLog) ? bt.P / 8192 : 1;
+  const long Pl = bt.P > bt.Py ? bt.P : bt.Py;
   int tiles = 0, kmx = 0;
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j] = sl[j];
     bt.s[j].buf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.buf[j]);
     bt.s[j].htab = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.htab[j]);
     bt.s[j].tbuf = reinterpret_cast<float2*>(static_cast<char*>(ws) + lay.tbuf[j]);
-    if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * bt.P * kMaxQf;
-    bt.s[j].n_buf = (long long)bt.P * sl[j].wp;
+    if (lay.loss) bt.s[j].loss_part = reinterpret_cast<double*>(static_cast<char*>(ws) + lay.loss) + (size_t)j * Pl * kMaxQf;
+    bt.s[j].n_buf = (long long)bt.Py * sl[j].wp;
     bt.s[j].n_tbuf = (long long)lay.tbuf_rows * sl[j].wp;
     bt.s[j].n_htab = (long long)(sl[j].kmax + 1) * sl[j].hp;
-    if (lay.loss) bt.s[j].n_loss = (long long)bt.P * kMaxQf;
+    if (lay.loss) bt.s[j].n_loss = (long long)Pl * kMaxQf;
     bt.s[j].tile_begin = tiles;
     tiles += sl[j].wp / col_tile(bt.P);
     if (sl[j].kmax > kmx) kmx = sl[j].kmax;
@@ -377,20 +447,29 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, int N, int pad, void* w
   }
   bt.total_tiles = tiles;
   bt.max_kmax = kmx;
-  if (!is_pow2(bt.P)) {
+  if (bt.Py != bt.P) {  // rectangular grid: one-CTA mixed-radix passes with a row and a column plan
+    bt.mr = 1;
+    bt.mr_Q = 1;
+    bt.mr_M = bt.P;
+    bt.mr_My = bt.Py;
+    const bool cx = set_plan(bt.P, bt.mr_nst, bt.mr_radix), cy = set_plan(bt.Py, bt.mr_nst_y, bt.mr_radix_y);
+    bt.mr_cmp = (cx || cy) ? 1 : 0;
+    bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
+    bt.mr_tw_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw_y);
+  } else if (!is_pow2(bt.P)) {
     const MrSplit sp = mr_split(bt.P);
-    const std::vector<int> pl = mr_radices(sp.M);
     bt.mr = 1;
     bt.mr_Q = sp.Q;
     bt.mr_M = sp.M;
     bt.qf = sp.Q;  // split rows write one loss partial per CTA
-    bt.mr_nst = (int)pl.size();
-    for (size_t s = 0; s < pl.size(); ++s) {
-      bt.mr_radix[s] = pl[s];
-      if (pl[s] == 9 || pl[s] == 15 || pl[s] == 16 || pl[s] == 25) bt.mr_cmp = 1;
-    }
+    bt.mr_cmp = set_plan(sp.M, bt.mr_nst, bt.mr_radix) ? 1 : 0;
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
     if (sp.Q > 1) bt.mr_twP = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP);
+    // square grid: the column transform is the row transform
+    bt.mr_My = bt.mr_M;
+    bt.mr_nst_y = bt.mr_nst;
+    for (int s = 0; s < bt.mr_nst; ++s) bt.mr_radix_y[s] = bt.mr_radix[s];
+    bt.mr_tw_y = bt.mr_tw;
   }
 }
 
@@ -418,13 +497,14 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
   if (rc != DOE_OK) return rc;
   for (int r = 0; r < n_req; ++r)
     if (!h[r] || !out[r]) return DOE_EINVAL;
-  const int N = geoms[0].nx, pad = geoms[0].pad;
-  const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, N, DOE_OP_PSF, n_req, geoms);
+  const Grid gr = grid_of(&geoms[0]);
+  const int N = geoms[0].nx;
+  const long P = gr.Px;
+  const Layout lay = make_layout(sl, DOE_OP_PSF, n_req, geoms);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
-  init_batch(bt, sl, N, pad, ws, lay);
+  init_batch(bt, sl, &geoms[0], ws, lay);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Lanczos-3 requests: interpolate their layouts onto the simulation grid first
   std::vector<const float*> hr(h, h + n_req);
@@ -444,11 +524,11 @@ int run_forward(int n_req, const doe_geom* geoms, const float* const* h, const f
     bt.s[j].h = hr[r];
     bt.s[j].e_in = e_in ? reinterpret_cast<const float2*>(e_in[r]) : nullptr;
     const size_t esz = out_kind == OUT_PSF ? sizeof(float) : sizeof(float2);
-    bt.s[j].out = static_cast<char*>(out[r]) + (size_t)jr * P * P * esz;
-    const long nl = lanczos(&geoms[r]) ? N : (N >> upsample_log2(&geoms[r]));
-    bt.s[j].n_h = (long long)nl * nl;
-    bt.s[j].n_ein = e_in && e_in[r] ? (long long)N * N : 0;
-    bt.s[j].n_out = (long long)P * P;
+    bt.s[j].out = static_cast<char*>(out[r]) + (size_t)jr * gr.Py * gr.Px * esz;
+    const int u = lanczos(&geoms[r]) ? 0 : upsample_log2(&geoms[r]);
+    bt.s[j].n_h = (long long)(gr.Ny >> u) * (gr.Nx >> u);
+    bt.s[j].n_ein = e_in && e_in[r] ? (long long)gr.Ny * gr.Nx : 0;
+    bt.s[j].n_out = (long long)gr.Py * gr.Px;
   }
   if ((rc = forward_passes(bt, st)) != DOE_OK) return rc;
   bt.mode = out_kind;
@@ -469,7 +549,7 @@ size_t doe_workspace_bytes_many(int n_req, const doe_geom* geoms, int op) {
   std::vector<Slice> sl;
   std::vector<int> req_of;
   if (collect_slices(n_req, geoms, sl, req_of) != DOE_OK) return 0;
-  return make_layout(sl, (long)geoms[0].pad * geoms[0].nx, geoms[0].nx, op, n_req, geoms).total;
+  return make_layout(sl, op, n_req, geoms).total;
 }
 
 size_t doe_workspace_bytes(const doe_geom* g, int op) { return doe_workspace_bytes_many(1, g, op); }
@@ -503,13 +583,14 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   std::vector<Slice> sl;
   std::vector<int> req_of;
   if ((rc = collect_slices(1, g, sl, req_of)) != DOE_OK) return rc;
-  const int N = g->nx, pad = g->pad;
-  const long P = (long)pad * N;
-  const Layout lay = make_layout(sl, P, N, DOE_OP_GRAD, 1, g);
+  const Grid gr = grid_of(g);
+  const int N = g->nx;
+  const long P = gr.Px;
+  const Layout lay = make_layout(sl, DOE_OP_GRAD, 1, g);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
-  init_batch(bt, sl, N, pad, ws, lay);
+  init_batch(bt, sl, g, ws, lay);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool lz = lanczos(g);
   const float* hsim = lz ? reinterpret_cast<const float*>(static_cast<char*>(ws) + lay.hsim[0]) : nullptr;
@@ -521,14 +602,14 @@ int doe_grad(const doe_geom* g, const float* h, const float* e_in, const float* 
   for (int j = 0; j < bt.S; ++j) {
     bt.s[j].h = lz ? hsim : h;
     bt.s[j].e_in = reinterpret_cast<const float2*>(e_in);
-    bt.s[j].tgt = t_or_dldi + (size_t)j * P * P;
-    const long nl = lz ? N : (N >> uf);
-    bt.s[j].n_h = (long long)nl * nl;
-    bt.s[j].n_ein = e_in ? (long long)N * N : 0;
-    bt.s[j].n_tgt = (long long)P * P;
+    bt.s[j].tgt = t_or_dldi + (size_t)j * gr.Py * gr.Px;
+    const int u = lz ? 0 : uf;
+    bt.s[j].n_h = (long long)(gr.Ny >> u) * (gr.Nx >> u);
+    bt.s[j].n_ein = e_in ? (long long)gr.Ny * gr.Nx : 0;
+    bt.s[j].n_tgt = (long long)gr.Py * gr.Px;
   }
   bt.grad = uf ? reinterpret_cast<float*>(static_cast<char*>(ws) + lay.gsim) : grad_h;
-  bt.n_grad = (long long)N * N;
+  bt.n_grad = (long long)gr.Ny * gr.Nx;
   const int lg = ilog2(P);
   if (recompute && (rc = forward_passes(bt, st)) != DOE_OK) return rc;
   if (!recompute && bt.mr && launch_mr_twiddles(bt, st) != cudaSuccess) return DOE_ECUDA;
@@ -558,8 +639,17 @@ int doe_band_limits(const doe_geom* g, int32_t* kmax, int64_t* m_ev) {
   const long P = (long)g->pad * g->nx;
   for (int j = 0; j < g->n_lambda; ++j) {
     kmax[j] = (int32_t)band_kmax(g->lambda[j], g->dx, P, g->z, (g->flags & DOE_BANDLIMIT) != 0);
-    m_ev[j] = (int64_t)band_mlim(g, g->lambda[j], P);
+    m_ev[j] = (int64_t)(rect(g) ? rect_mev(P, (long)g->pad * g->ny, g->dx, g->lambda[j]) : band_mlim(g, g->lambda[j], P));
   }
+  return DOE_OK;
+}
+
+int doe_band_limits_xy(const doe_geom* g, int32_t* kmax_x, int32_t* kmax_y, int64_t* m_ev) {
+  const int rc = doe_band_limits(g, kmax_x, m_ev);
+  if (rc != DOE_OK) return rc;
+  if (!kmax_y) return DOE_EINVAL;
+  for (int j = 0; j < g->n_lambda; ++j)
+    kmax_y[j] = (int32_t)band_kmax(g->lambda[j], g->dx, (long)g->pad * g->ny, g->z, (g->flags & DOE_BANDLIMIT) != 0);
   return DOE_OK;
 }
 
@@ -574,12 +664,11 @@ int doe_debug_band_mask(const doe_geom* g, int j, uint8_t* mask, void* ws, size_
   std::vector<Slice> sl;
   std::vector<int> req_of;
   if ((rc = collect_slices(1, &one, sl, req_of)) != DOE_OK) return rc;
-  const long P = (long)g->pad * g->nx;
-  const Layout lay = make_layout(sl, P, g->nx, DOE_OP_PSF, 1, g);
+  const Layout lay = make_layout(sl, DOE_OP_PSF, 1, g);
   if ((rc = ws_ok(ws, ws_bytes, lay.total)) != DOE_OK) return rc;
   if ((rc = ensure_device()) != DOE_OK) return rc;
   static thread_local Batch bt;
-  init_batch(bt, sl, g->nx, g->pad, ws, lay);
+  init_batch(bt, sl, g, ws, lay);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (launch_htab(bt, st) != cudaSuccess) return DOE_ECUDA;
   if (launch_band_mask(bt, mask, st) != cudaSuccess) return DOE_ECUDA;

@@ -58,11 +58,24 @@ constexpr float kInvTwoPi = 0.15915494309189533577f;
 // no large phase is ever rounded to FP32: the drop phi0 g (g = q / (1 + sqrt(1 - q))) is kept
 // in double-float, reduced mod 2 pi in double-float, and subtracted from phi0 mod 2 pi
 // (computed on the host in FP64).  The caller has checked m < mev (propagating sample).
+// The phase from q = c m in double-float (the steps below transfer_value's product).
+__device__ __forceinline__ float2 transfer_from_q(dfl q, const Slice& s);
 __device__ __forceinline__ float2 transfer_value(unsigned int m, const Slice& s) {
   const float m_hi = (float)(m & 0xFFFFF000u);  // exact: at most 20 significant bits
   const float m_lo = (float)(m & 0x00000FFFu);  // exact
   const dfl c = {s.c_hi, s.c_lo};
-  const dfl q = df_add(df_mul_f(c, m_hi), df_mul_f(c, m_lo));
+  return transfer_from_q(df_add(df_mul_f(c, m_hi), df_mul_f(c, m_lo)), s);
+}
+// Rectangular grids: m = kt^2 sqb + lt^2 sqa < 2^50, split into three exactly representable
+// 24-bit parts.
+__device__ __forceinline__ float2 transfer_value64(unsigned long long m, const Slice& s) {
+  const float m0 = (float)(m & 0xFFFFFFull);                // exact: 24 bits
+  const float m1 = (float)(m & 0xFFFFFF000000ull);          // exact: 24 significant bits
+  const float m2 = (float)(m & 0xFFFF000000000000ull);      // exact
+  const dfl c = {s.c_hi, s.c_lo};
+  return transfer_from_q(df_add(df_add(df_mul_f(c, m2), df_mul_f(c, m1)), df_mul_f(c, m0)), s);
+}
+__device__ __forceinline__ float2 transfer_from_q(dfl q, const Slice& s) {
   const dfl u = df_add({1.f, 0.f}, df_neg(q));  // 1 - q in (0, 1]
   // sqrt(u): one Newton step from the FP32 root doubles the precision
   const float s0 = sqrtf(u.hi);

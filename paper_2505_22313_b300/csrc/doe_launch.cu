@@ -255,7 +255,7 @@ cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cu
 }
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st) {
   Traced tr(TR_MASK, st);
-  band_mask_kernel<<<bt.P, 256, 0, st>>>(bt, mask);
+  band_mask_kernel<<<bt.Py, 256, 0, st>>>(bt, mask);
   return cudaGetLastError();
 }
 

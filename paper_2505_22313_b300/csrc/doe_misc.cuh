@@ -11,13 +11,16 @@ namespace doe {
 // covers |kt|, |lt| <= kmax; a sample is zero iff kt^2 + lt^2 >= mev (evanescent).
 __global__ void __launch_bounds__(256) htab_kernel(const __grid_constant__ Batch bt) {
   const Slice& sl = bt.s[blockIdx.y];
-  const int b = blockIdx.x;
+  const int b = blockIdx.x;  // |kt| (row frequency)
   if (b > sl.kmax) return;
   float2* row = sl.htab + (size_t)b * sl.hp;
-  for (int a = threadIdx.x; a <= sl.kmax; a += blockDim.x) {
-    const long long m = (long long)b * b + (long long)a * a;
+  const bool square = sl.sqa == 1 && sl.sqb == 1;
+  for (int a = threadIdx.x; a <= sl.kmax_y; a += blockDim.x) {  // a = |lt| (column frequency)
+    const long long m = (long long)b * b * sl.sqb + (long long)a * a * sl.sqa;
     if (DOE_IN((size_t)b * sl.hp + htab_col(sl, a), sl.n_htab))
-      row[htab_col(sl, a)] = (m < sl.mev) ? transfer_value((unsigned int)m, sl) : make_float2(0.f, 0.f);
+      row[htab_col(sl, a)] = m >= sl.mev ? make_float2(0.f, 0.f)
+                             : square    ? transfer_value((unsigned int)m, sl)
+                                         : transfer_value64((unsigned long long)m, sl);
   }
 }
 
@@ -183,7 +186,7 @@ __global__ void radial_grad_final_kernel(const double* __restrict__ part, int bl
 __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant__ Batch bt, double* loss) {
   __shared__ double red[32];
   double acc = 0.0;
-  const int n = bt.P * bt.qf;  // per-row (and, for split rows, per-CTA) partials
+  const int n = bt.Py * bt.qf;  // per-row of the Py output rows (and, for split rows, per-CTA) partials
   for (int j = 0; j < bt.S; ++j)
     for (int y = threadIdx.x; y < n; y += 1024)
       if (DOE_IN(y, bt.s[j].n_loss)) acc += bt.s[j].loss_part[y];
@@ -194,13 +197,13 @@ __global__ void __launch_bounds__(1024) loss_reduce_kernel(const __grid_constant
 // Debug: band mask of slice 0 read back from its transfer table, [P][P] uint8 in FFT order.
 __global__ void band_mask_kernel(const __grid_constant__ Batch bt, uint8_t* mask) {
   const Slice& sl = bt.s[0];
-  const int l = blockIdx.x;
+  const int l = blockIdx.x;  // row of the [Py][Px] mask: column frequency lt
   const int P = bt.P;
-  const int a = abs_signed(l, P);
+  const int a = abs_signed(l, bt.Py);
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
     const int b = abs_signed(k, P);
     uint8_t mv = 0;
-    if (a <= sl.kmax && b <= sl.kmax) {
+    if (a <= sl.kmax_y && b <= sl.kmax) {
       const float2 hv = DOE_IN((size_t)b * sl.hp + htab_col(sl, a), sl.n_htab) ? sl.htab[(size_t)b * sl.hp + htab_col(sl, a)]
                                                                            : make_float2(0.f, 0.f);
       mv = (hv.x != 0.f || hv.y != 0.f) ? 1 : 0;

@@ -222,12 +222,16 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
 // CMP: the plan has composite stages (9, 15, 16, 25); kernels are compiled both ways because
 // those stages raise the register count (about 125 against 66), which costs occupancy to the
 // short transforms that do not use them.
+// ycol: the column (y) plan of a rectangular grid instead of the row plan.
 template <bool CMP>
-__device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t) {
-  const int P = bt.mr_M;  // the transform length: P, or the chunk length M of a split transform
+__device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t,
+                                          bool ycol = false) {
+  // the transform length: P (Py), or the chunk length M of a split transform
+  const int P = ycol ? bt.mr_My : bt.mr_M;
+  const int nst = ycol ? bt.mr_nst_y : bt.mr_nst;
   int Ns = 1;
-  for (int s = 0; s < bt.mr_nst; ++s) {
-    const int R = bt.mr_radix[s];
+  for (int s = 0; s < nst; ++s) {
+    const int R = ycol ? bt.mr_radix_y[s] : bt.mr_radix[s];
     if (CMP && R == 25) mr_stage2<5, 5>(a, b, P, Ns, tw, inv, t);
     else if (CMP && R == 16) mr_stage2<4, 4>(a, b, P, Ns, tw, inv, t);
     else if (CMP && R == 9) mr_stage2<3, 3>(a, b, P, Ns, tw, inv, t);
@@ -249,12 +253,15 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
 // Shared memory of a mixed-radix CTA: the twiddle table, then two transform buffers (3 M
 // samples, M = bt.mr_M the length each CTA transforms).  Copies the table in; the caller's
 // first barrier publishes it.
-__device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t) {
-  for (int m = t; m < bt.mr_M; m += kMrT) sm[m] = __ldg(bt.mr_tw + m);
-  return sm + bt.mr_M;
+__device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t, bool ycol = false) {
+  const int M = ycol ? bt.mr_My : bt.mr_M;
+  const float2* tw = ycol ? bt.mr_tw_y : bt.mr_tw;
+  for (int m = t; m < M; m += kMrT) sm[m] = __ldg(tw + m);
+  return sm + M;
 }
 
 // E_doe of Eq. 2 at DOE sample (i, x): transmittance, parametric incident field, E_in array.
+// N: the DOE's row length (its x side).
 __device__ __forceinline__ float2 mr_doe_field(const Slice& sl, int i, int x, int N, IncRow ir) {
   const size_t o = (size_t)(i >> sl.uf) * (N >> sl.uf) + (x >> sl.uf);  // layout cell of DOE row i
   const float hv = DOE_IN(o, sl.n_h) ? __ldg(sl.h + o) : 0.f;
@@ -266,14 +273,18 @@ __device__ __forceinline__ float2 mr_doe_field(const Slice& sl, int i, int x, in
 // Band-limited transfer function at column frequency index kc, row index lr (FFT order), from
 // the slice's quarter table; conjugated for the adjoint.  H depends on kt^2 + lt^2 only, so
 // the column's values are read along a table row (contiguous in lr).
-__device__ __forceinline__ float2 mr_transfer(const Slice& sl, int kc, int lr, int P, bool conj_h) {
-  const int a = abs_signed(kc, P), b = abs_signed(lr, P);
-  if (a > sl.kmax || b > sl.kmax) return make_float2(0.f, 0.f);
+__device__ __forceinline__ float2 mr_transfer(const Slice& sl, int kc, int lr, int Px, int Py, bool conj_h) {
+  const int a = abs_signed(kc, Px), b = abs_signed(lr, Py);
+  if (a > sl.kmax || b > sl.kmax_y) return make_float2(0.f, 0.f);
   if (!DOE_IN((size_t)a * sl.hp + b, sl.n_htab)) return make_float2(0.f, 0.f);
   float2 h = __ldg(sl.htab + (size_t)a * sl.hp + b);
   if (conj_h) h.y = -h.y;
   return h;
 }
+
+// Rectangular grids: rows run along x (Px = bt.P samples, the DOE's Nx = bt.N columns at offset
+// bt.off), columns along y (Py = bt.Py samples, the DOE's Ny = bt.Ny rows at offset bt.offy); the
+// buffers are row-major with rows of Px samples.  On square grids the two axes coincide.
 
 // ---- pass A (mixed radix): DOE row i of slice blockIdx.y -> its row spectrum, tbuf row i.
 template <bool CMP>
@@ -284,7 +295,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
   const float2* tw = sm_mr;
   float2* xa = mr_smem_setup(sm_mr, bt, t);
   float2* xb = xa + P;
-  const IncRow ir = incident_row(sl, i - N / 2);
+  const IncRow ir = incident_row(sl, i - bt.Ny / 2);
   for (int c = t; c < P; c += kMrT) {
     const int x = c - off;
     xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, i, x, N, ir) : make_float2(0.f, 0.f);
@@ -296,41 +307,41 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
     if (DOE_IN((size_t)i * P + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
 }
 
-// ---- pass B / B* (mixed radix): one column kc per CTA.  Forward: the N row spectra (tbuf rows
-// 0..N-1) placed at rows off..off+N-1, FFT, x H, IFFT, all P rows to buf.  Adjoint
-// (bt.mode == MODE_ADJ): all P rows of tbuf, FFT, x conj(H), IFFT, rows off..off+N-1 back to
-// tbuf rows 0..N-1 (in place: the CTA owns its column).  Neighbouring CTAs read the other
+// ---- pass B / B* (mixed radix): one column kc per CTA.  Forward: the Ny row spectra (tbuf rows
+// 0..Ny-1) placed at rows offy..offy+Ny-1, FFT, x H, IFFT, all Py rows to buf.  Adjoint
+// (bt.mode == MODE_ADJ): all Py rows of tbuf, FFT, x conj(H), IFFT, rows offy..offy+Ny-1 back to
+// tbuf rows 0..Ny-1 (in place: the CTA owns its column).  Neighbouring CTAs read the other
 // samples of each 32-byte sector, which they find in L2.
 template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
-  const int kc = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
+  const int kc = blockIdx.x, t = threadIdx.x, Ny = bt.Ny, Px = bt.P, Py = bt.Py, offy = bt.offy;
   const bool adj = bt.mode == MODE_ADJ;
   const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
-  float2* xb = xa + P;
-  for (int l = t; l < P; l += kMrT) {
-    const int r = adj ? l : l - off;
-    xa[l] = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + kc, sl.n_tbuf)
-                ? __ldcs(sl.tbuf + (size_t)r * P + kc) : make_float2(0.f, 0.f);
+  float2* xa = mr_smem_setup(sm_mr, bt, t, true);
+  float2* xb = xa + Py;
+  for (int l = t; l < Py; l += kMrT) {
+    const int r = adj ? l : l - offy;
+    xa[l] = (unsigned)r < (unsigned)(adj ? Py : Ny) && DOE_IN((size_t)r * Px + kc, sl.n_tbuf)
+                ? __ldcs(sl.tbuf + (size_t)r * Px + kc) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
+  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t, true);
   float2* z = y == xa ? xb : xa;
-  for (int l = t; l < P; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, P, adj));
+  for (int l = t; l < Py; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, Px, Py, adj));
   __syncthreads();
-  y = mr_fft<CMP>(y, z, bt, tw, true, t);
+  y = mr_fft<CMP>(y, z, bt, tw, true, t, true);
   if (!adj) {
-    for (int l = t; l < P; l += kMrT)
-      if (DOE_IN((size_t)l * P + kc, sl.n_buf)) __stcs(sl.buf + (size_t)l * P + kc, y[l]);
+    for (int l = t; l < Py; l += kMrT)
+      if (DOE_IN((size_t)l * Px + kc, sl.n_buf)) __stcs(sl.buf + (size_t)l * Px + kc, y[l]);
   } else {
-    for (int r = t; r < N; r += kMrT)
-      if (DOE_IN((size_t)r * P + kc, sl.n_tbuf)) __stcs(sl.tbuf + (size_t)r * P + kc, y[r + off]);
+    for (int r = t; r < Ny; r += kMrT)
+      if (DOE_IN((size_t)r * Px + kc, sl.n_tbuf)) __stcs(sl.tbuf + (size_t)r * Px + kc, y[r + offy]);
   }
 }
 
-// ---- pass C (mixed radix): output row y: IFFT, 1/P^2, then |E|^2 (OUT_PSF) or E.
+// ---- pass C (mixed radix): output row y: IFFT, 1/(Px Py), then |E|^2 (OUT_PSF) or E.
 template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
@@ -357,8 +368,8 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
   }
 }
 
-// ---- pass C' (mixed radix): output row y: E = IFFT / P^2, g = 2 (I - T) E (L2, with the row's
-// loss partial) or (dL/dI) E (VJP), forward FFT of g into tbuf row y.
+// ---- pass C' (mixed radix): output row y: E = IFFT / (Px Py), g = 2 (I - T) E (L2, with the
+// row's loss partial) or (dL/dI) E (VJP), forward FFT of g into tbuf row y.
 template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
@@ -398,8 +409,8 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
 }
 
 // ---- pass A* (mixed radix): DOE row i, summed over the slices in order: g_doe = IFFT(tbuf
-// row i) / P^2 on the DOE columns, dL/dh += -2 k' Im(conj(g_doe) E_doe).  Each thread owns its
-// DOE columns, so the running sum lives in the gradient row itself.
+// row i) / (Px Py) on the DOE columns, dL/dh += -2 k' Im(conj(g_doe) E_doe).  Each thread owns
+// its DOE columns, so the running sum lives in the gradient row itself.
 template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_consta
     for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)i * P + c, sl.n_tbuf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
     __syncthreads();
     const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
-    const IncRow ir = incident_row(sl, i - N / 2);
+    const IncRow ir = incident_row(sl, i - bt.Ny / 2);
     const float k2 = -2.f * sl.kp_hi;
     for (int x = t; x < N; x += kMrT) {
       if (!DOE_IN((size_t)i * N + x, bt.n_grad)) continue;

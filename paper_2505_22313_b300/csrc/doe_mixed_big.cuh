@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
   cl.sync();  // chunk k1 of the column is complete in xa
   float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
   const int kc = mrq_freq(c, Q, M);
-  for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, adj));
+  for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, P, adj));
   __syncthreads();
   float2* z = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, true, t);
   float2* remz[Q];

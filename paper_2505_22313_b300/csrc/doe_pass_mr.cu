@@ -32,19 +32,19 @@ cudaError_t prep_mr_t() {
   return cudaSuccess;
 }
 
-// shared memory: the twiddle table plus two transform buffers
-size_t mr_smem(const Batch& bt) { return (size_t)3 * bt.P * sizeof(float2); }
+// shared memory: the twiddle table plus two transform buffers, of the longer axis
+size_t mr_smem(const Batch& bt) { return (size_t)3 * (bt.P > bt.Py ? bt.P : bt.Py) * sizeof(float2); }
 
 // one CTA per row / column (P <= kMrMax)
 template <bool CMP>
 cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
   const size_t sm = mr_smem(bt);
   switch (which) {
-    case PASS_A: mr_rows_fwd_kernel<CMP><<<dim3(bt.N, bt.S), kMrT, sm, st>>>(bt); break;
-    case PASS_B: mr_cols_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
-    case PASS_C: mr_rows_out_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
-    case PASS_C_ADJ: mr_rows_adj_c_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;
-    case PASS_A_ADJ: mr_rows_adj_a_kernel<CMP><<<dim3(bt.N), kMrT, sm, st>>>(bt); break;
+    case PASS_A: mr_rows_fwd_kernel<CMP><<<dim3(bt.Ny, bt.S), kMrT, sm, st>>>(bt); break;   // DOE rows
+    case PASS_B: mr_cols_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;        // Px columns
+    case PASS_C: mr_rows_out_kernel<CMP><<<dim3(bt.Py, bt.S), kMrT, sm, st>>>(bt); break;   // Py rows
+    case PASS_C_ADJ: mr_rows_adj_c_kernel<CMP><<<dim3(bt.Py, bt.S), kMrT, sm, st>>>(bt); break;
+    case PASS_A_ADJ: mr_rows_adj_a_kernel<CMP><<<dim3(bt.Ny), kMrT, sm, st>>>(bt); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -91,7 +91,11 @@ cudaError_t mr_twiddles(const Batch& bt, cudaStream_t st) {
   {
     Traced tr(TR_MR_TWIDDLES, st);
     mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && bt.mr_tw_y != bt.mr_tw) {  // rectangular grid: the column transform's table
+      mr_twiddle_kernel<<<(unsigned)((bt.mr_My + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw_y), bt.mr_My);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess || bt.mr_Q == 1) return e;
   }
   Traced tr(TR_MR_TWIDDLES, st);

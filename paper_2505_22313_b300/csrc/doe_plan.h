@@ -87,13 +87,15 @@ struct Slice {
   float2* htab;          // [kmax + 1][hp] transfer function quarter table H(|kt|, |lt|)
   const float* tgt;      // [P][P] target T or dL/dI (gradient)
   void* out;             // [P][P] float PSF or float2 field
-  double* loss_part;     // [P] per-row loss partial sums (gradient)
+  double* loss_part;     // [Py] per-row loss partial sums (gradient)
   float kp_hi, kp_lo;    // k' = 2 pi (n - 1) / lambda as a float pair
-  float c_hi, c_lo;      // (lambda du)^2
+  float c_hi, c_lo;      // q = lambda^2 (fx^2 + fy^2) = c m: c = (lambda du)^2, (lambda g / (Px Py dx))^2 on rectangles
   float phi0_hi, phi0_lo;  // 2 pi z / lambda
   float th0_hi, th0_lo;    // (2 pi z / lambda) mod 2 pi
-  long long mev;         // propagating iff kt^2 + lt^2 < mev
-  int kmax;              // band limit index per axis
+  long long mev;         // propagating iff m = kt^2 sqb + lt^2 sqa < mev
+  long long sqa, sqb;    // (Px / g)^2, (Py / g)^2 with g = gcd(Px, Py): 1, 1 on square grids
+  int kmax;              // band limit index of the row (x) frequencies kt
+  int kmax_y;            // band limit index of the column (y) frequencies lt (= kmax on square grids)
   int seg_a;             // length of the stored non-negative-frequency segment (even)
   int w;                 // stored columns: P if the band limit is inactive, else seg_a + even(kmax)
   int wp;                // row pitch of buf (w rounded up to kTile)
@@ -129,7 +131,8 @@ enum : int { GRAD_L2 = 0, GRAD_VJP = 1 };
 
 struct Batch {
   int S;             // slices
-  int N, P, off;     // DOE side, padded side, DOE offset in the padded grid
+  int N, P, off;     // DOE side, padded side, DOE offset in the padded grid (rows: the x axis)
+  int Ny, Py, offy;  // the same along the columns (y axis); equal to N, P, off on square grids
   int total_tiles;   // column tiles over all slices
   int mode;          // MODE_FWD / MODE_ADJ (column pass), OUT_* (row inverse pass), GRAD_* (adjoint row pass)
   int max_kmax;      // largest kmax over the slices (table builder grid)
@@ -141,6 +144,10 @@ struct Batch {
   int mr_nst;        // mixed-radix plan of M: stages and their radices (2..8, 9, 15, 16, 25, primes)
   int mr_radix[kMrMaxStages];
   const float2* mr_tw;   // [M] twiddles exp(-2 pi i m / M) in the workspace
+  int mr_My;             // rectangular grids: the column transform's length, plan and twiddles
+  int mr_nst_y;          // (equal to the row's on square grids)
+  int mr_radix_y[kMrMaxStages];
+  const float2* mr_tw_y;
   const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)

@@ -84,6 +84,29 @@ def _geom(**kw):
     return Geometry.make(**base)
 
 
+def test_band_limits_rect_bit_exact_vs_oracle(lib):
+    """Per-axis kmax and the rectangular evanescent bound M_ev (kx^2 B^2 + ky^2 A^2 < M_ev)
+    equal the oracle's integers; on a square grid the x and y limits equal band_limits'."""
+    from paper_2505_22313_b300.api import band_limits_xy
+    rng = np.random.default_rng(17)
+    sides = [48, 64, 96, 100, 128, 160, 180, 250, 256, 400, 1000, 1024, 2000, 2048, 3000, 4000, 4096]
+    for _ in range(150):
+        Nx, Ny = (int(v) for v in rng.choice(sides, 2))
+        pad = int(rng.choice([1, 2])) if min(Nx, Ny) >= 64 else 2
+        dx = float(rng.uniform(0.2e-6, 4e-6))
+        z = float(10 ** rng.uniform(-5, -0.5))
+        lam = float(rng.uniform(380e-9, 780e-9))
+        g = Geometry.make(Nx, dx, z, [lam], pad=pad, Ny=Ny)
+        kx, ky, m = band_limits_xy(g)
+        ex, ey = oracle.kmax_rect(pad * Ny, pad * Nx, dx, z, lam)
+        assert (int(kx[0]), int(ky[0])) == (ex, ey), (Nx, Ny, pad)
+        if Nx != Ny:
+            assert int(m[0]) == oracle.mev_rect(pad * Ny, pad * Nx, dx, lam)[2], (Nx, Ny, pad)
+        else:
+            k1, m1 = band_limits(g)
+            assert int(kx[0]) == int(ky[0]) == int(k1[0]) and int(m[0]) == int(m1[0])
+
+
 @pytest.mark.parametrize(
     "g",
     [_geom(N=49), _geom(N=8), _geom(N=278, pad=1), _geom(N=4106), _geom(N=36000), _geom(N=4192), _geom(N=262, pad=1),
@@ -105,9 +128,16 @@ def test_bad_pad_and_unsupported_size(lib):
     big = _geom(N=32768).c()  # P = 65536 needs the multi-CTA transform
     rc = lib.doe_psf(ctypes.byref(big), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None)
     assert rc in (L.DOE_OK, L.DOE_ENOWS, L.DOE_EUNSUPPORTED)
-    rect = _geom().c()
-    rect.ny = 128
-    assert lib.doe_psf(ctypes.byref(rect), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_EUNSUPPORTED
+    # rectangles run on the one-CTA mixed-radix passes: both padded sides <= 8192, plain
+    # incidence, no upsampling, rectangular band
+    rect = _geom(Ny=128).c()
+    assert lib.doe_workspace_bytes(ctypes.byref(rect), L.DOE_OP_GRAD) > 0
+    assert lib.doe_psf(ctypes.byref(rect), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_ENOWS
+    for kw in (dict(Ny=8000), dict(Ny=128, upsample=2), dict(Ny=128, bandlimit="circular"), dict(Ny=128, theta_x=0.01),
+               dict(Ny=128, src_d=0.1), dict(Ny=4000, N=4200)):
+        c = _geom(**kw).c()
+        assert lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_PSF) == 0, kw
+        assert lib.doe_psf(ctypes.byref(c), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_EUNSUPPORTED, kw
 
 
 def test_workspace_checked_before_launch(lib):

@@ -1,8 +1,8 @@
 """The bounds-checked build (libdoe_debug.so, every kernel compiled with DOE_DEBUG): small
 cases of every pass family run through its C ABI -- power-of-two grids (one CTA per transform),
 split grids (32768 = 4 x 8192 and 65536 = 8 x 8192, the 16-CTA column clusters), mixed-radix
-grids (one CTA; split over a cluster), the adjoint passes, upsampled and Lanczos layouts,
-incident fields, the circular band, render and Wiener.  In that build every global, shared and
+grids (one CTA; split over a cluster), rectangular grids, the adjoint passes, upsampled and
+Lanczos layouts, incident fields, the circular band, render and Wiener.  In that build every global, shared and
 distributed-shared-memory index is checked against its buffer before the access; the fault
 word must stay 0, and the results must equal the release build's."""
 import ctypes
@@ -43,7 +43,7 @@ def _ws(lib, g, op):
 
 def _psf(lib, g, h, e_in=None, field=False):
     ws, n = _ws(lib, g, L.DOE_OP_PROPAGATE if field else L.DOE_OP_PSF)
-    out = torch.full((g.L, g.P, g.P) + ((2,) if field else ()), float("nan"), dtype=torch.float32, device="cuda")
+    out = torch.full((g.L, g.Py, g.P) + ((2,) if field else ()), float("nan"), dtype=torch.float32, device="cuda")
     gc = g.c()
     fn = lib.doe_propagate if field else lib.doe_psf
     assert fn(ctypes.byref(gc), _p(h), _p(e_in), _p(out), _p(ws), n, _stream()) == L.DOE_OK
@@ -52,7 +52,7 @@ def _psf(lib, g, h, e_in=None, field=False):
 
 def _grad(lib, g, h, T, e_in=None):
     ws, n = _ws(lib, g, L.DOE_OP_GRAD)
-    gr = torch.full((g.NL, g.NL), float("nan"), dtype=torch.float32, device="cuda")
+    gr = torch.full((g.NLy, g.NL), float("nan"), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     gc = g.c()
     assert lib.doe_grad(ctypes.byref(gc), _p(h), _p(e_in), _p(T), L.DOE_GRAD_L2_TARGET, _p(gr), _p(loss), 1, _p(ws), n,
@@ -86,6 +86,9 @@ CASES = [
     ("mixed_radix_split", 4500, 2, 1e-6, 5e-3, [550e-9], {}, True),
     ("split_32768", 16384, 2, 1e-6, 50e-3, [550e-9], {}, True),
     ("split_65536", 32768, 2, 1e-6, 100e-3, [550e-9], {}, False),
+    ("rect_mixed", 160, 2, 1e-6, 2e-3, [450e-9, 600e-9], dict(Ny=96), True),
+    ("rect_pow2_pad1", 256, 1, 1e-6, 2e-3, [550e-9], dict(Ny=512), True),
+    ("rect_large", 4000, 2, 1e-6, 20e-3, [550e-9], dict(Ny=3000), True),
 ]
 
 
@@ -94,7 +97,12 @@ def test_bounds_checked_build_matches_release(libs, name, N, pad, dx, z, lams, k
     rel, dbg = libs
     g = Geometry.make(N, dx, z, lams, pad=pad, **kw)
     nl = g.NL
-    h = torch.from_numpy(inputs.heights(nl, 4000 + N)).cuda() if nl <= 8192 else inputs.heights_device(nl, 4000 + N, "cuda")
+    if g.Ny != N:  # rectangle: the top-left Ny x N block of a square map
+        h = torch.from_numpy(np.ascontiguousarray(inputs.heights(max(N, g.Ny), 4000 + N)[:g.Ny, :N])).cuda()
+    elif nl <= 8192:
+        h = torch.from_numpy(inputs.heights(nl, 4000 + N)).cuda()
+    else:
+        h = inputs.heights_device(nl, 4000 + N, "cuda")
     e_in = None
     if name == "pow2":
         rng = np.random.default_rng(1)
@@ -104,12 +112,12 @@ def test_bounds_checked_build_matches_release(libs, name, N, pad, dx, z, lams, k
     assert _faults(dbg) == 0
     _same(a, _psf(rel, g, h, e_in))
     del a
-    if name in ("pow2", "mixed_radix"):
+    if name in ("pow2", "mixed_radix", "rect_mixed"):
         f = _psf(dbg, g, h, e_in, field=True)
         assert _faults(dbg) == 0
         _same(f, _psf(rel, g, h, e_in, field=True))
     if grad:
-        T = inputs.spot_target_device(g.P, N, g.L, 5000 + N, "cuda")
+        T = inputs.spot_target_device(max(g.P, g.Py), max(N, g.Ny), g.L, 5000 + N, "cuda")[:, :g.Py, :g.P].contiguous()
         gd, ld = _grad(dbg, g, h, T, e_in)
         assert _faults(dbg) == 0
         gr, lr = _grad(rel, g, h, T, e_in)

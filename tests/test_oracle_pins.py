@@ -199,8 +199,27 @@ def test_gaussian_beam_paraxial():
 
 
 # ------------------------------------------------------------------ rectangular grids
+@pytest.mark.parametrize("Py,Px,dx,lam", [(96, 160, 1e-6, 550e-9), (64, 48, 0.25e-6, 700e-9), (6000, 8000, 1e-6, 450e-9),
+                                          (120, 200, 0.3e-6, 400e-9)])
+def test_rect_evanescent_integer_rule(Py, Px, dx, lam):
+    # kx^2 B^2 + ky^2 A^2 < ceil((Px Py dx / (g lambda))^2) against lambda^2 (fx^2 + fy^2) < 1
+    # in floating point (they agree away from exact ties, and no sample sits on one here)
+    a2, b2, mev = oracle.mev_rect(Py, Px, dx, lam)
+    g = np.gcd(Px, Py)
+    assert a2 == (Px // g) ** 2 and b2 == (Py // g) ** 2
+    kx = np.where(np.arange(Px) < Px // 2, np.arange(Px), np.arange(Px) - Px).astype(np.int64)
+    ky = np.where(np.arange(Py) < Py // 2, np.arange(Py), np.arange(Py) - Py).astype(np.int64)
+    m = kx[None, :] ** 2 * b2 + ky[:, None] ** 2 * a2
+    q = lam**2 * ((kx[None, :] / (Px * dx)) ** 2 + (ky[:, None] / (Py * dx)) ** 2)
+    assert np.array_equal(m < mev, q < 1.0)
+    mask = oracle.band_mask_rect(Py, Px, dx, 1e-9, lam)  # z -> 0: the band limit is inactive
+    assert np.array_equal(mask.astype(bool), q < 1.0)
+
+
+
 def test_rect_oracle_reduces_to_the_square_one():
-    # numpy FFT and the FP64 transfer rule here against the C oracle (its own FFT and H)
+    # the rectangular rules (per-axis band, the gcd form of the evanescent cut) and its Python
+    # assembly of the chain against the C oracle's square path (its own H and chain)
     for N, pad, dx, z, lam, bl in ((64, 2, 1e-6, 2e-3, 550e-9, True), (90, 2, 0.5e-6, 1e-3, 450e-9, True),
                                    (48, 1, 1e-6, 5e-3, 650e-9, False)):
         h = inputs.heights(N, 30 + N)
