@@ -266,7 +266,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   s.hp = (int)((kmax + 2) & ~1L);  // kmax + 1 rounded up to even
   if (is_pow2(P) && P > (1L << kMaxLog)) {  // split grids: rows grouped by residue mod Q = P / 8192
     s.hqs = ilog2(P / 8192);
-    s.hq = (int)(kmax >> s.hqs) + 1;
+    s.hq = (int)(((kmax >> s.hqs) + 2) & ~1L);  // (kmax >> hqs) + 1 rounded up to even: 16-byte class runs
     s.hp = s.hq << s.hqs;
   }
   s.mev = band_mlim(g, lam, P);

@@ -193,7 +193,11 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_c_big_kern
 // ------------------------------------------------------------------ columns (pass B / B*)
 // Cluster of TC x Q CTAs (TC = big_tile(Q) adjacent stored columns x Q sub-transforms, at
 // most 16); rank = c Q + s.
-// Rows are stored in sub-transform order (the row passes above).
+// Rows are stored in sub-transform order (the row passes above).  Both exchanges between the
+// CTAs are pushes (remote stores, which no thread waits on): the decimation-in-frequency step
+// writes each sub-transform's inputs into its owner's buffer, and after the inverse
+// sub-transforms each CTA writes its results into the buffer of the CTA that combines those
+// rows.  The transfer-function entries arrive by bulk copy during the forward transform.
 template <int Q>
 __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kernel(const __grid_constant__ Batch bt) {
   constexpr int L = kBigL, T = L / 32, P = L * Q, TC = big_tile(Q), CL = TC * Q, SH = L / CL;
@@ -212,19 +216,23 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   const Slice& sl = bt.s[si];
   const int pos0 = (tile_g - sl.tile_begin) * TC;
   const int kcol = big_pos_to_k(pos0 + c, Q);
-  const bool live = pos0 + c < sl.w && abs_signed(kcol, P) <= sl.kmax;
-  if (live) {
-    // the two residue classes of this column's transfer-function row that sub-transform s
-    // reads after its forward transform (frequencies s + Q k2 below P/2 and their mirrors
-    // above): this CTA brings their lines into L2 now
-    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, P) * sl.hp;
-    const char* h0 = reinterpret_cast<const char*>(hrow + (size_t)s * sl.hq);
-    const char* h1 = reinterpret_cast<const char*>(hrow + (size_t)((Q - s) % Q) * sl.hq);
-    for (int o = 128 * t; o < sl.hq * (int)sizeof(float2); o += 128 * T) {
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(h0 + o));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(h1 + o));
-    }
-  }
+  const int ak = abs_signed(kcol, P);
+  const bool live = pos0 + c < sl.w && ak <= sl.kmax;
+  // The transfer-function entries sub-transform s multiplies after its forward transform are
+  // those of the frequencies f = s + Q k2: for f <= P/2 entry a = f (residue class s of the
+  // table row, position k2); above P/2 the mirror a = P - f (class (Q - s) mod Q, position
+  // L - k2 for s = 0, L - 1 - k2 otherwise).  Both runs are copied into the exchange buffer
+  // while the forward transform's last stage computes: class s at entry 0 (L/2 + 2 entries
+  // for s = 0, where it also holds the mirrors; L/2 otherwise), class Q - s at entry L/2 (L/2
+  // entries; none for s = Q/2, whose mirrors share class s).  Table rows hold hq (even)
+  // entries per class, so each run starts on a 16-byte boundary.
+  __shared__ __align__(8) uint64_t hbar;  // completion of the copies
+  const int hb = (Q - s) % Q;
+  const int nA = min(s == 0 ? L / 2 + 2 : L / 2, sl.hq), nB = hb == s ? 0 : min(L / 2, sl.hq);
+  const float2* hrow = sl.htab + (size_t)ak * sl.hp;
+  const bool hcopy = live && DOE_IN((size_t)ak * sl.hp + (size_t)s * sl.hq + nA - 1, sl.n_htab) &&
+                     (nB == 0 || DOE_IN((size_t)ak * sl.hp + (size_t)hb * sl.hq + nB - 1, sl.n_htab));
+  if (t == 0) mbar_init(&hbar, 1);
   const bool adj = bt.mode == MODE_ADJ;
   const int N = bt.N, off = bt.off;
   const int nin = adj ? P : N, yin0 = adj ? 0 : off;
@@ -278,47 +286,64 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
   cl.sync();
   float2 v[32];
   stage_load<L, 32, false, 0>(v, t, sm);
-  fft_run<L, 32, false>(v, t, sm);
+  fft_run_last<L, 32, false>(v, t, sm, [&] {
+    fence_proxy_async_smem();  // this thread's reads of the buffer come before the copies' writes
+    __syncthreads();
+    if (hcopy && t == 0) {
+      mbar_arrive_expect_tx(&hbar, (unsigned)(nA + nB) * sizeof(float2));
+      bulk_g2s(sm, hrow + (size_t)s * sl.hq, (unsigned)nA * sizeof(float2), &hbar);
+      if (nB) bulk_g2s(sm + L / 2, hrow + (size_t)hb * sl.hq, (unsigned)nB * sizeof(float2), &hbar);
+    }
+  });
+  const bool hok = !hcopy || mbar_wait(&hbar, 0);
+  if (!hok && t == 0) raise_fault(FAULT_WAIT_TIMEOUT);
   {
-    const float2* hrow = sl.htab + (size_t)abs_signed(kcol, P) * sl.hp;
 #pragma unroll
     for (int b = 0; b < G::B; ++b)
 #pragma unroll
       for (int r = 0; r < G::R; ++r) {
-        const int a = abs_signed(s + Q * G::idx(t, b, r), P);
+        const int k2 = G::idx(t, b, r), f = s + Q * k2;
+        const int a = abs_signed(f, P);
+        const int e = f < P / 2 ? k2 : s == 0 ? L - k2 : nB == 0 ? L - 1 - k2 : L / 2 + L - 1 - k2;
         float2& x = v[b * G::R + r];
-        if (live && a <= sl.kmax && DOE_IN((size_t)abs_signed(kcol, P) * sl.hp + htab_col(sl, a), sl.n_htab)) {
-          const float2 hv = hrow[htab_col(sl, a)];  // consecutive threads: consecutive entries
+        if (hcopy && hok && a <= sl.kmax && DOE_IN(e, L)) {
+          const float2 hv = sm[e];
           x = adj ? cmulc(x, hv) : cmul(x, hv);
         } else {
           x = make_float2(0.f, 0.f);
         }
       }
   }
-  fft_run<L, 32, true>(v, t, sm);
-  __syncthreads();
+  // inverse transform; once every CTA of the cluster has loaded its last stage's inputs, the
+  // exchange buffers are free and each CTA pushes its results to the CTA that combines them:
+  // rows x2 in [d SH, (d + 1) SH) go to rank d, at entry rank SH + x2 mod SH of its buffer
+  fft_run_last<L, 32, true>(v, t, sm, [] { cluster_arrive(); });
+  cluster_wait();
   {
-    float4* s4 = reinterpret_cast<float4*>(sm);
 #pragma unroll
     for (int b = 0; b < Hh::B; b += 2)
 #pragma unroll
       for (int r = 0; r < Hh::R; ++r) {
+        const int x2 = Hh::idx(t, b, r);  // even: registers (b, r), (b + 1, r) hold x2, x2 + 1
         const float2 a = v[b * Hh::R + r], d = v[(b + 1) * Hh::R + r];
-        if (DOE_IN(swz(Hh::idx(t, b, r) >> 1), L / 2)) s4[swz(Hh::idx(t, b, r) >> 1)] = make_float4(a.x, a.y, d.x, d.y);
+        const int slot = rank * SH + (x2 % SH);
+        if (DOE_IN(slot >> 1, L / 2)) reinterpret_cast<float4*>(rsm(x2 / SH))[slot >> 1] = make_float4(a.x, a.y, d.x, d.y);
       }
   }
   cl.sync();
-  // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2 (pairs y2, y2 + 1)
+  // decimation-in-time combine over the sub-transforms, rows y = y1 L + y2 (pairs y2, y2 + 1),
+  // from this CTA's own buffer
+  const float4* r4 = reinterpret_cast<const float4*>(sm);
 #pragma unroll
   for (int it = 0; it < SH / (2 * T); ++it) {
-    const int y2 = rank * SH + 2 * t + it * 2 * T;
+    const int y2l = 2 * t + it * 2 * T, y2 = rank * SH + y2l;
     float2 out[2][TC][Q];
 #pragma unroll
     for (int cc = 0; cc < TC; ++cc) {
 #pragma unroll
       for (int sp = 0; sp < Q; ++sp) {
-        const float4 q4 = DOE_IN(swz(y2 >> 1), L / 2) ? reinterpret_cast<const float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)]
-                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ch = ((cc * Q + sp) * SH + y2l) >> 1;
+        const float4 q4 = DOE_IN(ch, L / 2) ? r4[ch] : make_float4(0.f, 0.f, 0.f, 0.f);
         out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * y2));
         out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (y2 + 1)));
       }
@@ -343,7 +368,7 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
         }
       }
   }
-  cluster_sync_relaxed();
+  // no closing barrier: after the last cluster barrier no CTA touches another's shared memory
 }
 
 // ------------------------------------------------------------------ rows, adjoint (pass C')

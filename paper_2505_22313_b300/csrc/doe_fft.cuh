@@ -384,6 +384,24 @@ __device__ __forceinline__ void fft_run(float2 (&v)[E], int t, float2* sm) {
   }
 }
 
+// fft_run with a callback at the last stage: at_last() runs after the last stage's inputs are
+// loaded from shared memory and before its butterflies (which need no shared memory), so a
+// callback that starts with a barrier finds the exchange buffer free for other uses.
+template <int L, int E, bool INV, int S = 0, class F>
+__device__ __forceinline__ void fft_run_last(float2 (&v)[E], int t, float2* sm, F&& at_last) {
+  if constexpr (S + 1 < St<L, E, INV, S>::NST) {
+    stage_compute<L, E, INV, S>(v, t);
+    __syncthreads();
+    stage_store<L, E, INV, S>(v, t, sm);
+    __syncthreads();
+    stage_load<L, E, INV, S + 1>(v, t, sm);
+    fft_run_last<L, E, INV, S + 1>(v, t, sm, at_last);
+  } else {
+    at_last();
+    stage_compute<L, E, INV, S>(v, t);
+  }
+}
+
 // Layout helpers for the kernels: the first stage's input layout and the last stage's output
 // layout.  Register b*R + r holds transform element idx(t, b, r); registers (b, r) and
 // (b + 1, r) for even b hold the adjacent elements e, e + 1.

@@ -208,6 +208,11 @@ __device__ __forceinline__ float4 ein_pair(const Slice& s, int N, int i, int x) 
 __device__ __forceinline__ void cluster_sync_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
+// The two halves of a cluster barrier, for work placed between them: the arrival releases this
+// thread's earlier memory accesses (shared-memory reads included), the wait acquires every
+// other thread's.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 // Position of entry a (= |lt|) in a row of the transfer-function table.  Split grids group a
 // row by residue mod Q (the cluster size of their column pass): entry a at (a mod Q) hq + a / Q,

@@ -101,7 +101,7 @@ struct Slice {
   int wp;                // row pitch of buf (w rounded up to kTile)
   int hp;                // row pitch of htab: kmax + 1 rounded up to even, or hq << hqs
   int hqs;               // split grids: row entries grouped by residue mod 2^hqs (0: natural order)
-  int hq;                // split grids: entries per residue class of a row
+  int hq;                // split grids: entries per residue class of a row (even)
   int tile_begin;        // first global column-tile index of this slice (column pass)
   int uf;                // log2 of the nearest-upsampling factor of the heights (0: none)
   int illum;             // parametric incident field: ILLUM_TILT | ILLUM_SPHERE (0: none)
