@@ -190,6 +190,55 @@ def _traffic(workload: str, kernel: str):
     return e.get("dram_bytes_per_launch") if e else None
 
 
+# kernel (demangled ncu name) -> pass name of the library's trace, for the PSF + render step
+_TRAFFIC_KERNELS = (("htab_kernel", "transfer_table"), ("pass_a_kernel", "pass_a_rows"),
+                    ("pass_b_kernel", "pass_b_columns"), ("pass_c_kernel", "pass_c_rows"),
+                    ("render_rows_kernel", "render_rows"), ("render_cols_kernel", "render_columns"),
+                    ("render_out_kernel", "render_output"))
+
+
+def ingest_traffic(csv_path: str, workload: str, command: str) -> dict:
+    """Writes profiles/traffic.json from an ncu CSV of dram__bytes_read.sum,
+    dram__bytes_write.sum and gpu__time_duration.sum (one row per metric and launch): per pass
+    of a PSF + render step, the mean DRAM bytes per launch, keyed on the current kernel sources.
+    Entries of other workloads taken on the same sources are kept."""
+    import csv
+    import re
+
+    launches = {}
+    with open(csv_path, newline="") as f:
+        rows = [r for r in csv.reader(line for line in f if line.startswith('"'))]
+    head = rows[0]
+    ix = {k: head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Value")}
+    for r in rows[1:]:
+        e = launches.setdefault(r[ix["ID"]], {"kernel": r[ix["Kernel Name"]]})
+        e[r[ix["Metric Name"]]] = float(r[ix["Metric Value"]].replace(",", ""))
+    per = {}
+    for e in launches.values():
+        name = next((p for k, p in _TRAFFIC_KERNELS if re.search(rf"\b{k}\b", e["kernel"])), None)
+        if name is None or "dram__bytes_read.sum" not in e:
+            continue
+        per.setdefault(name, []).append(e)
+    out = {}
+    for name, es in per.items():
+        rd = sum(e["dram__bytes_read.sum"] for e in es) / len(es)
+        wr = sum(e["dram__bytes_write.sum"] for e in es) / len(es)
+        dur = sum(e.get("gpu__time_duration.sum", 0.0) for e in es) / len(es)
+        out[name] = {"dram_bytes_per_launch": int(rd + wr), "read_bytes": int(rd), "write_bytes": int(wr),
+                     "duration_ns": round(dur, 1), "launches": len(es), "kernel": es[0]["kernel"]}
+    p = ROOT / "profiles" / "traffic.json"
+    sha = _source_hash()
+    d = json.loads(p.read_text()) if p.exists() else {}
+    if d.get("source_sha") != sha:
+        d = {}
+    d.update({"_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch (mean over the captured launches) "
+                       "from ncu captures of the named workloads; valid only for the kernel sources with this source_sha",
+              "source_sha": sha})
+    d.setdefault("workloads", {})[workload] = {"_command": command, **out}
+    p.write_text(json.dumps(d, indent=1) + "\n")
+    return d
+
+
 class _Nvml:
     """Read-only NVML queries: pynvml when importable, else the driver's libnvidia-ml through
     ctypes (same public entry points)."""
@@ -822,10 +871,17 @@ def main():
     ap.add_argument("--requests", type=int, default=None, help="serving trace length (--config 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing and error checks")
     ap.add_argument("--no-sub", action="store_true", help="skip the per-configuration sub-records")
+    ap.add_argument("--ingest-traffic", metavar="CSV", default=None,
+                    help="write profiles/traffic.json from an ncu CSV of the PSF + render step and exit")
+    ap.add_argument("--ncu-command", default="", help="the ncu command that wrote the CSV (recorded with it)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.config is not None and args.config.isdigit():
         args.config = int(args.config)
+    if args.ingest_traffic:
+        wl = CONFIGS[args.config if args.config is not None else 2]["workload"]
+        print(json.dumps(ingest_traffic(args.ingest_traffic, wl, args.ncu_command)["workloads"][wl], indent=1))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
