@@ -311,6 +311,7 @@ struct Layout {
   size_t mrtw = 0;           // mixed radix: the [M] twiddle table of the per-CTA transform
   size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
   size_t mrtw_y = 0;         // rectangular grids: the [Py] twiddle table of the column transform
+  size_t mrtws = 0, mrtws_y = 0;  // per-stage (lane-contiguous) twiddles of the row / column plans
   long tbuf_rows = 0;        // rows of the column-tiled buffers (Ny forward, Py with the adjoint)
 };
 
@@ -359,9 +360,15 @@ Layout make_layout(const std::vector<Slice>& sl, int op, int n_req, const doe_ge
     off = align256(off + (size_t)P * sizeof(float2));
     L.mrtw_y = off;
     off = align256(off + (size_t)Py * sizeof(float2));
+    L.mrtws = off;
+    off = align256(off + (size_t)P * sizeof(float2));
+    L.mrtws_y = off;
+    off = align256(off + (size_t)Py * sizeof(float2));
   } else if (!is_pow2(P)) {
     const MrSplit sp = mr_split(P);
     L.mrtw = off;
+    off = align256(off + (size_t)sp.M * sizeof(float2));
+    L.mrtws = off;
     off = align256(off + (size_t)sp.M * sizeof(float2));
     if (sp.Q > 1) {
       L.mrtwP = off;
@@ -456,6 +463,8 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, const doe_geom* g0, voi
     bt.mr_cmp = (cx || cy) ? 1 : 0;
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
     bt.mr_tw_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw_y);
+    bt.mr_tws = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtws);
+    bt.mr_tws_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtws_y);
   } else if (!is_pow2(bt.P)) {
     const MrSplit sp = mr_split(bt.P);
     bt.mr = 1;
@@ -464,12 +473,14 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, const doe_geom* g0, voi
     bt.qf = sp.Q;  // split rows write one loss partial per CTA
     bt.mr_cmp = set_plan(sp.M, bt.mr_nst, bt.mr_radix) ? 1 : 0;
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
+    bt.mr_tws = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtws);
     if (sp.Q > 1) bt.mr_twP = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP);
     // square grid: the column transform is the row transform
     bt.mr_My = bt.mr_M;
     bt.mr_nst_y = bt.mr_nst;
     for (int s = 0; s < bt.mr_nst; ++s) bt.mr_radix_y[s] = bt.mr_radix[s];
     bt.mr_tw_y = bt.mr_tw;
+    bt.mr_tws_y = bt.mr_tws;
   }
 }
 

@@ -7,10 +7,14 @@
 // 9, 15, 16, 25 (split in registers), and a direct-DFT stage for each larger prime factor.  Stage
 // with Ns = product of the earlier radices: butterfly j < P/R reads x[j + r P/R] (r < R),
 // multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
-// output r to y[(j - k) R + k + r Ns].  Twiddles w_P^m = exp(-2 pi i m / P) come from a table
-// of P entries built per call in FP64 (mr_twiddle_kernel) and copied into shared memory by
-// every CTA.  Stages go out of place between two shared buffers (one barrier per stage), one
-// butterfly in registers at a time.
+// output r to y[(j - k) R + k + r Ns].  The stage twiddles w_(Ns R)^(r k) come from a per-stage
+// table laid out [stage][r][k] (mr_stage_twiddle_kernel; M - 1 entries in all, since the stages'
+// (R - 1) Ns sum to M - 1), copied into shared memory by every CTA: the lanes of a warp, which
+// hold consecutive k, read consecutive entries, free of bank conflicts.  The composite stages'
+// inner twiddles w_R^m are compile-time constants; the direct-DFT stages of larger primes read
+// the table of all P powers w_P^m from global memory.  Both tables are built per call in FP64.
+// Stages go out of place between two shared buffers (one barrier per stage), one butterfly in
+// registers at a time.
 //
 // Buffers (natural row-major layout, rows of P samples): tbuf holds the row spectra of the N
 // DOE rows (forward) or of all P rows (adjoint), buf the field after the column pass.
@@ -21,6 +25,10 @@ namespace doe {
 
 constexpr int kMrT = 256;  // threads per CTA of every mixed-radix pass
 
+struct MrRadices {  // a plan's radices, by value (kernel argument)
+  int r[kMrMaxStages];
+};
+
 // Twiddle table w_P^m, m < P, from FP64 sincospi of the exact ratio 2 m / P.
 __global__ void __launch_bounds__(256) mr_twiddle_kernel(float2* __restrict__ tw, int P) {
   const int m = blockIdx.x * 256 + threadIdx.x;
@@ -28,6 +36,22 @@ __global__ void __launch_bounds__(256) mr_twiddle_kernel(float2* __restrict__ tw
   double s, c;
   sincospi(-2.0 * (double)m / (double)P, &s, &c);
   tw[m] = make_float2((float)c, (float)s);
+}
+
+// Per-stage twiddles of a plan of M (radices R_s): stage s with sub-transform size Ns holds
+// w_(Ns R)^(r k) = exp(-2 pi i r k / (Ns R)) at (Ns - 1) + (r - 1) Ns + k (1 <= r < R, k < Ns),
+// from FP64 sincospi of the exact ratio.  One thread per entry, e < M - 1.
+__global__ void __launch_bounds__(256) mr_stage_twiddle_kernel(float2* __restrict__ tws, int M, int nst,
+                                                               MrRadices rad) {
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  if (e >= M - 1) return;
+  int Ns = 1, s = 0;
+  while (s + 1 < nst && e >= Ns * rad.r[s] - 1) Ns *= rad.r[s++];  // stage s covers [Ns - 1, Ns R - 1)
+  const int R = rad.r[s], o = e - (Ns - 1);
+  const int r = 1 + o / Ns, k = o % Ns;
+  double sn, cs;
+  sincospi(-2.0 * (double)((long long)r * k) / ((double)Ns * R), &sn, &cs);
+  tws[e] = make_float2((float)cs, (float)sn);
 }
 
 // R-point DFTs (forward kernel exp(-2 pi i n k / R); inv: exp(+...)), written from the
@@ -114,21 +138,24 @@ __device__ __forceinline__ void mr_dft<8>(float2 (&v)[8], bool inv) {
 
 // One Stockham stage of radix R: src -> dst (both P samples of shared memory), see the file
 // comment; ends with a barrier so that dst is visible.  One butterfly in registers at a time.
+// tws: this stage's twiddle rows (shared memory), w_(Ns R)^(r k) at (r - 1) Ns + k.
 template <int R>
-__device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, int Ns, const float2* tw, bool inv,
+__device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, int Ns, const float2* tws, bool inv,
                                          int t) {
-  const int nb = P / R, step = P / (Ns * R);
+  const int nb = P / R;
 #pragma unroll 2
   for (int j = t; j < nb; j += kMrT) {
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = DOE_IN(j + r * nb, P) ? src[j + r * nb] : make_float2(0.f, 0.f);
     const int k = j % Ns;
+    if (Ns > 1) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      float2 w = DOE_IN(r * k * step, P) ? tw[r * k * step] : make_float2(0.f, 0.f);  // r k step < P
-      if (inv) w.y = -w.y;
-      v[r] = cmul(v[r], w);
+      for (int r = 1; r < R; ++r) {
+        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? tws[(r - 1) * Ns + k] : make_float2(0.f, 0.f);
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
     }
     mr_dft<R>(v, inv);
     const int base = (j - k) * R + k;
@@ -139,25 +166,67 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
   __syncthreads();
 }
 
+// cos and sin of 2 pi m / R (m < R): the inner twiddles w_R^m = cos - i sin of the composite
+// radices 9, 15, 16, 25 (mathematical constants, rounded to FP32).
+template <int R>
+__host__ __device__ constexpr float wr_cos(int m) {
+  if constexpr (R == 9) {
+    constexpr float c[9] = {1.000000000f, 7.660444431e-1f, 1.736481777e-1f, -5.000000000e-1f, -9.396926208e-1f, -9.396926208e-1f, -5.000000000e-1f, 1.736481777e-1f, 7.660444431e-1f};
+    return c[m];
+  } else if constexpr (R == 15) {
+    constexpr float c[15] = {1.000000000f, 9.135454576e-1f, 6.691306064e-1f, 3.090169944e-1f, -1.045284633e-1f, -5.000000000e-1f, -8.090169944e-1f, -9.781476007e-1f, -9.781476007e-1f, -8.090169944e-1f, -5.000000000e-1f, -1.045284633e-1f, 3.090169944e-1f, 6.691306064e-1f, 9.135454576e-1f};
+    return c[m];
+  } else if constexpr (R == 16) {
+    constexpr float c[16] = {1.000000000f, 9.238795325e-1f, 7.071067812e-1f, 3.826834324e-1f, 0.f, -3.826834324e-1f, -7.071067812e-1f, -9.238795325e-1f, -1.000000000f, -9.238795325e-1f, -7.071067812e-1f, -3.826834324e-1f, 0.f, 3.826834324e-1f, 7.071067812e-1f, 9.238795325e-1f};
+    return c[m];
+  } else if constexpr (R == 25) {
+    constexpr float c[25] = {1.000000000f, 9.685831611e-1f, 8.763066800e-1f, 7.289686274e-1f, 5.358267950e-1f, 3.090169944e-1f, 6.279051953e-2f, -1.873813146e-1f, -4.257792916e-1f, -6.374239897e-1f, -8.090169944e-1f, -9.297764859e-1f, -9.921147013e-1f, -9.921147013e-1f, -9.297764859e-1f, -8.090169944e-1f, -6.374239897e-1f, -4.257792916e-1f, -1.873813146e-1f, 6.279051953e-2f, 3.090169944e-1f, 5.358267950e-1f, 7.289686274e-1f, 8.763066800e-1f, 9.685831611e-1f};
+    return c[m];
+  } else {
+    return 1.f;
+  }
+}
+template <int R>
+__host__ __device__ constexpr float wr_sin(int m) {
+  if constexpr (R == 9) {
+    constexpr float s[9] = {0.f, 6.427876097e-1f, 9.848077530e-1f, 8.660254038e-1f, 3.420201433e-1f, -3.420201433e-1f, -8.660254038e-1f, -9.848077530e-1f, -6.427876097e-1f};
+    return s[m];
+  } else if constexpr (R == 15) {
+    constexpr float s[15] = {0.f, 4.067366431e-1f, 7.431448255e-1f, 9.510565163e-1f, 9.945218954e-1f, 8.660254038e-1f, 5.877852523e-1f, 2.079116908e-1f, -2.079116908e-1f, -5.877852523e-1f, -8.660254038e-1f, -9.945218954e-1f, -9.510565163e-1f, -7.431448255e-1f, -4.067366431e-1f};
+    return s[m];
+  } else if constexpr (R == 16) {
+    constexpr float s[16] = {0.f, 3.826834324e-1f, 7.071067812e-1f, 9.238795325e-1f, 1.000000000f, 9.238795325e-1f, 7.071067812e-1f, 3.826834324e-1f, 0.f, -3.826834324e-1f, -7.071067812e-1f, -9.238795325e-1f, -1.000000000f, -9.238795325e-1f, -7.071067812e-1f, -3.826834324e-1f};
+    return s[m];
+  } else if constexpr (R == 25) {
+    constexpr float s[25] = {0.f, 2.486898872e-1f, 4.817536741e-1f, 6.845471059e-1f, 8.443279255e-1f, 9.510565163e-1f, 9.980267284e-1f, 9.822872507e-1f, 9.048270525e-1f, 7.705132428e-1f, 5.877852523e-1f, 3.681245527e-1f, 1.253332336e-1f, -1.253332336e-1f, -3.681245527e-1f, -5.877852523e-1f, -7.705132428e-1f, -9.048270525e-1f, -9.822872507e-1f, -9.980267284e-1f, -9.510565163e-1f, -8.443279255e-1f, -6.845471059e-1f, -4.817536741e-1f, -2.486898872e-1f};
+    return s[m];
+  } else {
+    return 0.f;
+  }
+}
+
 // One Stockham stage of a composite radix R = R1 R2 (16 = 4 x 4, 25 = 5 x 5, 9 = 3 x 3, 15 = 3 x 5):
 // the R-point DFT of each butterfly is split in registers (n = n1 + R1 n2, k = k2 + R2 k1):
 //   X[k2 + R2 k1] = sum_n1 w_R1^(n1 k1) [ w_R^(n1 k2) sum_n2 v[n1 + R1 n2] w_R2^(n2 k2) ],
 // which halves the shared-memory passes (and barriers) of a plan.  w_R^e = w_P^(e P/R).
+// tws: this stage's twiddle rows (shared memory).
 template <int R1, int R2>
-__device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P, int Ns, const float2* tw, bool inv,
+__device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P, int Ns, const float2* tws, bool inv,
                                           int t) {
   constexpr int R = R1 * R2;
-  const int nb = P / R, step = P / (Ns * R);
+  const int nb = P / R;
   for (int j = t; j < nb; j += kMrT) {
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = DOE_IN(j + r * nb, P) ? src[j + r * nb] : make_float2(0.f, 0.f);
     const int k = j % Ns;
+    if (Ns > 1) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      float2 w = DOE_IN(r * k * step, P) ? tw[r * k * step] : make_float2(0.f, 0.f);  // r k step < P
-      if (inv) w.y = -w.y;
-      v[r] = cmul(v[r], w);
+      for (int r = 1; r < R; ++r) {
+        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? tws[(r - 1) * Ns + k] : make_float2(0.f, 0.f);
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
     }
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
@@ -168,8 +237,8 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) {
         if (n1 && k2) {
-          float2 w = DOE_IN(n1 * k2 * nb, P) ? tw[n1 * k2 * nb] : make_float2(0.f, 0.f);  // w_R^(n1 k2); n1 k2 nb < P
-          if (inv) w.y = -w.y;
+          // w_R^(n1 k2): compile-time constants
+          const float2 w = make_float2(wr_cos<R>((n1 * k2) % R), inv ? wr_sin<R>((n1 * k2) % R) : -wr_sin<R>((n1 * k2) % R));
           a[k2] = cmul(a[k2], w);
         }
         v[n1 + R1 * k2] = a[k2];
@@ -195,7 +264,7 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
 //   dst[(j - k) R + k + r Ns] = sum_m src[j + m P/R] w_P^(m e),  e = k P/(Ns R) + r P/R
 // (w_P^(m k P/(Ns R)) w_R^(m r) = w_P^(m e)); the exponent m e is kept reduced mod P.
 __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, int P, int Ns, int R,
-                                               const float2* tw, bool inv, int t) {
+                                               const float2* twg, bool inv, int t) {
   const int nb = P / R, step = P / (Ns * R);
   for (int o = t; o < P; o += kMrT) {
     const int j = o / R, r = o - j * R, k = j % Ns;
@@ -203,7 +272,7 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
     float2 acc = make_float2(0.f, 0.f);
     int idx = 0;
     for (int m = 0; m < R; ++m) {
-      float2 w = DOE_IN(idx, P) ? tw[idx] : make_float2(0.f, 0.f);
+      float2 w = DOE_IN(idx, P) ? __ldg(twg + idx) : make_float2(0.f, 0.f);
       if (inv) w.y = -w.y;
       const float2 v = DOE_IN(j + m * nb, P) ? src[j + m * nb] : make_float2(0.f, 0.f);
       acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
@@ -217,31 +286,33 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
 }
 
 // Unnormalised transform of the P samples at a (shared memory; b is a second buffer of P) with
-// the batch's plan and the twiddles tw (shared memory).  The caller has made a's contents
-// visible (barrier).  Returns the buffer holding the result (a or b).
+// the batch's plan and its per-stage twiddles tws (shared memory, mr_smem_setup).  The caller
+// has made a's contents visible (barrier).  Returns the buffer holding the result (a or b).
 // CMP: the plan has composite stages (9, 15, 16, 25); kernels are compiled both ways because
 // those stages raise the register count (about 125 against 66), which costs occupancy to the
 // short transforms that do not use them.
 // ycol: the column (y) plan of a rectangular grid instead of the row plan.
 template <bool CMP>
-__device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tw, bool inv, int t,
+__device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tws, bool inv, int t,
                                           bool ycol = false) {
   // the transform length: P (Py), or the chunk length M of a split transform
   const int P = ycol ? bt.mr_My : bt.mr_M;
   const int nst = ycol ? bt.mr_nst_y : bt.mr_nst;
+  const float2* twg = ycol ? bt.mr_tw_y : bt.mr_tw;
   int Ns = 1;
   for (int s = 0; s < nst; ++s) {
     const int R = ycol ? bt.mr_radix_y[s] : bt.mr_radix[s];
-    if (CMP && R == 25) mr_stage2<5, 5>(a, b, P, Ns, tw, inv, t);
-    else if (CMP && R == 16) mr_stage2<4, 4>(a, b, P, Ns, tw, inv, t);
-    else if (CMP && R == 9) mr_stage2<3, 3>(a, b, P, Ns, tw, inv, t);
-    else if (CMP && R == 15) mr_stage2<3, 5>(a, b, P, Ns, tw, inv, t);
-    else if (R == 8) mr_stage<8>(a, b, P, Ns, tw, inv, t);
-    else if (R == 5) mr_stage<5>(a, b, P, Ns, tw, inv, t);
-    else if (R == 4) mr_stage<4>(a, b, P, Ns, tw, inv, t);
-    else if (R == 3) mr_stage<3>(a, b, P, Ns, tw, inv, t);
-    else if (R == 2) mr_stage<2>(a, b, P, Ns, tw, inv, t);
-    else mr_stage_prime(a, b, P, Ns, R, tw, inv, t);
+    const float2* ts = tws + (Ns - 1);  // this stage's rows
+    if (CMP && R == 25) mr_stage2<5, 5>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 16) mr_stage2<4, 4>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 9) mr_stage2<3, 3>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 15) mr_stage2<3, 5>(a, b, P, Ns, ts, inv, t);
+    else if (R == 8) mr_stage<8>(a, b, P, Ns, ts, inv, t);
+    else if (R == 5) mr_stage<5>(a, b, P, Ns, ts, inv, t);
+    else if (R == 4) mr_stage<4>(a, b, P, Ns, ts, inv, t);
+    else if (R == 3) mr_stage<3>(a, b, P, Ns, ts, inv, t);
+    else if (R == 2) mr_stage<2>(a, b, P, Ns, ts, inv, t);
+    else mr_stage_prime(a, b, P, Ns, R, twg, inv, t);
     Ns *= R;
     float2* c = a;
     a = b;
@@ -250,13 +321,13 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
   return a;
 }
 
-// Shared memory of a mixed-radix CTA: the twiddle table, then two transform buffers (3 M
-// samples, M = bt.mr_M the length each CTA transforms).  Copies the table in; the caller's
-// first barrier publishes it.
+// Shared memory of a mixed-radix CTA: the per-stage twiddle table (M - 1 entries, one slot
+// spare), then two transform buffers (3 M samples, M = bt.mr_M the length each CTA
+// transforms).  Copies the table in; the caller's first barrier publishes it.
 __device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t, bool ycol = false) {
   const int M = ycol ? bt.mr_My : bt.mr_M;
-  const float2* tw = ycol ? bt.mr_tw_y : bt.mr_tw;
-  for (int m = t; m < M; m += kMrT) sm[m] = __ldg(tw + m);
+  const float2* tws = ycol ? bt.mr_tws_y : bt.mr_tws;
+  for (int m = t; m < M - 1; m += kMrT) sm[m] = __ldg(tws + m);
   return sm + M;
 }
 

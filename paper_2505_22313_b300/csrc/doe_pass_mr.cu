@@ -87,14 +87,25 @@ cudaError_t mr_pass(int which, const Batch& bt, cudaStream_t st) {
   }
 }
 
+// The per-stage table of a plan of M (M - 1 entries).
+static cudaError_t stage_twiddles(const float2* tws, int M, int nst, const int* radix, cudaStream_t st) {
+  MrRadices rad{};
+  for (int s = 0; s < nst && s < kMrMaxStages; ++s) rad.r[s] = radix[s];
+  if (M > 1)
+    mr_stage_twiddle_kernel<<<(unsigned)((M - 1 + 255) / 256), 256, 0, st>>>(const_cast<float2*>(tws), M, nst, rad);
+  return cudaGetLastError();
+}
+
 cudaError_t mr_twiddles(const Batch& bt, cudaStream_t st) {
   {
     Traced tr(TR_MR_TWIDDLES, st);
     mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && bt.mr_tw_y != bt.mr_tw) {  // rectangular grid: the column transform's table
+    if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws, bt.mr_M, bt.mr_nst, bt.mr_radix, st);
+    if (e == cudaSuccess && bt.mr_tw_y != bt.mr_tw) {  // rectangular grid: the column transform's tables
       mr_twiddle_kernel<<<(unsigned)((bt.mr_My + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw_y), bt.mr_My);
       e = cudaGetLastError();
+      if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws_y, bt.mr_My, bt.mr_nst_y, bt.mr_radix_y, st);
     }
     if (e != cudaSuccess || bt.mr_Q == 1) return e;
   }

@@ -149,6 +149,10 @@ struct Batch {
   int mr_radix_y[kMrMaxStages];
   const float2* mr_tw_y;
   const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
+  // per-stage twiddles of the plan, lane-contiguous: stage s (sub-transform size Ns, radix R)
+  // holds w_(Ns R)^(r k) at (Ns - 1) + (r - 1) Ns + k for 1 <= r < R, k < Ns (M - 1 entries in all)
+  const float2* mr_tws;
+  const float2* mr_tws_y;  // of the column transform of a rectangular grid
   float inv_p2;      // 1 / P^2 (inverse transform normalisation)
   float* grad;       // [N][N] gradient on the simulation grid (DOE-row adjoint pass)
   long long n_grad;  // its extent (bounds checks of the DOE_DEBUG build)
