@@ -9,8 +9,8 @@
 // multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
 // output r to y[(j - k) R + k + r Ns].  The stage twiddles w_(Ns R)^(r k) come from a per-stage
 // table laid out [stage][r][k] (mr_stage_twiddle_kernel; M - 1 entries in all, since the stages'
-// (R - 1) Ns sum to M - 1), copied into shared memory by every CTA: the lanes of a warp, which
-// hold consecutive k, read consecutive entries, free of bank conflicts.  The composite stages'
+// (R - 1) Ns sum to M - 1), read through L1: the lanes of a warp, which hold consecutive k,
+// read consecutive entries (one 256-byte run per warp and radix term).  The composite stages'
 // inner twiddles w_R^m are compile-time constants; the direct-DFT stages of larger primes read
 // the table of all P powers w_P^m from global memory.  Both tables are built per call in FP64.
 // Stages go out of place between two shared buffers (one barrier per stage), one butterfly in
@@ -138,8 +138,9 @@ __device__ __forceinline__ void mr_dft<8>(float2 (&v)[8], bool inv) {
 
 // One Stockham stage of radix R: src -> dst (both P samples of shared memory), see the file
 // comment; ends with a barrier so that dst is visible.  One butterfly in registers at a time.
-// tws: this stage's twiddle rows (shared memory), w_(Ns R)^(r k) at (r - 1) Ns + k.
-template <int R>
+// tws: this stage's twiddle rows, w_(Ns R)^(r k) at (r - 1) Ns + k (GTW: in global memory, read
+// through L1; else in shared memory).
+template <int R, bool GTW>
 __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, int Ns, const float2* tws, bool inv,
                                          int t) {
   const int nb = P / R;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void mr_stage(const float2* src, float2* dst, int P, 
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? tws[(r - 1) * Ns + k] : make_float2(0.f, 0.f);
+        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? (GTW ? __ldg(tws + (r - 1) * Ns + k) : tws[(r - 1) * Ns + k]) : make_float2(0.f, 0.f);
         if (inv) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -209,8 +210,8 @@ __host__ __device__ constexpr float wr_sin(int m) {
 // the R-point DFT of each butterfly is split in registers (n = n1 + R1 n2, k = k2 + R2 k1):
 //   X[k2 + R2 k1] = sum_n1 w_R1^(n1 k1) [ w_R^(n1 k2) sum_n2 v[n1 + R1 n2] w_R2^(n2 k2) ],
 // which halves the shared-memory passes (and barriers) of a plan.  w_R^e = w_P^(e P/R).
-// tws: this stage's twiddle rows (shared memory).
-template <int R1, int R2>
+// tws: this stage's twiddle rows (GTW: global memory).
+template <int R1, int R2, bool GTW>
 __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P, int Ns, const float2* tws, bool inv,
                                           int t) {
   constexpr int R = R1 * R2;
@@ -223,7 +224,7 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? tws[(r - 1) * Ns + k] : make_float2(0.f, 0.f);
+        float2 w = DOE_IN((Ns - 1) + (r - 1) * Ns + k, P) ? (GTW ? __ldg(tws + (r - 1) * Ns + k) : tws[(r - 1) * Ns + k]) : make_float2(0.f, 0.f);
         if (inv) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -286,13 +287,15 @@ __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, i
 }
 
 // Unnormalised transform of the P samples at a (shared memory; b is a second buffer of P) with
-// the batch's plan and its per-stage twiddles tws (shared memory, mr_smem_setup).  The caller
-// has made a's contents visible (barrier).  Returns the buffer holding the result (a or b).
+// the batch's plan and its per-stage twiddles tws: the table in global memory, read through L1
+// (GTW: the one-CTA passes), or its copy in shared memory (mr_smem_setup<true>: the split
+// passes, whose L1 also serves the split's own twiddles).  The caller has made a's contents visible
+// (barrier).  Returns the buffer holding the result (a or b).
 // CMP: the plan has composite stages (9, 15, 16, 25); kernels are compiled both ways because
 // those stages raise the register count (about 125 against 66), which costs occupancy to the
 // short transforms that do not use them.
 // ycol: the column (y) plan of a rectangular grid instead of the row plan.
-template <bool CMP>
+template <bool CMP, bool GTW>
 __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt, const float2* tws, bool inv, int t,
                                           bool ycol = false) {
   // the transform length: P (Py), or the chunk length M of a split transform
@@ -303,15 +306,15 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
   for (int s = 0; s < nst; ++s) {
     const int R = ycol ? bt.mr_radix_y[s] : bt.mr_radix[s];
     const float2* ts = tws + (Ns - 1);  // this stage's rows
-    if (CMP && R == 25) mr_stage2<5, 5>(a, b, P, Ns, ts, inv, t);
-    else if (CMP && R == 16) mr_stage2<4, 4>(a, b, P, Ns, ts, inv, t);
-    else if (CMP && R == 9) mr_stage2<3, 3>(a, b, P, Ns, ts, inv, t);
-    else if (CMP && R == 15) mr_stage2<3, 5>(a, b, P, Ns, ts, inv, t);
-    else if (R == 8) mr_stage<8>(a, b, P, Ns, ts, inv, t);
-    else if (R == 5) mr_stage<5>(a, b, P, Ns, ts, inv, t);
-    else if (R == 4) mr_stage<4>(a, b, P, Ns, ts, inv, t);
-    else if (R == 3) mr_stage<3>(a, b, P, Ns, ts, inv, t);
-    else if (R == 2) mr_stage<2>(a, b, P, Ns, ts, inv, t);
+    if (CMP && R == 25) mr_stage2<5, 5, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 16) mr_stage2<4, 4, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 9) mr_stage2<3, 3, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (CMP && R == 15) mr_stage2<3, 5, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (R == 8) mr_stage<8, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (R == 5) mr_stage<5, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (R == 4) mr_stage<4, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (R == 3) mr_stage<3, GTW>(a, b, P, Ns, ts, inv, t);
+    else if (R == 2) mr_stage<2, GTW>(a, b, P, Ns, ts, inv, t);
     else mr_stage_prime(a, b, P, Ns, R, twg, inv, t);
     Ns *= R;
     float2* c = a;
@@ -321,14 +324,25 @@ __device__ __forceinline__ float2* mr_fft(float2* a, float2* b, const Batch& bt,
   return a;
 }
 
-// Shared memory of a mixed-radix CTA: the per-stage twiddle table (M - 1 entries, one slot
-// spare), then two transform buffers (3 M samples, M = bt.mr_M the length each CTA
-// transforms).  Copies the table in; the caller's first barrier publishes it.
+// Shared memory of a mixed-radix CTA: two transform buffers (2 M samples, M = bt.mr_M the
+// length each CTA transforms, or the column length My), behind a copy of the per-stage twiddle
+// table (M entries) if COPY.  Returns the first buffer; the caller's first barrier publishes
+// the copy.
+template <bool COPY>
 __device__ __forceinline__ float2* mr_smem_setup(float2* sm, const Batch& bt, int t, bool ycol = false) {
-  const int M = ycol ? bt.mr_My : bt.mr_M;
-  const float2* tws = ycol ? bt.mr_tws_y : bt.mr_tws;
-  for (int m = t; m < M - 1; m += kMrT) sm[m] = __ldg(tws + m);
-  return sm + M;
+  if constexpr (!COPY) {
+    return sm;
+  } else {
+    const int M = ycol ? bt.mr_My : bt.mr_M;
+    const float2* tws = ycol ? bt.mr_tws_y : bt.mr_tws;
+    for (int m = t; m < M - 1; m += kMrT) sm[m] = __ldg(tws + m);
+    return sm + M;
+  }
+}
+// the twiddle table mr_fft reads: global (no copy) or the shared copy at sm
+template <bool COPY>
+__device__ __forceinline__ const float2* mr_tws_of(const float2* sm, const Batch& bt, bool ycol = false) {
+  return COPY ? sm : (ycol ? bt.mr_tws_y : bt.mr_tws);
 }
 
 // E_doe of Eq. 2 at DOE sample (i, x): transmittance, parametric incident field, E_in array.
@@ -363,8 +377,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
   const int i = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<false>(sm_mr, bt, t);
   float2* xb = xa + P;
   const IncRow ir = incident_row(sl, i - bt.Ny / 2);
   for (int c = t; c < P; c += kMrT) {
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_fwd_kernel(const __grid_constant
     xa[c] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, i, x, N, ir) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
+  const float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt), false, t);
   float2* dst = sl.tbuf + (size_t)i * P;
   for (int c = t; c < P; c += kMrT)
     if (DOE_IN((size_t)i * P + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
@@ -389,8 +402,7 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
   const Slice& sl = bt.s[blockIdx.y];
   const int kc = blockIdx.x, t = threadIdx.x, Ny = bt.Ny, Px = bt.P, Py = bt.Py, offy = bt.offy;
   const bool adj = bt.mode == MODE_ADJ;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t, true);
+  float2* xa = mr_smem_setup<false>(sm_mr, bt, t, true);
   float2* xb = xa + Py;
   for (int l = t; l < Py; l += kMrT) {
     const int r = adj ? l : l - offy;
@@ -398,11 +410,11 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
                 ? __ldcs(sl.tbuf + (size_t)r * Px + kc) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t, true);
+  float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt, true), false, t, true);
   float2* z = y == xa ? xb : xa;
   for (int l = t; l < Py; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, Px, Py, adj));
   __syncthreads();
-  y = mr_fft<CMP>(y, z, bt, tw, true, t, true);
+  y = mr_fft<CMP, true>(y, z, bt, mr_tws_of<false>(sm_mr, bt, true), true, t, true);
   if (!adj) {
     for (int l = t; l < Py; l += kMrT)
       if (DOE_IN((size_t)l * Px + kc, sl.n_buf)) __stcs(sl.buf + (size_t)l * Px + kc, y[l]);
@@ -418,13 +430,12 @@ __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant
   extern __shared__ float2 sm_mr[];
   const Slice& sl = bt.s[blockIdx.y];
   const int row = blockIdx.x, t = threadIdx.x, P = bt.P;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<false>(sm_mr, bt, t);
   float2* xb = xa + P;
   const float2* src = sl.buf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)row * P + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
-  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+  const float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt), true, t);
   const float s = bt.inv_p2;
   if (bt.mode == OUT_PSF) {
     float* dst = static_cast<float*>(sl.out) + (size_t)row * P;
@@ -447,13 +458,12 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
   __shared__ double red[32];
   const Slice& sl = bt.s[blockIdx.y];
   const int row = blockIdx.x, t = threadIdx.x, P = bt.P;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<false>(sm_mr, bt, t);
   float2* xb = xa + P;
   const float2* src = sl.buf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)row * P + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
-  float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+  float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt), true, t);
   const float s = bt.inv_p2;
   const float* trow = sl.tgt + (size_t)row * P;
   float acc = 0.f;
@@ -471,7 +481,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_c_kernel(const __grid_consta
     y[c] = cscale(e, w);
   }
   __syncthreads();
-  y = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, false, t);
+  y = mr_fft<CMP, true>(y, y == xa ? xb : xa, bt, mr_tws_of<false>(sm_mr, bt), false, t);
   float2* dst = sl.tbuf + (size_t)row * P;
   for (int c = t; c < P; c += kMrT)
     if (DOE_IN((size_t)row * P + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
@@ -486,8 +496,7 @@ template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_constant__ Batch bt) {
   extern __shared__ float2 sm_mr[];
   const int i = blockIdx.x, t = threadIdx.x, N = bt.N, P = bt.P, off = bt.off;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<false>(sm_mr, bt, t);
   float2* xb = xa + P;
   float* grow = bt.grad + (size_t)i * N;
   for (int j = 0; j < bt.S; ++j) {
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(kMrT) mr_rows_adj_a_kernel(const __grid_consta
     const float2* src = sl.tbuf + (size_t)i * P;
     for (int c = t; c < P; c += kMrT) xa[c] = DOE_IN((size_t)i * P + c, sl.n_tbuf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
     __syncthreads();
-    const float2* y = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+    const float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt), true, t);
     const IncRow ir = incident_row(sl, i - bt.Ny / 2);
     const float k2 = -2.f * sl.kp_hi;
     for (int x = t; x < N; x += kMrT) {

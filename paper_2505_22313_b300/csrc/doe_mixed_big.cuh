@@ -59,8 +59,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
   const int k1 = (int)cl.block_rank();
   const Slice& sl = bt.s[blockIdx.y];
   const int i = blockIdx.x / Q, t = threadIdx.x, N = bt.N, M = bt.mr_M, off = bt.off;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
   float2* rem[Q];
   mrq_map<Q>(cl, xa, rem);
@@ -77,7 +76,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
   cl.sync();  // chunk k1 is complete in xa (and the twiddle table visible)
-  const float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
+  const float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t);
   float2* dst = sl.tbuf + (size_t)i * bt.P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT)
     if (DOE_IN((size_t)i * bt.P + (size_t)k1 * M + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
@@ -91,14 +90,13 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
   const int k1 = (int)cl.block_rank();
   const Slice& sl = bt.s[blockIdx.y];
   const int row = blockIdx.x / Q, t = threadIdx.x, P = bt.P, M = bt.mr_M;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT)
     xa[c] = DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
-  float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+  float2* z = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), true, t);
   float2* rem[Q];
   mrq_map<Q>(cl, z, rem);
   cl.sync();  // every chunk is transformed
@@ -129,14 +127,13 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
   const int k1 = (int)cl.block_rank();
   const Slice& sl = bt.s[blockIdx.y];
   const int row = blockIdx.x / Q, t = threadIdx.x, P = bt.P, M = bt.mr_M;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
   const float2* src = sl.buf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT)
     xa[c] = DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_buf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
   __syncthreads();
-  float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+  float2* z = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), true, t);
   float2* w = z == xa ? xb : xa;  // the same buffer in every CTA (same plan)
   float2* remz[Q];
   float2* remw[Q];
@@ -167,7 +164,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
     mrq_scatter_fwd<Q>(v, n2, bt, remw);
   }
   cl.sync();  // w holds chunk k1 of the forward step in every CTA; reads of z are done
-  const float2* y = mr_fft<CMP>(w, z, bt, tw, false, t);
+  const float2* y = mr_fft<CMP, false>(w, z, bt, mr_tws_of<true>(sm_mr, bt), false, t);
   float2* dst = sl.tbuf + (size_t)row * P + (size_t)k1 * M;
   for (int c = t; c < M; c += kMrT)
     if (DOE_IN((size_t)row * P + (size_t)k1 * M + c, sl.n_tbuf)) __stcs(dst + c, y[c]);
@@ -183,8 +180,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
   cg::cluster_group cl = cg::this_cluster();
   const int k1 = (int)cl.block_rank();
   const int i = blockIdx.x / Q, t = threadIdx.x, N = bt.N, P = bt.P, M = bt.mr_M, off = bt.off;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
   const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
   float* grow = bt.grad + (size_t)i * N;
@@ -194,7 +190,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
     for (int c = t; c < M; c += kMrT)
       xa[c] = DOE_IN((size_t)i * P + (size_t)k1 * M + c, sl.n_tbuf) ? __ldcs(src + c) : make_float2(0.f, 0.f);
     __syncthreads();
-    float2* z = mr_fft<CMP>(xa, xb, bt, tw, true, t);
+    float2* z = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), true, t);
     float2* rem[Q];
     mrq_map<Q>(cl, z, rem);
     cl.sync();  // every chunk of this slice is transformed
@@ -230,8 +226,7 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
   const Slice& sl = bt.s[blockIdx.y];
   const int c = blockIdx.x / Q, t = threadIdx.x, N = bt.N, P = bt.P, M = bt.mr_M, off = bt.off;
   const bool adj = bt.mode == MODE_ADJ;
-  const float2* tw = sm_mr;
-  float2* xa = mr_smem_setup(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
   float2* rem[Q];
   mrq_map<Q>(cl, xa, rem);
@@ -248,11 +243,11 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
     mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
   cl.sync();  // chunk k1 of the column is complete in xa
-  float2* y = mr_fft<CMP>(xa, xb, bt, tw, false, t);
+  float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t);
   const int kc = mrq_freq(c, Q, M);
   for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, P, adj));
   __syncthreads();
-  float2* z = mr_fft<CMP>(y, y == xa ? xb : xa, bt, tw, true, t);
+  float2* z = mr_fft<CMP, false>(y, y == xa ? xb : xa, bt, mr_tws_of<true>(sm_mr, bt), true, t);
   float2* remz[Q];
   mrq_map<Q>(cl, z, remz);
   cl.sync();  // every chunk is back in the row domain

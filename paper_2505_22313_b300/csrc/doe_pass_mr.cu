@@ -11,7 +11,7 @@ namespace {
 template <int Q, bool CMP>
 cudaError_t prep_mrq_t() {
   cudaError_t e;
-  constexpr int b = 3 * kMrMax * (int)sizeof(float2);
+  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddle copy and two buffers
   if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_out_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_adj_a_kernel<Q, CMP>, b, kMrT)))
@@ -21,7 +21,7 @@ cudaError_t prep_mrq_t() {
 template <bool CMP>
 cudaError_t prep_mr_t() {
   cudaError_t e;
-  constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddles and two buffers
+  constexpr int b = 2 * kMrMax * (int)sizeof(float2);  // two buffers
   if ((e = prep_one(mr_rows_fwd_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_cols_kernel<CMP>, b, kMrT)) ||
       (e = prep_one(mr_rows_out_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel<CMP>, b, kMrT)) ||
       (e = prep_one(mr_rows_adj_a_kernel<CMP>, b, kMrT)))
@@ -32,8 +32,8 @@ cudaError_t prep_mr_t() {
   return cudaSuccess;
 }
 
-// shared memory: the twiddle table plus two transform buffers, of the longer axis
-size_t mr_smem(const Batch& bt) { return (size_t)3 * (bt.P > bt.Py ? bt.P : bt.Py) * sizeof(float2); }
+// shared memory: two transform buffers, of the longer axis
+size_t mr_smem(const Batch& bt) { return (size_t)2 * (bt.P > bt.Py ? bt.P : bt.Py) * sizeof(float2); }
 
 // one CTA per row / column (P <= kMrMax)
 template <bool CMP>
@@ -64,6 +64,7 @@ cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
   const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which) : mrq_fn<Q, false>(which);
   const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.N : bt.P;
   void* args[] = {const_cast<Batch*>(&bt)};
+  // a shared copy of the per-stage twiddle table and two buffers
   return launch_cluster(fn, dim3(lines * Q, which == PASS_A_ADJ ? 1 : bt.S), Q, (size_t)3 * bt.mr_M * sizeof(float2),
                         st, args, kMrT);
 }
