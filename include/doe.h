@@ -286,6 +286,13 @@ long long doe_launch_count(void);
 int doe_fault_status(uint32_t* word);
 int doe_debug_build(void);
 
+/* Check of the fault path of the bounded waits: launches one CTA on `stream` that announces 16
+ * bytes of asynchronous copies on an mbarrier and issues none, so its wait gives up after
+ * `polls` polls (1 <= polls <= 2^20; DOE_EINVAL otherwise) and sets DOE_FAULT_WAIT_TIMEOUT,
+ * which the next doe_fault_status() reports.  Nothing faults and the context stays usable.
+ * Not part of the paper: diagnostics. */
+int doe_check_wait_timeout(uint32_t polls, void* stream);
+
 /* Human-readable text for a status code. */
 const char* doe_strerror(int code);
 

@@ -37,6 +37,7 @@ EXPORTS = (
     "doe_radial_workspace_bytes", "doe_radial_grad",
     "doe_band_limits", "doe_band_limits_xy", "doe_debug_band_mask", "doe_strerror", "doe_trace_enable", "doe_trace_read",
     "doe_pass_name", "doe_launch_count", "doe_psf_noalloc", "doe_fault_status", "doe_debug_build",
+    "doe_check_wait_timeout",
 )
 
 
@@ -116,6 +117,7 @@ def open_library(p: Path) -> ctypes.CDLL:
         "doe_psf_noalloc": ([G, F, F, F, V], I),
         "doe_fault_status": ([ctypes.POINTER(ctypes.c_uint32)], I),
         "doe_debug_build": ([], I),
+        "doe_check_wait_timeout": ([ctypes.c_uint32, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

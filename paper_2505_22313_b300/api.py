@@ -362,6 +362,12 @@ def debug_build() -> bool:
     return bool(L.load().doe_debug_build())
 
 
+def check_wait_timeout(polls: int = 1 << 12, stream=None) -> None:
+    """Launch the check of the bounded waits' failure path (a wait on a copy that is never
+    issued); the next fault_status() reports DOE_FAULT_WAIT_TIMEOUT."""
+    L.check(L.load().doe_check_wait_timeout(int(polls), _stream(stream)), "doe_check_wait_timeout")
+
+
 def launch_count() -> int:
     """Number of kernels libdoe has launched in this process."""
     return int(L.load().doe_launch_count())

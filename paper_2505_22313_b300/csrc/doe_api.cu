@@ -728,6 +728,11 @@ int doe_fault_status(uint32_t* word) {
   return DOE_OK;
 }
 
+int doe_check_wait_timeout(uint32_t polls, void* stream) {
+  if (polls < 1 || polls > (1u << 20)) return DOE_EINVAL;
+  return launch_wait_check(polls, static_cast<cudaStream_t>(stream)) == cudaSuccess ? DOE_OK : DOE_ECUDA;
+}
+
 int doe_debug_build(void) {
 #ifdef DOE_DEBUG
   return 1;

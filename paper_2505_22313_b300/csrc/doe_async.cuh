@@ -43,10 +43,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Waits for the phase of parity `parity` of mbar to complete.  Returns false if it did not
-// within kMbarMaxPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
+// within max_polls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity, unsigned max_polls = kMbarMaxPolls) {
   const unsigned a = smem_addr(mbar);
-  for (unsigned i = 0; i < kMbarMaxPolls; ++i) {
+  for (unsigned i = 0; i < max_polls; ++i) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

@@ -259,4 +259,9 @@ cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_wait_check(unsigned polls, cudaStream_t st) {
+  wait_check_kernel<<<1, 32, 0, st>>>(polls);
+  return cudaGetLastError();
+}
+
 }  // namespace doe

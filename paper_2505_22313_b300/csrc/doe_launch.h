@@ -19,6 +19,7 @@ cudaError_t launch_pass_c_adj(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_pass_a_adj(int lg, const Batch& bt, cudaStream_t st);
 cudaError_t launch_loss_reduce(const Batch& bt, double* loss, cudaStream_t st);
 cudaError_t launch_band_mask(const Batch& bt, uint8_t* mask, cudaStream_t st);
+cudaError_t launch_wait_check(unsigned polls, cudaStream_t st);  // a bounded wait that runs out
 cudaError_t launch_upsample_adjoint(const float* g, float* gc, int N, int uf, cudaStream_t st);
 cudaError_t launch_lanczos_up(const float* hl, float* tmp, float* hs, int N, const LanczosTab& tb, cudaStream_t st);
 cudaError_t launch_lanczos_adjoint(const float* g, float* tmp, float* gl, int N, const LanczosTab& tb,

@@ -212,4 +212,17 @@ __global__ void band_mask_kernel(const __grid_constant__ Batch bt, uint8_t* mask
   }
 }
 
+// Check of the bounded waits' failure path: one CTA announces 16 bytes of copies on an mbarrier
+// and issues none, so the phase never completes; every thread's wait gives up after `polls`
+// polls and the fault word records DOE_FAULT_WAIT_TIMEOUT.  No copy is in flight when it exits.
+__global__ void __launch_bounds__(32) wait_check_kernel(unsigned polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  if (!mbar_wait(&bar, 0, polls) && threadIdx.x == 0) raise_fault(FAULT_WAIT_TIMEOUT);
+}
+
 }  // namespace doe

@@ -176,3 +176,9 @@ def test_mixed_radix_sizes_accepted(lib, N, pad):
     assert need >= P * P * 8 + N * P * 8  # natural-layout field buffers, no band compaction
     cg = _geom(N=N, pad=pad, lambdas=[450e-9, 650e-9]).c()
     assert lib.doe_workspace_bytes(ctypes.byref(cg), L.DOE_OP_GRAD) > 2 * need - 2 * N * P * 8
+
+
+def test_wait_check_rejects_bad_bounds(lib):
+    # validated before any launch
+    assert lib.doe_check_wait_timeout(0, None) == L.DOE_EINVAL
+    assert lib.doe_check_wait_timeout((1 << 20) + 1, None) == L.DOE_EINVAL
