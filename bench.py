@@ -57,6 +57,10 @@ CONFIGS = {
     "table2_28800": dict(workload="table2_28800", N=14400, dx=0.25e-6, z=10e-3, lambdas=[520.6e-9],
                          step="psf+grad", upsample=8, h_seed=15400, tgt_seed=16400),
     "split_9000": dict(workload="split_9000", N=4500, dx=1e-6, z=5e-3, lambdas=[550e-9], step="psf", h_seed=5500),
+    # the serving mix's largest requests: a 16384^2 DOE padded to 32768^2 (columns and rows split
+    # over clusters of 4 CTAs of 8192 points), PSF + L2 gradient
+    "grid_32768": dict(workload="grid_32768", N=16384, dx=1e-6, z=50e-3, lambdas=[550e-9], step="psf+grad",
+                       h_seed=6384, tgt_seed=7384),
 }
 SERVING = dict(workload="serving_poisson_mix", requests=40, rate_hz=200.0, seed=3000,
                sides=(1024, 2048, 4096, 8192, 16384), max_lambda=31)
