@@ -111,10 +111,11 @@ __device__ __forceinline__ void load_tiled_col(float2 (&v)[32], int t, const flo
 // CTA q reads its own column of SA and of SB straight into registers, keeps the image column's
 // spectrum in sma while the kernel column is transformed in smb, multiplies, inverse-transforms,
 // and the cluster gathers rows [H/2, 3H/2) of its four columns as 32-byte row segments of SC.
-// Up to 4096 points two 32 KB buffers let 3 CTAs share an SM; the Wiener filter would push
-// registers past that, so its instantiation is capped to match.
+// From 1024 to 4096 points the two buffers let 384 threads (3 CTAs at 4096 points) share an SM, and
+// the registers are capped to match, 168 per thread (without the cap the two spectra and their
+// product take 230: 2 CTAs).
 template <int L, bool WIENER>
-__global__ void __launch_bounds__(L / 32, WIENER && L <= 4096 ? 3 : 1) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
+__global__ void __launch_bounds__(L / 32, L >= 1024 && L <= 4096 ? 12288 / L : 1) render_cols_kernel(const __grid_constant__ RenderArgs ra) {
   using G = Last<L, false>;
   using Hh = Last<L, true>;
   constexpr int T = L / 32;
