@@ -475,7 +475,8 @@ def _time_steps(wl, K, W, dev, ws_n, flush=False):
 def _roofline(wl, t, dev, workload):
     alg, flops = wl.alg()
     per = t["per"]
-    dom = max(per, key=lambda k: sum(per[k]))
+    # the dominant pass among those with algorithmic bytes (a table set-up pass has none)
+    dom = max((k for k in per if alg.get(k)), key=lambda k: sum(per[k]))
     avg_ms = sum(per[dom]) / len(per[dom])
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (avg_ms / 1e3) / 1e9
