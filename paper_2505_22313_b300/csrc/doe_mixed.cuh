@@ -424,6 +424,109 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
   }
 }
 
+// ---- pass B / B* (mixed radix) on clusters of 4 CTAs (Px a multiple of 4): the same
+// transforms as mr_cols_kernel, one column per CTA, with the global accesses of the four
+// adjacent columns kc0..kc0+3 done together as 32-byte row segments.  Each CTA loads a quarter
+// of the rows (pairs of rows: two 16-byte loads per row) and pushes each column's pair of
+// samples into that column's CTA (distributed shared memory, one 16-byte remote store), and
+// after the inverse transform gathers a quarter of the output rows of all four columns from the
+// cluster and stores them as 32-byte segments.  The column's transfer-function row arrives in
+// shared memory by bulk copy while the input is exchanged and the forward transform runs.
+// Shared memory: two buffers of Py samples, then the H row (hp entries).
+template <bool CMP>
+__global__ void __launch_bounds__(kMrT) mr_cols4_kernel(const __grid_constant__ Batch bt) {
+  extern __shared__ __align__(16) float2 sm_mr[];
+  __shared__ __align__(8) uint64_t hbar;  // completion of the H-row copy
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const Slice& sl = bt.s[blockIdx.y];
+  const int kc = blockIdx.x, kc0 = kc - q, t = threadIdx.x, Ny = bt.Ny, Px = bt.P, Py = bt.Py, offy = bt.offy;
+  const bool adj = bt.mode == MODE_ADJ;
+  float2* xa = sm_mr;
+  float2* xb = xa + Py;
+  float2* hs = xb + Py;
+  const int ak = abs_signed(kc, Px);
+  const bool hcopy = ak <= sl.kmax && sl.hp <= Py / 2 + 2 && DOE_IN((size_t)ak * sl.hp + sl.hp - 1, sl.n_htab);
+  if (t == 0) {
+    mbar_init(&hbar, 1);
+    if (hcopy) {
+      mbar_arrive_expect_tx(&hbar, (unsigned)sl.hp * sizeof(float2));
+      bulk_g2s(hs, sl.htab + (size_t)ak * sl.hp, (unsigned)sl.hp * sizeof(float2), &hbar);
+    }
+  }
+  cluster_sync_relaxed();  // every CTA of the cluster has started before its shared memory is written
+  // input: sample l of the column transform is row l - offy of the Ny row spectra (forward) or
+  // row l of the Py rows (adjoint); rows outside are zero.  This CTA covers the pairs
+  // (l0, l0 + 1), l0 even, of its quarter and writes them into all four columns' buffers.
+  const int np = Py / 2, pb = q * np / 4, pe = (q + 1) * np / 4;
+  const int nin = adj ? Py : Ny, l_in = adj ? 0 : offy;
+  for (int p = pb + t; p < pe; p += kMrT) {
+    float4 lo[2], hi[2];  // rows l0, l0 + 1: columns (0, 1) in lo, (2, 3) in hi
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int r = 2 * p + u - l_in;
+      lo[u] = hi[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((unsigned)r < (unsigned)nin && DOE_IN((size_t)r * Px + kc0 + 3, sl.n_tbuf)) {
+        const float4* src = reinterpret_cast<const float4*>(sl.tbuf + (size_t)r * Px + kc0);
+        lo[u] = __ldcs(src);
+        hi[u] = __ldcs(src + 1);
+      }
+    }
+    if (DOE_IN(p, Py / 2)) {
+      reinterpret_cast<float4*>(cl.map_shared_rank(xa, 0))[p] = make_float4(lo[0].x, lo[0].y, lo[1].x, lo[1].y);
+      reinterpret_cast<float4*>(cl.map_shared_rank(xa, 1))[p] = make_float4(lo[0].z, lo[0].w, lo[1].z, lo[1].w);
+      reinterpret_cast<float4*>(cl.map_shared_rank(xa, 2))[p] = make_float4(hi[0].x, hi[0].y, hi[1].x, hi[1].y);
+      reinterpret_cast<float4*>(cl.map_shared_rank(xa, 3))[p] = make_float4(hi[0].z, hi[0].w, hi[1].z, hi[1].w);
+    }
+  }
+  cl.sync();  // every column's input is in place
+  float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt, true), false, t, true);
+  float2* z = y == xa ? xb : xa;
+  const bool hok = !hcopy || mbar_wait(&hbar, 0);
+  if (!hok && t == 0) raise_fault(FAULT_WAIT_TIMEOUT);
+  for (int l = t; l < Py; l += kMrT) {
+    const int b = abs_signed(l, Py);
+    float2 hv = make_float2(0.f, 0.f);
+    if (hcopy && hok && b <= sl.kmax_y && DOE_IN(b, sl.hp)) hv = hs[b];
+    if (adj) hv.y = -hv.y;
+    y[l] = cmul(y[l], hv);
+  }
+  __syncthreads();
+  y = mr_fft<CMP, true>(y, z, bt, mr_tws_of<false>(sm_mr, bt, true), true, t, true);
+  cl.sync();  // every column's result is in its CTA's buffer y (the same offset in every CTA)
+  // output: forward, all Py rows l to buf; adjoint, the DOE rows r = l - offy < Ny back to tbuf
+  const int nout = adj ? Ny : Py, l_out = adj ? offy : 0;
+  float2* dst0 = adj ? sl.tbuf : sl.buf;
+  [[maybe_unused]] const long long ndst = adj ? sl.n_tbuf : sl.n_buf;
+  const int op = nout / 2, ob = q * op / 4, oe = (q + 1) * op / 4;
+  for (int p = ob + t; p < oe; p += kMrT) {
+    float2 v[2][4];  // rows 2p, 2p + 1 (output numbering) of columns 0..3
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float2* ry = cl.map_shared_rank(y, c);
+      const int l = 2 * p + l_out;
+      if ((l_out & 1) == 0) {  // the pair is one 16-byte chunk of the peer's buffer
+        const float4 w = DOE_IN(l + 1, Py) ? reinterpret_cast<const float4*>(ry)[l >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[0][c] = make_float2(w.x, w.y);
+        v[1][c] = make_float2(w.z, w.w);
+      } else {
+        v[0][c] = DOE_IN(l, Py) ? ry[l] : make_float2(0.f, 0.f);
+        v[1][c] = DOE_IN(l + 1, Py) ? ry[l + 1] : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const size_t o = (size_t)(2 * p + u) * Px + kc0;
+      if (DOE_IN(o + 3, ndst)) {
+        float4* d = reinterpret_cast<float4*>(dst0 + o);
+        __stcs(d, make_float4(v[u][0].x, v[u][0].y, v[u][1].x, v[u][1].y));
+        __stcs(d + 1, make_float4(v[u][2].x, v[u][2].y, v[u][3].x, v[u][3].y));
+      }
+    }
+  }
+  cluster_sync_relaxed();  // the peers have read this CTA's buffer (their loads feed stores issued before)
+}
+
 // ---- pass C (mixed radix): output row y: IFFT, 1/(Px Py), then |E|^2 (OUT_PSF) or E.
 template <bool CMP>
 __global__ void __launch_bounds__(kMrT) mr_rows_out_kernel(const __grid_constant__ Batch bt) {

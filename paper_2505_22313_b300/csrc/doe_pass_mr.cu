@@ -22,6 +22,9 @@ template <bool CMP>
 cudaError_t prep_mr_t() {
   cudaError_t e;
   constexpr int b = 2 * kMrMax * (int)sizeof(float2);  // two buffers
+  // the cluster column pass: two buffers and the transfer-function row (at most Py / 2 + 2)
+  constexpr int b4 = (2 * kMrMax + kMrMax / 2 + 2) * (int)sizeof(float2);
+  if ((e = prep_one(mr_cols4_kernel<CMP>, b4, kMrT))) return e;
   if ((e = prep_one(mr_rows_fwd_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_cols_kernel<CMP>, b, kMrT)) ||
       (e = prep_one(mr_rows_out_kernel<CMP>, b, kMrT)) || (e = prep_one(mr_rows_adj_c_kernel<CMP>, b, kMrT)) ||
       (e = prep_one(mr_rows_adj_a_kernel<CMP>, b, kMrT)))
@@ -41,7 +44,15 @@ cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
   const size_t sm = mr_smem(bt);
   switch (which) {
     case PASS_A: mr_rows_fwd_kernel<CMP><<<dim3(bt.Ny, bt.S), kMrT, sm, st>>>(bt); break;   // DOE rows
-    case PASS_B: mr_cols_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt); break;        // Px columns
+    case PASS_B:  // Px columns: clusters of 4 adjacent columns when Px is a multiple of 4
+      if (bt.P % 4 == 0) {
+        const int py = bt.Py;
+        void* args[] = {const_cast<Batch*>(&bt)};
+        return launch_cluster((const void*)mr_cols4_kernel<CMP>, dim3(bt.P, bt.S), 4,
+                              (size_t)(2 * py + py / 2 + 2) * sizeof(float2), st, args, kMrT);
+      }
+      mr_cols_kernel<CMP><<<dim3(bt.P, bt.S), kMrT, sm, st>>>(bt);
+      break;
     case PASS_C: mr_rows_out_kernel<CMP><<<dim3(bt.Py, bt.S), kMrT, sm, st>>>(bt); break;   // Py rows
     case PASS_C_ADJ: mr_rows_adj_c_kernel<CMP><<<dim3(bt.Py, bt.S), kMrT, sm, st>>>(bt); break;
     case PASS_A_ADJ: mr_rows_adj_a_kernel<CMP><<<dim3(bt.Ny), kMrT, sm, st>>>(bt); break;

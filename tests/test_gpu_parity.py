@@ -730,9 +730,10 @@ def test_radial_design_loop_matches_oracle():
 
 
 # -------------------------------------------------------------- non-power-of-two grids
-@pytest.mark.parametrize("N,pad", [(24, 2), (90, 2), (180, 2), (360, 1), (1500, 2)])
+@pytest.mark.parametrize("N,pad", [(24, 2), (90, 2), (180, 2), (360, 1), (1500, 2), (90, 1), (150, 1)])
 def test_mixed_radix_propagate_vs_oracle(N, pad):
-    # P = 48, 180, 360, 360, 3000: radix 2, 3, 4, 5, 8 stages
+    # P = 48, 180, 360, 360, 3000: radix 2, 3, 4, 5, 8 stages; P = 90, 150 (not multiples of 4):
+    # the column pass without clusters
     dx, z, lam = 1e-6, 2e-3, 550e-9
     h = _h(N, 9500 + N)
     g = Geometry.make(N, dx, z, [lam], pad=pad)
