@@ -94,24 +94,51 @@ std::vector<int> mr_radices(long M) {
   for (; n % 3 == 0; n /= 3) ++c3;
   for (; n % 2 == 0; n /= 2) ++a;
   if (n != 1) return {};
-  if (M >= 2048) {
-    for (; c5 >= 2; c5 -= 2) r.push_back(25);
-    for (; c3 >= 2; c3 -= 2) r.push_back(9);
-    if (c5 && c3) {
-      r.push_back(15);
-      c5 = c3 = 0;
+  // the plan with n25 stages of 25, n9 of 9, n15 of 15, n16 of 16, then 5s, 3s and the powers
+  // of two as 8s (4 4 for a remainder of 4, a single 2 only for a remainder of 1)
+  auto plan = [&](int n25, int n9, int n15, int n16) {
+    std::vector<int> p = r;
+    p.insert(p.end(), n25, 25);
+    p.insert(p.end(), n9, 9);
+    p.insert(p.end(), n15, 15);
+    p.insert(p.end(), n16, 16);
+    p.insert(p.end(), c5 - 2 * n25 - n15, 5);
+    p.insert(p.end(), c3 - 2 * n9 - n15, 3);
+    for (int b = a - 4 * n16; b > 0;) {
+      const int e = (b == 4 || b == 2) ? 2 : (b >= 3 ? 3 : 1);
+      p.push_back(1 << e);
+      b -= e;
     }
-    for (; a >= 4; a -= 4) r.push_back(16);
+    return p;
+  };
+  if (M < 2048) {  // short transforms: no composite stages (their kernels keep the occupancy)
+    r = plan(0, 0, 0, 0);
+    return (int)r.size() > kMrMaxStages ? std::vector<int>{} : r;
   }
-  for (; c5 > 0; --c5) r.push_back(5);
-  for (; c3 > 0; --c3) r.push_back(3);
-  while (a > 0) {  // 8s, with 4 4 for a remainder of 4 and a single 2 only for a = 1
-    const int e = (a == 4 || a == 2) ? 2 : (a >= 3 ? 3 : 1);
-    r.push_back(1 << e);
-    a -= e;
-  }
-  if ((int)r.size() > kMrMaxStages) return {};
-  return r;
+  // composite stages (25 = 5 x 5, 9 = 3 x 3, 15 = 3 x 5, 16 = 4 x 4, split in registers) save
+  // shared-memory passes, but a stage of radix R has M / R butterflies for kMrT threads: take the
+  // plan of least estimated time, each stage costing its rounds ceil(M / R / kMrT) of R-point
+  // butterflies (about R (3 + log2 R) operations: loads, twiddles, DFT, stores) plus a barrier
+  auto cost = [&](const std::vector<int>& p) {
+    double c = 0.0;
+    for (int R : p) c += (double)((M / R + kMrT - 1) / kMrT) * R * (3.0 + std::log2((double)R)) + 30.0;
+    return c;
+  };
+  std::vector<int> best;
+  double bc = 1e300;
+  for (int n25 = 0; 2 * n25 <= c5; ++n25)
+    for (int n9 = 0; 2 * n9 <= c3; ++n9)
+      for (int n15 = 0; n15 <= c5 - 2 * n25 && n15 <= c3 - 2 * n9; ++n15)
+        for (int n16 = 0; 4 * n16 <= a; ++n16) {
+          const std::vector<int> p = plan(n25, n9, n15, n16);
+          if ((int)p.size() > kMrMaxStages) continue;
+          const double c = cost(p);
+          if (c < bc - 1e-9 || (c < bc + 1e-9 && p.size() < best.size())) {
+            bc = c;
+            best = p;
+          }
+        }
+  return best;
 }
 
 // Split of a non-power-of-two side P into Q CTAs of M = P / Q points: Q = 1 up to kMrMax

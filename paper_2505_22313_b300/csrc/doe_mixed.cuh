@@ -23,7 +23,6 @@
 
 namespace doe {
 
-constexpr int kMrT = 256;  // threads per CTA of every mixed-radix pass
 
 struct MrRadices {  // a plan's radices, by value (kernel argument)
   int r[kMrMaxStages];

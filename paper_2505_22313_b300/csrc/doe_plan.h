@@ -74,6 +74,7 @@ constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536
 constexpr int kMrMax = 8192;        // longest mixed-radix (non-power-of-two) transform, one CTA
 constexpr int kMrMaxStages = 16;    // radix stages of a mixed-radix plan
 constexpr int kMrMaxPrime = 127;    // largest prime factor taken as a direct-DFT stage
+constexpr int kMrT = 256;           // threads per CTA of every mixed-radix pass
 constexpr int kMaxRadial = 9;       // coefficients of the radial height polynomial (degree 16 in rho / R)
 constexpr int kRadialBlocks = 592;  // CTAs of the radial gradient reduction (4 per SM)
 
