@@ -214,53 +214,80 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
   }
 }
 
-// ---- pass B / B* (split): column c (stored position; true frequency mrq_freq(c)) over a cluster.
-// Forward: padded rows M n1 + n2 from the DOE rows of tbuf (rows off..off+N-1), forward
-// transform, x H, inverse, all P rows to buf.  Adjoint: all P rows of tbuf, x conj(H), rows
-// off..off+N-1 back to tbuf rows 0..N-1 (the cluster owns the column).
-template <int Q, bool CMP>
+// ---- pass B / B* (split): TC adjacent columns c0 + cc (stored positions; true frequencies
+// mrq_freq(c)) over a cluster of TC Q CTAs, rank cc Q + k1.  Forward: padded rows M n1 + n2 from
+// the DOE rows of tbuf (rows off..off+N-1), forward transform, x H, inverse, all P rows to buf.
+// Adjoint: all P rows of tbuf, x conj(H), rows off..off+N-1 back to tbuf rows 0..N-1 (the
+// cluster owns its columns).  With TC = 2 the columns' samples of a row are read and written
+// together as one 16-byte pair; the Q-point steps of each n2 are done by one CTA for both.
+template <int Q, int TC, bool CMP>
 __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ Batch bt) {
+  static_assert(TC == 1 || TC == 2, "one or two columns per cluster");
+  constexpr int CL = TC * Q;
   extern __shared__ float2 sm_mr[];
   cg::cluster_group cl = cg::this_cluster();
-  const int k1 = (int)cl.block_rank();
+  const int rank = (int)cl.block_rank(), cc = rank / Q, k1 = rank % Q;
   const Slice& sl = bt.s[blockIdx.y];
-  const int c = blockIdx.x / Q, t = threadIdx.x, N = bt.N, P = bt.P, M = bt.mr_M, off = bt.off;
+  const int c0 = (blockIdx.x / CL) * TC, c = c0 + cc, t = threadIdx.x, N = bt.N, P = bt.P, M = bt.mr_M,
+            off = bt.off;
   const bool adj = bt.mode == MODE_ADJ;
   float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
   float2* xb = xa + M;
-  float2* rem[Q];
-  mrq_map<Q>(cl, xa, rem);
-  const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
+  const int Mc = (M + CL - 1) / CL, n2a = rank * Mc, n2b = min(M, n2a + Mc);
   cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
-  for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
-    float2 v[Q];
+  {
+    float2* rem[TC][Q];
 #pragma unroll
-    for (int n1 = 0; n1 < Q; ++n1) {
-      const int r = M * n1 + n2 - (adj ? 0 : off);
-      v[n1] = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + c, sl.n_tbuf)
-                  ? __ldcs(sl.tbuf + (size_t)r * P + c) : make_float2(0.f, 0.f);
+    for (int u = 0; u < TC; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) rem[u][q] = cl.map_shared_rank(xa, u * Q + q);
+    for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
+      float2 v[TC][Q];
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) {
+        const int r = M * n1 + n2 - (adj ? 0 : off);
+        const bool in = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + c0 + TC - 1, sl.n_tbuf);
+        if constexpr (TC == 2) {
+          const float4 w = in ? __ldcs(reinterpret_cast<const float4*>(sl.tbuf + (size_t)r * P + c0))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[0][n1] = make_float2(w.x, w.y);
+          v[1][n1] = make_float2(w.z, w.w);
+        } else {
+          v[0][n1] = in ? __ldcs(sl.tbuf + (size_t)r * P + c0) : make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TC; ++u) mrq_scatter_fwd<Q>(v[u], n2, bt, rem[u]);
     }
-    mrq_scatter_fwd<Q>(v, n2, bt, rem);
   }
-  cl.sync();  // chunk k1 of the column is complete in xa
+  cl.sync();  // chunk k1 of column c is complete in xa
   float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t);
   const int kc = mrq_freq(c, Q, M);
   for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, P, adj));
   __syncthreads();
   float2* z = mr_fft<CMP, false>(y, y == xa ? xb : xa, bt, mr_tws_of<true>(sm_mr, bt), true, t);
-  float2* remz[Q];
-  mrq_map<Q>(cl, z, remz);
   cl.sync();  // every chunk is back in the row domain
-  for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
-    float2 v[Q];
-    mrq_gather_inv<Q>(v, n2, bt, remz);
+  {
+    float2* remz[TC][Q];
 #pragma unroll
-    for (int n1 = 0; n1 < Q; ++n1) {
-      const int r = M * n1 + n2;
-      if (!adj) {
-        if (DOE_IN((size_t)r * P + c, sl.n_buf)) __stcs(sl.buf + (size_t)r * P + c, v[n1]);
-      } else if ((unsigned)(r - off) < (unsigned)N && DOE_IN((size_t)(r - off) * P + c, sl.n_tbuf)) {
-        __stcs(sl.tbuf + (size_t)(r - off) * P + c, v[n1]);
+    for (int u = 0; u < TC; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) remz[u][q] = cl.map_shared_rank(z, u * Q + q);
+    for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
+      float2 v[TC][Q];
+#pragma unroll
+      for (int u = 0; u < TC; ++u) mrq_gather_inv<Q>(v[u], n2, bt, remz[u]);
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) {
+        const int r = M * n1 + n2;
+        const int ro = adj ? r - off : r;  // output row
+        if (adj ? (unsigned)ro >= (unsigned)N : false) continue;
+        float2* dst = adj ? sl.tbuf : sl.buf;
+        if (!DOE_IN((size_t)ro * P + c0 + TC - 1, adj ? sl.n_tbuf : sl.n_buf)) continue;
+        if constexpr (TC == 2)
+          __stcs(reinterpret_cast<float4*>(dst + (size_t)ro * P + c0), make_float4(v[0][n1].x, v[0][n1].y, v[1][n1].x, v[1][n1].y));
+        else
+          __stcs(dst + (size_t)ro * P + c0, v[0][n1]);
       }
     }
   }

@@ -12,10 +12,14 @@ template <int Q, bool CMP>
 cudaError_t prep_mrq_t() {
   cudaError_t e;
   constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddle copy and two buffers
-  if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, CMP>, b, kMrT)) ||
+  if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, 1, CMP>, b, kMrT)) ||
+      (e = prep_one(mrq_cols_kernel<Q, 2, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_out_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_adj_a_kernel<Q, CMP>, b, kMrT)))
     return e;
+  if constexpr (2 * Q > 8)  // two columns per cluster: 10 or 16 CTAs, a non-portable size
+    if ((e = cudaFuncSetAttribute(mrq_cols_kernel<Q, 2, CMP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)))
+      return e;
   return cudaSuccess;
 }
 template <bool CMP>
@@ -63,21 +67,24 @@ cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
 
 // split sides (bt.mr_Q > 1): cluster launches
 template <int Q, bool CMP>
-const void* mrq_fn(int which) {
+const void* mrq_fn(int which, bool two) {
   return which == PASS_A   ? (const void*)mrq_rows_fwd_kernel<Q, CMP>
-         : which == PASS_B ? (const void*)mrq_cols_kernel<Q, CMP>
+         : which == PASS_B ? (two ? (const void*)mrq_cols_kernel<Q, 2, CMP> : (const void*)mrq_cols_kernel<Q, 1, CMP>)
          : which == PASS_C ? (const void*)mrq_rows_out_kernel<Q, CMP>
          : which == PASS_C_ADJ ? (const void*)mrq_rows_adj_c_kernel<Q, CMP>
                                : (const void*)mrq_rows_adj_a_kernel<Q, CMP>;
 }
 template <int Q>
 cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
-  const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which) : mrq_fn<Q, false>(which);
+  // the column pass takes two adjacent columns per cluster (16-byte row pairs) for transforms
+  // with composite stages, whose registers already hold the CTAs to two per SM, while two CTAs
+  // of its shared memory still fit on an SM
+  const size_t smem = (size_t)3 * bt.mr_M * sizeof(float2);  // twiddle copy and two buffers
+  const bool two = which == PASS_B && bt.mr_cmp && 2 * smem <= (size_t)220 * 1024;
+  const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which, two) : mrq_fn<Q, false>(which, two);
   const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.N : bt.P;
   void* args[] = {const_cast<Batch*>(&bt)};
-  // a shared copy of the per-stage twiddle table and two buffers
-  return launch_cluster(fn, dim3(lines * Q, which == PASS_A_ADJ ? 1 : bt.S), Q, (size_t)3 * bt.mr_M * sizeof(float2),
-                        st, args, kMrT);
+  return launch_cluster(fn, dim3(lines * Q, which == PASS_A_ADJ ? 1 : bt.S), two ? 2 * Q : Q, smem, st, args, kMrT);
 }
 
 }  // namespace

@@ -84,6 +84,7 @@ CASES = [
     ("circular", 256, 2, 2e-6, 20e-3, [550e-9], dict(bandlimit="circular"), True),
     ("mixed_radix", 180, 2, 1e-6, 2e-3, [450e-9, 600e-9], {}, True),
     ("mixed_radix_split", 4500, 2, 1e-6, 5e-3, [550e-9], {}, True),
+    ("mixed_radix_split_pairs", 9000, 2, 1e-6, 5e-3, [550e-9], {}, True),  # 18000 = 8 x 2250: two columns per 16-CTA cluster
     ("split_32768", 16384, 2, 1e-6, 50e-3, [550e-9], {}, True),
     ("split_65536", 32768, 2, 1e-6, 100e-3, [550e-9], {}, False),
     ("rect_mixed", 160, 2, 1e-6, 2e-3, [450e-9, 600e-9], dict(Ny=96), True),
