@@ -275,9 +275,13 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
     for (int cc = 0; cc < TC; ++cc) {
       dft<Q, false>(col[0][cc]);
       dft<Q, false>(col[1][cc]);
+    }
 #pragma unroll
-      for (int sp = 0; sp < Q; ++sp) {
-        const float2 a = cmul(col[0][cc][sp], wbig<P>(y2 * sp)), d = cmul(col[1][cc][sp], wbig<P>((y2 + 1) * sp));
+    for (int sp = 0; sp < Q; ++sp) {
+      const float2 w0 = wbig<P>(y2 * sp), w1 = wbig<P>((y2 + 1) * sp);  // shared by the TC columns
+#pragma unroll
+      for (int cc = 0; cc < TC; ++cc) {
+        const float2 a = cmul(col[0][cc][sp], w0), d = cmul(col[1][cc][sp], w1);
         if (DOE_IN(swz(y2 >> 1), L / 2))
           reinterpret_cast<float4*>(rsm(cc * Q + sp))[swz(y2 >> 1)] = make_float4(a.x, a.y, d.x, d.y);
       }
@@ -339,14 +343,18 @@ __global__ void __launch_bounds__(kBigL / 32, min_blocks(kBigL)) pass_b_big_kern
     const int y2l = 2 * t + it * 2 * T, y2 = rank * SH + y2l;
     float2 out[2][TC][Q];
 #pragma unroll
-    for (int cc = 0; cc < TC; ++cc) {
+    for (int sp = 0; sp < Q; ++sp) {
+      const float2 w0 = wbig<P>(sp * y2), w1 = wbig<P>(sp * (y2 + 1));  // shared by the TC columns
 #pragma unroll
-      for (int sp = 0; sp < Q; ++sp) {
+      for (int cc = 0; cc < TC; ++cc) {
         const int ch = ((cc * Q + sp) * SH + y2l) >> 1;
         const float4 q4 = DOE_IN(ch, L / 2) ? r4[ch] : make_float4(0.f, 0.f, 0.f, 0.f);
-        out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), wbig<P>(sp * y2));
-        out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), wbig<P>(sp * (y2 + 1)));
+        out[0][cc][sp] = cmulc(make_float2(q4.x, q4.y), w0);
+        out[1][cc][sp] = cmulc(make_float2(q4.z, q4.w), w1);
       }
+    }
+#pragma unroll
+    for (int cc = 0; cc < TC; ++cc) {
       dft<Q, true>(out[0][cc]);
       dft<Q, true>(out[1][cc]);
     }
