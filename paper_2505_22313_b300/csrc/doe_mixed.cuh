@@ -9,15 +9,19 @@
 // multiplies input r by w_P^(r k P/(Ns R)) (k = j mod Ns), takes the R-point DFT and writes
 // output r to y[(j - k) R + k + r Ns].  The stage twiddles w_(Ns R)^(r k) come from a per-stage
 // table laid out [stage][r][k] (mr_stage_twiddle_kernel; M - 1 entries in all, since the stages'
-// (R - 1) Ns sum to M - 1), read through L1: the lanes of a warp, which hold consecutive k,
-// read consecutive entries (one 256-byte run per warp and radix term).  The composite stages'
-// inner twiddles w_R^m are compile-time constants; the direct-DFT stages of larger primes read
-// the table of all P powers w_P^m from global memory.  Both tables are built per call in FP64.
+// (R - 1) Ns sum to M - 1): the lanes of a warp, which hold consecutive k, read consecutive
+// entries (one 256-byte run per warp and radix term), through L1 in the one-CTA passes and from
+// a shared copy in the cluster-split passes of doe_mixed_big.cuh.  The composite stages' inner
+// twiddles w_R^m are compile-time constants; the direct-DFT stages of larger primes read the
+// table of all P powers w_P^m from global memory.  Both tables are built per call in FP64.
 // Stages go out of place between two shared buffers (one barrier per stage), one butterfly in
 // registers at a time.
 //
-// Buffers (natural row-major layout, rows of P samples): tbuf holds the row spectra of the N
-// DOE rows (forward) or of all P rows (adjoint), buf the field after the column pass.
+// Buffers (natural row-major layout, rows of Px samples): tbuf holds the row spectra of the Ny
+// DOE rows (forward) or of all Py rows (adjoint), buf the field after the column pass.  Square
+// grids have Px = Py; rectangles use a row plan (Px) and a column plan (Py).  The column pass
+// runs on clusters of 4 CTAs when Px is a multiple of 4 (mr_cols4_kernel), else one CTA per
+// column (mr_cols_kernel).
 #pragma once
 #include "doe_kernels.cuh"
 
