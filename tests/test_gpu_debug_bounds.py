@@ -82,6 +82,8 @@ CASES = [
     ("tilt_sphere_upsampled", 256, 2, 1e-6, 5e-3, [500e-9], dict(upsample=2, theta_x=0.01, src_d=-0.05), True),
     ("lanczos", 256, 2, 1e-6, 5e-3, [520e-9], dict(upsample=4, lanczos=True), True),
     ("circular", 256, 2, 2e-6, 20e-3, [550e-9], dict(bandlimit="circular"), True),
+    ("kmax0", 128, 2, 1e-6, 0.1, [550e-9], {}, True),  # one stored column pair, a 2-entry H row
+    ("kmax0_mixed", 90, 2, 1e-6, 0.1, [550e-9], {}, True),
     ("mixed_radix", 180, 2, 1e-6, 2e-3, [450e-9, 600e-9], {}, True),
     ("mixed_radix_split", 4500, 2, 1e-6, 5e-3, [550e-9], {}, True),
     ("mixed_radix_split_pairs", 9000, 2, 1e-6, 5e-3, [550e-9], {}, True),  # 18000 = 8 x 2250: two columns per 16-CTA cluster

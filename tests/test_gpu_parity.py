@@ -988,3 +988,33 @@ def test_circular_band_split_grid_rows_vs_oracle():
     got = I[0, torch.from_numpy(rows).cuda(), :].cpu().numpy()
     ref = oracle.psf_rows(h, dx, z, lam, rows, bandlimit="circular")
     assert rel_l2(got, ref) < TOL_PSF, rel_l2(got, ref)
+
+
+# -------------------------------------------------------------- degenerate bands
+@pytest.mark.parametrize("N,dx,z,lams,regime", [
+    (128, 1e-6, 0.1, [550e-9], "kmax0"),            # only the zero-frequency row and column pass
+    (128, 1e-6, 0.05, [550e-9], "kmax1"),
+    (90, 1e-6, 0.1, [550e-9], "kmax0"),             # mixed radix, P = 180
+    (64, 0.25e-6, 5e-6, [400e-9, 700e-9], "evanescent"),  # pitch below lambda / 2: the evanescent cut binds
+])
+def test_degenerate_bands_vs_oracle(N, dx, z, lams, regime):
+    P = 2 * N
+    for lam in lams:
+        k = oracle.kmax(lam, dx, P, z)
+        if regime == "kmax0":
+            assert k == 0
+        elif regime == "kmax1":
+            assert k == 1
+        else:  # the evanescent disc cuts the corners of the square band
+            assert oracle.m_ev(lam, dx, P) <= 2 * k * k
+    h = _h(N, 9300 + N)
+    T = inputs.spot_target(P, N, len(lams), 9400 + N)
+    g = Geometry.make(N, dx, z, lams)
+    ht = torch.from_numpy(h).cuda()
+    I = api.psf(ht, g).cpu().numpy()
+    assert np.isfinite(I).all()
+    assert rel_l2(I, oracle.psf(h, dx, z, lams)) < TOL_PSF, rel_l2(I, oracle.psf(h, dx, z, lams))
+    gr, loss = api.grad(ht, g, torch.from_numpy(T).cuda())
+    gref, lref = oracle.grad(h, dx, z, lams, T)
+    assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
+    assert abs(loss.item() - lref) <= 1e-5 * lref
