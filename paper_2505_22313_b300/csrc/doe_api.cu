@@ -229,13 +229,24 @@ LanczosTab lanczos_table(int N, int u) {
 
 bool rect(const doe_geom* g) { return g->nx != g->ny; }
 
-// Rectangular grids (nx != ny) run on the one-CTA mixed-radix passes, which take any supported
-// length up to kMrMax on either axis (powers of two included).
+// Split of one side of a rectangular grid: one CTA per transform up to kMrMax (any length with a
+// plan, powers of two included), else the first of Q = 8, 5, 4, 3, 2 that divides it into
+// sub-transforms of at most kMrMax points with a plan.  {0, 0} when the side is unsupported.
+MrSplit axis_split(long P) {
+  if (P < 2 || (P & 1)) return {0, 0};
+  if (P <= kMrMax) return mr_radices(P).empty() ? MrSplit{0, 0} : MrSplit{1, (int)P};
+  for (int q : {8, 5, 4, 3, 2})
+    if (P % q == 0 && P / q <= kMrMax && !mr_radices(P / q).empty()) return {q, (int)(P / q)};
+  return {0, 0};
+}
+
+// Rectangular grids (nx != ny) run on the mixed-radix passes with a row plan and a column plan:
+// each side one CTA per transform up to kMrMax (powers of two included), or split over a
+// cluster (axis_split) above.
 bool rect_supported(const doe_geom* g) {
   const long px = (long)g->pad * g->nx, py = (long)g->pad * g->ny;
-  return px <= kMrMax && py <= kMrMax && !mr_radices(px).empty() && !mr_radices(py).empty() &&
-         upsample_log2(g) == 0 && !(g->flags & DOE_BANDLIMIT_CIRCULAR) && g->theta_x == 0.0 && g->theta_y == 0.0 &&
-         g->src_d == 0.0;
+  return axis_split(px).Q > 0 && axis_split(py).Q > 0 && upsample_log2(g) == 0 &&
+         !(g->flags & DOE_BANDLIMIT_CIRCULAR) && g->theta_x == 0.0 && g->theta_y == 0.0 && g->src_d == 0.0;
 }
 
 int check_geom(const doe_geom* g) {
@@ -250,7 +261,7 @@ int check_geom(const doe_geom* g) {
     if (!(g->n_index[j] >= 1.0) || !std::isfinite(g->n_index[j])) return DOE_EINVAL;
   }
   if (rect(g) && !rect_supported(g)) return DOE_EUNSUPPORTED;
-  if ((long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;
+  if ((long)g->pad * g->nx > (1L << kBigLog) || (long)g->pad * g->ny > (1L << kBigLog)) return DOE_EUNSUPPORTED;
   if (!rect(g) && !is_pow2((long)g->pad * g->nx) && mr_split((long)g->pad * g->nx).Q == 0) return DOE_EUNSUPPORTED;
   const int u = upsample_log2(g);
   if ((g->nx >> u) < 4 || (g->ny >> u) < 4 || (g->nx & ((1 << u) - 1)) || (g->ny & ((1 << u) - 1))) return DOE_EINVAL;
@@ -291,7 +302,7 @@ void fill_slice(Slice& s, const doe_geom* g, int j) {
   }
   s.wp = (s.w + kTile - 1) / kTile * kTile;
   s.hp = (int)((kmax + 2) & ~1L);  // kmax + 1 rounded up to even
-  if (is_pow2(P) && P > (1L << kMaxLog)) {  // split grids: rows grouped by residue mod Q = P / 8192
+  if (is_pow2(P) && P > (1L << kMaxLog) && !rect(g)) {  // split grids: rows grouped by residue mod Q = P / 8192
     s.hqs = ilog2(P / 8192);
     s.hq = (int)(((kmax >> s.hqs) + 2) & ~1L);  // (kmax >> hqs) + 1 rounded up to even: 16-byte class runs
     s.hp = s.hq << s.hqs;
@@ -339,6 +350,7 @@ struct Layout {
   size_t mrtwP = 0;          // mixed radix split over a cluster: the [P] twiddle table
   size_t mrtw_y = 0;         // rectangular grids: the [Py] twiddle table of the column transform
   size_t mrtws = 0, mrtws_y = 0;  // per-stage (lane-contiguous) twiddles of the row / column plans
+  size_t mrtwP_y = 0;        // rectangular grids with a split column transform: the [Py] table
   long tbuf_rows = 0;        // rows of the column-tiled buffers (Ny forward, Py with the adjoint)
 };
 
@@ -383,14 +395,23 @@ Layout make_layout(const std::vector<Slice>& sl, int op, int n_req, const doe_ge
     }
   }
   if (Py != P) {  // rectangular grid: twiddle tables of the row and of the column transform
+    const MrSplit sx = axis_split(P), sy = axis_split(Py);
     L.mrtw = off;
-    off = align256(off + (size_t)P * sizeof(float2));
+    off = align256(off + (size_t)sx.M * sizeof(float2));
     L.mrtw_y = off;
-    off = align256(off + (size_t)Py * sizeof(float2));
+    off = align256(off + (size_t)sy.M * sizeof(float2));
     L.mrtws = off;
-    off = align256(off + (size_t)P * sizeof(float2));
+    off = align256(off + (size_t)sx.M * sizeof(float2));
     L.mrtws_y = off;
-    off = align256(off + (size_t)Py * sizeof(float2));
+    off = align256(off + (size_t)sy.M * sizeof(float2));
+    if (sx.Q > 1) {
+      L.mrtwP = off;
+      off = align256(off + (size_t)P * sizeof(float2));
+    }
+    if (sy.Q > 1) {
+      L.mrtwP_y = off;
+      off = align256(off + (size_t)Py * sizeof(float2));
+    }
   } else if (!is_pow2(P)) {
     const MrSplit sp = mr_split(P);
     L.mrtw = off;
@@ -482,16 +503,21 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, const doe_geom* g0, voi
   bt.total_tiles = tiles;
   bt.max_kmax = kmx;
   if (bt.Py != bt.P) {  // rectangular grid: one-CTA mixed-radix passes with a row and a column plan
+    const MrSplit sx = axis_split(bt.P), sy = axis_split(bt.Py);
     bt.mr = 1;
-    bt.mr_Q = 1;
-    bt.mr_M = bt.P;
-    bt.mr_My = bt.Py;
-    const bool cx = set_plan(bt.P, bt.mr_nst, bt.mr_radix), cy = set_plan(bt.Py, bt.mr_nst_y, bt.mr_radix_y);
+    bt.mr_Q = sx.Q;
+    bt.mr_M = sx.M;
+    bt.mr_Qy = sy.Q;
+    bt.mr_My = sy.M;
+    bt.qf = sx.Q;  // split rows write one loss partial per CTA
+    const bool cx = set_plan(sx.M, bt.mr_nst, bt.mr_radix), cy = set_plan(sy.M, bt.mr_nst_y, bt.mr_radix_y);
     bt.mr_cmp = (cx || cy) ? 1 : 0;
     bt.mr_tw = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw);
     bt.mr_tw_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtw_y);
     bt.mr_tws = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtws);
     bt.mr_tws_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtws_y);
+    if (sx.Q > 1) bt.mr_twP = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP);
+    if (sy.Q > 1) bt.mr_twP_y = reinterpret_cast<const float2*>(static_cast<char*>(ws) + lay.mrtwP_y);
   } else if (!is_pow2(bt.P)) {
     const MrSplit sp = mr_split(bt.P);
     bt.mr = 1;
@@ -508,6 +534,8 @@ void init_batch(Batch& bt, const std::vector<Slice>& sl, const doe_geom* g0, voi
     for (int s = 0; s < bt.mr_nst; ++s) bt.mr_radix_y[s] = bt.mr_radix[s];
     bt.mr_tw_y = bt.mr_tw;
     bt.mr_tws_y = bt.mr_tws;
+    bt.mr_Qy = bt.mr_Q;
+    bt.mr_twP_y = bt.mr_twP;
   }
 }
 

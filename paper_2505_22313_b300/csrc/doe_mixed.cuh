@@ -28,6 +28,10 @@
 namespace doe {
 
 
+// frequency index of the stored position p = k1 M + k2 of a spectrum split over Q sub-transforms
+// of M points (stored in chunk order)
+__device__ __forceinline__ int mrq_freq(int p, int Q, int M) { return p / M + Q * (p % M); }
+
 struct MrRadices {  // a plan's radices, by value (kernel argument)
   int r[kMrMaxStages];
 };
@@ -415,7 +419,8 @@ __global__ void __launch_bounds__(kMrT) mr_cols_kernel(const __grid_constant__ B
   __syncthreads();
   float2* y = mr_fft<CMP, true>(xa, xb, bt, mr_tws_of<false>(sm_mr, bt, true), false, t, true);
   float2* z = y == xa ? xb : xa;
-  for (int l = t; l < Py; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kc, l, Px, Py, adj));
+  const int kf = bt.mr_Q > 1 ? mrq_freq(kc, bt.mr_Q, bt.mr_M) : kc;  // rows split: stored in chunk order
+  for (int l = t; l < Py; l += kMrT) y[l] = cmul(y[l], mr_transfer(sl, kf, l, Px, Py, adj));
   __syncthreads();
   y = mr_fft<CMP, true>(y, z, bt, mr_tws_of<false>(sm_mr, bt, true), true, t, true);
   if (!adj) {
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(kMrT) mr_cols4_kernel(const __grid_constant__ 
   float2* xa = sm_mr;
   float2* xb = xa + Py;
   float2* hs = xb + Py;
-  const int ak = abs_signed(kc, Px);
+  const int ak = abs_signed(bt.mr_Q > 1 ? mrq_freq(kc, bt.mr_Q, bt.mr_M) : kc, Px);  // rows split: chunk order
   const bool hcopy = ak <= sl.kmax && sl.hp <= Py / 2 + 2 && DOE_IN((size_t)ak * sl.hp + sl.hp - 1, sl.n_htab);
   if (t == 0) {
     mbar_init(&hbar, 1);

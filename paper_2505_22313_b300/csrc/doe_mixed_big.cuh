@@ -16,12 +16,19 @@
 
 namespace doe {
 
-// frequency index of the stored position p = k1 M + k2 of a split spectrum
-__device__ __forceinline__ int mrq_freq(int p, int Q, int M) { return p / M + Q * (p % M); }
+// One axis of a split transform: P = Q M points, sub-transforms of M, the [P] table w_P^m.
+// Rows use the row axis (bt.P, bt.mr_M, bt.mr_twP), columns the column axis (bt.Py, bt.mr_My,
+// bt.mr_twP_y); the two coincide on square grids.
+struct MrqAxis {
+  int P, M;
+  const float2* twP;
+};
+__device__ __forceinline__ MrqAxis mrq_rows_axis(const Batch& bt) { return {bt.P, bt.mr_M, bt.mr_twP}; }
+__device__ __forceinline__ MrqAxis mrq_cols_axis(const Batch& bt) { return {bt.Py, bt.mr_My, bt.mr_twP_y}; }
 
 // w_P^(n2 k1) (n2 k1 < P), conjugated for the inverse
-__device__ __forceinline__ float2 mrq_tw(const Batch& bt, int n2, int k1, bool inv) {
-  float2 w = DOE_IN(n2 * k1, bt.P) ? __ldg(bt.mr_twP + n2 * k1) : make_float2(0.f, 0.f);
+__device__ __forceinline__ float2 mrq_tw(const MrqAxis& ax, int n2, int k1, bool inv) {
+  float2 w = DOE_IN(n2 * k1, ax.P) ? __ldg(ax.twP + n2 * k1) : make_float2(0.f, 0.f);
   if (inv) w.y = -w.y;
   return w;
 }
@@ -29,18 +36,18 @@ __device__ __forceinline__ float2 mrq_tw(const Batch& bt, int n2, int k1, bool i
 // Forward Q-point step for n2: v[n1] = x[M n1 + n2] -> DFT over n1, times w_P^(n2 k1), written
 // to CTA k1's buffer at n2.
 template <int Q>
-__device__ __forceinline__ void mrq_scatter_fwd(float2 (&v)[Q], int n2, const Batch& bt, float2* const (&dst)[Q]) {
+__device__ __forceinline__ void mrq_scatter_fwd(float2 (&v)[Q], int n2, const MrqAxis& ax, float2* const (&dst)[Q]) {
   mr_dft<Q>(v, false);
 #pragma unroll
   for (int k1 = 0; k1 < Q; ++k1)
-    if (DOE_IN(n2, bt.mr_M)) dst[k1][n2] = cmul(v[k1], mrq_tw(bt, n2, k1, false));
+    if (DOE_IN(n2, ax.M)) dst[k1][n2] = cmul(v[k1], mrq_tw(ax, n2, k1, false));
 }
 // Inverse Q-point step for n2: z_k1[n2] from CTA k1, times w_P^(-n2 k1), IDFT over k1:
 // v[n1] = x[M n1 + n2] (unnormalised).
 template <int Q>
-__device__ __forceinline__ void mrq_gather_inv(float2 (&v)[Q], int n2, const Batch& bt, float2* const (&src)[Q]) {
+__device__ __forceinline__ void mrq_gather_inv(float2 (&v)[Q], int n2, const MrqAxis& ax, float2* const (&src)[Q]) {
 #pragma unroll
-  for (int k1 = 0; k1 < Q; ++k1) v[k1] = DOE_IN(n2, bt.mr_M) ? cmul(src[k1][n2], mrq_tw(bt, n2, k1, true)) : make_float2(0.f, 0.f);
+  for (int k1 = 0; k1 < Q; ++k1) v[k1] = DOE_IN(n2, ax.M) ? cmul(src[k1][n2], mrq_tw(ax, n2, k1, true)) : make_float2(0.f, 0.f);
   mr_dft<Q>(v, true);
 }
 
@@ -63,7 +70,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
   float2* xb = xa + M;
   float2* rem[Q];
   mrq_map<Q>(cl, xa, rem);
-  const IncRow ir = incident_row(sl, i - N / 2);
+  const IncRow ir = incident_row(sl, i - bt.Ny / 2);
   const int Mc = (M + Q - 1) / Q, n2a = k1 * Mc, n2b = min(M, n2a + Mc);
   cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
   for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
@@ -73,7 +80,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_fwd_kernel(const __grid_constan
       const int x = M * n1 + n2 - off;
       v[n1] = (unsigned)x < (unsigned)N ? mr_doe_field(sl, i, x, N, ir) : make_float2(0.f, 0.f);
     }
-    mrq_scatter_fwd<Q>(v, n2, bt, rem);
+    mrq_scatter_fwd<Q>(v, n2, mrq_rows_axis(bt), rem);
   }
   cl.sync();  // chunk k1 is complete in xa (and the twiddle table visible)
   const float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t);
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_out_kernel(const __grid_constan
   const float s = bt.inv_p2;
   for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
     float2 v[Q];
-    mrq_gather_inv<Q>(v, n2, bt, rem);
+    mrq_gather_inv<Q>(v, n2, mrq_rows_axis(bt), rem);
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const float2 e = cscale(v[n1], s);
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
   float acc = 0.f;
   for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
     float2 v[Q];
-    mrq_gather_inv<Q>(v, n2, bt, remz);
+    mrq_gather_inv<Q>(v, n2, mrq_rows_axis(bt), remz);
 #pragma unroll
     for (int n1 = 0; n1 < Q; ++n1) {
       const float2 e = cscale(v[n1], s);
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_c_kernel(const __grid_const
       }
       v[n1] = cscale(e, g);
     }
-    mrq_scatter_fwd<Q>(v, n2, bt, remw);
+    mrq_scatter_fwd<Q>(v, n2, mrq_rows_axis(bt), remw);
   }
   cl.sync();  // w holds chunk k1 of the forward step in every CTA; reads of z are done
   const float2* y = mr_fft<CMP, false>(w, z, bt, mr_tws_of<true>(sm_mr, bt), false, t);
@@ -194,11 +201,11 @@ __global__ void __launch_bounds__(kMrT) mrq_rows_adj_a_kernel(const __grid_const
     float2* rem[Q];
     mrq_map<Q>(cl, z, rem);
     cl.sync();  // every chunk of this slice is transformed
-    const IncRow ir = incident_row(sl, i - N / 2);
+    const IncRow ir = incident_row(sl, i - bt.Ny / 2);
     const float k2 = -2.f * sl.kp_hi;
     for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
       float2 v[Q];
-      mrq_gather_inv<Q>(v, n2, bt, rem);
+      mrq_gather_inv<Q>(v, n2, mrq_rows_axis(bt), rem);
 #pragma unroll
       for (int n1 = 0; n1 < Q; ++n1) {
         const int x = M * n1 + n2 - off;
@@ -228,10 +235,11 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cc = rank / Q, k1 = rank % Q;
   const Slice& sl = bt.s[blockIdx.y];
-  const int c0 = (blockIdx.x / CL) * TC, c = c0 + cc, t = threadIdx.x, N = bt.N, P = bt.P, M = bt.mr_M,
-            off = bt.off;
+  // the column axis: Py = Q M rows (Ny DOE rows at offset offy), rows of Px = bt.P samples
+  const int c0 = (blockIdx.x / CL) * TC, c = c0 + cc, t = threadIdx.x, N = bt.Ny, Px = bt.P, P = bt.Py, M = bt.mr_My,
+            off = bt.offy;
   const bool adj = bt.mode == MODE_ADJ;
-  float2* xa = mr_smem_setup<true>(sm_mr, bt, t);
+  float2* xa = mr_smem_setup<true>(sm_mr, bt, t, true);
   float2* xb = xa + M;
   const int Mc = (M + CL - 1) / CL, n2a = rank * Mc, n2b = min(M, n2a + Mc);
   cluster_sync_relaxed();  // every CTA of the cluster runs before its shared memory is written
@@ -246,26 +254,27 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
 #pragma unroll
       for (int n1 = 0; n1 < Q; ++n1) {
         const int r = M * n1 + n2 - (adj ? 0 : off);
-        const bool in = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * P + c0 + TC - 1, sl.n_tbuf);
+        const bool in = (unsigned)r < (unsigned)(adj ? P : N) && DOE_IN((size_t)r * Px + c0 + TC - 1, sl.n_tbuf);
         if constexpr (TC == 2) {
-          const float4 w = in ? __ldcs(reinterpret_cast<const float4*>(sl.tbuf + (size_t)r * P + c0))
+          const float4 w = in ? __ldcs(reinterpret_cast<const float4*>(sl.tbuf + (size_t)r * Px + c0))
                               : make_float4(0.f, 0.f, 0.f, 0.f);
           v[0][n1] = make_float2(w.x, w.y);
           v[1][n1] = make_float2(w.z, w.w);
         } else {
-          v[0][n1] = in ? __ldcs(sl.tbuf + (size_t)r * P + c0) : make_float2(0.f, 0.f);
+          v[0][n1] = in ? __ldcs(sl.tbuf + (size_t)r * Px + c0) : make_float2(0.f, 0.f);
         }
       }
 #pragma unroll
-      for (int u = 0; u < TC; ++u) mrq_scatter_fwd<Q>(v[u], n2, bt, rem[u]);
+      for (int u = 0; u < TC; ++u) mrq_scatter_fwd<Q>(v[u], n2, mrq_cols_axis(bt), rem[u]);
     }
   }
   cl.sync();  // chunk k1 of column c is complete in xa
-  float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t);
-  const int kc = mrq_freq(c, Q, M);
-  for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, P, P, adj));
+  float2* y = mr_fft<CMP, false>(xa, xb, bt, mr_tws_of<true>(sm_mr, bt), false, t, true);
+  // the column's frequency: rows are stored in chunk order when the row transform is split
+  const int kc = bt.mr_Q > 1 ? mrq_freq(c, bt.mr_Q, bt.mr_M) : c;
+  for (int k2 = t; k2 < M; k2 += kMrT) y[k2] = cmul(y[k2], mr_transfer(sl, kc, k1 + Q * k2, Px, P, adj));
   __syncthreads();
-  float2* z = mr_fft<CMP, false>(y, y == xa ? xb : xa, bt, mr_tws_of<true>(sm_mr, bt), true, t);
+  float2* z = mr_fft<CMP, false>(y, y == xa ? xb : xa, bt, mr_tws_of<true>(sm_mr, bt), true, t, true);
   cl.sync();  // every chunk is back in the row domain
   {
     float2* remz[TC][Q];
@@ -276,18 +285,18 @@ __global__ void __launch_bounds__(kMrT) mrq_cols_kernel(const __grid_constant__ 
     for (int n2 = n2a + t; n2 < n2b; n2 += kMrT) {
       float2 v[TC][Q];
 #pragma unroll
-      for (int u = 0; u < TC; ++u) mrq_gather_inv<Q>(v[u], n2, bt, remz[u]);
+      for (int u = 0; u < TC; ++u) mrq_gather_inv<Q>(v[u], n2, mrq_cols_axis(bt), remz[u]);
 #pragma unroll
       for (int n1 = 0; n1 < Q; ++n1) {
         const int r = M * n1 + n2;
         const int ro = adj ? r - off : r;  // output row
         if (adj ? (unsigned)ro >= (unsigned)N : false) continue;
         float2* dst = adj ? sl.tbuf : sl.buf;
-        if (!DOE_IN((size_t)ro * P + c0 + TC - 1, adj ? sl.n_tbuf : sl.n_buf)) continue;
+        if (!DOE_IN((size_t)ro * Px + c0 + TC - 1, adj ? sl.n_tbuf : sl.n_buf)) continue;
         if constexpr (TC == 2)
-          __stcs(reinterpret_cast<float4*>(dst + (size_t)ro * P + c0), make_float4(v[0][n1].x, v[0][n1].y, v[1][n1].x, v[1][n1].y));
+          __stcs(reinterpret_cast<float4*>(dst + (size_t)ro * Px + c0), make_float4(v[0][n1].x, v[0][n1].y, v[1][n1].x, v[1][n1].y));
         else
-          __stcs(dst + (size_t)ro * P + c0, v[0][n1]);
+          __stcs(dst + (size_t)ro * Px + c0, v[0][n1]);
       }
     }
   }

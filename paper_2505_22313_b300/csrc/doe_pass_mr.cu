@@ -39,13 +39,13 @@ cudaError_t prep_mr_t() {
   return cudaSuccess;
 }
 
-// shared memory: two transform buffers, of the longer axis
-size_t mr_smem(const Batch& bt) { return (size_t)2 * (bt.P > bt.Py ? bt.P : bt.Py) * sizeof(float2); }
+// shared memory of a one-CTA pass: two transform buffers of its axis (rows: Px; columns: Py)
+size_t mr_smem(const Batch& bt, int which) { return (size_t)2 * (which == PASS_B ? bt.Py : bt.P) * sizeof(float2); }
 
 // one CTA per row / column (P <= kMrMax)
 template <bool CMP>
 cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
-  const size_t sm = mr_smem(bt);
+  const size_t sm = mr_smem(bt, which);
   switch (which) {
     case PASS_A: mr_rows_fwd_kernel<CMP><<<dim3(bt.Ny, bt.S), kMrT, sm, st>>>(bt); break;   // DOE rows
     case PASS_B:  // Px columns: clusters of 4 adjacent columns when Px is a multiple of 4
@@ -79,10 +79,12 @@ cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
   // the column pass takes two adjacent columns per cluster (16-byte row pairs) for transforms
   // with composite stages, whose registers already hold the CTAs to two per SM, while two CTAs
   // of its shared memory still fit on an SM
-  const size_t smem = (size_t)3 * bt.mr_M * sizeof(float2);  // twiddle copy and two buffers
+  const int M = which == PASS_B ? bt.mr_My : bt.mr_M;  // the column pass splits the column axis
+  const size_t smem = (size_t)3 * M * sizeof(float2);   // twiddle copy and two buffers
   const bool two = which == PASS_B && bt.mr_cmp && 2 * smem <= (size_t)220 * 1024;
   const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which, two) : mrq_fn<Q, false>(which, two);
-  const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.N : bt.P;
+  // DOE rows (A, A*), output rows (C, C'), or columns (B)
+  const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.Ny : which == PASS_B ? bt.P : bt.Py;
   void* args[] = {const_cast<Batch*>(&bt)};
   return launch_cluster(fn, dim3(lines * Q, which == PASS_A_ADJ ? 1 : bt.S), two ? 2 * Q : Q, smem, st, args, kMrT);
 }
@@ -95,7 +97,8 @@ cudaError_t mr_pass(int which, const Batch& bt, cudaStream_t st) {
                : which == PASS_C ? TR_PASS_C
                : which == PASS_C_ADJ ? TR_PASS_C_ADJ : TR_PASS_A_ADJ;
   Traced t(tr, st);
-  switch (bt.mr_Q) {
+  // the row passes follow the row transform's split, the column pass the column transform's
+  switch (which == PASS_B ? bt.mr_Qy : bt.mr_Q) {
     case 1: return bt.mr_cmp ? mr_one_t<true>(which, bt, st) : mr_one_t<false>(which, bt, st);
     case 2: return mrq_launch<2>(which, bt, st);
     case 3: return mrq_launch<3>(which, bt, st);
@@ -116,21 +119,24 @@ static cudaError_t stage_twiddles(const float2* tws, int M, int nst, const int* 
 }
 
 cudaError_t mr_twiddles(const Batch& bt, cudaStream_t st) {
-  {
-    Traced tr(TR_MR_TWIDDLES, st);
-    mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws, bt.mr_M, bt.mr_nst, bt.mr_radix, st);
-    if (e == cudaSuccess && bt.mr_tw_y != bt.mr_tw) {  // rectangular grid: the column transform's tables
-      mr_twiddle_kernel<<<(unsigned)((bt.mr_My + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw_y), bt.mr_My);
-      e = cudaGetLastError();
-      if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws_y, bt.mr_My, bt.mr_nst_y, bt.mr_radix_y, st);
-    }
-    if (e != cudaSuccess || bt.mr_Q == 1) return e;
-  }
   Traced tr(TR_MR_TWIDDLES, st);
-  mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_twP), bt.P);
-  return cudaGetLastError();
+  mr_twiddle_kernel<<<(unsigned)((bt.mr_M + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw), bt.mr_M);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws, bt.mr_M, bt.mr_nst, bt.mr_radix, st);
+  if (e == cudaSuccess && bt.mr_tw_y != bt.mr_tw) {  // rectangular grid: the column transform's tables
+    mr_twiddle_kernel<<<(unsigned)((bt.mr_My + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_tw_y), bt.mr_My);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = stage_twiddles(bt.mr_tws_y, bt.mr_My, bt.mr_nst_y, bt.mr_radix_y, st);
+  }
+  if (e == cudaSuccess && bt.mr_Q > 1) {  // the row split's [Px] table
+    mr_twiddle_kernel<<<(unsigned)((bt.P + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_twP), bt.P);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && bt.mr_Qy > 1 && bt.mr_twP_y != bt.mr_twP) {  // a rectangle's column split: [Py]
+    mr_twiddle_kernel<<<(unsigned)((bt.Py + 255) / 256), 256, 0, st>>>(const_cast<float2*>(bt.mr_twP_y), bt.Py);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t mr_prepare() {

@@ -150,6 +150,8 @@ struct Batch {
   int mr_radix_y[kMrMaxStages];
   const float2* mr_tw_y;
   const float2* mr_twP;  // [P] twiddles exp(-2 pi i m / P) of the split (Q > 1)
+  int mr_Qy;               // the column transform's split (Py = mr_Qy mr_My; equal to mr_Q on square grids)
+  const float2* mr_twP_y;  // [Py] twiddles of the column split (rectangular grids, mr_Qy > 1)
   // per-stage twiddles of the plan, lane-contiguous: stage s (sub-transform size Ns, radix R)
   // holds w_(Ns R)^(r k) at (Ns - 1) + (r - 1) Ns + k for 1 <= r < R, k < Ns (M - 1 entries in all)
   const float2* mr_tws;

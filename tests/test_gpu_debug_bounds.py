@@ -92,6 +92,8 @@ CASES = [
     ("rect_mixed", 160, 2, 1e-6, 2e-3, [450e-9, 600e-9], dict(Ny=96), True),
     ("rect_pow2_pad1", 256, 1, 1e-6, 2e-3, [550e-9], dict(Ny=512), True),
     ("rect_large", 4000, 2, 1e-6, 20e-3, [550e-9], dict(Ny=3000), True),
+    ("rect_split_rows", 4500, 2, 1e-6, 10e-3, [550e-9], dict(Ny=500), True),      # Px = 9000 = 8 x 1125
+    ("rect_split_cols_pairs", 300, 2, 1e-6, 10e-3, [550e-9], dict(Ny=9000), True),  # Py = 18000 = 8 x 2250
 ]
 
 

@@ -136,3 +136,33 @@ def test_rect_medium_grad_vs_oracle():
     gref, lref = oracle.grad_rect(h, dx, z, lams, T)
     assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
     assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+# sides above one CTA's transform: split over a cluster per axis.  (Ny, Nx): the row transform
+# split (Px = 9000 = 8 x 1125, 18000 = 8 x 2250 with composite stages), the column transform
+# split (Py = 9000, 18000: two columns per cluster), and both.
+SPLIT_SHAPES = [(1000, 4500), (4500, 1000), (300, 9000), (9000, 300), (4800, 4500)]
+
+
+@pytest.mark.parametrize("Ny,Nx", SPLIT_SHAPES)
+def test_rect_split_sides_psf_vs_oracle(Ny, Nx):
+    dx, z, lam = 1e-6, 10e-3, 550e-9
+    h = _h(Ny, Nx, 12800 + Nx + Ny)
+    g = Geometry.make(Nx, dx, z, [lam], Ny=Ny)
+    I = api.psf(torch.from_numpy(h).cuda(), g).cpu().numpy()
+    ref = oracle.psf_rect(h, dx, z, [lam])
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    m = api.debug_band_mask(g, 0).cpu().numpy()
+    assert np.array_equal(m, oracle.band_mask_rect(2 * Ny, 2 * Nx, dx, z, lam))
+
+
+@pytest.mark.parametrize("Ny,Nx", [(500, 4500), (4500, 500)])
+def test_rect_split_sides_grad_vs_oracle(Ny, Nx):
+    dx, z, lams = 1e-6, 5e-3, [500e-9, 620e-9]
+    h = _h(Ny, Nx, 12900 + Nx)
+    T = _target(2 * Ny, 2 * Nx, Ny, Nx, 2, 12901 + Nx)
+    g = Geometry.make(Nx, dx, z, lams, Ny=Ny)
+    gr, loss = api.grad(torch.from_numpy(h).cuda(), g, torch.from_numpy(T).cuda())
+    gref, lref = oracle.grad_rect(h, dx, z, lams, T)
+    assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
+    assert abs(loss.item() - lref) <= 1e-5 * lref
