@@ -230,12 +230,13 @@ LanczosTab lanczos_table(int N, int u) {
 bool rect(const doe_geom* g) { return g->nx != g->ny; }
 
 // Split of one side of a rectangular grid: one CTA per transform up to kMrMax (any length with a
-// plan, powers of two included), else the first of Q = 8, 5, 4, 3, 2 that divides it into
-// sub-transforms of at most kMrMax points with a plan.  {0, 0} when the side is unsupported.
+// plan, powers of two included), else the first of Q = 8, 5, 4, 3, 2, 16 that divides it into
+// sub-transforms of at most kMrMax points with a plan (16: sides up to 131072, such as Table 2's
+// 128640 = 16 x 8040 and 85760 = 16 x 5360).  {0, 0} when the side is unsupported.
 MrSplit axis_split(long P) {
   if (P < 2 || (P & 1)) return {0, 0};
   if (P <= kMrMax) return mr_radices(P).empty() ? MrSplit{0, 0} : MrSplit{1, (int)P};
-  for (int q : {8, 5, 4, 3, 2})
+  for (int q : {8, 5, 4, 3, 2, 16})
     if (P % q == 0 && P / q <= kMrMax && !mr_radices(P / q).empty()) return {q, (int)(P / q)};
   return {0, 0};
 }
@@ -261,7 +262,7 @@ int check_geom(const doe_geom* g) {
     if (!(g->n_index[j] >= 1.0) || !std::isfinite(g->n_index[j])) return DOE_EINVAL;
   }
   if (rect(g) && !rect_supported(g)) return DOE_EUNSUPPORTED;
-  if ((long)g->pad * g->nx > (1L << kBigLog) || (long)g->pad * g->ny > (1L << kBigLog)) return DOE_EUNSUPPORTED;
+  if (!rect(g) && (long)g->pad * g->nx > (1L << kBigLog)) return DOE_EUNSUPPORTED;  // rectangles: axis_split
   if (!rect(g) && !is_pow2((long)g->pad * g->nx) && mr_split((long)g->pad * g->nx).Q == 0) return DOE_EUNSUPPORTED;
   const int u = upsample_log2(g);
   if ((g->nx >> u) < 4 || (g->ny >> u) < 4 || (g->nx & ((1 << u) - 1)) || (g->ny & ((1 << u) - 1))) return DOE_EINVAL;

@@ -1,5 +1,6 @@
 // doe_mixed_big.cuh -- non-power-of-two sides longer than one CTA's transform, P = Q M with
-// Q in {2, 3, 4, 5, 8} and M <= 8192 (Table 2's 28800 = 8 x 3600 and 40000 = 8 x 5000 grids):
+// Q in {2, 3, 4, 5, 8, 16} and M <= 8192 (Table 2's 28800 = 8 x 3600 and 40000 = 8 x 5000 grids,
+// and its 128640 x 85760 large-area grid, 16 x 8040 by 16 x 5360):
 // every row / column transform of length P runs on a thread-block cluster of Q CTAs.
 //
 // Four-step split with n = M n1 + n2 (n1 < Q, n2 < M) and k = k1 + Q k2 (k1 < Q, k2 < M):
@@ -15,6 +16,30 @@
 #include "doe_mixed.cuh"
 
 namespace doe {
+
+// 16-point DFT for the Q = 16 split steps, as 4 x 4 in registers (n = n1 + 4 n2, k = k2 + 4 k1):
+//   X[k2 + 4 k1] = sum_n1 w_4^(n1 k1) [ w_16^(n1 k2) sum_n2 v[n1 + 4 n2] w_4^(n2 k2) ]
+template <>
+__device__ __forceinline__ void mr_dft<16>(float2 (&v)[16], bool inv) {
+  float2 u[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 a[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+    mr_dft<4>(a, inv);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      const float2 w = make_float2(wr_cos<16>(n1 * k2), inv ? wr_sin<16>(n1 * k2) : -wr_sin<16>(n1 * k2));
+      u[n1 + 4 * k2] = (n1 && k2) ? cmul(a[k2], w) : a[k2];
+    }
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 b[4] = {u[4 * k2], u[4 * k2 + 1], u[4 * k2 + 2], u[4 * k2 + 3]};
+    mr_dft<4>(b, inv);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = b[k1];
+  }
+}
 
 // One axis of a split transform: P = Q M points, sub-transforms of M, the [P] table w_P^m.
 // Rows use the row axis (bt.P, bt.mr_M, bt.mr_twP), columns the column axis (bt.Py, bt.mr_My,

@@ -13,13 +13,21 @@ cudaError_t prep_mrq_t() {
   cudaError_t e;
   constexpr int b = 3 * kMrMax * (int)sizeof(float2);  // twiddle copy and two buffers
   if ((e = prep_one(mrq_rows_fwd_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_cols_kernel<Q, 1, CMP>, b, kMrT)) ||
-      (e = prep_one(mrq_cols_kernel<Q, 2, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_out_kernel<Q, CMP>, b, kMrT)) || (e = prep_one(mrq_rows_adj_c_kernel<Q, CMP>, b, kMrT)) ||
       (e = prep_one(mrq_rows_adj_a_kernel<Q, CMP>, b, kMrT)))
     return e;
-  if constexpr (2 * Q > 8)  // two columns per cluster: 10 or 16 CTAs, a non-portable size
+  if constexpr (Q <= 8)  // two columns per cluster (2 Q CTAs, at most 16)
+    if ((e = prep_one(mrq_cols_kernel<Q, 2, CMP>, b, kMrT))) return e;
+  if constexpr (2 * Q > 8 && 2 * Q <= 16)  // two columns per cluster: 10 or 16 CTAs, a non-portable size
     if ((e = cudaFuncSetAttribute(mrq_cols_kernel<Q, 2, CMP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)))
       return e;
+  if constexpr (Q > 8) {  // 16-CTA clusters for every pass
+    const void* fns[] = {(const void*)mrq_rows_fwd_kernel<Q, CMP>, (const void*)mrq_cols_kernel<Q, 1, CMP>,
+                         (const void*)mrq_rows_out_kernel<Q, CMP>, (const void*)mrq_rows_adj_c_kernel<Q, CMP>,
+                         (const void*)mrq_rows_adj_a_kernel<Q, CMP>};
+    for (const void* f : fns)
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
+  }
   return cudaSuccess;
 }
 template <bool CMP>
@@ -34,7 +42,7 @@ cudaError_t prep_mr_t() {
       (e = prep_one(mr_rows_adj_a_kernel<CMP>, b, kMrT)))
     return e;
   if ((e = prep_mrq_t<2, CMP>()) || (e = prep_mrq_t<3, CMP>()) || (e = prep_mrq_t<4, CMP>()) ||
-      (e = prep_mrq_t<5, CMP>()) || (e = prep_mrq_t<8, CMP>()))
+      (e = prep_mrq_t<5, CMP>()) || (e = prep_mrq_t<8, CMP>()) || (e = prep_mrq_t<16, CMP>()))
     return e;
   return cudaSuccess;
 }
@@ -69,7 +77,8 @@ cudaError_t mr_one_t(int which, const Batch& bt, cudaStream_t st) {
 template <int Q, bool CMP>
 const void* mrq_fn(int which, bool two) {
   return which == PASS_A   ? (const void*)mrq_rows_fwd_kernel<Q, CMP>
-         : which == PASS_B ? (two ? (const void*)mrq_cols_kernel<Q, 2, CMP> : (const void*)mrq_cols_kernel<Q, 1, CMP>)
+         : which == PASS_B ? (two && Q <= 8 ? (const void*)mrq_cols_kernel<(Q <= 8 ? Q : 8), 2, CMP>
+                                          : (const void*)mrq_cols_kernel<Q, 1, CMP>)
          : which == PASS_C ? (const void*)mrq_rows_out_kernel<Q, CMP>
          : which == PASS_C_ADJ ? (const void*)mrq_rows_adj_c_kernel<Q, CMP>
                                : (const void*)mrq_rows_adj_a_kernel<Q, CMP>;
@@ -81,7 +90,7 @@ cudaError_t mrq_launch(int which, const Batch& bt, cudaStream_t st) {
   // of its shared memory still fit on an SM
   const int M = which == PASS_B ? bt.mr_My : bt.mr_M;  // the column pass splits the column axis
   const size_t smem = (size_t)3 * M * sizeof(float2);   // twiddle copy and two buffers
-  const bool two = which == PASS_B && bt.mr_cmp && 2 * smem <= (size_t)220 * 1024;
+  const bool two = which == PASS_B && bt.mr_cmp && 2 * Q <= 16 && 2 * smem <= (size_t)220 * 1024;
   const void* fn = bt.mr_cmp ? mrq_fn<Q, true>(which, two) : mrq_fn<Q, false>(which, two);
   // DOE rows (A, A*), output rows (C, C'), or columns (B)
   const int lines = (which == PASS_A || which == PASS_A_ADJ) ? bt.Ny : which == PASS_B ? bt.P : bt.Py;
@@ -105,6 +114,7 @@ cudaError_t mr_pass(int which, const Batch& bt, cudaStream_t st) {
     case 4: return mrq_launch<4>(which, bt, st);
     case 5: return mrq_launch<5>(which, bt, st);
     case 8: return mrq_launch<8>(which, bt, st);
+    case 16: return mrq_launch<16>(which, bt, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -70,7 +70,7 @@ __host__ __device__ constexpr int last_radix() { return plan_radix(ilog2c(L), IN
 constexpr int kMaxSlices = 64;  // wavelengths (over all requests) per launch
 constexpr int kRenderColsMax = 8192;  // render column transform length limit (2 buffers of 64 KB)
 constexpr int kTile = 4;    // tile width of the column-tiled buffer (4 x 8 B = one 32-byte sector); columns per cluster for P <= 8192
-constexpr int kMaxQf = 8;   // sub-transforms per row at the largest grid (65536 = 8 x 8192)
+constexpr int kMaxQf = 16;  // sub-transforms per row at the longest split side (rectangles: 16 x 8192)
 constexpr int kMrMax = 8192;        // longest mixed-radix (non-power-of-two) transform, one CTA
 constexpr int kMrMaxStages = 16;    // radix stages of a mixed-radix plan
 constexpr int kMrMaxPrime = 127;    // largest prime factor taken as a direct-DFT stage

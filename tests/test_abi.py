@@ -130,11 +130,11 @@ def test_bad_pad_and_unsupported_size(lib):
     assert rc in (L.DOE_OK, L.DOE_ENOWS, L.DOE_EUNSUPPORTED)
     # rectangles run on the mixed-radix passes (each side one CTA per transform up to 8192, split
     # over a cluster above, up to 65536), plain incidence, no upsampling, rectangular band
-    for kw in (dict(Ny=128), dict(Ny=8000), dict(Ny=4000, N=4200), dict(Ny=8192, N=200)):
+    for kw in (dict(Ny=128), dict(Ny=8000), dict(Ny=4000, N=4200), dict(Ny=8192, N=200), dict(Ny=42880, N=64320)):
         rect = _geom(**kw).c()
         assert lib.doe_workspace_bytes(ctypes.byref(rect), L.DOE_OP_GRAD) > 0, kw
         assert lib.doe_psf(ctypes.byref(rect), ctypes.c_void_p(16), None, ctypes.c_void_p(16), None, 0, None) == L.DOE_ENOWS
-    for kw in (dict(Ny=40000), dict(Ny=262), dict(Ny=128, upsample=2), dict(Ny=128, bandlimit="circular"),
+    for kw in (dict(Ny=70000), dict(Ny=262), dict(Ny=128, upsample=2), dict(Ny=128, bandlimit="circular"),
                dict(Ny=128, theta_x=0.01), dict(Ny=128, src_d=0.1)):
         c = _geom(**kw).c()
         assert lib.doe_workspace_bytes(ctypes.byref(c), L.DOE_OP_PSF) == 0, kw

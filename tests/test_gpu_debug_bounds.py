@@ -94,6 +94,7 @@ CASES = [
     ("rect_large", 4000, 2, 1e-6, 20e-3, [550e-9], dict(Ny=3000), True),
     ("rect_split_rows", 4500, 2, 1e-6, 10e-3, [550e-9], dict(Ny=500), True),      # Px = 9000 = 8 x 1125
     ("rect_split_cols_pairs", 300, 2, 1e-6, 10e-3, [550e-9], dict(Ny=9000), True),  # Py = 18000 = 8 x 2250
+    ("rect_split16_rows", 64320, 2, 1e-6, 20e-3, [550e-9], dict(Ny=100), True),  # Px = 128640 = 16 x 8040
 ]
 
 
@@ -102,7 +103,9 @@ def test_bounds_checked_build_matches_release(libs, name, N, pad, dx, z, lams, k
     rel, dbg = libs
     g = Geometry.make(N, dx, z, lams, pad=pad, **kw)
     nl = g.NL
-    if g.Ny != N:  # rectangle: the top-left Ny x N block of a square map
+    if g.Ny != N and max(N, g.Ny) > 16384:  # a long thin rectangle: uniform random heights
+        h = torch.from_numpy(np.random.default_rng(4000 + N).random((g.Ny, N), dtype=np.float32) * np.float32(1.2e-6)).cuda()
+    elif g.Ny != N:  # rectangle: the top-left Ny x N block of a square map
         h = torch.from_numpy(np.ascontiguousarray(inputs.heights(max(N, g.Ny), 4000 + N)[:g.Ny, :N])).cuda()
     elif nl <= 8192:
         h = torch.from_numpy(inputs.heights(nl, 4000 + N)).cuda()
@@ -122,7 +125,11 @@ def test_bounds_checked_build_matches_release(libs, name, N, pad, dx, z, lams, k
         assert _faults(dbg) == 0
         _same(f, _psf(rel, g, h, e_in, field=True))
     if grad:
-        T = inputs.spot_target_device(max(g.P, g.Py), max(N, g.Ny), g.L, 5000 + N, "cuda")[:, :g.Py, :g.P].contiguous()
+        if max(g.P, g.Py) > 32768:  # long thin rectangle: a uniform random target of the grid's shape
+            gen = torch.Generator(device="cuda").manual_seed(5000 + N)
+            T = torch.rand((g.L, g.Py, g.P), generator=gen, device="cuda") * (N * g.Ny / (g.P * g.Py))
+        else:
+            T = inputs.spot_target_device(max(g.P, g.Py), max(N, g.Ny), g.L, 5000 + N, "cuda")[:, :g.Py, :g.P].contiguous()
         gd, ld = _grad(dbg, g, h, T, e_in)
         assert _faults(dbg) == 0
         gr, lr = _grad(rel, g, h, T, e_in)

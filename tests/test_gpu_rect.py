@@ -166,3 +166,24 @@ def test_rect_split_sides_grad_vs_oracle(Ny, Nx):
     gref, lref = oracle.grad_rect(h, dx, z, lams, T)
     assert rel_l2(gr.cpu().numpy(), gref) < TOL_GRAD
     assert abs(loss.item() - lref) <= 1e-5 * lref
+
+
+def _h_uniform(Ny, Nx, seed):
+    """Uniform random heights in [0, 1.2 um) for long thin grids (the smoothed square generator
+    would build a max(Nx, Ny)^2 map)."""
+    return (np.random.default_rng(seed).random((Ny, Nx), dtype=np.float32) * np.float32(1.2e-6)).astype(np.float32)
+
+
+# Table 2's large-area sides, 128640 = 16 x 8040 and 85760 = 16 x 5360 (prime 67 in both
+# sub-transforms, 16-CTA clusters), each against a short other side so that the oracle runs
+# in full
+@pytest.mark.parametrize("Ny,Nx", [(100, 64320), (42880, 100)])
+def test_rect_table2_sides_psf_vs_oracle(Ny, Nx):
+    dx, z, lam = 1e-6, 20e-3, 550e-9
+    h = _h_uniform(Ny, Nx, 13000 + Ny)
+    g = Geometry.make(Nx, dx, z, [lam], Ny=Ny)
+    I = api.psf(torch.from_numpy(h).cuda(), g).cpu().numpy()
+    ref = oracle.psf_rect(h, dx, z, [lam])
+    assert rel_l2(I, ref) < TOL_PSF, rel_l2(I, ref)
+    m = api.debug_band_mask(g, 0).cpu().numpy()
+    assert np.array_equal(m, oracle.band_mask_rect(2 * Ny, 2 * Nx, dx, z, lam))
