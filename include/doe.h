@@ -38,10 +38,12 @@
  *    frequency step (1 / (Px dx), 1 / (Py dx)) and band limit (the square rule per axis); a
  *    sample propagates iff lambda^2 (fx^2 + fy^2) < 1, in integers kt^2 B^2 + lt^2 A^2 <
  *    ceil((Px Py dx / (g lambda))^2) with g = gcd(Px, Py), A = Px / g, B = Py / g.  Supported
- *    when both Px and Py are at most 8192 with the factors above (powers of two included; the
- *    mixed-radix passes run one CTA per transform), with the separable band, no upsampling and
- *    no parametric incident field (an e_in array is supported).  Other rectangles return
- *    DOE_EUNSUPPORTED.
+ *    on the mixed-radix passes when each side is at most 8192 with the factors above (powers of
+ *    two included; one CTA per transform) or splits as Q x M with Q in {8, 5, 4, 3, 2, 16} and
+ *    M <= 8192 with those factors (a cluster of Q CTAs per transform, sides up to 131072, such
+ *    as Table 2's 128640 x 85760 = 16 x 8040 by 16 x 5360), with the separable band, no
+ *    upsampling and no parametric incident field (an e_in array is supported).  Other
+ *    rectangles return DOE_EUNSUPPORTED.
  */
 #ifndef DOE_H
 #define DOE_H
