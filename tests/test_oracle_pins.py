@@ -30,8 +30,9 @@ def test_fft_matches_brute_force_dft(n, inverse):
     assert np.abs(oracle.dft(x, inverse=inverse) - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("n", [128, 720, 1024, 3600, 4096, 8040])
+@pytest.mark.parametrize("n", [128, 720, 1024, 3600, 4096, 8040, 5360, 85760, 128640])
 def test_fft_matches_numpy(n):
+    # 128640 and 85760: Table 2's large-area sides (factor 67), transformed whole by the oracle
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     assert rel_l2(oracle.fft(x), np.fft.fft(x)) < 1e-12
     assert rel_l2(oracle.fft(x, inverse=True), np.fft.ifft(x) * n) < 1e-12
