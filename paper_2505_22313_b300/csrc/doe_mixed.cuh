@@ -270,23 +270,41 @@ __device__ __forceinline__ void mr_stage2(const float2* src, float2* dst, int P,
 // One stage of a prime radix R > 5 (Table 2's large-area grid carries 67): one thread per
 // output (butterfly j, output r), a direct R-point DFT fused with the stage twiddle:
 //   dst[(j - k) R + k + r Ns] = sum_m src[j + m P/R] w_P^(m e),  e = k P/(Ns R) + r P/R
-// (w_P^(m k P/(Ns R)) w_R^(m r) = w_P^(m e)); the exponent m e is kept reduced mod P.
+// (w_P^(m k P/(Ns R)) w_R^(m r) = w_P^(m e)); the exponents are kept reduced mod P.  With
+// m = 8 q + u, w_P^(m e) = w_P^(8 q e) w_P^(u e): 8 + ceil(R / 8) table entries per output
+// (17 at R = 67) and one complex product per term, instead of one table entry per term.
 __device__ __forceinline__ void mr_stage_prime(const float2* src, float2* dst, int P, int Ns, int R,
                                                const float2* twg, bool inv, int t) {
   const int nb = P / R, step = P / (Ns * R);
   for (int o = t; o < P; o += kMrT) {
     const int j = o / R, r = o - j * R, k = j % Ns;
     const int e = k * step + r * nb;  // < P
-    float2 acc = make_float2(0.f, 0.f);
+    float2 lo[8];                     // w_P^(u e), u < 8
     int idx = 0;
-    for (int m = 0; m < R; ++m) {
-      float2 w = DOE_IN(idx, P) ? __ldg(twg + idx) : make_float2(0.f, 0.f);
-      if (inv) w.y = -w.y;
-      const float2 v = DOE_IN(j + m * nb, P) ? src[j + m * nb] : make_float2(0.f, 0.f);
-      acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
-      acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      lo[u] = DOE_IN(idx, P) ? __ldg(twg + idx) : make_float2(0.f, 0.f);
       idx += e;
       if (idx >= P) idx -= P;
+    }
+    const int e8 = idx;  // 8 e mod P
+    float2 acc = make_float2(0.f, 0.f);
+    int hidx = 0;        // 8 q e mod P
+    for (int q = 0; 8 * q < R; ++q) {
+      const float2 hi = DOE_IN(hidx, P) ? __ldg(twg + hidx) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int m = 8 * q + u;
+        if (m < R) {
+          float2 w = cmul(hi, lo[u]);
+          if (inv) w.y = -w.y;
+          const float2 v = DOE_IN(j + m * nb, P) ? src[j + m * nb] : make_float2(0.f, 0.f);
+          acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
+          acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+        }
+      }
+      hidx += e8;
+      if (hidx >= P) hidx -= P;
     }
     if (DOE_IN((j - k) * R + k + r * Ns, P)) dst[(j - k) * R + k + r * Ns] = acc;
   }
